@@ -1,0 +1,104 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA parity tests and
+the benchmark.
+
+This module holds no decoding arithmetic: only seeded random bit patterns,
+the named workload recipes, and the conversion between the oracle's
+one-byte-per-bit layout ``[sample][3L^3]`` and the library's bit-sliced layout
+``[3L^3][words]`` (sample ``64*w + j`` is bit ``j`` of word ``w``).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+def n_bits(L: int) -> int:
+    """Number of qubits (edges) and of Z checks (faces) of the L x L x L lattice."""
+    return 3 * L * L * L
+
+
+def words_for(n_samples: int) -> int:
+    return (n_samples + 63) // 64
+
+
+def random_bits(n_samples: int, n: int, density: float, seed: int) -> np.ndarray:
+    """iid Bernoulli(density) bits, shape [n_samples][n], uint8."""
+    rng = np.random.default_rng(seed)
+    return (rng.random((n_samples, n)) < density).astype(np.uint8)
+
+
+def all_patterns(n: int) -> np.ndarray:
+    """Every n-bit pattern, shape [2^n][n], uint8 (sample i has bit k = (i >> k) & 1)."""
+    idx = np.arange(1 << n, dtype=np.int64)
+    return ((idx[:, None] >> np.arange(n, dtype=np.int64)[None, :]) & 1).astype(np.uint8)
+
+
+def low_weight_patterns(n: int, max_weight: int) -> np.ndarray:
+    """All patterns of weight 0..max_weight, shape [count][n], uint8."""
+    from itertools import combinations
+    rows = []
+    for w in range(max_weight + 1):
+        for c in combinations(range(n), w):
+            r = np.zeros(n, dtype=np.uint8)
+            r[list(c)] = 1
+            rows.append(r)
+    return np.stack(rows)
+
+
+def pack(bits: np.ndarray) -> np.ndarray:
+    """[S][n] uint8 bits -> [n][ceil(S/64)] uint64 words (tail lanes zero)."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    S, n = bits.shape
+    W = words_for(S)
+    padded = np.zeros((W * 64, n), dtype=np.uint8)
+    padded[:S] = bits
+    by = np.packbits(padded.T.reshape(n, W, 64), axis=2, bitorder="little")  # [n][W][8]
+    return np.ascontiguousarray(by).view(np.uint64).reshape(n, W)
+
+
+def unpack(words: np.ndarray, n_samples: int) -> np.ndarray:
+    """[n][W] uint64 words -> [n_samples][n] uint8 bits."""
+    words = np.ascontiguousarray(words, dtype=np.uint64)
+    n, W = words.shape
+    by = words.view(np.uint8).reshape(n, W, 8)
+    bits = np.unpackbits(by, axis=2, bitorder="little").reshape(n, W * 64)
+    return np.ascontiguousarray(bits[:, :n_samples].T)
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """A named synthetic workload: lattice size, noise, decoder and batch."""
+
+    name: str
+    L: int
+    p: float
+    q: float
+    T: int
+    n_samples: int
+    seed: int
+    decoder: str            # "flip" | "pflip" | "bp_pflip" | "bp"
+    schedule: str = ""
+    n_apply: int = 0            # rule applications per cycle (schedule string cycled)
+    bp_iters: int = 0
+    bp_meas_nodes: bool = True
+    perfect_round: bool = False
+    perfect_max_sweeps: int = 0
+
+
+# Workload recipes (phenomenological noise with p = q throughout, as in the
+# paper's simulations; every input is drawn from the seeded Philox streams).
+WORKLOADS = {
+    # plain flip, L=4, T=4 + perfect round, up to 32 sweeps, 10^4 samples
+    "flip_L4": Workload("flip_L4", 4, 0.01, 0.01, 4, 10_000, 0, "flip", "F", 32,
+                        perfect_round=True, perfect_max_sweeps=32),
+    # p-flip with the Sec. 3.2 example schedule FFPFF, T=L, 10^6 samples per point
+    "pflip_L8": Workload("pflip_L8", 8, 0.03, 0.03, 8, 1_000_000, 1000, "pflip", "FFPFF", 5),
+    "pflip_L16": Workload("pflip_L16", 16, 0.03, 0.03, 16, 1_000_000, 1000, "pflip", "FFPFF", 5),
+    # BP (16 FP32 iterations) + 32 applications cycling PFFPFF, T=L
+    "bp_pflip_L16": Workload("bp_pflip_L16", 16, 0.04, 0.04, 16, 100_000, 7, "bp_pflip",
+                             "PFFPFF", 32, bp_iters=16),
+    # throughput point: L=32, p=q=4%, T=L, 10^5 samples, BP16 + 32 x PFFPFF
+    "bp_pflip_L32": Workload("bp_pflip_L32", 32, 0.04, 0.04, 32, 100_000, 11, "bp_pflip",
+                             "PFFPFF", 32, bp_iters=16),
+}
