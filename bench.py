@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput benchmark: BP + p-flip decoding of the 3D toric code.
+
+Default workload (``bp_pflip_L32``): L = 32 (98,304 edge qubits), p = q = 4%,
+BP with 16 FP32 iterations (measurement-error variables on) followed by 32
+flip / p-flip applications cycling P F F P F F, 10^5 samples per GPU.  One
+step = one code cycle through the public entry point ``toric3d_run_cycles``
+(qubit noise, noisy measurement, BP, the schedule, and the logical readout of
+the residual error).  The metric is decoded qubit-cycles per second over all
+GPUs (3 L^3 x samples x cycles / time); every rank decodes its own disjoint
+sample range (weak scaling, no data-path collective).
+
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload instead.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import toric3d_inputs as inp  # noqa: E402
+
+METRIC = "qubit-cycles decoded/s at L=32 p=4%: BP+p-flip"
+UNIT = "qubit-cycles/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--workload", default="bp_pflip_L32", choices=sorted(inp.WORKLOADS))
+    ap.add_argument("--samples", type=int, default=0, help="samples per GPU (default: the workload's)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(w, S):
+    return {"workload": w.name, "L": w.L, "qubits": inp.n_bits(w.L), "p": w.p, "q": w.q,
+            "decoder": w.decoder, "bp_iters": w.bp_iters, "bp_meas_nodes": w.bp_meas_nodes,
+            "schedule": w.schedule, "n_apply": w.n_apply, "samples_per_gpu": S,
+            "cycles_per_step": 1, "T": w.T, "seed": w.seed,
+            "l2": "inputs larger than L2 (state and BP messages are GBs)"}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def _oracle_worker(args):
+    L, p, q, seed, kw, sample0, count, cycle0 = args
+    import oracle
+    cfg = oracle.make_cfg(L, 1, p, q, seed, cycle0=cycle0, **kw)
+    oracle.run_batch(cfg, sample0, count)
+    return count
+
+
+def oracle_kwargs(w):
+    return dict(use_bp=w.decoder.startswith("bp"), bp_iters=w.bp_iters, bp_meas_nodes=w.bp_meas_nodes,
+                schedule=w.schedule, n_apply=w.n_apply)
+
+
+def time_oracle(w, budget_s, cycle0=0):
+    """Time the oracle on one code cycle of a bounded number of samples, one
+    process per host core (spawned, so no CUDA state is inherited)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    cfg = oracle.make_cfg(w.L, 1, w.p, w.q, w.seed, **oracle_kwargs(w))
+    t0 = time.perf_counter()
+    oracle.run_batch(cfg, 0, 1)
+    one = max(time.perf_counter() - t0, 1e-4)
+    per_core = max(1, int(budget_s / one))
+    ctx = mp.get_context("spawn")
+    jobs = [(w.L, w.p, w.q, w.seed, oracle_kwargs(w), 64 * 1024 * i, per_core, cycle0) for i in range(cores)]
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_worker, jobs))
+        dt = time.perf_counter() - t0
+    value = inp.n_bits(w.L) * done / dt
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} samples x 1 code cycle at L={w.L} ({per_core} per process, {cores} processes)",
+            "seconds": dt}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = inp.WORKLOADS[args.workload]
+    S = args.samples or w.n_samples
+    budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup):
+        time_oracle(w, budget / 4, cycle0=i)
+    vals, secs, last = [], [], None
+    for i in range(args.steps):
+        last = time_oracle(w, budget, cycle0=args.warmup + i)
+        vals.append(last["value"])
+        secs.append(last["seconds"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Philox noise)", "config": workload_config(w, S),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CUDA arm
+def cuda_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_06985_gb300 as t3d
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = inp.WORKLOADS[args.workload]
+    S = args.samples or w.n_samples
+    stride = (S + 63) // 64 * 64
+    sample0 = rank * stride
+    L = w.L
+    n = inp.n_bits(L)
+    W = inp.words_for(S)
+    kw = dict(use_bp=w.decoder.startswith("bp"), bp_iters=w.bp_iters, bp_meas_nodes=w.bp_meas_nodes,
+              schedule=w.schedule, n_apply=w.n_apply)
+    chunk = min(S, 25024)
+    cfg = t3d.make_run_cfg(L, 1, w.p, w.q, w.seed, S, sample0=sample0, bp_chunk_samples=chunk, **kw)
+    stream = torch.cuda.Stream(device=dev)
+    e = torch.zeros((n, W), dtype=torch.int64, device=dev)
+    work = torch.empty(t3d.toric3d_run_workspace_bytes(cfg), dtype=torch.uint8, device=dev)
+    mask = torch.zeros(S, dtype=torch.uint8, device=dev)
+    counts = torch.zeros(8, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+
+    def step(t):
+        cfg.cycle0 = t
+        t3d.toric3d_run_cycles(cfg, e, work, mask, counts, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for t in range(args.warmup):
+            step(t)
+    stream.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t3d.toric3d_profile_reset()
+    t3d.toric3d_profile_enable(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for t in range(args.warmup, args.warmup + args.steps):
+            step(t)
+        ev1.record(stream)
+    ev1.synchronize()
+    t3d.toric3d_profile_enable(False)
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = {k: t3d.toric3d_profile_read(k) for k in t3d.KERNEL_KINDS}
+    t3d.toric3d_profile_reset()
+    launches = sum(v[1] for v in prof.values())
+
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    total_qc = n * S * world * args.steps
+    value = total_qc / (ms / 1e3)
+
+    # dominant kernel: BP iteration (algorithmic bytes per edge-sample: 16 B read + 16 B written;
+    # the first iteration of each chunk reads nothing)
+    bp_ms, bp_launches = prof["bp_step"]
+    chunks = math.ceil(S / chunk)
+    full_iters = (w.bp_iters - 1) * args.steps * chunks
+    first_iters = args.steps * chunks
+    alg_bytes = n * S * args.steps * (32.0 * (w.bp_iters - 1) + 16.0)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg_bytes / (bp_ms / 1e3) / 1e9 if bp_ms > 0 else 0.0
+    roofline = {"kernel": "k_bp_step", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
+                "launches": bp_launches, "avg_launch_ms": bp_ms / max(bp_launches, 1),
+                "share_of_step": bp_ms / ms if ms else None,
+                "expected_launches": full_iters + first_iters}
+
+    # end-to-end: the state round-trips through pinned host memory every step
+    e2e = None
+    if not args.no_e2e:
+        e_host = torch.empty((n, W), dtype=torch.int64, pin_memory=True)
+        e_host.copy_(e)
+        mask_host = torch.empty(S, dtype=torch.uint8, pin_memory=True)
+        counts_host = torch.empty(8, dtype=torch.int64, pin_memory=True)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(args.e2e_steps):
+                e.copy_(e_host, non_blocking=True)
+                step(args.warmup + args.steps + i)
+                e_host.copy_(e, non_blocking=True)
+                mask_host.copy_(mask, non_blocking=True)
+                counts_host.copy_(counts, non_blocking=True)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        dt_t = torch.tensor([dt], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
+        dt = float(dt_t.item())
+        e2e = {"value": n * S * world * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": n * W * 8, "d2h_bytes_per_step": n * W * 8 + S + 64,
+               "steps": args.e2e_steps,
+               "note": "error state uploaded from and downloaded to pinned host memory every step"}
+
+    fail_counts = counts.cpu().tolist()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(w, args.cpu_seconds)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
+                "data": "synthetic (seeded Philox phenomenological noise)",
+                "config": dict(workload_config(w, S), parallelism=f"replicas{world}"),
+                "samples_per_s": S * world * args.steps / (ms / 1e3) / 1,  # sample-cycles per second
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "kernels_ms": {k: v[0] for k, v in prof.items() if v[1]},
+                "kernels_launches": {k: v[1] for k, v in prof.items() if v[1]},
+                "clocks": clk, "last_cycle_logical_counts": fail_counts}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return cuda_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

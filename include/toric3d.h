@@ -1,0 +1,257 @@
+/*
+ * toric3d.h -- C ABI of the GB300 (sm_103a) library for Monte Carlo decoding of
+ * the 3D toric code with flip, p-flip and belief propagation, after Scruby &
+ * Nemoto, "Local Probabilistic Decoding of a Quantum Code" (arXiv:2212.06985).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ * Lattice (Sec. 2): periodic L x L x L cubic lattice, qubits on the 3L^3
+ * edges, Z checks on the 3L^3 faces (primal picture; the paper draws the
+ * equivalent dual one).  Index layout:
+ *     edge (d, x, y, z) -> ((d*L + z)*L + y)*L + x        d = edge direction
+ *     face (n, x, y, z) -> ((n*L + z)*L + y)*L + x        n = face normal
+ * The face with normal n at r is spanned by the two axes a < b other than n
+ * and holds the a-edges at r and r+e_b and the b-edges at r and r+e_a.
+ *
+ * Bit-sliced state: an error or syndrome array is uint64_t[3L^3][words];
+ * sample 64*w + j of a batch is bit j of word w.  Lanes past the last sample of
+ * the final word are scratch: calls may change them and never report them.
+ *
+ * Memory: every pointer is a device pointer owned by the caller unless stated
+ * otherwise; the library allocates no device memory.  Arrays of uint64_t must
+ * be 8-byte aligned, float arrays and workspaces 16-byte aligned.
+ *
+ * Streams: every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream) and returns once its kernels are enqueued.
+ *
+ * Errors: a call returns T3D_OK or an error code and launches nothing when its
+ * arguments are invalid (T3D_EINVAL).  T3D_ECUDA reports a CUDA runtime error
+ * seen while enqueuing.  toric3d_last_error() returns a message describing the
+ * calling thread's last failure.  No exception crosses the ABI.
+ *
+ * Random numbers (the paper only says "random number in (0,1)", Sec. 3.2):
+ * Philox4x64-10 (Salmon et al., SC'11) with key (seed, 0) and counter
+ * (group, site, cycle, stream<<48 | sweep<<8 | block), group = sample / 64.
+ * Bernoulli(p) for a sample in lane j compares the 32-bit U whose bit 31-i is
+ * bit j of word i (word i = output i%4 of block i/4) with P = floor(p*2^32 +
+ * 1/2): the event happens iff U < P.  Streams: 0 qubit flips (site = edge),
+ * 1 measurement flips (site = face), 2 p-flip coins (site = edge, coin = bit j
+ * of output 0 of block 0).  `sample0` (a multiple of 64) is the global index
+ * of a batch's first sample, so disjoint sample ranges on different GPUs or
+ * in resumed runs draw exactly the numbers one large batch would.
+ */
+#ifndef TORIC3D_H
+#define TORIC3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    T3D_OK = 0,
+    T3D_EINVAL = 1,     /* invalid argument; nothing was launched */
+    T3D_ECUDA = 2,      /* CUDA runtime error while enqueuing work */
+    T3D_ETIMEOUT = 3,   /* a bounded device-side wait gave up */
+    T3D_EINTERNAL = 4   /* internal consistency check failed */
+} t3d_status;
+
+typedef void* t3d_stream; /* cudaStream_t */
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* toric3d_last_error(void);
+
+/* ABI revision of this header. */
+int toric3d_abi_version(void);
+
+/*
+ * Phenomenological qubit noise (Sec. 3.1, Fig. 2 caption): for every edge and
+ * every sample of the batch, e ^= Bernoulli(p), drawn from stream 0 at
+ * (site = edge, cycle, sweep = 0).  e: uint64_t[3L^3][words], in place.
+ * 2 <= L <= 256, words >= 1, 0 <= p <= 1.
+ */
+t3d_status toric3d_noise(int L, int64_t words, uint64_t* e, double p, uint64_t seed,
+                         uint64_t sample0, uint32_t cycle, t3d_stream stream);
+
+/*
+ * One noisy syndrome measurement (Sec. 2, Sec. 3.1): s_f = XOR of the four
+ * edges of face f, then s ^= Bernoulli(q) from stream 1 at (site = face,
+ * cycle).  q = 0 gives the noiseless syndrome H e.  e is read, s overwritten;
+ * both uint64_t[3L^3][words] and must not overlap.
+ */
+t3d_status toric3d_syndrome(int L, int64_t words, const uint64_t* e, uint64_t* s, double q,
+                            uint64_t seed, uint64_t sample0, uint32_t cycle,
+                            t3d_stream stream);
+
+/* Workspace for toric3d_flip / toric3d_pflip: one bit-sliced syndrome array. */
+size_t toric3d_flip_workspace_bytes(int L, int64_t words);
+
+/*
+ * Parallel flip (Sec. 3.1 rule; Sec. 3.2 on the parallel version): `sweeps`
+ * synchronous applications; in each, every qubit with more unsatisfied than
+ * satisfied checks (3 or 4 of its 4 faces) flips, all deciding from the same
+ * syndrome snapshot, and the syndrome is updated by the flips (s ^= H f).
+ * e and s in place.  work: >= toric3d_flip_workspace_bytes(L, words) bytes of
+ * device scratch whose contents are not preserved.
+ */
+t3d_status toric3d_flip(int L, int64_t words, uint64_t* e, uint64_t* s, int sweeps, void* work,
+                        size_t work_bytes, t3d_stream stream);
+
+/*
+ * flip + p-flip on a schedule (Sec. 3.2 p-flip rule and schedule list,
+ * Table 1 footnote, Sec. 4.2): n_apply synchronous applications whose kinds
+ * cycle through `schedule`, a host string over {'F','P'} of length 1..63.  A
+ * 'P' application also flips each qubit with exactly 2 of 4 unsatisfied checks
+ * whose coin is 1; application k uses coin sweep index sweep0 + k.  e and s in
+ * place; work as for toric3d_flip.
+ */
+t3d_status toric3d_pflip(int L, int64_t words, uint64_t* e, uint64_t* s, const char* schedule,
+                         int n_apply, uint32_t sweep0, uint64_t seed, uint64_t sample0,
+                         uint32_t cycle, void* work, size_t work_bytes, t3d_stream stream);
+
+/*
+ * Belief propagation messages.  Samples are processed in groups of 32
+ * (sample 32g + lane).  A message buffer for n samples is
+ * float[ceil(n/32)][L^3][3][4][32]: entry (g, site, d, k, lane) is the
+ * check->variable message M_{f->v} into edge v = (d, site) from its k-th face.
+ * For an edge along axis a at r, with c0 < c1 the two other axes, its faces
+ * are k = 0: normal 3-a-c0 at r; k = 1: that face at r - e_c0; k = 2: normal
+ * 3-a-c1 at r; k = 3: that face at r - e_c1.
+ */
+size_t toric3d_bp_message_bytes(int L, int64_t n_samples);
+
+/*
+ * One flooding BP iteration (Sec. 4.1, Eqs. 2-3): from the check->variable
+ * messages msg_in (NULL: the first iteration, every variable->check message
+ * equal to the prior l0 = log((1-p)/p), Eq. 1) compute every
+ * variable->check message l0 + sum of the other three incoming messages
+ * (Eq. 3) and from those every new check->variable message
+ * (-1)^{s_f} 2 atanh(tq * prod of tanh(m/2) over the other three edges)
+ * (Eq. 2), clamped to |M| <= 30, into msg_out.  tq = tanh(lq/2) with
+ * lq = log((1-q_meas)/q_meas) is the message of the measurement-error
+ * variable attached to each check (Sec. 4.1); q_meas = 0 leaves them out.
+ * s: uint64_t[3L^3][ceil(n_samples/64)].  FP32 arithmetic.  msg_in and
+ * msg_out must not overlap.
+ */
+t3d_status toric3d_bp_step(int L, int64_t n_samples, const uint64_t* s, double p, double q_meas,
+                           const float* msg_in, float* msg_out, t3d_stream stream);
+
+/*
+ * BP hard decision (Sec. 4.1, after Eq. 4): posterior l_v = l0 + sum of the
+ * four incoming messages (msg NULL: l_v = l0); every qubit with l_v < 0 is
+ * corrected, e ^= d and s ^= H d.  llr_out (nullable) receives l_v as
+ * float[3L^3][n_samples].
+ */
+t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* msg, double p, uint64_t* e,
+                             uint64_t* s, float* llr_out, t3d_stream stream);
+
+/* Workspace for toric3d_bp processing `chunk_samples` samples at a time. */
+size_t toric3d_bp_workspace_bytes(int L, int64_t chunk_samples);
+
+/*
+ * Local BP decoder (Sec. 4.1): `iters` flooding iterations from the priors,
+ * then the hard decision applied to e and s.  Samples are processed in chunks
+ * as large as the workspace allows (at least 32 samples must fit; see
+ * toric3d_bp_workspace_bytes).  llr_out as for toric3d_bp_decide.
+ */
+t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p,
+                      double q_meas, int iters, void* work, size_t work_bytes, float* llr_out,
+                      t3d_stream stream);
+
+/*
+ * Logical readout (Sec. 3.1 and its footnote, Fig. 2 caption, App. A.2): for
+ * each axis d the L^2 straight lines of d-edges are a complete set of
+ * disjoint logical Z operators; the number c_d of lines with odd residual
+ * parity decides a logical X error on qubit d iff 2 c_d >= L^2 (a tie counts
+ * as a failure).  mask: uint8_t[n_samples], bit d = axis d.  counts8
+ * (nullable): int64_t[8], overwritten with the number of samples showing each
+ * mask value.
+ */
+t3d_status toric3d_logical(int L, int64_t n_samples, const uint64_t* e, uint8_t* mask,
+                           int64_t* counts8, t3d_stream stream);
+
+/*
+ * Layout conversion: bits uint8_t[n_samples][n_bits] (one sample per row, 0/1
+ * values) <-> words uint64_t[n_bits][ceil(n_samples/64)].  Packing zeroes the
+ * unused tail lanes.
+ */
+t3d_status toric3d_pack(int64_t n_bits, int64_t n_samples, const uint8_t* bits, uint64_t* words,
+                        t3d_stream stream);
+t3d_status toric3d_unpack(int64_t n_bits, int64_t n_samples, const uint64_t* words,
+                          uint8_t* bits, t3d_stream stream);
+
+/*
+ * A whole Monte Carlo run (Sec. 3.1 Fig. 2, Sec. 3.2, Sec. 4.2).  For cycles
+ * t = cycle0+1 .. cycle0+T: qubit noise (p), one noisy measurement (q),
+ * optional BP (bp_iters iterations, measurement-error variables iff
+ * bp_meas_nodes) with its hard decision, then n_apply flip/p-flip
+ * applications cycling through `schedule` (application k keys the coins with
+ * sweep index k).  Optionally a final noiseless measurement (cycle0+T+1)
+ * decoded by up to perfect_max_sweeps flip applications.  Finally the
+ * logical readout into mask / counts8.
+ */
+typedef struct {
+    int32_t L;
+    int32_t T;
+    double p;
+    double q;
+    uint64_t seed;
+    uint64_t sample0;          /* multiple of 64 */
+    int64_t n_samples;
+    int32_t use_bp;
+    int32_t bp_iters;
+    int32_t bp_meas_nodes;
+    int32_t n_apply;
+    char schedule[64];         /* NUL-terminated, over {'F','P'}; may be empty iff n_apply == 0 */
+    int32_t perfect_round;
+    int32_t perfect_max_sweeps;
+    uint32_t cycle0;
+    int32_t use_graph;         /* 1: capture the T cycles in a CUDA graph and launch it once */
+    int64_t bp_chunk_samples;  /* BP chunk size; 0 = as large as the workspace allows */
+} t3d_run_cfg;
+
+/* Workspace toric3d_run_cycles needs for `cfg` (uses cfg->bp_chunk_samples, 0 = all). */
+size_t toric3d_run_workspace_bytes(const t3d_run_cfg* cfg);
+
+/*
+ * e: uint64_t[3L^3][ceil(n_samples/64)], the error state, read at the start
+ * (zero it for a fresh code) and left holding the final residual error, so a
+ * run split at any cycle resumes exactly.  mask / counts8 as for
+ * toric3d_logical (either may be NULL).  cfg is read on the host during the
+ * call only.
+ */
+t3d_status toric3d_run_cycles(const t3d_run_cfg* cfg, uint64_t* e, void* work, size_t work_bytes,
+                              uint8_t* mask, int64_t* counts8, t3d_stream stream);
+
+/*
+ * Kernel timing (not in the paper; measurement support).  While enabled, every
+ * kernel the library enqueues outside a stream capture is bracketed by a pair
+ * of CUDA events on its own stream.  toric3d_profile_read() waits for the
+ * recorded events and returns, for one kernel kind, the summed device time in
+ * milliseconds and the number of launches; toric3d_profile_reset() forgets
+ * them.  Host-side state is global to the process; do not toggle it while
+ * another thread is enqueuing toric3d work.
+ */
+typedef enum {
+    T3D_K_NOISE = 0,
+    T3D_K_SYNDROME = 1,
+    T3D_K_FLIP = 2,
+    T3D_K_PFLIP = 3,
+    T3D_K_BP_STEP = 4,
+    T3D_K_BP_DECIDE = 5,
+    T3D_K_LOGICAL = 6,
+    T3D_K_LAYOUT = 7,
+    T3D_K_COUNT = 8
+} t3d_kernel_kind;
+
+void toric3d_profile_enable(int on);
+void toric3d_profile_reset(void);
+t3d_status toric3d_profile_read(int kind, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TORIC3D_H */

@@ -1,0 +1,268 @@
+"""GB300-native Monte Carlo decoding of the 3D toric code (arXiv:2212.06985).
+
+Thin ctypes binding over the C ABI of ``include/toric3d.h`` (libtoric3d.so,
+built for sm_103a by ``build.py``).  Every function here only marshals
+arguments -- torch tensors become device pointers, the current torch stream
+becomes the CUDA stream -- and every step of the decoding path runs in the
+library's CUDA kernels.  There is no CPU path: if the library cannot be
+loaded, every call raises.
+
+Bit-sliced arrays are torch.int64 tensors used as raw 64-bit words
+(``[3L^3, words]``; sample 64*w + j is bit j of word w).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "T3DError", "RunCfg", "lib", "n_bits", "words_for", "table1_schedule",
+    "toric3d_noise", "toric3d_syndrome", "toric3d_flip", "toric3d_pflip",
+    "toric3d_bp_step", "toric3d_bp_decide", "toric3d_bp", "toric3d_logical",
+    "toric3d_pack", "toric3d_unpack", "toric3d_run_cycles",
+    "toric3d_flip_workspace_bytes", "toric3d_bp_message_bytes",
+    "toric3d_bp_workspace_bytes", "toric3d_run_workspace_bytes", "make_run_cfg",
+    "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "KERNEL_KINDS",
+    "EXPORTED_SYMBOLS",
+]
+
+EXPORTED_SYMBOLS = [
+    "toric3d_last_error", "toric3d_abi_version", "toric3d_noise", "toric3d_syndrome",
+    "toric3d_flip_workspace_bytes", "toric3d_flip", "toric3d_pflip", "toric3d_bp_message_bytes",
+    "toric3d_bp_step", "toric3d_bp_decide", "toric3d_bp_workspace_bytes", "toric3d_bp",
+    "toric3d_logical", "toric3d_pack", "toric3d_unpack", "toric3d_run_workspace_bytes",
+    "toric3d_run_cycles", "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read",
+]
+
+KERNEL_KINDS = {"noise": 0, "syndrome": 1, "flip": 2, "pflip": 3, "bp_step": 4, "bp_decide": 5,
+                "logical": 6, "layout": 7}
+
+
+class T3DError(RuntimeError):
+    """A toric3d call returned an error status."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"toric3d error {status}: {message}")
+        self.status = status
+
+
+class RunCfg(ctypes.Structure):
+    """Mirror of ``t3d_run_cfg`` in include/toric3d.h."""
+
+    _fields_ = [
+        ("L", ctypes.c_int32),
+        ("T", ctypes.c_int32),
+        ("p", ctypes.c_double),
+        ("q", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("sample0", ctypes.c_uint64),
+        ("n_samples", ctypes.c_int64),
+        ("use_bp", ctypes.c_int32),
+        ("bp_iters", ctypes.c_int32),
+        ("bp_meas_nodes", ctypes.c_int32),
+        ("n_apply", ctypes.c_int32),
+        ("schedule", ctypes.c_char * 64),
+        ("perfect_round", ctypes.c_int32),
+        ("perfect_max_sweeps", ctypes.c_int32),
+        ("cycle0", ctypes.c_uint32),
+        ("use_graph", ctypes.c_int32),
+        ("bp_chunk_samples", ctypes.c_int64),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load libtoric3d.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            handle = ctypes.CDLL(path)
+            _declare(handle)
+            _lib = handle
+    return _lib
+
+
+def _declare(h):
+    i32, i64, u32, u64, dbl, sz = (ctypes.c_int, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64,
+                                   ctypes.c_double, ctypes.c_size_t)
+    sig = {
+        "toric3d_last_error": (ctypes.c_char_p, []),
+        "toric3d_abi_version": (i32, []),
+        "toric3d_noise": (i32, [i32, i64, _P, dbl, u64, u64, u32, _P]),
+        "toric3d_syndrome": (i32, [i32, i64, _P, _P, dbl, u64, u64, u32, _P]),
+        "toric3d_flip_workspace_bytes": (sz, [i32, i64]),
+        "toric3d_flip": (i32, [i32, i64, _P, _P, i32, _P, sz, _P]),
+        "toric3d_pflip": (i32, [i32, i64, _P, _P, ctypes.c_char_p, i32, u32, u64, u64, u32, _P, sz, _P]),
+        "toric3d_bp_message_bytes": (sz, [i32, i64]),
+        "toric3d_bp_step": (i32, [i32, i64, _P, dbl, dbl, _P, _P, _P]),
+        "toric3d_bp_decide": (i32, [i32, i64, _P, dbl, _P, _P, _P, _P]),
+        "toric3d_bp_workspace_bytes": (sz, [i32, i64]),
+        "toric3d_bp": (i32, [i32, i64, _P, _P, dbl, dbl, i32, _P, sz, _P, _P]),
+        "toric3d_logical": (i32, [i32, i64, _P, _P, _P, _P]),
+        "toric3d_pack": (i32, [i64, i64, _P, _P, _P]),
+        "toric3d_unpack": (i32, [i64, i64, _P, _P, _P]),
+        "toric3d_run_workspace_bytes": (sz, [ctypes.POINTER(RunCfg)]),
+        "toric3d_run_cycles": (i32, [ctypes.POINTER(RunCfg), _P, _P, sz, _P, _P, _P]),
+        "toric3d_profile_enable": (None, [i32]),
+        "toric3d_profile_reset": (None, []),
+        "toric3d_profile_read": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(h, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().toric3d_last_error()
+        raise T3DError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("toric3d needs CUDA tensors (the library has no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError("toric3d needs contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def n_bits(L: int) -> int:
+    return 3 * L ** 3
+
+
+def words_for(n_samples: int) -> int:
+    return (n_samples + 63) // 64
+
+
+def table1_schedule(n_A: int, lambda_p: int) -> str:
+    """F/P schedule of n_A rule applications in one code cycle where every
+    lambda_p-th application (counted within the cycle) is p-flip (Table 1 and
+    its footnote; Sec. 3.2 prints n_A = 5, lambda_p = 3 as F F P F F)."""
+    if n_A < 1 or lambda_p < 1:
+        raise ValueError("n_A and lambda_p must be positive")
+    return "".join("P" if k % lambda_p == 0 else "F" for k in range(1, n_A + 1))
+
+
+# ------------------------------------------------------------------ sizes
+def toric3d_flip_workspace_bytes(L: int, words: int) -> int:
+    return int(lib().toric3d_flip_workspace_bytes(L, words))
+
+
+def toric3d_bp_message_bytes(L: int, n_samples: int) -> int:
+    return int(lib().toric3d_bp_message_bytes(L, n_samples))
+
+
+def toric3d_bp_workspace_bytes(L: int, chunk_samples: int) -> int:
+    return int(lib().toric3d_bp_workspace_bytes(L, chunk_samples))
+
+
+def toric3d_run_workspace_bytes(cfg: RunCfg) -> int:
+    return int(lib().toric3d_run_workspace_bytes(ctypes.byref(cfg)))
+
+
+# ------------------------------------------------------------------ calls
+def toric3d_noise(L, e, p, seed, sample0, cycle, stream=None):
+    _check(lib().toric3d_noise(L, e.shape[-1], _ptr(e), float(p), seed, sample0, cycle, _stream(stream)))
+
+
+def toric3d_syndrome(L, e, s, q, seed, sample0, cycle, stream=None):
+    _check(lib().toric3d_syndrome(L, e.shape[-1], _ptr(e), _ptr(s), float(q), seed, sample0, cycle,
+                                  _stream(stream)))
+
+
+def toric3d_flip(L, e, s, sweeps, work, stream=None):
+    _check(lib().toric3d_flip(L, e.shape[-1], _ptr(e), _ptr(s), sweeps, _ptr(work),
+                              work.numel() * work.element_size(), _stream(stream)))
+
+
+def toric3d_pflip(L, e, s, schedule, n_apply, sweep0, seed, sample0, cycle, work, stream=None):
+    _check(lib().toric3d_pflip(L, e.shape[-1], _ptr(e), _ptr(s), schedule.encode(), n_apply, sweep0,
+                               seed, sample0, cycle, _ptr(work), work.numel() * work.element_size(),
+                               _stream(stream)))
+
+
+def toric3d_bp_step(L, n_samples, s, p, q_meas, msg_in, msg_out, stream=None):
+    _check(lib().toric3d_bp_step(L, n_samples, _ptr(s), float(p), float(q_meas), _ptr(msg_in),
+                                 _ptr(msg_out), _stream(stream)))
+
+
+def toric3d_bp_decide(L, n_samples, msg, p, e, s, llr_out=None, stream=None):
+    _check(lib().toric3d_bp_decide(L, n_samples, _ptr(msg), float(p), _ptr(e), _ptr(s),
+                                   _ptr(llr_out), _stream(stream)))
+
+
+def toric3d_bp(L, n_samples, e, s, p, q_meas, iters, work, llr_out=None, stream=None):
+    _check(lib().toric3d_bp(L, n_samples, _ptr(e), _ptr(s), float(p), float(q_meas), iters,
+                            _ptr(work), work.numel() * work.element_size(), _ptr(llr_out),
+                            _stream(stream)))
+
+
+def toric3d_logical(L, n_samples, e, mask=None, counts8=None, stream=None):
+    _check(lib().toric3d_logical(L, n_samples, _ptr(e), _ptr(mask), _ptr(counts8), _stream(stream)))
+
+
+def toric3d_pack(n_bits_, n_samples, bits, words, stream=None):
+    _check(lib().toric3d_pack(n_bits_, n_samples, _ptr(bits), _ptr(words), _stream(stream)))
+
+
+def toric3d_unpack(n_bits_, n_samples, words, bits, stream=None):
+    _check(lib().toric3d_unpack(n_bits_, n_samples, _ptr(words), _ptr(bits), _stream(stream)))
+
+
+def make_run_cfg(L, T, p, q, seed, n_samples, *, sample0=0, use_bp=False, bp_iters=0,
+                 bp_meas_nodes=True, schedule="", n_apply=None, perfect_round=False,
+                 perfect_max_sweeps=0, cycle0=0, use_graph=False, bp_chunk_samples=0) -> RunCfg:
+    c = RunCfg()
+    c.L, c.T, c.p, c.q, c.seed = L, T, float(p), float(q), seed
+    c.sample0, c.n_samples = sample0, n_samples
+    c.use_bp, c.bp_iters, c.bp_meas_nodes = int(use_bp), bp_iters, int(bp_meas_nodes)
+    c.n_apply = len(schedule) if n_apply is None else n_apply
+    c.schedule = schedule.encode()
+    c.perfect_round, c.perfect_max_sweeps = int(perfect_round), perfect_max_sweeps
+    c.cycle0, c.use_graph, c.bp_chunk_samples = cycle0, int(use_graph), bp_chunk_samples
+    return c
+
+
+def toric3d_run_cycles(cfg: RunCfg, e, work, mask=None, counts8=None, stream=None):
+    _check(lib().toric3d_run_cycles(ctypes.byref(cfg), _ptr(e), _ptr(work),
+                                    work.numel() * work.element_size(), _ptr(mask), _ptr(counts8),
+                                    _stream(stream)))
+
+
+# ------------------------------------------------------------------ kernel timing
+def toric3d_profile_enable(on: bool = True):
+    lib().toric3d_profile_enable(int(on))
+
+
+def toric3d_profile_reset():
+    lib().toric3d_profile_reset()
+
+
+def toric3d_profile_read(kind) -> tuple[float, int]:
+    """(summed device milliseconds, launches) recorded for one kernel kind."""
+    k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(lib().toric3d_profile_read(k, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value

@@ -1,0 +1,145 @@
+// Library-wide host helpers: the per-thread error message behind
+// toric3d_last_error() and the argument checks every entry point shares.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "t3d_host.hpp"
+
+namespace t3d {
+
+namespace {
+thread_local char g_error[512] = "";
+}
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_error, sizeof(g_error), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_error[0] = '\0'; }
+
+t3d_status check_lattice(int L)
+{
+    if (L < 2 || L > kMaxL) {
+        set_error("L=%d outside [2, %d]", L, kMaxL);
+        return T3D_EINVAL;
+    }
+    return T3D_OK;
+}
+
+t3d_status check_words(const void* p, const char* name)
+{
+    if (p == nullptr) {
+        set_error("%s is NULL", name);
+        return T3D_EINVAL;
+    }
+    if (!aligned(p, 8)) {
+        set_error("%s must be 8-byte aligned", name);
+        return T3D_EINVAL;
+    }
+    return T3D_OK;
+}
+
+// ------------------------------------------------------------ kernel timing
+namespace {
+
+struct Record {
+    int kind;
+    cudaEvent_t start, stop;
+};
+
+std::mutex g_prof_mutex;
+bool g_prof_on = false;
+std::vector<Record> g_records;       // recorded pairs, in launch order
+std::vector<cudaEvent_t> g_free;     // events ready for reuse
+
+cudaEvent_t take_event()
+{
+    if (!g_free.empty()) {
+        cudaEvent_t ev = g_free.back();
+        g_free.pop_back();
+        return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    return ev;
+}
+
+}  // namespace
+
+int prof_begin(int kind, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    if (!g_prof_on) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return -1;
+    Record r{kind, take_event(), take_event()};
+    if (!r.start || !r.stop) return -1;
+    cudaEventRecord(r.start, st);
+    g_records.push_back(r);
+    return (int)g_records.size() - 1;
+}
+
+void prof_end(int handle, cudaStream_t st)
+{
+    if (handle < 0) return;
+    std::lock_guard<std::mutex> lock(g_prof_mutex);
+    if (handle < (int)g_records.size()) cudaEventRecord(g_records[handle].stop, st);
+}
+
+}  // namespace t3d
+
+extern "C" void toric3d_profile_enable(int on)
+{
+    std::lock_guard<std::mutex> lock(t3d::g_prof_mutex);
+    t3d::g_prof_on = on != 0;
+}
+
+extern "C" void toric3d_profile_reset(void)
+{
+    std::lock_guard<std::mutex> lock(t3d::g_prof_mutex);
+    for (auto& r : t3d::g_records) {
+        cudaEventSynchronize(r.stop);
+        t3d::g_free.push_back(r.start);
+        t3d::g_free.push_back(r.stop);
+    }
+    t3d::g_records.clear();
+}
+
+extern "C" t3d_status toric3d_profile_read(int kind, double* total_ms, int64_t* launches)
+{
+    t3d::clear_error();
+    if (kind < 0 || kind >= T3D_K_COUNT || !total_ms || !launches) {
+        t3d::set_error("bad profile query");
+        return T3D_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(t3d::g_prof_mutex);
+    double sum = 0.0;
+    int64_t n = 0;
+    for (auto& r : t3d::g_records) {
+        if (r.kind != kind) continue;
+        cudaError_t err = cudaEventSynchronize(r.stop);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, r.start, r.stop);
+        if (err != cudaSuccess) {
+            t3d::set_error("profile event: %s", cudaGetErrorString(err));
+            return T3D_ECUDA;
+        }
+        sum += ms;
+        ++n;
+    }
+    *total_ms = sum;
+    *launches = n;
+    return T3D_OK;
+}
+
+extern "C" const char* toric3d_last_error(void) { return t3d::g_error; }
+
+extern "C" int toric3d_abi_version(void) { return 1; }

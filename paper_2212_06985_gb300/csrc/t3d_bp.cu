@@ -1,0 +1,332 @@
+// Product-sum belief propagation on the face Tanner graph of the 3D toric
+// code (Sec. 4.1 of arXiv:2212.06985, Eqs. 1-4), FP32, one sample per thread.
+//
+// Layout: a message buffer is float[groups][L^3][3][4][32]; entry
+// (g, site, d, k, lane) is M_{f->v} into edge v = (d, site) from its k-th face
+// (slot order of edge_faces()) for sample 32 g + lane.  A warp handles one
+// face for 32 samples, so every message access is a coalesced 128-byte row.
+//
+// Check-node arithmetic.  For inputs x_i (variable->check messages) let
+// t_i = tanh(|x_i|/2) and d_i = 1 - t_i = 2 e^{-|x_i|} / (1 + e^{-|x_i|}).
+// Products of (t, d) pairs are formed as (tA tB, dA + tA dB), which is exact
+// algebra with no cancellation, so P = prod t and D = 1 - P are both accurate
+// even when P rounds to 1 in FP32.  The output magnitude is
+// 2 atanh(P) = log1p(2P / D), and its sign is (-1)^{s_f} times the signs of
+// the other inputs.  The measurement-error variable of Sec. 4.1 enters as one
+// more constant pair (tq, dq).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <utility>
+
+#include "t3d_device.cuh"
+#include "t3d_host.hpp"
+
+namespace t3d {
+namespace {
+
+constexpr int kBpThreads = 256;
+constexpr int kLanes = 32;
+constexpr float kMsgClamp = 30.0f;
+
+struct TD {
+    float t;  // tanh(|x|/2)
+    float d;  // 1 - tanh(|x|/2)
+};
+
+__device__ __forceinline__ TD td_mul(TD A, TD B) { return TD{A.t * B.t, fmaf(A.t, B.d, A.d)}; }
+
+__device__ __forceinline__ TD td_of(float x)
+{
+    float a = fabsf(x);
+    float E = expf(-a);
+    TD r;
+    r.t = tanhf(0.5f * a);
+    r.d = (2.0f * E) / (1.0f + E);
+    return r;
+}
+
+// Eq. 2 for the four edges of one face: y[j] from the other three inputs.
+__device__ __forceinline__ void check_node(const float x[4], bool s_neg, TD q, float y[4])
+{
+    TD in[4];
+    unsigned neg = s_neg ? 1u : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        in[j] = td_of(x[j]);
+        neg ^= (x[j] < 0.0f) ? 1u : 0u;
+    }
+    const TD one{1.0f, 0.0f};
+    TD pre[4], suf[4];
+    pre[0] = q;
+    pre[1] = td_mul(pre[0], in[0]);
+    pre[2] = td_mul(pre[1], in[1]);
+    pre[3] = td_mul(pre[2], in[2]);
+    suf[3] = one;
+    suf[2] = in[3];
+    suf[1] = td_mul(in[2], suf[2]);
+    suf[0] = td_mul(in[1], suf[1]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        TD o = td_mul(pre[j], suf[j]);
+        float mag = log1pf((2.0f * o.t) / o.d);
+        mag = fminf(mag, kMsgClamp);
+        unsigned sgn = neg ^ ((x[j] < 0.0f) ? 1u : 0u);
+        y[j] = sgn ? -mag : mag;
+    }
+}
+
+struct FaceWarp {
+    int64_t g;
+    int site;
+    int n;
+};
+
+__device__ __forceinline__ bool face_warp(const Lattice& lat, int64_t n_groups, FaceWarp& fw)
+{
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t per_g = 3LL * lat.L3;
+    fw.g = warp / per_g;
+    if (fw.g >= n_groups) return false;
+    const int rem = (int)(warp - fw.g * per_g);
+    fw.site = rem / 3;
+    fw.n = rem - 3 * fw.site;
+    return true;
+}
+
+// Offset of edge (d, site)'s 4x32 message block within group g.
+__device__ __forceinline__ int64_t edge_block(const Lattice& lat, int64_t g, int site, int d)
+{
+    return ((g * lat.L3 + site) * 3 + d) * (4 * kLanes);
+}
+
+// One flooding iteration: Eq. 3 (variable->check, from msg_in or the prior)
+// followed by Eq. 2 (check->variable) into msg_out.
+__global__ void __launch_bounds__(kBpThreads)
+k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__ s, float l0,
+          TD q, const float* __restrict__ msg_in, float* __restrict__ msg_out)
+{
+    FaceWarp fw;
+    if (!face_warp(lat, n_groups, fw)) return;
+    const int lane = threadIdx.x & 31;
+    const uint64_t sw = s[((int64_t)fw.n * lat.L3 + fw.site) * W + (fw.g >> 1)];
+    const bool s_neg = (sw >> ((fw.g & 1) * 32 + lane)) & 1ULL;
+    const FaceEdges fe = face_edges(lat, fw.n, site_coord(lat, fw.site));
+    float x[4];
+    int64_t base[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        base[j] = edge_block(lat, fw.g, fe.site[j], fe.dir[j]) + lane;
+        if (msg_in) {
+            float acc = l0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k != fe.slot[j]) acc += msg_in[base[j] + k * kLanes];
+            x[j] = acc;
+        } else {
+            x[j] = l0;
+        }
+    }
+    float y[4];
+    check_node(x, s_neg, q, y);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) msg_out[base[j] + fe.slot[j] * kLanes] = y[j];
+}
+
+// Eq. 4 posterior and the hard decision: every edge with l < 0 is corrected.
+// The warp of face f XORs the parity of its edges' decisions into s_f and
+// applies the decision of the edge it owns to e (each 32-sample half of a
+// 64-bit word is written by exactly one warp).
+__global__ void __launch_bounds__(kBpThreads)
+k_bp_decide(Lattice lat, int64_t n_groups, int64_t W, int64_t n_samples, float l0,
+            const float* __restrict__ msg, uint32_t* __restrict__ e32, uint32_t* __restrict__ s32,
+            float* __restrict__ llr_out)
+{
+    FaceWarp fw;
+    if (!face_warp(lat, n_groups, fw)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t sample = fw.g * kLanes + lane;
+    const bool valid = sample < n_samples;
+    const FaceEdges fe = face_edges(lat, fw.n, site_coord(lat, fw.site));
+    const int own = owned_edge_slot(fw.n);
+    unsigned par = 0, own_bits = 0;
+    float own_l = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float l = l0;
+        if (msg) {
+            const int64_t b = edge_block(lat, fw.g, fe.site[j], fe.dir[j]) + lane;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) l += msg[b + k * kLanes];
+        }
+        unsigned bits = __ballot_sync(0xffffffffu, valid && l < 0.0f);
+        par ^= bits;
+        if (j == own) {
+            own_bits = bits;
+            own_l = l;
+        }
+    }
+    const int64_t half = 2 * (fw.g >> 1) + (fw.g & 1);
+    if (lane == 0) {
+        const int64_t f = (int64_t)fw.n * lat.L3 + fw.site;
+        const int64_t v = (int64_t)fe.dir[own] * lat.L3 + fe.site[own];
+        if (par) s32[2 * f * W + half] ^= par;
+        if (own_bits) e32[2 * v * W + half] ^= own_bits;
+    }
+    if (llr_out && valid) {
+        const int64_t v = (int64_t)fe.dir[own] * lat.L3 + fe.site[own];
+        llr_out[v * n_samples + sample] = own_l;
+    }
+}
+
+Lattice make_lattice(int L) { return Lattice{L, L * L, L * L * L}; }
+
+TD meas_pair(double q_meas)
+{
+    if (!(q_meas > 0.0)) return TD{1.0f, 0.0f};
+    double lq = std::log((1.0 - q_meas) / q_meas);
+    double E = std::exp(-std::fabs(lq));
+    double t = std::tanh(lq / 2.0);
+    return TD{(float)t, (float)(2.0 * E / (1.0 + E))};
+}
+
+float prior(double p) { return (float)std::log((1.0 - p) / p); }
+
+int64_t group_floats(int L) { return 3LL * L * L * L * 4 * kLanes; }
+
+unsigned warps_grid(int64_t n_warps)
+{
+    return (unsigned)((n_warps * 32 + kBpThreads - 1) / kBpThreads);
+}
+
+t3d_status launch_step(int L, int64_t n_groups, int64_t W, const uint64_t* s, double p, double q_meas,
+                       const float* in, float* out, cudaStream_t st)
+{
+    Lattice lat = make_lattice(L);
+    ProfScope prof(T3D_K_BP_STEP, st);
+    k_bp_step<<<warps_grid(n_groups * 3LL * lat.L3), kBpThreads, 0, st>>>(
+        lat, n_groups, W, s, prior(p), meas_pair(q_meas), in, out);
+    T3D_LAUNCH_CHECK("bp step");
+    return T3D_OK;
+}
+
+t3d_status launch_decide(int L, int64_t n_groups, int64_t W, int64_t n_samples, double p,
+                         const float* msg, uint64_t* e, uint64_t* s, float* llr, cudaStream_t st)
+{
+    Lattice lat = make_lattice(L);
+    ProfScope prof(T3D_K_BP_DECIDE, st);
+    k_bp_decide<<<warps_grid(n_groups * 3LL * lat.L3), kBpThreads, 0, st>>>(
+        lat, n_groups, W, n_samples, prior(p), msg, reinterpret_cast<uint32_t*>(e),
+        reinterpret_cast<uint32_t*>(s), llr);
+    T3D_LAUNCH_CHECK("bp decide");
+    return T3D_OK;
+}
+
+}  // namespace
+
+// Chunks of chunk_groups groups; buf holds two chunk-sized message buffers.
+// The s/e words of chunk c start at group c*chunk_groups, so the kernels see
+// the chunk's slice of the arrays through offset pointers and a local group
+// count (groups are aligned to 64-sample words when chunk_groups is even).
+t3d_status launch_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p, double q_meas,
+                     int iters, float* buf, int64_t chunk_groups, float* llr_out, cudaStream_t st)
+{
+    const int64_t G = groups_for(n_samples);
+    const int64_t W = words_for(n_samples);
+    float* A = buf;
+    float* B = buf + chunk_groups * group_floats(L);
+    for (int64_t g0 = 0; g0 < G; g0 += chunk_groups) {
+        const int64_t gc = std::min(chunk_groups, G - g0);
+        // the chunk's words begin at word g0/2 (g0 is even: chunk_groups is even or g0 == 0)
+        const int64_t w0 = g0 / 2;
+        const uint64_t* s_chunk = s + w0;
+        const float* last = nullptr;
+        for (int it = 0; it < iters; ++it) {
+            T3D_TRY(launch_step(L, gc, W, s_chunk, p, q_meas, last, A, st));
+            last = A;
+            std::swap(A, B);
+        }
+        const int64_t n_chunk = std::min<int64_t>(gc * kLanes, n_samples - g0 * kLanes);
+        T3D_TRY(launch_decide(L, gc, W, n_chunk, p, last, e + w0, s + w0,
+                              llr_out ? llr_out + g0 * kLanes : nullptr, st));
+    }
+    return T3D_OK;
+}
+
+}  // namespace t3d
+
+using namespace t3d;
+
+extern "C" size_t toric3d_bp_message_bytes(int L, int64_t n_samples)
+{
+    if (L < 2 || L > kMaxL || n_samples < 1) return 0;
+    return (size_t)groups_for(n_samples) * (size_t)group_floats(L) * sizeof(float);
+}
+
+extern "C" size_t toric3d_bp_workspace_bytes(int L, int64_t chunk_samples)
+{
+    if (L < 2 || L > kMaxL || chunk_samples < 1) return 0;
+    int64_t g = groups_for(chunk_samples);
+    g += g & 1;  // chunks hold whole 64-sample words
+    return 2 * (size_t)g * (size_t)group_floats(L) * sizeof(float);
+}
+
+static t3d_status bp_common_checks(int L, int64_t n_samples, double p, double q_meas)
+{
+    T3D_TRY(check_lattice(L));
+    T3D_REQUIRE(n_samples >= 1 && words_for(n_samples) <= (1LL << 40), "n_samples out of range");
+    T3D_REQUIRE(p > 0.0 && p < 1.0, "BP needs 0 < p < 1 (p=%g)", p);
+    T3D_REQUIRE(q_meas >= 0.0 && q_meas < 0.5, "BP needs 0 <= q_meas < 0.5 (q=%g)", q_meas);
+    return T3D_OK;
+}
+
+extern "C" t3d_status toric3d_bp_step(int L, int64_t n_samples, const uint64_t* s, double p,
+                                      double q_meas, const float* msg_in, float* msg_out,
+                                      t3d_stream stream)
+{
+    clear_error();
+    T3D_TRY(bp_common_checks(L, n_samples, p, q_meas));
+    T3D_TRY(check_words(s, "s"));
+    T3D_REQUIRE(msg_out != nullptr && aligned(msg_out, 16), "msg_out must be 16-byte aligned");
+    T3D_REQUIRE(msg_in == nullptr || aligned(msg_in, 16), "msg_in must be 16-byte aligned");
+    T3D_REQUIRE(msg_in != msg_out, "msg_in and msg_out must differ");
+    return launch_step(L, groups_for(n_samples), words_for(n_samples), s, p, q_meas, msg_in, msg_out,
+                       as_stream(stream));
+}
+
+extern "C" t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* msg, double p,
+                                        uint64_t* e, uint64_t* s, float* llr_out,
+                                        t3d_stream stream)
+{
+    clear_error();
+    T3D_TRY(bp_common_checks(L, n_samples, p, 0.0));
+    T3D_TRY(check_words(e, "e"));
+    T3D_TRY(check_words(s, "s"));
+    T3D_REQUIRE(msg == nullptr || aligned(msg, 16), "msg must be 16-byte aligned");
+    T3D_REQUIRE(llr_out == nullptr || aligned(llr_out, 4), "llr_out must be 4-byte aligned");
+    return launch_decide(L, groups_for(n_samples), words_for(n_samples), n_samples, p, msg, e, s,
+                         llr_out, as_stream(stream));
+}
+
+extern "C" t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p,
+                                 double q_meas, int iters, void* work, size_t work_bytes,
+                                 float* llr_out, t3d_stream stream)
+{
+    clear_error();
+    T3D_TRY(bp_common_checks(L, n_samples, p, q_meas));
+    T3D_TRY(check_words(e, "e"));
+    T3D_TRY(check_words(s, "s"));
+    T3D_REQUIRE(iters >= 0, "iters must be >= 0");
+    T3D_REQUIRE(work != nullptr && aligned(work, 16), "work must be a 16-byte aligned device pointer");
+    const size_t per_pair = 2 * (size_t)group_floats(L) * sizeof(float);
+    int64_t chunk = (int64_t)(work_bytes / per_pair);
+    const int64_t G = groups_for(n_samples);
+    if (chunk < G) chunk &= ~1LL;  // partial chunks must cover whole 64-sample words
+    T3D_REQUIRE(chunk >= 1, "workspace too small: %zu bytes, need at least %zu", work_bytes,
+                toric3d_bp_workspace_bytes(L, 64));
+    chunk = std::min(chunk, G);
+    T3D_REQUIRE(llr_out == nullptr || chunk >= G, "llr_out requires a workspace for the whole batch");
+    return launch_bp(L, n_samples, e, s, p, q_meas, iters, static_cast<float*>(work), chunk, llr_out,
+                     as_stream(stream));
+}

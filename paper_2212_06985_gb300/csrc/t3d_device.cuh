@@ -1,0 +1,183 @@
+// Device-side building blocks shared by the toric3d kernels: lattice index
+// arithmetic for the periodic L^3 cubic lattice (Sec. 2 of arXiv:2212.06985,
+// primal picture: qubits on edges, Z checks on faces), the Philox4x64-10
+// counter-based generator and the bit-sliced Bernoulli comparator.
+#pragma once
+
+#include <cstdint>
+
+namespace t3d {
+
+// ----------------------------------------------------------------- lattice
+// site = (z*L + y)*L + x; edge (d, site) = d*L^3 + site; face (n, site) = n*L^3 + site.
+struct Lattice {
+    int L;
+    int L2;
+    int L3;
+};
+
+struct Coord {
+    int x[3];
+};
+
+__device__ __forceinline__ Coord site_coord(const Lattice& lat, int site)
+{
+    Coord r;
+    r.x[0] = site % lat.L;
+    int t = site / lat.L;
+    r.x[1] = t % lat.L;
+    r.x[2] = t / lat.L;
+    return r;
+}
+
+__device__ __forceinline__ int site_index(const Lattice& lat, const Coord& r)
+{
+    return (r.x[2] * lat.L + r.x[1]) * lat.L + r.x[0];
+}
+
+// r shifted by +1 or -1 along `axis`, periodic.
+__device__ __forceinline__ Coord shifted(const Lattice& lat, Coord r, int axis, int delta)
+{
+    int v = r.x[axis] + delta;
+    v = (v < 0) ? v + lat.L : (v >= lat.L ? v - lat.L : v);
+    r.x[axis] = v;
+    return r;
+}
+
+// The two in-plane axes a < b of a face with normal n.
+__device__ __forceinline__ void plane_axes(int n, int& a, int& b)
+{
+    a = (n == 0) ? 1 : 0;
+    b = (n == 2) ? 1 : 2;
+}
+
+// The four faces holding edge (a, r), in slot order k = 0..3: for the two
+// other axes c0 < c1, slot 2i is the face with normal 3-a-ci at r and slot
+// 2i+1 the same face at r - e_ci.
+__device__ __forceinline__ void edge_faces(const Lattice& lat, int a, const Coord& r, int out[4])
+{
+    int c0 = (a == 0) ? 1 : 0;
+    int c1 = (a == 2) ? 1 : 2;
+    int m0 = 3 - a - c0, m1 = 3 - a - c1;
+    out[0] = m0 * lat.L3 + site_index(lat, r);
+    out[1] = m0 * lat.L3 + site_index(lat, shifted(lat, r, c0, -1));
+    out[2] = m1 * lat.L3 + site_index(lat, r);
+    out[3] = m1 * lat.L3 + site_index(lat, shifted(lat, r, c1, -1));
+}
+
+// The four edges of face (n, r) and, for each, the slot that face occupies in
+// the edge's face list:  (a, r) slot 2(b-1);  (a, r+e_b) slot 2(b-1)+1;
+// (b, r) slot 2a;  (b, r+e_a) slot 2a+1.
+struct FaceEdges {
+    int dir[4];
+    int site[4];
+    int slot[4];
+};
+
+__device__ __forceinline__ FaceEdges face_edges(const Lattice& lat, int n, const Coord& r)
+{
+    int a, b;
+    plane_axes(n, a, b);
+    FaceEdges fe;
+    int s0 = site_index(lat, r);
+    fe.dir[0] = a; fe.site[0] = s0;                                   fe.slot[0] = 2 * (b - 1);
+    fe.dir[1] = a; fe.site[1] = site_index(lat, shifted(lat, r, b, 1)); fe.slot[1] = 2 * (b - 1) + 1;
+    fe.dir[2] = b; fe.site[2] = s0;                                   fe.slot[2] = 2 * a;
+    fe.dir[3] = b; fe.site[3] = site_index(lat, shifted(lat, r, a, 1)); fe.slot[3] = 2 * a + 1;
+    return fe;
+}
+
+// Face (n, r) owns edge ((n+1) mod 3, r) for in-place updates of e; this is a
+// bijection between faces and edges.  Returns the index 0..3 of that edge in
+// face_edges(): edge 0 = (a, r) when n != 1, edge 2 = (b, r) when n == 1.
+__device__ __forceinline__ int owned_edge_slot(int n) { return (n == 1) ? 2 : 0; }
+
+// ----------------------------------------------------------------- Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11): 10 rounds of two 64x64->128 multiplies and a word permutation, with
+// a Weyl key schedule.
+struct U64x4 {
+    uint64_t v[4];
+};
+
+__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                               uint64_t c3, uint64_t k0, uint64_t k1)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+        uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    U64x4 r;
+    r.v[0] = c0; r.v[1] = c1; r.v[2] = c2; r.v[3] = c3;
+    return r;
+}
+
+enum : uint32_t { kStreamQubit = 0, kStreamMeas = 1, kStreamCoin = 2 };
+
+__device__ __forceinline__ uint64_t stream_word3(uint32_t stream, uint32_t sweep, uint32_t block)
+{
+    return ((uint64_t)stream << 48) | ((uint64_t)sweep << 8) | (uint64_t)block;
+}
+
+// 64 Bernoulli(P / 2^32) bits, one per sample of word `group`: lane j is set
+// iff U_j < P, with U_j the 32-bit integer whose bit 31-i is bit j of output
+// word i (word i = output i%4 of block i/4).  Evaluated as a bit-sliced
+// most-significant-first comparison that stops once every lane is decided.
+__device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, uint32_t stream,
+                                                   uint64_t site, uint32_t cycle, uint32_t sweep,
+                                                   uint64_t group)
+{
+    if (thr == 0) return 0;
+    if (thr >= (1ULL << 32)) return ~0ULL;
+    uint64_t lt = 0, eq = ~0ULL;
+#pragma unroll 1
+    for (int blk = 0; blk < 8; ++blk) {
+        U64x4 w = philox4x64_10(group, site, cycle, stream_word3(stream, sweep, blk), seed, 0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int bit = 31 - (4 * blk + i);
+            if ((thr >> bit) & 1ULL) {
+                lt |= eq & ~w.v[i];
+                eq &= w.v[i];
+            } else {
+                eq &= ~w.v[i];
+            }
+        }
+        if (eq == 0) break;
+    }
+    return lt;
+}
+
+// p-flip coin word for 64 samples: output 0 of block 0 of stream 2.
+__device__ __forceinline__ uint64_t coin_word(uint64_t seed, uint64_t edge, uint32_t cycle,
+                                              uint32_t sweep, uint64_t group)
+{
+    return philox4x64_10(group, edge, cycle, stream_word3(kStreamCoin, sweep, 0), seed, 0).v[0];
+}
+
+// ----------------------------------------------------------------- majority logic
+// For four bit-sliced checks: lanes with >= 3 set, and lanes with exactly 2 set.
+__device__ __forceinline__ uint64_t at_least_three(uint64_t a, uint64_t b, uint64_t c, uint64_t d)
+{
+    return (a & b & (c | d)) | (c & d & (a | b));
+}
+
+__device__ __forceinline__ uint64_t exactly_two(uint64_t a, uint64_t b, uint64_t c, uint64_t d)
+{
+    return (a & b & ~(c | d)) | (c & d & ~(a | b)) | ((a ^ b) & (c ^ d));
+}
+
+}  // namespace t3d

@@ -1,0 +1,97 @@
+// Host-side helpers shared by the toric3d translation units: the per-thread
+// error message, argument checks, and launch-error capture.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/toric3d.h"
+
+namespace t3d {
+
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// Largest lattice accepted: 3 L^3 must index comfortably in 32 bits.
+constexpr int kMaxL = 256;
+
+inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+inline uint64_t prob_threshold(double p)
+{
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return 1ULL << 32;
+    return (uint64_t)(p * 4294967296.0 + 0.5);
+}
+
+inline int64_t words_for(int64_t n_samples) { return (n_samples + 63) / 64; }
+inline int64_t groups_for(int64_t n_samples) { return (n_samples + 31) / 32; }
+
+inline cudaStream_t as_stream(t3d_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+#define T3D_REQUIRE(cond, ...)            \
+    do {                                  \
+        if (!(cond)) {                    \
+            ::t3d::set_error(__VA_ARGS__); \
+            return T3D_EINVAL;            \
+        }                                 \
+    } while (0)
+
+#define T3D_CUDA_CHECK(expr)                                                              \
+    do {                                                                                  \
+        cudaError_t err_ = (expr);                                                        \
+        if (err_ != cudaSuccess) {                                                        \
+            ::t3d::set_error("%s failed: %s", #expr, cudaGetErrorString(err_));           \
+            return T3D_ECUDA;                                                             \
+        }                                                                                 \
+    } while (0)
+
+#define T3D_LAUNCH_CHECK(what)                                                            \
+    do {                                                                                  \
+        cudaError_t err_ = cudaGetLastError();                                            \
+        if (err_ != cudaSuccess) {                                                        \
+            ::t3d::set_error("launch of %s failed: %s", what, cudaGetErrorString(err_));  \
+            return T3D_ECUDA;                                                             \
+        }                                                                                 \
+    } while (0)
+
+#define T3D_TRY(expr)                      \
+    do {                                   \
+        t3d_status st_ = (expr);           \
+        if (st_ != T3D_OK) return st_;     \
+    } while (0)
+
+// Kernel timing: prof_begin() returns a handle (or -1 when profiling is off
+// or the stream is capturing) and records a start event; prof_end() records
+// the matching stop event after the launch.
+int prof_begin(int kind, cudaStream_t st);
+void prof_end(int handle, cudaStream_t st);
+
+struct ProfScope {
+    int h;
+    cudaStream_t st;
+    ProfScope(int kind, cudaStream_t s) : h(prof_begin(kind, s)), st(s) {}
+    ~ProfScope() { prof_end(h, st); }
+};
+
+t3d_status check_lattice(int L);
+t3d_status check_words(const void* p, const char* name);
+
+// Kernel launchers used across translation units (no argument validation).
+t3d_status launch_noise(int L, int64_t words, uint64_t* e, uint64_t thr, uint64_t seed,
+                        uint64_t group0, uint32_t cycle, cudaStream_t st);
+t3d_status launch_syndrome(int L, int64_t words, const uint64_t* e, uint64_t* s, uint64_t thr,
+                           uint64_t seed, uint64_t group0, uint32_t cycle, cudaStream_t st);
+t3d_status launch_sweeps(int L, int64_t words, uint64_t* e, uint64_t* s, uint64_t* tmp,
+                         const char* schedule, int slen, int n_apply, uint32_t sweep0,
+                         uint64_t seed, uint64_t group0, uint32_t cycle, cudaStream_t st);
+t3d_status launch_logical(int L, int64_t n_samples, const uint64_t* e, uint8_t* mask,
+                          int64_t* counts8, cudaStream_t st);
+t3d_status launch_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p,
+                     double q_meas, int iters, float* buf, int64_t chunk_groups,
+                     float* llr_out, cudaStream_t st);
+
+}  // namespace t3d

@@ -1,0 +1,94 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every entry point include/toric3d.h declares, sizes its
+workspaces, and rejects invalid arguments with T3D_EINVAL before touching the
+device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2212_06985_gb300 as t3d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+EINVAL = 1
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "toric3d.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(toric3d_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = t3d.lib()
+    declared = _declared()
+    assert len(declared) >= 17
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(t3d.EXPORTED_SYMBOLS) == declared
+
+
+def test_abi_version():
+    assert t3d.lib().toric3d_abi_version() == 1
+
+
+def test_workspace_sizes():
+    L, W = 4, 157
+    assert t3d.toric3d_flip_workspace_bytes(L, W) == 3 * 64 * W * 8
+    assert t3d.toric3d_flip_workspace_bytes(1, W) == 0
+    assert t3d.toric3d_bp_message_bytes(4, 100) == 4 * 3 * 64 * 4 * 32 * 4
+    assert t3d.toric3d_bp_workspace_bytes(4, 100) == 2 * 4 * 3 * 64 * 4 * 32 * 4
+    cfg = t3d.make_run_cfg(4, 4, 0.01, 0.01, 0, 10_000, schedule="F", n_apply=32)
+    assert t3d.toric3d_run_workspace_bytes(cfg) == 2 * ((3 * 64 * 157 * 8 + 255) // 256 * 256)
+    bad = t3d.make_run_cfg(4, 4, 0.01, 0.01, 0, 10_000, schedule="FX", n_apply=2)
+    assert t3d.toric3d_run_workspace_bytes(bad) == 0
+
+
+def _err():
+    return t3d.lib().toric3d_last_error().decode()
+
+
+FAKE = ctypes.c_void_p(0x10000)    # aligned, never dereferenced: calls fail validation first
+MIS = ctypes.c_void_p(0x10004)
+
+
+@pytest.mark.parametrize("call,needle", [
+    (lambda l: l.toric3d_noise(1, 4, FAKE, 0.1, 0, 0, 1, None), "L=1"),
+    (lambda l: l.toric3d_noise(4, 0, FAKE, 0.1, 0, 0, 1, None), "words"),
+    (lambda l: l.toric3d_noise(4, 4, None, 0.1, 0, 0, 1, None), "NULL"),
+    (lambda l: l.toric3d_noise(4, 4, MIS, 0.1, 0, 0, 1, None), "aligned"),
+    (lambda l: l.toric3d_noise(4, 4, FAKE, 1.5, 0, 0, 1, None), "p="),
+    (lambda l: l.toric3d_noise(4, 4, FAKE, 0.1, 0, 3, 1, None), "sample0"),
+    (lambda l: l.toric3d_syndrome(4, 4, FAKE, FAKE, 0.1, 0, 0, 1, None), "overlap"),
+    (lambda l: l.toric3d_flip(4, 4, FAKE, FAKE, 2, FAKE, 16, None), "workspace"),
+    (lambda l: l.toric3d_pflip(4, 4, FAKE, FAKE, b"FQ", 2, 0, 0, 0, 1, FAKE, 1 << 20, None), "schedule"),
+    (lambda l: l.toric3d_bp_step(4, 10, FAKE, 0.0, 0.1, None, FAKE, None), "0 < p < 1"),
+    (lambda l: l.toric3d_bp_step(4, 10, FAKE, 0.1, 0.6, None, FAKE, None), "q_meas"),
+    (lambda l: l.toric3d_bp(4, 10, FAKE, FAKE, 0.1, 0.1, 3, FAKE, 64, None, None), "workspace"),
+    (lambda l: l.toric3d_logical(4, 0, FAKE, None, None, None), "n_samples"),
+    (lambda l: l.toric3d_pack(0, 4, FAKE, FAKE, None), "empty"),
+])
+def test_invalid_arguments_are_rejected(call, needle):
+    assert call(t3d.lib()) == EINVAL
+    assert needle in _err()
+
+
+def test_run_cycles_rejects_bad_configs():
+    lib = t3d.lib()
+    for kw in (dict(L=1), dict(p=-0.1), dict(sample0=10), dict(schedule="FFX", n_apply=3),
+               dict(schedule="", n_apply=2), dict(use_bp=True, bp_iters=4, p=0.0)):
+        base = dict(L=4, T=2, p=0.01, q=0.01, seed=0, n_samples=100, schedule="F", n_apply=1)
+        base.update(kw)
+        cfg = t3d.make_run_cfg(**base)
+        assert lib.toric3d_run_cycles(ctypes.byref(cfg), FAKE, FAKE, 1 << 30, None, None, None) == EINVAL
+    cfg = t3d.make_run_cfg(4, 2, 0.01, 0.01, 0, 100, schedule="F", n_apply=1)
+    assert lib.toric3d_run_cycles(ctypes.byref(cfg), FAKE, FAKE, 64, None, None, None) == EINVAL
+    assert "workspace" in _err()
+
+
+def test_table1_schedule_matches_paper():
+    import json
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "schedules.json")))
+    for row in g["table1"]:
+        assert t3d.table1_schedule(row["n_A"], row["lambda_p"]) == row["schedule"]
