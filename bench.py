@@ -196,8 +196,7 @@ def cuda_arm(args):
 
     w = inp.WORKLOADS[args.workload]
     S = args.samples or w.n_samples
-    stride = (S + 63) // 64 * 64
-    sample0 = rank * stride
+    sample0 = t3d.replica_sample0(rank, S)
     L = w.L
     n = inp.n_bits(L)
     W = inp.words_for(S)

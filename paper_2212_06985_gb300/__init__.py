@@ -28,7 +28,7 @@ __all__ = [
     "toric3d_flip_workspace_bytes", "toric3d_bp_message_bytes",
     "toric3d_bp_workspace_bytes", "toric3d_run_workspace_bytes", "make_run_cfg",
     "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "KERNEL_KINDS",
-    "EXPORTED_SYMBOLS",
+    "EXPORTED_SYMBOLS", "replica_sample0",
 ]
 
 EXPORTED_SYMBOLS = [
@@ -266,3 +266,11 @@ def toric3d_profile_read(kind) -> tuple[float, int]:
     n = ctypes.c_int64()
     _check(lib().toric3d_profile_read(k, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+# ------------------------------------------------------------------ replicas
+def replica_sample0(rank: int, samples_per_rank: int) -> int:
+    """First global sample of a rank's disjoint range.  Ranges start on
+    64-sample word boundaries, so every replica draws exactly the random
+    numbers one large batch would (the generator is keyed by global sample)."""
+    return rank * ((samples_per_rank + 63) // 64 * 64)

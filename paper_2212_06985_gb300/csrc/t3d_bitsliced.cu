@@ -234,7 +234,7 @@ __global__ void k_unpack(int64_t n_bits, int64_t n_samples, int64_t W, const uin
     bits[sample * n_bits + i] = (uint8_t)((words[i * W + sample / 64] >> (sample % 64)) & 1ULL);
 }
 
-Lattice make_lattice(int L) { return Lattice{L, L * L, L * L * L}; }
+Lattice make_lattice(int L) { return make_lattice_host(L); }
 
 }  // namespace
 

@@ -37,17 +37,76 @@ struct TD {
 
 __device__ __forceinline__ TD td_mul(TD A, TD B) { return TD{A.t * B.t, fmaf(A.t, B.d, A.d)}; }
 
-__device__ __forceinline__ TD td_of(float x)
+// MUFU approximations (PTX ex2/rcp/lg2 .approx.ftz, a few ulp); the
+// formulations below only feed them arguments where that relative accuracy
+// carries through without cancellation.
+__device__ __forceinline__ float ex2_approx(float x)
 {
-    float a = fabsf(x);
-    float E = expf(-a);
-    TD r;
-    r.t = tanhf(0.5f * a);
-    r.d = (2.0f * E) / (1.0f + E);
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
-// Eq. 2 for the four edges of one face: y[j] from the other three inputs.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// (tanh(|x|/2), 1 - tanh(|x|/2)) = ((1 - E), 2E) / (1 + E) with E = e^{-|x|}.
+// For |x| < 1/2 the difference 1 - E is taken from its Taylor series
+// sum_{k>=1} (-1)^{k+1} |x|^k / k! (through k = 7, truncation < 3e-7 relative)
+// instead of subtracting two nearly equal numbers.
+__device__ __forceinline__ TD td_of(float x)
+{
+    const float a = fabsf(x);
+    const float E = ex2_approx(-a * kLog2e);
+    const float r = rcp_approx(1.0f + E);
+    float om = 1.0f - E;
+    if (a < 0.5f) {
+        float h = fmaf(a, 1.0f / 5040.0f, -1.0f / 720.0f);
+        h = fmaf(a, h, 1.0f / 120.0f);
+        h = fmaf(a, h, -1.0f / 24.0f);
+        h = fmaf(a, h, 1.0f / 6.0f);
+        h = fmaf(a, h, -0.5f);
+        h = fmaf(a, h, 1.0f);
+        om = a * h;
+    }
+    return TD{om * r, (E + E) * r};
+}
+
+// 2 atanh(P) for P = prod t, D = 1 - P: for P < 0.3 the odd series
+// 2 sum_k P^{2k+1}/(2k+1) (through P^13, truncation < 1e-8 relative); above it
+// log((1 + P) / D), whose argument exceeds 1.85 so the logarithm carries no
+// cancellation.  D = 0 (underflow) gives +inf, which the clamp turns into 30.
+__device__ __forceinline__ float two_atanh(float P, float D)
+{
+    if (P < 0.3f) {
+        const float u = P * P;
+        float h = fmaf(u, 1.0f / 13.0f, 1.0f / 11.0f);
+        h = fmaf(u, h, 1.0f / 9.0f);
+        h = fmaf(u, h, 1.0f / 7.0f);
+        h = fmaf(u, h, 1.0f / 5.0f);
+        h = fmaf(u, h, 1.0f / 3.0f);
+        h = fmaf(u, h, 1.0f);
+        return 2.0f * P * h;
+    }
+    return kLn2 * lg2_approx((1.0f + P) * rcp_approx(D));
+}
+
+// Eq. 2 for the four edges of one face: y[j] from the other three inputs and
+// the measurement-variable pair q.
 __device__ __forceinline__ void check_node(const float x[4], bool s_neg, TD q, float y[4])
 {
     TD in[4];
@@ -57,26 +116,22 @@ __device__ __forceinline__ void check_node(const float x[4], bool s_neg, TD q, f
         in[j] = td_of(x[j]);
         neg ^= (x[j] < 0.0f) ? 1u : 0u;
     }
-    const TD one{1.0f, 0.0f};
-    TD pre[4], suf[4];
-    pre[0] = q;
-    pre[1] = td_mul(pre[0], in[0]);
-    pre[2] = td_mul(pre[1], in[1]);
-    pre[3] = td_mul(pre[2], in[2]);
-    suf[3] = one;
-    suf[2] = in[3];
-    suf[1] = td_mul(in[2], suf[2]);
-    suf[0] = td_mul(in[1], suf[1]);
+    const TD pre1 = td_mul(q, in[0]);
+    const TD pre2 = td_mul(pre1, in[1]);
+    const TD suf2 = in[3];
+    const TD suf1 = td_mul(in[2], suf2);
+    const TD o[4] = {td_mul(q, td_mul(in[1], suf1)), td_mul(pre1, suf1), td_mul(pre2, suf2),
+                     td_mul(pre2, in[2])};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        TD o = td_mul(pre[j], suf[j]);
-        float mag = log1pf((2.0f * o.t) / o.d);
-        mag = fminf(mag, kMsgClamp);
-        unsigned sgn = neg ^ ((x[j] < 0.0f) ? 1u : 0u);
+        const float mag = fminf(two_atanh(o[j].t, o[j].d), kMsgClamp);
+        const unsigned sgn = neg ^ ((x[j] < 0.0f) ? 1u : 0u);
         y[j] = sgn ? -mag : mag;
     }
 }
 
+// Grid: x covers the 3L^3 faces of a group, one warp per face (faces ordered
+// site-major, normal innermost); y (and z past 65535) is the group.
 struct FaceWarp {
     int64_t g;
     int site;
@@ -85,13 +140,11 @@ struct FaceWarp {
 
 __device__ __forceinline__ bool face_warp(const Lattice& lat, int64_t n_groups, FaceWarp& fw)
 {
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t per_g = 3LL * lat.L3;
-    fw.g = warp / per_g;
-    if (fw.g >= n_groups) return false;
-    const int rem = (int)(warp - fw.g * per_g);
-    fw.site = rem / 3;
-    fw.n = rem - 3 * fw.site;
+    const int f = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    fw.g = (int64_t)blockIdx.z * 65535 + blockIdx.y;
+    if (f >= 3 * lat.L3 || fw.g >= n_groups) return false;
+    fw.site = f / 3;
+    fw.n = f - 3 * fw.site;
     return true;
 }
 
@@ -102,7 +155,8 @@ __device__ __forceinline__ int64_t edge_block(const Lattice& lat, int64_t g, int
 }
 
 // One flooding iteration: Eq. 3 (variable->check, from msg_in or the prior)
-// followed by Eq. 2 (check->variable) into msg_out.
+// followed by Eq. 2 (check->variable) into msg_out.  Each input sums the three
+// messages of its edge other than this face's slot (that slot is not read).
 __global__ void __launch_bounds__(kBpThreads)
 k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__ s, float l0,
           TD q, const float* __restrict__ msg_in, float* __restrict__ msg_out)
@@ -118,15 +172,13 @@ k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         base[j] = edge_block(lat, fw.g, fe.site[j], fe.dir[j]) + lane;
+        float acc = l0;
         if (msg_in) {
-            float acc = l0;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (k != fe.slot[j]) acc += msg_in[base[j] + k * kLanes];
-            x[j] = acc;
-        } else {
-            x[j] = l0;
         }
+        x[j] = acc;
     }
     float y[4];
     check_node(x, s_neg, q, y);
@@ -180,7 +232,7 @@ k_bp_decide(Lattice lat, int64_t n_groups, int64_t W, int64_t n_samples, float l
     }
 }
 
-Lattice make_lattice(int L) { return Lattice{L, L * L, L * L * L}; }
+Lattice make_lattice(int L) { return make_lattice_host(L); }
 
 TD meas_pair(double q_meas)
 {
@@ -195,9 +247,12 @@ float prior(double p) { return (float)std::log((1.0 - p) / p); }
 
 int64_t group_floats(int L) { return 3LL * L * L * L * 4 * kLanes; }
 
-unsigned warps_grid(int64_t n_warps)
+dim3 face_grid(int L, int64_t n_groups)
 {
-    return (unsigned)((n_warps * 32 + kBpThreads - 1) / kBpThreads);
+    const int64_t faces = 3LL * L * L * L;
+    const int warps_per_block = kBpThreads / 32;
+    return dim3((unsigned)((faces + warps_per_block - 1) / warps_per_block),
+                (unsigned)std::min<int64_t>(n_groups, 65535), (unsigned)((n_groups + 65534) / 65535));
 }
 
 t3d_status launch_step(int L, int64_t n_groups, int64_t W, const uint64_t* s, double p, double q_meas,
@@ -205,7 +260,7 @@ t3d_status launch_step(int L, int64_t n_groups, int64_t W, const uint64_t* s, do
 {
     Lattice lat = make_lattice(L);
     ProfScope prof(T3D_K_BP_STEP, st);
-    k_bp_step<<<warps_grid(n_groups * 3LL * lat.L3), kBpThreads, 0, st>>>(
+    k_bp_step<<<face_grid(L, n_groups), kBpThreads, 0, st>>>(
         lat, n_groups, W, s, prior(p), meas_pair(q_meas), in, out);
     T3D_LAUNCH_CHECK("bp step");
     return T3D_OK;
@@ -216,7 +271,7 @@ t3d_status launch_decide(int L, int64_t n_groups, int64_t W, int64_t n_samples, 
 {
     Lattice lat = make_lattice(L);
     ProfScope prof(T3D_K_BP_DECIDE, st);
-    k_bp_decide<<<warps_grid(n_groups * 3LL * lat.L3), kBpThreads, 0, st>>>(
+    k_bp_decide<<<face_grid(L, n_groups), kBpThreads, 0, st>>>(
         lat, n_groups, W, n_samples, prior(p), msg, reinterpret_cast<uint32_t*>(e),
         reinterpret_cast<uint32_t*>(s), llr);
     T3D_LAUNCH_CHECK("bp decide");

@@ -14,7 +14,20 @@ struct Lattice {
     int L;
     int L2;
     int L3;
+    uint32_t magic;  // floor(2^32 / L) + 1: n / L == __umulhi(n, magic) for 0 <= n < 2^32 / L
 };
+
+inline Lattice make_lattice_host(int L)
+{
+    return Lattice{L, L * L, L * L * L, (uint32_t)((1ULL << 32) / (uint64_t)L + 1)};
+}
+
+// Exact n / L for 0 <= n < 2^24 (at most 256^3 sites): with magic = 2^32/L + eps,
+// 0 < eps <= 1, n*magic/2^32 = n/L + n*eps/2^32 exceeds n/L by less than 1/L.
+__device__ __forceinline__ int div_L(const Lattice& lat, int n)
+{
+    return (int)__umulhi((uint32_t)n, lat.magic);
+}
 
 struct Coord {
     int x[3];
@@ -23,10 +36,11 @@ struct Coord {
 __device__ __forceinline__ Coord site_coord(const Lattice& lat, int site)
 {
     Coord r;
-    r.x[0] = site % lat.L;
-    int t = site / lat.L;
-    r.x[1] = t % lat.L;
-    r.x[2] = t / lat.L;
+    int t = div_L(lat, site);
+    r.x[0] = site - t * lat.L;
+    int z = div_L(lat, t);
+    r.x[1] = t - z * lat.L;
+    r.x[2] = z;
     return r;
 }
 

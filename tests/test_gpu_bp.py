@@ -3,14 +3,22 @@
 Per-iteration protocol: iteration 1 starts both sides from the priors; for
 every later iteration the oracle is seeded with the GPU's FP32 messages of the
 previous iteration, so each comparison isolates one iteration of FP32
-arithmetic.  Tolerance per message:
-    |gpu - ref| <= 1e-5 |ref| + 1e-6 + 2.3e-16 exp(|ref|)
-The first two terms are the FP32 target; the last bounds the oracle's own
-binary64 error in 2 atanh(P) when P is within a few ulps of 1 (messages near
-the clamp of 30), where 1 - P carries one ulp of 2^-53 relative to e^-|ref|.
-End to end (all iterations on each side), posteriors agree to a tolerance
-derived from the per-iteration bound grown over the iterations, and hard
-decisions agree exactly wherever |l| > 1e-4."""
+arithmetic.  Tolerance per message (derived from the arithmetic):
+    |gpu - ref| <= 1e-5 |ref| + 1e-6                       FP32 target
+                 + 2.3e-16 exp(|ref|)                      oracle's own error
+                 + 3 u sum_{i != j} (|l0| + sum |m_in|)    FP32 input sums
+The second term bounds the oracle's binary64 error in 2 atanh(P) when 1 - P
+~ e^-|ref| is resolved to one ulp of 2^-53 (messages near the clamp of 30).
+The third bounds the FP32 rounding of each variable->check input
+x = l0 + m_a + m_b + m_c (three roundings of at most u = 2^-24 times the sum
+of magnitudes), propagated through Eq. 2, whose output moves by at most
+|dx| per input; it only matters when opposite-sign saturated messages cancel
+(measurement variables off).
+End to end (all iterations on each side), with measurement variables on or
+consistent syndromes, posteriors agree closely and hard decisions agree
+exactly wherever |l| > 1e-4.  Loopy BP on an inconsistent syndrome without
+measurement variables is chaotic (messages pinned at the clamp flip sign), so
+there only the per-iteration protocol is meaningful."""
 import numpy as np
 import pytest
 import torch
@@ -23,8 +31,27 @@ from gpu_util import dev, download_bits, gpu_messages_to_oracle, message_index, 
 pytestmark = pytest.mark.gpu
 
 
-def _tol(ref):
-    return 1e-5 * np.abs(ref) + 1e-6 + 2.3e-16 * np.exp(np.minimum(np.abs(ref), 40.0))
+U32 = 2.0 ** -24
+
+
+def _tol(ref, input_bound=0.0):
+    return (1e-5 * np.abs(ref) + 1e-6 + 2.3e-16 * np.exp(np.minimum(np.abs(ref), 40.0))
+            + input_bound)
+
+
+def _input_rounding_bound(m_in, face_edges, l0):
+    """Per Tanner edge (f -> E_j): 3u times the sum, over the face's other three
+    edges i, of |l0| + the magnitudes of the three messages summed into x_{i->f}."""
+    S, ne = m_in.shape
+    n = ne // 4
+    fe = np.asarray(face_edges, dtype=np.int64).reshape(-1)      # Tanner edge -> variable
+    absm = np.abs(m_in)
+    A = np.zeros((S, n))
+    np.add.at(A, (slice(None), fe), absm)                        # sum of |incoming| per edge
+    xin = abs(l0) + A[:, fe] - absm                              # magnitudes summed into x_{v->f}
+    per_face = xin.reshape(S, n, 4)
+    others = per_face.sum(axis=2, keepdims=True) - per_face
+    return (3 * U32 * others).reshape(S, ne)
 
 
 def _noisy_syndromes(L, S, p, q, seed):
@@ -47,22 +74,32 @@ def test_bp_each_iteration_matches_oracle(L, S, p, q, meas):
     t3d.toric3d_bp_step(L, S, s, p, qm, None, A)
     gpu = gpu_messages_to_oracle(A, L, S, idx)
     ref, _ = oracle.bp_batch(L, sbits, p, q, meas, 1)
+    l0 = float(np.log((1 - p) / p))
+    bound = 0.0
     worst = 0.0
-    for it in range(2, 17):
-        assert (np.abs(gpu - ref) <= _tol(ref)).all(), f"iteration {it - 1}"
+    for it in range(1, 17):
+        tol = _tol(ref, bound)
+        bad = np.abs(gpu - ref) > tol
+        if bad.any():
+            i = np.argwhere(bad)[0]
+            raise AssertionError(f"iteration {it}: sample {i[0]} tanner edge {i[1]}: gpu {gpu[tuple(i)]!r} "
+                                 f"ref {ref[tuple(i)]!r} tol {tol[tuple(i)]!r} ({int(bad.sum())} bad)")
         worst = max(worst, float((np.abs(gpu - ref) / _tol(ref)).max()))
+        if it == 16:
+            break
         t3d.toric3d_bp_step(L, S, s, p, qm, A, B)
         ref, _ = oracle.bp_batch(L, sbits, p, q, meas, 1, m_in=gpu)
+        bound = _input_rounding_bound(gpu, fe, l0)
         gpu = gpu_messages_to_oracle(B, L, S, idx)
         A, B = B, A
-    assert (np.abs(gpu - ref) <= _tol(ref)).all()
-    print(f"worst error / tolerance over 16 iterations: {worst:.3f}")
+    print(f"worst error / (1e-5 rel + 1e-6 abs + oracle term) over 16 iterations: {worst:.3f}")
 
 
-@pytest.mark.parametrize("L,S,iters,meas", [(4, 200, 16, True), (6, 70, 20, True), (4, 100, 30, False)])
-def test_bp_end_to_end_posteriors_and_decisions(L, S, iters, meas):
+@pytest.mark.parametrize("L,S,iters,meas,q_noise", [(4, 200, 16, True, 0.04), (6, 70, 20, True, 0.04),
+                                                   (4, 100, 30, False, 0.0)])
+def test_bp_end_to_end_posteriors_and_decisions(L, S, iters, meas, q_noise):
     p = q = 0.04
-    ebits, sbits = _noisy_syndromes(L, S, p, q, seed=3 + L)
+    ebits, sbits = _noisy_syndromes(L, S, p, q_noise, seed=3 + L)
     e, s = upload_bits(ebits), upload_bits(sbits)
     n = 3 * L ** 3
     llr = torch.zeros((n, S), dtype=torch.float32, device=dev())
