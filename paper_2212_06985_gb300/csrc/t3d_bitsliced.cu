@@ -68,51 +68,70 @@ __global__ void k_syndrome(Lattice lat, int64_t W, const uint64_t* __restrict__ 
     s[(int64_t)f * W + w] = acc;
 }
 
-// One synchronous flip (or p-flip) application, face-centric: the thread of
-// face f recomputes the decision of each of its four edges from the old
-// syndrome snapshot s_in (each edge's 4 faces), writes s_out[f] = s_in[f] ^
-// (flips of its edges), and applies the flip of the one edge it owns to e.
+// Periodic neighbour offsets of a site: step[a] and the +1 / -1 moves along
+// each axis expressed as index deltas.
+struct Moves {
+    int plus[3];
+    int minus[3];
+};
+
+__device__ __forceinline__ Moves site_moves(const Lattice& lat, int site)
+{
+    const Coord r = site_coord(lat, site);
+    const int step[3] = {1, lat.L, lat.L2};
+    Moves m;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        m.plus[a] = (r.x[a] + 1 == lat.L) ? step[a] * (1 - lat.L) : step[a];
+        m.minus[a] = (r.x[a] == 0) ? step[a] * (lat.L - 1) : -step[a];
+    }
+    return m;
+}
+
+// One synchronous flip (or p-flip) application for the three faces at a site.
+// The thread of site r decides the nine edges its faces touch -- (x,r), (y,r),
+// (z,r), (x,r+e_y), (x,r+e_z), (y,r+e_x), (y,r+e_z), (z,r+e_x), (z,r+e_y) --
+// each from its four faces in the old snapshot s_in, writes s_out at its three
+// faces (old value XOR its four edges' flips) and applies the flips of the
+// three edges at r to e.  Edge (a, r') lies on the faces with normal 3-a-c at
+// r' and r' - e_c for the two axes c != a.
 template <bool kProbabilistic>
 __global__ void k_sweep(Lattice lat, int64_t W, uint64_t* __restrict__ e,
                         const uint64_t* __restrict__ s_in, uint64_t* __restrict__ s_out,
                         uint64_t seed, uint64_t group0, uint32_t cycle, uint32_t sweep)
 {
-    int f;
+    int r;
     int64_t w;
-    if (!site_word(3LL * lat.L3, W, f, w)) return;
-    int n = f / lat.L3, site = f - n * lat.L3;
-    Coord r = site_coord(lat, site);
-    int a, b;
-    plane_axes(n, a, b);
-    const Coord er[4] = {r, shifted(lat, r, b, 1), r, shifted(lat, r, a, 1)};
-    const int ed[4] = {a, a, b, b};
-    const int own = owned_edge_slot(n);
-    uint64_t acc = s_in[(int64_t)f * W + w];
-    uint64_t own_flip = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int ff[4];
-        edge_faces(lat, ed[j], er[j], ff);
-        uint64_t c0 = s_in[(int64_t)ff[0] * W + w];
-        uint64_t c1 = s_in[(int64_t)ff[1] * W + w];
-        uint64_t c2 = s_in[(int64_t)ff[2] * W + w];
-        uint64_t c3 = s_in[(int64_t)ff[3] * W + w];
-        uint64_t fl = at_least_three(c0, c1, c2, c3);
+    if (!site_word(lat.L3, W, r, w)) return;
+    const Moves mv = site_moves(lat, r);
+    const int rx = r + mv.plus[0], ry = r + mv.plus[1], rz = r + mv.plus[2];
+    const int64_t L3 = lat.L3;
+    auto S = [&](int n, int site) { return s_in[((int64_t)n * L3 + site) * W + w]; };
+    const uint64_t s0 = S(0, r), s1 = S(1, r), s2 = S(2, r);
+    const uint64_t group = group0 + (uint64_t)w;
+    auto decide = [&](uint64_t a, uint64_t b, uint64_t c, uint64_t d, int dir, int site) {
+        uint64_t fl = at_least_three(a, b, c, d);
         if (kProbabilistic) {
-            uint64_t two = exactly_two(c0, c1, c2, c3);
-            if (two) {
-                uint64_t edge = (uint64_t)ed[j] * lat.L3 + site_index(lat, er[j]);
-                fl |= two & coin_word(seed, edge, cycle, sweep, group0 + w);
-            }
+            const uint64_t two = exactly_two(a, b, c, d);
+            if (two) fl |= two & coin_word(seed, (uint64_t)dir * L3 + site, cycle, sweep, group);
         }
-        acc ^= fl;
-        if (j == own) own_flip = fl;
-    }
-    s_out[(int64_t)f * W + w] = acc;
-    if (own_flip) {
-        int64_t edge = (int64_t)ed[own] * lat.L3 + site;
-        e[edge * W + w] ^= own_flip;
-    }
+        return fl;
+    };
+    const uint64_t fx0 = decide(s2, S(2, r + mv.minus[1]), s1, S(1, r + mv.minus[2]), 0, r);
+    const uint64_t fy0 = decide(s2, S(2, r + mv.minus[0]), s0, S(0, r + mv.minus[2]), 1, r);
+    const uint64_t fz0 = decide(s1, S(1, r + mv.minus[0]), s0, S(0, r + mv.minus[1]), 2, r);
+    const uint64_t fxy = decide(S(2, ry), s2, S(1, ry), S(1, ry + mv.minus[2]), 0, ry);
+    const uint64_t fxz = decide(S(2, rz), S(2, rz + mv.minus[1]), S(1, rz), s1, 0, rz);
+    const uint64_t fyx = decide(S(2, rx), s2, S(0, rx), S(0, rx + mv.minus[2]), 1, rx);
+    const uint64_t fyz = decide(S(2, rz), S(2, rz + mv.minus[0]), S(0, rz), s0, 1, rz);
+    const uint64_t fzx = decide(S(1, rx), s1, S(0, rx), S(0, rx + mv.minus[1]), 2, rx);
+    const uint64_t fzy = decide(S(1, ry), S(1, ry + mv.minus[0]), S(0, ry), s0, 2, ry);
+    s_out[((int64_t)0 * L3 + r) * W + w] = s0 ^ fy0 ^ fyz ^ fz0 ^ fzy;
+    s_out[((int64_t)1 * L3 + r) * W + w] = s1 ^ fx0 ^ fxz ^ fz0 ^ fzx;
+    s_out[((int64_t)2 * L3 + r) * W + w] = s2 ^ fx0 ^ fxy ^ fy0 ^ fyx;
+    if (fx0) e[((int64_t)0 * L3 + r) * W + w] ^= fx0;
+    if (fy0) e[((int64_t)1 * L3 + r) * W + w] ^= fy0;
+    if (fz0) e[((int64_t)2 * L3 + r) * W + w] ^= fz0;
 }
 
 // Logical readout.  Block (32, 8): threadIdx.x = word of a 32-word tile,
@@ -264,7 +283,7 @@ t3d_status launch_sweeps(int L, int64_t words, uint64_t* e, uint64_t* s, uint64_
                          const char* schedule, int slen, int n_apply, uint32_t sweep0,
                          uint64_t seed, uint64_t group0, uint32_t cycle, cudaStream_t st)
 {
-    auto g = site_word_grid(3LL * L * L * L, words);
+    auto g = site_word_grid((int64_t)L * L * L, words);
     Lattice lat = make_lattice(L);
     uint64_t* bufs[2] = {s, tmp};
     for (int k = 0; k < n_apply; ++k) {

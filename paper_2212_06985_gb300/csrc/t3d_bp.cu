@@ -29,6 +29,8 @@ namespace {
 constexpr int kBpThreads = 256;
 constexpr int kLanes = 32;
 constexpr float kMsgClamp = 30.0f;
+// Message offsets within one group, 3 L^3 * 128 floats, stay below 2^31.
+constexpr int kMaxBpL = 128;
 
 struct TD {
     float t;  // tanh(|x|/2)
@@ -130,105 +132,160 @@ __device__ __forceinline__ void check_node(const float x[4], bool s_neg, TD q, f
     }
 }
 
-// Grid: x covers the 3L^3 faces of a group, one warp per face (faces ordered
-// site-major, normal innermost); y (and z past 65535) is the group.
-struct FaceWarp {
+// Grid: x covers the L^3 sites of a group, one warp per site handling the
+// three faces at that site (normals x, y, z); y (and z past 65535) is the
+// group.  With r the site and e_a the unit steps, the faces' edges and the
+// slot each face occupies in its edges' face lists are (edge_faces order):
+//   face n=0: (y,r) slot 2, (y,r+e_z) slot 3, (z,r) slot 2, (z,r+e_y) slot 3
+//   face n=1: (x,r) slot 2, (x,r+e_z) slot 3, (z,r) slot 0, (z,r+e_x) slot 1
+//   face n=2: (x,r) slot 0, (x,r+e_y) slot 1, (y,r) slot 0, (y,r+e_x) slot 1
+struct SiteWarp {
     int64_t g;
     int site;
-    int n;
+    int nb[3];  // site + e_x, site + e_y, site + e_z (periodic)
 };
 
-__device__ __forceinline__ bool face_warp(const Lattice& lat, int64_t n_groups, FaceWarp& fw)
+__device__ __forceinline__ bool site_warp(const Lattice& lat, int64_t n_groups, SiteWarp& sw)
 {
-    const int f = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
-    fw.g = (int64_t)blockIdx.z * 65535 + blockIdx.y;
-    if (f >= 3 * lat.L3 || fw.g >= n_groups) return false;
-    fw.site = f / 3;
-    fw.n = f - 3 * fw.site;
+    const int site = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    sw.g = (int64_t)blockIdx.z * 65535 + blockIdx.y;
+    if (site >= lat.L3 || sw.g >= n_groups) return false;
+    sw.site = site;
+    const Coord r = site_coord(lat, site);
+    const int step[3] = {1, lat.L, lat.L2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        sw.nb[a] = site + ((r.x[a] + 1 == lat.L) ? step[a] * (1 - lat.L) : step[a]);
     return true;
 }
 
-// Offset of edge (d, site)'s 4x32 message block within group g.
-__device__ __forceinline__ int64_t edge_block(const Lattice& lat, int64_t g, int site, int d)
+// Offset of edge (d, site)'s 4x32 message block within a group.
+__device__ __forceinline__ int msg_off(int site, int d) { return (site * 3 + d) * (4 * kLanes); }
+
+__device__ __forceinline__ bool syndrome_bit(const uint64_t* s, const Lattice& lat, int64_t W,
+                                             int n, int site, int64_t g, int lane)
 {
-    return ((g * lat.L3 + site) * 3 + d) * (4 * kLanes);
+    const uint64_t w = s[((int64_t)n * lat.L3 + site) * W + (g >> 1)];
+    return (w >> ((g & 1) * 32 + lane)) & 1ULL;
 }
 
-// One flooding iteration: Eq. 3 (variable->check, from msg_in or the prior)
-// followed by Eq. 2 (check->variable) into msg_out.  Each input sums the three
-// messages of its edge other than this face's slot (that slot is not read).
+// One flooding iteration for the three faces of a site: Eq. 3 (variable->check
+// inputs, each the prior plus the three messages of its edge other than the
+// face's own slot, which is not read) and Eq. 2 (check->variable) into msg_out.
+// msg_in == nullptr is the first iteration: every input is the prior l0.
 __global__ void __launch_bounds__(kBpThreads)
 k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__ s, float l0,
           TD q, const float* __restrict__ msg_in, float* __restrict__ msg_out)
 {
-    FaceWarp fw;
-    if (!face_warp(lat, n_groups, fw)) return;
+    SiteWarp sw;
+    if (!site_warp(lat, n_groups, sw)) return;
     const int lane = threadIdx.x & 31;
-    const uint64_t sw = s[((int64_t)fw.n * lat.L3 + fw.site) * W + (fw.g >> 1)];
-    const bool s_neg = (sw >> ((fw.g & 1) * 32 + lane)) & 1ULL;
-    const FaceEdges fe = face_edges(lat, fw.n, site_coord(lat, fw.site));
-    float x[4];
-    int64_t base[4];
+    const int64_t gbase = sw.g * (int64_t)lat.L3 * (3 * 4 * kLanes) + lane;
+    const int r = sw.site, rx = sw.nb[0], ry = sw.nb[1], rz = sw.nb[2];
+    // message blocks: edges at r (x, y, z) and the six neighbours used
+    const int oXr = msg_off(r, 0), oYr = msg_off(r, 1), oZr = msg_off(r, 2);
+    const int oXy = msg_off(ry, 0), oXz = msg_off(rz, 0);
+    const int oYx = msg_off(rx, 1), oYz = msg_off(rz, 1);
+    const int oZx = msg_off(rx, 2), oZy = msg_off(ry, 2);
+    // inputs x[face][edge] in face_edges order
+    float in0[4], in1[4], in2[4];
+    if (msg_in) {
+        const float* m = msg_in + gbase;
+#define MSG(o, k) m[(o) + (k) * kLanes]
+        const float xr0 = MSG(oXr, 0), xr1 = MSG(oXr, 1), xr2 = MSG(oXr, 2), xr3 = MSG(oXr, 3);
+        const float yr0 = MSG(oYr, 0), yr1 = MSG(oYr, 1), yr2 = MSG(oYr, 2), yr3 = MSG(oYr, 3);
+        const float zr0 = MSG(oZr, 0), zr1 = MSG(oZr, 1), zr2 = MSG(oZr, 2), zr3 = MSG(oZr, 3);
+        const float xs = l0 + xr1 + xr3, ys = l0 + yr1 + yr3, zs = l0 + zr1 + zr3;
+        // face 0: (y,r) excl 2, (y,r+z) excl 3, (z,r) excl 2, (z,r+y) excl 3
+        in0[0] = ys + yr0;
+        in0[1] = l0 + MSG(oYz, 0) + MSG(oYz, 1) + MSG(oYz, 2);
+        in0[2] = zs + zr0;
+        in0[3] = l0 + MSG(oZy, 0) + MSG(oZy, 1) + MSG(oZy, 2);
+        // face 1: (x,r) excl 2, (x,r+z) excl 3, (z,r) excl 0, (z,r+x) excl 1
+        in1[0] = xs + xr0;
+        in1[1] = l0 + MSG(oXz, 0) + MSG(oXz, 1) + MSG(oXz, 2);
+        in1[2] = zs + zr2;
+        in1[3] = l0 + MSG(oZx, 0) + MSG(oZx, 2) + MSG(oZx, 3);
+        // face 2: (x,r) excl 0, (x,r+y) excl 1, (y,r) excl 0, (y,r+x) excl 1
+        in2[0] = xs + xr2;
+        in2[1] = l0 + MSG(oXy, 0) + MSG(oXy, 2) + MSG(oXy, 3);
+        in2[2] = ys + yr2;
+        in2[3] = l0 + MSG(oYx, 0) + MSG(oYx, 2) + MSG(oYx, 3);
+#undef MSG
+    } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        base[j] = edge_block(lat, fw.g, fe.site[j], fe.dir[j]) + lane;
-        float acc = l0;
-        if (msg_in) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k != fe.slot[j]) acc += msg_in[base[j] + k * kLanes];
-        }
-        x[j] = acc;
+        for (int j = 0; j < 4; ++j) in0[j] = in1[j] = in2[j] = l0;
     }
     float y[4];
-    check_node(x, s_neg, q, y);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) msg_out[base[j] + fe.slot[j] * kLanes] = y[j];
+    float* o = msg_out + gbase;
+    check_node(in0, syndrome_bit(s, lat, W, 0, r, sw.g, lane), q, y);
+    o[oYr + 2 * kLanes] = y[0];
+    o[oYz + 3 * kLanes] = y[1];
+    o[oZr + 2 * kLanes] = y[2];
+    o[oZy + 3 * kLanes] = y[3];
+    check_node(in1, syndrome_bit(s, lat, W, 1, r, sw.g, lane), q, y);
+    o[oXr + 2 * kLanes] = y[0];
+    o[oXz + 3 * kLanes] = y[1];
+    o[oZr + 0 * kLanes] = y[2];
+    o[oZx + 1 * kLanes] = y[3];
+    check_node(in2, syndrome_bit(s, lat, W, 2, r, sw.g, lane), q, y);
+    o[oXr + 0 * kLanes] = y[0];
+    o[oXy + 1 * kLanes] = y[1];
+    o[oYr + 0 * kLanes] = y[2];
+    o[oYx + 1 * kLanes] = y[3];
 }
 
-// Eq. 4 posterior and the hard decision: every edge with l < 0 is corrected.
-// The warp of face f XORs the parity of its edges' decisions into s_f and
-// applies the decision of the edge it owns to e (each 32-sample half of a
-// 64-bit word is written by exactly one warp).
+// Eq. 4 posterior and the hard decision for the three edges at a site (the
+// edges this site's faces own): l = l0 + the four incoming messages, d = [l < 0].
+// The warp XORs d into e at r and, for each face at r, the parity of its four
+// edges' decisions into s (each 32-sample half word has exactly one writer).
 __global__ void __launch_bounds__(kBpThreads)
 k_bp_decide(Lattice lat, int64_t n_groups, int64_t W, int64_t n_samples, float l0,
             const float* __restrict__ msg, uint32_t* __restrict__ e32, uint32_t* __restrict__ s32,
             float* __restrict__ llr_out)
 {
-    FaceWarp fw;
-    if (!face_warp(lat, n_groups, fw)) return;
+    SiteWarp sw;
+    if (!site_warp(lat, n_groups, sw)) return;
     const int lane = threadIdx.x & 31;
-    const int64_t sample = fw.g * kLanes + lane;
+    const int64_t sample = sw.g * kLanes + lane;
     const bool valid = sample < n_samples;
-    const FaceEdges fe = face_edges(lat, fw.n, site_coord(lat, fw.site));
-    const int own = owned_edge_slot(fw.n);
-    unsigned par = 0, own_bits = 0;
-    float own_l = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    const int64_t gbase = sw.g * (int64_t)lat.L3 * (3 * 4 * kLanes) + lane;
+    auto post = [&](int site, int d) {
         float l = l0;
         if (msg) {
-            const int64_t b = edge_block(lat, fw.g, fe.site[j], fe.dir[j]) + lane;
+            const float* m = msg + gbase + msg_off(site, d);
+            l += m[0];
+            l += m[kLanes];
+            l += m[2 * kLanes];
+            l += m[3 * kLanes];
+        }
+        return l;
+    };
+    const int r = sw.site;
+    float lr[3];
+    unsigned dr[3];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) l += msg[b + k * kLanes];
-        }
-        unsigned bits = __ballot_sync(0xffffffffu, valid && l < 0.0f);
-        par ^= bits;
-        if (j == own) {
-            own_bits = bits;
-            own_l = l;
-        }
+    for (int d = 0; d < 3; ++d) {
+        lr[d] = post(r, d);
+        dr[d] = __ballot_sync(0xffffffffu, valid && lr[d] < 0.0f);
     }
-    const int64_t half = 2 * (fw.g >> 1) + (fw.g & 1);
-    if (lane == 0) {
-        const int64_t f = (int64_t)fw.n * lat.L3 + fw.site;
-        const int64_t v = (int64_t)fe.dir[own] * lat.L3 + fe.site[own];
-        if (par) s32[2 * f * W + half] ^= par;
-        if (own_bits) e32[2 * v * W + half] ^= own_bits;
+    const unsigned dXy = __ballot_sync(0xffffffffu, valid && post(sw.nb[1], 0) < 0.0f);
+    const unsigned dXz = __ballot_sync(0xffffffffu, valid && post(sw.nb[2], 0) < 0.0f);
+    const unsigned dYx = __ballot_sync(0xffffffffu, valid && post(sw.nb[0], 1) < 0.0f);
+    const unsigned dYz = __ballot_sync(0xffffffffu, valid && post(sw.nb[2], 1) < 0.0f);
+    const unsigned dZx = __ballot_sync(0xffffffffu, valid && post(sw.nb[0], 2) < 0.0f);
+    const unsigned dZy = __ballot_sync(0xffffffffu, valid && post(sw.nb[1], 2) < 0.0f);
+    const unsigned par[3] = {dr[1] ^ dYz ^ dr[2] ^ dZy, dr[0] ^ dXz ^ dr[2] ^ dZx,
+                             dr[0] ^ dXy ^ dr[1] ^ dYx};
+    const int64_t half = 2 * (sw.g >> 1) + (sw.g & 1);
+    if (lane < 3) {
+        const int64_t idx = 2 * ((int64_t)lane * lat.L3 + r) * W + half;
+        if (par[lane]) s32[idx] ^= par[lane];
+        if (dr[lane]) e32[idx] ^= dr[lane];
     }
     if (llr_out && valid) {
-        const int64_t v = (int64_t)fe.dir[own] * lat.L3 + fe.site[own];
-        llr_out[v * n_samples + sample] = own_l;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) llr_out[((int64_t)d * lat.L3 + r) * n_samples + sample] = lr[d];
     }
 }
 
@@ -249,9 +306,9 @@ int64_t group_floats(int L) { return 3LL * L * L * L * 4 * kLanes; }
 
 dim3 face_grid(int L, int64_t n_groups)
 {
-    const int64_t faces = 3LL * L * L * L;
+    const int64_t sites = (int64_t)L * L * L;
     const int warps_per_block = kBpThreads / 32;
-    return dim3((unsigned)((faces + warps_per_block - 1) / warps_per_block),
+    return dim3((unsigned)((sites + warps_per_block - 1) / warps_per_block),
                 (unsigned)std::min<int64_t>(n_groups, 65535), (unsigned)((n_groups + 65534) / 65535));
 }
 
@@ -330,6 +387,7 @@ extern "C" size_t toric3d_bp_workspace_bytes(int L, int64_t chunk_samples)
 static t3d_status bp_common_checks(int L, int64_t n_samples, double p, double q_meas)
 {
     T3D_TRY(check_lattice(L));
+    T3D_REQUIRE(L <= kMaxBpL, "BP supports L <= %d (L=%d)", kMaxBpL, L);
     T3D_REQUIRE(n_samples >= 1 && words_for(n_samples) <= (1LL << 40), "n_samples out of range");
     T3D_REQUIRE(p > 0.0 && p < 1.0, "BP needs 0 < p < 1 (p=%g)", p);
     T3D_REQUIRE(q_meas >= 0.0 && q_meas < 0.5, "BP needs 0 <= q_meas < 0.5 (q=%g)", q_meas);
