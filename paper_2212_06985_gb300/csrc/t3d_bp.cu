@@ -76,14 +76,15 @@ __device__ __forceinline__ TD td_of(float x)
     const float E = ex2_approx(-a * kLog2e);
     const float r = rcp_approx(1.0f + E);
     float om = 1.0f - E;
-    if (a < 0.5f) {
+    // warp-uniform test: the series costs nothing in warps without a small input
+    if (__any_sync(0xffffffffu, a < 0.5f)) {
         float h = fmaf(a, 1.0f / 5040.0f, -1.0f / 720.0f);
         h = fmaf(a, h, 1.0f / 120.0f);
         h = fmaf(a, h, -1.0f / 24.0f);
         h = fmaf(a, h, 1.0f / 6.0f);
         h = fmaf(a, h, -0.5f);
         h = fmaf(a, h, 1.0f);
-        om = a * h;
+        if (a < 0.5f) om = a * h;
     }
     return TD{om * r, (E + E) * r};
 }
@@ -94,7 +95,10 @@ __device__ __forceinline__ TD td_of(float x)
 // cancellation.  D = 0 (underflow) gives +inf, which the clamp turns into 30.
 __device__ __forceinline__ float two_atanh(float P, float D)
 {
-    if (P < 0.3f) {
+    const bool small = P < 0.3f;
+    float y = 0.0f;
+    // both tests are warp-uniform so each branch runs only where some lane needs it
+    if (__any_sync(0xffffffffu, small)) {
         const float u = P * P;
         float h = fmaf(u, 1.0f / 13.0f, 1.0f / 11.0f);
         h = fmaf(u, h, 1.0f / 9.0f);
@@ -102,9 +106,13 @@ __device__ __forceinline__ float two_atanh(float P, float D)
         h = fmaf(u, h, 1.0f / 5.0f);
         h = fmaf(u, h, 1.0f / 3.0f);
         h = fmaf(u, h, 1.0f);
-        return 2.0f * P * h;
+        y = 2.0f * P * h;
     }
-    return kLn2 * lg2_approx((1.0f + P) * rcp_approx(D));
+    if (__any_sync(0xffffffffu, !small)) {
+        const float big = kLn2 * lg2_approx((1.0f + P) * rcp_approx(D));
+        if (!small) y = big;
+    }
+    return y;
 }
 
 // Eq. 2 for the four edges of one face: y[j] from the other three inputs and
@@ -162,24 +170,43 @@ __device__ __forceinline__ bool site_warp(const Lattice& lat, int64_t n_groups, 
 // Offset of edge (d, site)'s 4x32 message block within a group.
 __device__ __forceinline__ int msg_off(int site, int d) { return (site * 3 + d) * (4 * kLanes); }
 
-__device__ __forceinline__ bool syndrome_bit(const uint64_t* s, const Lattice& lat, int64_t W,
-                                             int n, int site, int64_t g, int lane)
+// The 32-sample half word of face (n, site)'s syndrome for group g.
+__device__ __forceinline__ uint32_t syndrome_half(const uint64_t* s, const Lattice& lat, int64_t W,
+                                                  int n, int site, int64_t g)
 {
     const uint64_t w = s[((int64_t)n * lat.L3 + site) * W + (g >> 1)];
-    return (w >> ((g & 1) * 32 + lane)) & 1ULL;
+    return (uint32_t)(w >> ((g & 1) * 32));
 }
+
+// Where an iteration takes the syndrome from: the caller's bit-sliced words
+// (kSynWords), the same and also a per-group copy for later iterations
+// (kSynWordsSave: uint4 per site and group, faces 0..2 in .x .y .z), or that
+// copy (kSynSaved), which puts the three faces' bits in one 16-byte load.
+enum SynMode { kSynWords = 0, kSynWordsSave = 1, kSynSaved = 2 };
 
 // One flooding iteration for the three faces of a site: Eq. 3 (variable->check
 // inputs, each the prior plus the three messages of its edge other than the
 // face's own slot, which is not read) and Eq. 2 (check->variable) into msg_out.
 // msg_in == nullptr is the first iteration: every input is the prior l0.
+template <int kSyn>
 __global__ void __launch_bounds__(kBpThreads)
-k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__ s, float l0,
-          TD q, const float* __restrict__ msg_in, float* __restrict__ msg_out)
+k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__ s,
+          uint4* __restrict__ syn, float l0, TD q, const float* __restrict__ msg_in,
+          float* __restrict__ msg_out)
 {
     SiteWarp sw;
     if (!site_warp(lat, n_groups, sw)) return;
     const int lane = threadIdx.x & 31;
+    uint4 sh;
+    if (kSyn == kSynSaved) {
+        sh = syn[sw.g * lat.L3 + sw.site];
+    } else {
+        sh.x = syndrome_half(s, lat, W, 0, sw.site, sw.g);
+        sh.y = syndrome_half(s, lat, W, 1, sw.site, sw.g);
+        sh.z = syndrome_half(s, lat, W, 2, sw.site, sw.g);
+        sh.w = 0;
+        if (kSyn == kSynWordsSave && lane == 0) syn[sw.g * lat.L3 + sw.site] = sh;
+    }
     const int64_t gbase = sw.g * (int64_t)lat.L3 * (3 * 4 * kLanes) + lane;
     const int r = sw.site, rx = sw.nb[0], ry = sw.nb[1], rz = sw.nb[2];
     // message blocks: edges at r (x, y, z) and the six neighbours used
@@ -218,21 +245,24 @@ k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__
     }
     float y[4];
     float* o = msg_out + gbase;
-    check_node(in0, syndrome_bit(s, lat, W, 0, r, sw.g, lane), q, y);
-    o[oYr + 2 * kLanes] = y[0];
-    o[oYz + 3 * kLanes] = y[1];
-    o[oZr + 2 * kLanes] = y[2];
-    o[oZy + 3 * kLanes] = y[3];
-    check_node(in1, syndrome_bit(s, lat, W, 1, r, sw.g, lane), q, y);
-    o[oXr + 2 * kLanes] = y[0];
-    o[oXz + 3 * kLanes] = y[1];
-    o[oZr + 0 * kLanes] = y[2];
-    o[oZx + 1 * kLanes] = y[3];
-    check_node(in2, syndrome_bit(s, lat, W, 2, r, sw.g, lane), q, y);
-    o[oXr + 0 * kLanes] = y[0];
-    o[oXy + 1 * kLanes] = y[1];
-    o[oYr + 0 * kLanes] = y[2];
-    o[oYx + 1 * kLanes] = y[3];
+    // the new messages are not read again in this launch: store them evict-first
+#define PUT(off, v) __stcs(o + (off), (v))
+    check_node(in0, (sh.x >> lane) & 1u, q, y);
+    PUT(oYr + 2 * kLanes, y[0]);
+    PUT(oYz + 3 * kLanes, y[1]);
+    PUT(oZr + 2 * kLanes, y[2]);
+    PUT(oZy + 3 * kLanes, y[3]);
+    check_node(in1, (sh.y >> lane) & 1u, q, y);
+    PUT(oXr + 2 * kLanes, y[0]);
+    PUT(oXz + 3 * kLanes, y[1]);
+    PUT(oZr + 0 * kLanes, y[2]);
+    PUT(oZx + 1 * kLanes, y[3]);
+    check_node(in2, (sh.z >> lane) & 1u, q, y);
+    PUT(oXr + 0 * kLanes, y[0]);
+    PUT(oXy + 1 * kLanes, y[1]);
+    PUT(oYr + 0 * kLanes, y[2]);
+    PUT(oYx + 1 * kLanes, y[3]);
+#undef PUT
 }
 
 // Eq. 4 posterior and the hard decision for the three edges at a site (the
@@ -303,6 +333,7 @@ TD meas_pair(double q_meas)
 float prior(double p) { return (float)std::log((1.0 - p) / p); }
 
 int64_t group_floats(int L) { return 3LL * L * L * L * 4 * kLanes; }
+int64_t group_syn(int L) { return (int64_t)L * L * L; }  // uint4 per site
 
 dim3 face_grid(int L, int64_t n_groups)
 {
@@ -312,13 +343,21 @@ dim3 face_grid(int L, int64_t n_groups)
                 (unsigned)std::min<int64_t>(n_groups, 65535), (unsigned)((n_groups + 65534) / 65535));
 }
 
-t3d_status launch_step(int L, int64_t n_groups, int64_t W, const uint64_t* s, double p, double q_meas,
-                       const float* in, float* out, cudaStream_t st)
+t3d_status launch_step(int L, int64_t n_groups, int64_t W, const uint64_t* s, uint4* syn, int mode,
+                       double p, double q_meas, const float* in, float* out, cudaStream_t st)
 {
     Lattice lat = make_lattice(L);
     ProfScope prof(T3D_K_BP_STEP, st);
-    k_bp_step<<<face_grid(L, n_groups), kBpThreads, 0, st>>>(
-        lat, n_groups, W, s, prior(p), meas_pair(q_meas), in, out);
+    const dim3 grid = face_grid(L, n_groups);
+    if (mode == kSynWordsSave)
+        k_bp_step<kSynWordsSave><<<grid, kBpThreads, 0, st>>>(lat, n_groups, W, s, syn, prior(p),
+                                                              meas_pair(q_meas), in, out);
+    else if (mode == kSynSaved)
+        k_bp_step<kSynSaved><<<grid, kBpThreads, 0, st>>>(lat, n_groups, W, s, syn, prior(p),
+                                                          meas_pair(q_meas), in, out);
+    else
+        k_bp_step<kSynWords><<<grid, kBpThreads, 0, st>>>(lat, n_groups, W, s, syn, prior(p),
+                                                          meas_pair(q_meas), in, out);
     T3D_LAUNCH_CHECK("bp step");
     return T3D_OK;
 }
@@ -337,7 +376,13 @@ t3d_status launch_decide(int L, int64_t n_groups, int64_t W, int64_t n_samples, 
 
 }  // namespace
 
-// Chunks of chunk_groups groups; buf holds two chunk-sized message buffers.
+size_t bp_bytes_per_group(int L)
+{
+    return 2 * (size_t)group_floats(L) * sizeof(float) + (size_t)group_syn(L) * sizeof(uint4);
+}
+
+// Chunks of chunk_groups groups; buf holds two chunk-sized message buffers
+// followed by the chunk's saved syndrome words.
 // The s/e words of chunk c start at group c*chunk_groups, so the kernels see
 // the chunk's slice of the arrays through offset pointers and a local group
 // count (groups are aligned to 64-sample words when chunk_groups is even).
@@ -348,6 +393,7 @@ t3d_status launch_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double 
     const int64_t W = words_for(n_samples);
     float* A = buf;
     float* B = buf + chunk_groups * group_floats(L);
+    uint4* syn = reinterpret_cast<uint4*>(buf + 2 * chunk_groups * group_floats(L));
     for (int64_t g0 = 0; g0 < G; g0 += chunk_groups) {
         const int64_t gc = std::min(chunk_groups, G - g0);
         // the chunk's words begin at word g0/2 (g0 is even: chunk_groups is even or g0 == 0)
@@ -355,7 +401,8 @@ t3d_status launch_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double 
         const uint64_t* s_chunk = s + w0;
         const float* last = nullptr;
         for (int it = 0; it < iters; ++it) {
-            T3D_TRY(launch_step(L, gc, W, s_chunk, p, q_meas, last, A, st));
+            T3D_TRY(launch_step(L, gc, W, s_chunk, syn, it == 0 ? kSynWordsSave : kSynSaved, p, q_meas,
+                                last, A, st));
             last = A;
             std::swap(A, B);
         }
@@ -381,7 +428,7 @@ extern "C" size_t toric3d_bp_workspace_bytes(int L, int64_t chunk_samples)
     if (L < 2 || L > kMaxL || chunk_samples < 1) return 0;
     int64_t g = groups_for(chunk_samples);
     g += g & 1;  // chunks hold whole 64-sample words
-    return 2 * (size_t)g * (size_t)group_floats(L) * sizeof(float);
+    return (size_t)g * bp_bytes_per_group(L);
 }
 
 static t3d_status bp_common_checks(int L, int64_t n_samples, double p, double q_meas)
@@ -404,8 +451,8 @@ extern "C" t3d_status toric3d_bp_step(int L, int64_t n_samples, const uint64_t* 
     T3D_REQUIRE(msg_out != nullptr && aligned(msg_out, 16), "msg_out must be 16-byte aligned");
     T3D_REQUIRE(msg_in == nullptr || aligned(msg_in, 16), "msg_in must be 16-byte aligned");
     T3D_REQUIRE(msg_in != msg_out, "msg_in and msg_out must differ");
-    return launch_step(L, groups_for(n_samples), words_for(n_samples), s, p, q_meas, msg_in, msg_out,
-                       as_stream(stream));
+    return launch_step(L, groups_for(n_samples), words_for(n_samples), s, nullptr, kSynWords, p, q_meas,
+                       msg_in, msg_out, as_stream(stream));
 }
 
 extern "C" t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* msg, double p,
@@ -432,8 +479,7 @@ extern "C" t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t
     T3D_TRY(check_words(s, "s"));
     T3D_REQUIRE(iters >= 0, "iters must be >= 0");
     T3D_REQUIRE(work != nullptr && aligned(work, 16), "work must be a 16-byte aligned device pointer");
-    const size_t per_pair = 2 * (size_t)group_floats(L) * sizeof(float);
-    int64_t chunk = (int64_t)(work_bytes / per_pair);
+    int64_t chunk = (int64_t)(work_bytes / bp_bytes_per_group(L));
     const int64_t G = groups_for(n_samples);
     if (chunk < G) chunk &= ~1LL;  // partial chunks must cover whole 64-sample words
     T3D_REQUIRE(chunk >= 1, "workspace too small: %zu bytes, need at least %zu", work_bytes,

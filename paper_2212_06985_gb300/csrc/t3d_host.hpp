@@ -90,6 +90,8 @@ t3d_status launch_sweeps(int L, int64_t words, uint64_t* e, uint64_t* s, uint64_
                          uint64_t seed, uint64_t group0, uint32_t cycle, cudaStream_t st);
 t3d_status launch_logical(int L, int64_t n_samples, const uint64_t* e, uint8_t* mask,
                           int64_t* counts8, cudaStream_t st);
+// Bytes of BP workspace per 32-sample group (two message buffers + syndrome copy).
+size_t bp_bytes_per_group(int L);
 t3d_status launch_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p,
                      double q_meas, int iters, float* buf, int64_t chunk_groups,
                      float* llr_out, cudaStream_t st);

@@ -23,7 +23,6 @@ size_t state_bytes(const t3d_run_cfg& c)
     return (size_t)3 * c.L * c.L * c.L * (size_t)words_for(c.n_samples) * sizeof(uint64_t);
 }
 
-size_t bp_group_bytes(int L) { return (size_t)3 * L * L * L * 4 * 32 * sizeof(float); }
 
 struct Plan {
     uint64_t* s;
@@ -68,7 +67,7 @@ t3d_status plan_workspace(const t3d_run_cfg& c, void* work, size_t work_bytes, P
     pl.chunk_groups = 0;
     if (c.use_bp && c.bp_iters > 0) {
         const int64_t G = groups_for(c.n_samples);
-        int64_t chunk = (int64_t)((work_bytes - 2 * sb) / (2 * bp_group_bytes(c.L)));
+        int64_t chunk = (int64_t)((work_bytes - 2 * sb) / bp_bytes_per_group(c.L));
         if (c.bp_chunk_samples > 0) chunk = std::min(chunk, groups_for(c.bp_chunk_samples));
         if (chunk < G) chunk &= ~1LL;
         T3D_REQUIRE(chunk >= 1, "workspace too small for one BP chunk");
@@ -201,7 +200,7 @@ extern "C" size_t toric3d_run_workspace_bytes(const t3d_run_cfg* cfg)
                                               : cfg->n_samples;
         int64_t g = groups_for(n);
         if (g < groups_for(cfg->n_samples)) g += g & 1;
-        total += 2 * (size_t)g * bp_group_bytes(cfg->L);
+        total += (size_t)g * bp_bytes_per_group(cfg->L);
     }
     return total;
 }
