@@ -33,6 +33,11 @@ sys.path.insert(0, ROOT)
 import toric3d_inputs as inp  # noqa: E402
 
 METRIC = "qubit-cycles decoded/s at L=32 p=4%: BP+p-flip"
+
+# DRAM bytes (read + write) per launch of the dominant kernel from an ncu
+# capture of the current kernel, scaled to a full launch by the units
+# processed (profiles/ has the capture); None until one exists.
+TRAFFIC = {}
 UNIT = "qubit-cycles/s"
 
 
@@ -48,11 +53,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
 def workload_config(w, S):
-    return {"workload": w.name, "L": w.L, "qubits": inp.n_bits(w.L), "p": w.p, "q": w.q,
+    return {"workload": w.name, "L": list(w.sizes), "qubits": sum(inp.n_bits(L) for L in w.sizes),
+            "p": w.p, "q": w.q,
             "decoder": w.decoder, "bp_iters": w.bp_iters, "bp_meas_nodes": w.bp_meas_nodes,
             "schedule": w.schedule, "n_apply": w.n_apply, "samples_per_gpu": S,
             "cycles_per_step": 1, "T": w.T, "seed": w.seed,
@@ -74,27 +81,31 @@ def oracle_kwargs(w):
 
 
 def time_oracle(w, budget_s, cycle0=0):
-    """Time the oracle on one code cycle of a bounded number of samples, one
-    process per host core (spawned, so no CUDA state is inherited)."""
+    """Time the oracle on one code cycle of a bounded number of samples of every
+    lattice size of the workload, one process per host core (spawned, so no
+    CUDA state is inherited)."""
     import multiprocessing as mp
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    cfg = oracle.make_cfg(w.L, 1, w.p, w.q, w.seed, **oracle_kwargs(w))
-    t0 = time.perf_counter()
-    oracle.run_batch(cfg, 0, 1)
-    one = max(time.perf_counter() - t0, 1e-4)
-    per_core = max(1, int(budget_s / one))
+    jobs, per_size = [], {}
+    for L in w.sizes:
+        cfg = oracle.make_cfg(L, 1, w.p, w.q, w.seed, **oracle_kwargs(w))
+        t0 = time.perf_counter()
+        oracle.run_batch(cfg, 0, 1)
+        one = max(time.perf_counter() - t0, 1e-4)
+        per_core = max(1, int(budget_s / len(w.sizes) / one))
+        per_size[L] = per_core * cores
+        jobs += [(L, w.p, w.q, w.seed, oracle_kwargs(w), 64 * 1024 * i, per_core, cycle0) for i in range(cores)]
     ctx = mp.get_context("spawn")
-    jobs = [(w.L, w.p, w.q, w.seed, oracle_kwargs(w), 64 * 1024 * i, per_core, cycle0) for i in range(cores)]
     with ctx.Pool(cores) as pool:
         t0 = time.perf_counter()
-        done = sum(pool.map(_oracle_worker, jobs))
+        pool.map(_oracle_worker, jobs)
         dt = time.perf_counter() - t0
-    value = inp.n_bits(w.L) * done / dt
+    value = sum(inp.n_bits(L) * k for L, k in per_size.items()) / dt
+    sample = ", ".join(f"{k} samples at L={L}" for L, k in per_size.items())
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} samples x 1 code cycle at L={w.L} ({per_core} per process, {cores} processes)",
-            "seconds": dt}
+            "sample": f"{sample}, 1 code cycle each, {cores} processes", "seconds": dt}
 
 
 def reference_arm(args):
@@ -197,25 +208,31 @@ def cuda_arm(args):
     w = inp.WORKLOADS[args.workload]
     S = args.samples or w.n_samples
     sample0 = t3d.replica_sample0(rank, S)
-    L = w.L
-    n = inp.n_bits(L)
+    sizes = w.sizes
     W = inp.words_for(S)
     kw = dict(use_bp=w.decoder.startswith("bp"), bp_iters=w.bp_iters, bp_meas_nodes=w.bp_meas_nodes,
               schedule=w.schedule, n_apply=w.n_apply)
     chunk = min(S, 25024)
-    cfg = t3d.make_run_cfg(L, 1, w.p, w.q, w.seed, S, sample0=sample0, bp_chunk_samples=chunk, **kw)
+    cfg = t3d.make_run_cfg(w.L, 1, w.p, w.q, w.seed, S, sample0=sample0, bp_chunk_samples=chunk, **kw)
     stream = torch.cuda.Stream(device=dev)
-    e = torch.zeros((n, W), dtype=torch.int64, device=dev)
-    work = torch.empty(t3d.toric3d_run_workspace_bytes(cfg), dtype=torch.uint8, device=dev)
-    mask = torch.zeros(S, dtype=torch.uint8, device=dev)
-    counts = torch.zeros(8, dtype=torch.int64, device=dev)
+    states = [torch.zeros((inp.n_bits(L), W), dtype=torch.int64, device=dev) for L in sizes]
+    masks = [torch.zeros(S, dtype=torch.uint8, device=dev) for _ in sizes]
+    counts = [torch.zeros(8, dtype=torch.int64, device=dev) for _ in sizes]
+    batch = t3d.make_batch([dict(L=L, n_samples=S, sample0=sample0, e=e, mask=m, counts8=c)
+                            for L, e, m, c in zip(sizes, states, masks, counts)])
+    work = torch.empty(t3d.toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
+    qubits = sum(inp.n_bits(L) for L in sizes)
     torch.cuda.synchronize()
 
     def step(t):
         cfg.cycle0 = t
-        t3d.toric3d_run_cycles(cfg, e, work, mask, counts, stream=stream)
+        t3d.toric3d_run_batch(cfg, batch, work, stream=stream)
 
+    tuned = None
     with torch.cuda.stream(stream):
+        if kw["use_bp"] and not args.no_autotune:
+            cap, ms_it = t3d.toric3d_autotune_batch(cfg, batch, work, stream=stream)
+            tuned = {"bp_step_blocks_per_sm": cap, "bp_step_ms": ms_it}
         for t in range(args.warmup):
             step(t)
     stream.synchronize()
@@ -247,56 +264,61 @@ def cuda_arm(args):
     if world > 1:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
     ms = float(t_max.item())
-    total_qc = n * S * world * args.steps
+    total_qc = qubits * S * world * args.steps
     value = total_qc / (ms / 1e3)
 
     # dominant kernel: BP iteration (algorithmic bytes per edge-sample: 16 B read + 16 B written;
     # the first iteration of each chunk reads nothing)
     bp_ms, bp_launches = prof["bp_step"]
-    chunks = math.ceil(S / chunk)
-    full_iters = (w.bp_iters - 1) * args.steps * chunks
-    first_iters = args.steps * chunks
-    alg_bytes = n * S * args.steps * (32.0 * (w.bp_iters - 1) + 16.0)
+    rounds = math.ceil(S / chunk)
+    alg_bytes = qubits * S * args.steps * (32.0 * (w.bp_iters - 1) + 16.0)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / (bp_ms / 1e3) / 1e9 if bp_ms > 0 else 0.0
     roofline = {"kernel": "k_bp_step", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s",
+                "frac": achieved / hbm_peak, "traffic": TRAFFIC.get(args.workload),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
                 "launches": bp_launches, "avg_launch_ms": bp_ms / max(bp_launches, 1),
                 "share_of_step": bp_ms / ms if ms else None,
-                "expected_launches": full_iters + first_iters}
+                "expected_launches": w.bp_iters * rounds * args.steps,
+                "algorithmic_bytes_per_launch": alg_bytes / max(bp_launches, 1)}
 
-    # end-to-end: the state round-trips through pinned host memory every step
+    # end-to-end: the error states round-trip through pinned host memory every step
     e2e = None
     if not args.no_e2e:
-        e_host = torch.empty((n, W), dtype=torch.int64, pin_memory=True)
-        e_host.copy_(e)
-        mask_host = torch.empty(S, dtype=torch.uint8, pin_memory=True)
-        counts_host = torch.empty(8, dtype=torch.int64, pin_memory=True)
+        hosts = [torch.empty_like(e, device="cpu").pin_memory() for e in states]
+        for h, e in zip(hosts, states):
+            h.copy_(e)
+        mask_host = [torch.empty(S, dtype=torch.uint8, pin_memory=True) for _ in sizes]
+        counts_host = [torch.empty(8, dtype=torch.int64, pin_memory=True) for _ in sizes]
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for i in range(args.e2e_steps):
-                e.copy_(e_host, non_blocking=True)
+                for h, e in zip(hosts, states):
+                    e.copy_(h, non_blocking=True)
                 step(args.warmup + args.steps + i)
-                e_host.copy_(e, non_blocking=True)
-                mask_host.copy_(mask, non_blocking=True)
-                counts_host.copy_(counts, non_blocking=True)
+                for h, e in zip(hosts, states):
+                    h.copy_(e, non_blocking=True)
+                for mh, m in zip(mask_host, masks):
+                    mh.copy_(m, non_blocking=True)
+                for ch, c in zip(counts_host, counts):
+                    ch.copy_(c, non_blocking=True)
         stream.synchronize()
         dt = time.perf_counter() - t0
         dt_t = torch.tensor([dt], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
         dt = float(dt_t.item())
-        e2e = {"value": n * S * world * args.e2e_steps / dt, "unit": UNIT,
-               "h2d_bytes_per_step": n * W * 8, "d2h_bytes_per_step": n * W * 8 + S + 64,
+        state_bytes = sum(e.numel() * 8 for e in states)
+        e2e = {"value": qubits * S * world * args.e2e_steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes + len(sizes) * (S + 64),
                "steps": args.e2e_steps,
-               "note": "error state uploaded from and downloaded to pinned host memory every step"}
+               "note": "error states uploaded from and downloaded to pinned host memory every step"}
 
-    fail_counts = counts.cpu().tolist()
+    fail_counts = [c.cpu().tolist() for c in counts]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(w, args.cpu_seconds)
@@ -312,7 +334,7 @@ def cuda_arm(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "kernels_ms": {k: v[0] for k, v in prof.items() if v[1]},
                 "kernels_launches": {k: v[1] for k, v in prof.items() if v[1]},
-                "clocks": clk, "last_cycle_logical_counts": fail_counts}
+                "clocks": clk, "autotune": tuned, "last_cycle_logical_counts": fail_counts}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

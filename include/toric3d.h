@@ -226,6 +226,47 @@ t3d_status toric3d_run_cycles(const t3d_run_cfg* cfg, uint64_t* e, void* work, s
                               uint8_t* mask, int64_t* counts8, t3d_stream stream);
 
 /*
+ * Batched runs over lattices of different sizes (measurement support for the
+ * paper's multi-size threshold plots, Fig. 2, 6, 7).  Up to 8 independent
+ * ensembles, each with its own L, sample range and state, advance through the
+ * same cycles with the decoder settings of `cfg` (its L, n_samples and sample0
+ * are ignored); every step is one persistent launch over all ensembles.  e,
+ * mask and counts8 of each item are as for toric3d_run_cycles.  BP chunks are
+ * sized per item so the workspace holds one chunk of every item (rounds are
+ * added until it does).
+ */
+typedef struct {
+    int32_t L;
+    int64_t n_samples;
+    uint64_t sample0;          /* multiple of 64 */
+    uint64_t* e;               /* device, uint64_t[3L^3][ceil(n_samples/64)], in/out */
+    uint8_t* mask;             /* device, uint8_t[n_samples], nullable */
+    int64_t* counts8;          /* device, int64_t[8], nullable */
+} t3d_batch_item;
+
+size_t toric3d_run_batch_workspace_bytes(const t3d_run_cfg* cfg, const t3d_batch_item* items,
+                                         int n_items);
+t3d_status toric3d_run_batch(const t3d_run_cfg* cfg, const t3d_batch_item* items, int n_items,
+                             void* work, size_t work_bytes, t3d_stream stream);
+
+/*
+ * Launch tuning (not in the paper).  Every run kernel is a persistent
+ * grid-stride kernel of SMs x resident blocks; a positive cap limits the
+ * resident blocks per SM of one kernel kind (0 restores the occupancy limit).
+ * toric3d_autotune_batch() plans `work` exactly as toric3d_run_batch() would,
+ * measures one noisy syndrome of the items' states into it (e is only read),
+ * times the BP iteration on every item's first chunk under each cap and keeps
+ * the fastest for the process; it synchronises `stream`, so call it outside
+ * stream capture, before the runs it tunes.  The chosen cap and the time of
+ * one iteration are returned through the nullable out pointers.
+ */
+void toric3d_set_blocks_per_sm(int kind, int blocks_per_sm);
+int toric3d_get_blocks_per_sm(int kind);
+t3d_status toric3d_autotune_batch(const t3d_run_cfg* cfg, const t3d_batch_item* items, int n_items,
+                                  void* work, size_t work_bytes, int* bp_blocks_per_sm, float* bp_ms,
+                                  t3d_stream stream);
+
+/*
  * Kernel timing (not in the paper; measurement support).  While enabled, every
  * kernel the library enqueues outside a stream capture is bracketed by a pair
  * of CUDA events on its own stream.  toric3d_profile_read() waits for the

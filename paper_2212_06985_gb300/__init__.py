@@ -28,7 +28,9 @@ __all__ = [
     "toric3d_flip_workspace_bytes", "toric3d_bp_message_bytes",
     "toric3d_bp_workspace_bytes", "toric3d_run_workspace_bytes", "make_run_cfg",
     "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "KERNEL_KINDS",
-    "EXPORTED_SYMBOLS", "replica_sample0",
+    "EXPORTED_SYMBOLS", "replica_sample0", "BatchItem", "make_batch", "toric3d_run_batch",
+    "toric3d_run_batch_workspace_bytes", "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm",
+    "toric3d_autotune_batch",
 ]
 
 EXPORTED_SYMBOLS = [
@@ -36,7 +38,9 @@ EXPORTED_SYMBOLS = [
     "toric3d_flip_workspace_bytes", "toric3d_flip", "toric3d_pflip", "toric3d_bp_message_bytes",
     "toric3d_bp_step", "toric3d_bp_decide", "toric3d_bp_workspace_bytes", "toric3d_bp",
     "toric3d_logical", "toric3d_pack", "toric3d_unpack", "toric3d_run_workspace_bytes",
-    "toric3d_run_cycles", "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read",
+    "toric3d_run_cycles", "toric3d_run_batch_workspace_bytes", "toric3d_run_batch",
+    "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm", "toric3d_autotune_batch",
+    "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read",
 ]
 
 KERNEL_KINDS = {"noise": 0, "syndrome": 1, "flip": 2, "pflip": 3, "bp_step": 4, "bp_decide": 5,
@@ -72,6 +76,19 @@ class RunCfg(ctypes.Structure):
         ("cycle0", ctypes.c_uint32),
         ("use_graph", ctypes.c_int32),
         ("bp_chunk_samples", ctypes.c_int64),
+    ]
+
+
+class BatchItem(ctypes.Structure):
+    """Mirror of ``t3d_batch_item`` in include/toric3d.h."""
+
+    _fields_ = [
+        ("L", ctypes.c_int32),
+        ("n_samples", ctypes.c_int64),
+        ("sample0", ctypes.c_uint64),
+        ("e", ctypes.c_void_p),
+        ("mask", ctypes.c_void_p),
+        ("counts8", ctypes.c_void_p),
     ]
 
 
@@ -113,6 +130,12 @@ def _declare(h):
         "toric3d_unpack": (i32, [i64, i64, _P, _P, _P]),
         "toric3d_run_workspace_bytes": (sz, [ctypes.POINTER(RunCfg)]),
         "toric3d_run_cycles": (i32, [ctypes.POINTER(RunCfg), _P, _P, sz, _P, _P, _P]),
+        "toric3d_run_batch_workspace_bytes": (sz, [ctypes.POINTER(RunCfg), ctypes.POINTER(BatchItem), i32]),
+        "toric3d_run_batch": (i32, [ctypes.POINTER(RunCfg), ctypes.POINTER(BatchItem), i32, _P, sz, _P]),
+        "toric3d_set_blocks_per_sm": (None, [i32, i32]),
+        "toric3d_get_blocks_per_sm": (i32, [i32]),
+        "toric3d_autotune_batch": (i32, [ctypes.POINTER(RunCfg), ctypes.POINTER(BatchItem), i32, _P, sz,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), _P]),
         "toric3d_profile_enable": (None, [i32]),
         "toric3d_profile_reset": (None, []),
         "toric3d_profile_read": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
@@ -248,6 +271,60 @@ def toric3d_run_cycles(cfg: RunCfg, e, work, mask=None, counts8=None, stream=Non
     _check(lib().toric3d_run_cycles(ctypes.byref(cfg), _ptr(e), _ptr(work),
                                     work.numel() * work.element_size(), _ptr(mask), _ptr(counts8),
                                     _stream(stream)))
+
+
+# ------------------------------------------------------------------ batches of lattices
+def make_batch(items):
+    """items: iterable of dicts with L, n_samples, e (device int64 tensor) and
+    optional sample0, mask, counts8 -> ctypes array of BatchItem."""
+    items = list(items)
+    arr = (BatchItem * len(items))()
+    for a, it in zip(arr, items):
+        a.L, a.n_samples = it["L"], it["n_samples"]
+        a.sample0 = it.get("sample0", 0)
+        a.e = _ptr(it["e"])
+        a.mask = _ptr(it.get("mask"))
+        a.counts8 = _ptr(it.get("counts8"))
+    return arr
+
+
+def _as_batch(batch):
+    if isinstance(batch, ctypes.Array):
+        return batch
+    items = list(batch)
+    return (BatchItem * len(items))(*items)
+
+
+def toric3d_run_batch_workspace_bytes(cfg: RunCfg, batch) -> int:
+    batch = _as_batch(batch)
+    return int(lib().toric3d_run_batch_workspace_bytes(ctypes.byref(cfg), batch, len(batch)))
+
+
+def toric3d_run_batch(cfg: RunCfg, batch, work, stream=None):
+    batch = _as_batch(batch)
+    _check(lib().toric3d_run_batch(ctypes.byref(cfg), batch, len(batch), _ptr(work),
+                                   work.numel() * work.element_size(), _stream(stream)))
+
+
+def toric3d_set_blocks_per_sm(kind, blocks_per_sm: int):
+    k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+    lib().toric3d_set_blocks_per_sm(k, int(blocks_per_sm))
+
+
+def toric3d_get_blocks_per_sm(kind) -> int:
+    k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+    return int(lib().toric3d_get_blocks_per_sm(k))
+
+
+def toric3d_autotune_batch(cfg: RunCfg, batch, work, stream=None):
+    """Tune the BP iteration's blocks-per-SM cap; returns (cap, ms per iteration)."""
+    batch = _as_batch(batch)
+    cap = ctypes.c_int()
+    ms = ctypes.c_float()
+    _check(lib().toric3d_autotune_batch(ctypes.byref(cfg), batch, len(batch), _ptr(work),
+                                        work.numel() * work.element_size(), ctypes.byref(cap),
+                                        ctypes.byref(ms), _stream(stream)))
+    return cap.value, ms.value
 
 
 # ------------------------------------------------------------------ kernel timing

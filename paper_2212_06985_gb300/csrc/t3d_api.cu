@@ -47,6 +47,64 @@ t3d_status check_words(const void* p, const char* name)
     return T3D_OK;
 }
 
+// ------------------------------------------------------------ persistent grids
+namespace {
+
+struct GridEntry {
+    const void* kernel;
+    int threads;
+    int device;
+    int blocks_per_sm;
+};
+
+std::mutex g_grid_mutex;
+std::vector<GridEntry> g_grids;
+int g_sms[64] = {0};
+int g_tuned[T3D_K_COUNT] = {0};
+
+}  // namespace
+
+int tuned_blocks_per_sm(int kind)
+{
+    std::lock_guard<std::mutex> lock(g_grid_mutex);
+    return (kind >= 0 && kind < T3D_K_COUNT) ? g_tuned[kind] : 0;
+}
+
+void set_tuned_blocks_per_sm(int kind, int blocks_per_sm)
+{
+    std::lock_guard<std::mutex> lock(g_grid_mutex);
+    if (kind >= 0 && kind < T3D_K_COUNT) g_tuned[kind] = blocks_per_sm > 0 ? blocks_per_sm : 0;
+}
+
+unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_grid_mutex);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (g_sms[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        g_sms[dev] = n;
+    }
+    int per_sm = 0;
+    for (const auto& g : g_grids)
+        if (g.kernel == kernel && g.threads == threads && g.device == dev) per_sm = g.blocks_per_sm;
+    if (per_sm == 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n <= 0)
+            n = 1;
+        g_grids.push_back(GridEntry{kernel, threads, dev, n});
+        per_sm = n;
+    }
+    if (kind >= 0 && kind < T3D_K_COUNT && g_tuned[kind] > 0 && g_tuned[kind] < per_sm)
+        per_sm = g_tuned[kind];
+    int64_t grid = (int64_t)per_sm * g_sms[dev];
+    if (grid > blocks) grid = blocks;
+    if (grid < 1) grid = 1;
+    return (unsigned)grid;
+}
+
 // ------------------------------------------------------------ kernel timing
 namespace {
 
@@ -139,6 +197,13 @@ extern "C" t3d_status toric3d_profile_read(int kind, double* total_ms, int64_t* 
     *launches = n;
     return T3D_OK;
 }
+
+extern "C" void toric3d_set_blocks_per_sm(int kind, int blocks_per_sm)
+{
+    t3d::set_tuned_blocks_per_sm(kind, blocks_per_sm);
+}
+
+extern "C" int toric3d_get_blocks_per_sm(int kind) { return t3d::tuned_blocks_per_sm(kind); }
 
 extern "C" const char* toric3d_last_error(void) { return t3d::g_error; }
 

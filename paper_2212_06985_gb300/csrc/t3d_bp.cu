@@ -18,10 +18,12 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <utility>
 
 #include "t3d_device.cuh"
 #include "t3d_host.hpp"
+#include "t3d_items.cuh"
 
 namespace t3d {
 namespace {
@@ -69,23 +71,20 @@ constexpr float kLn2 = 0.6931471805599453f;
 // (tanh(|x|/2), 1 - tanh(|x|/2)) = ((1 - E), 2E) / (1 + E) with E = e^{-|x|}.
 // For |x| < 1/2 the difference 1 - E is taken from its Taylor series
 // sum_{k>=1} (-1)^{k+1} |x|^k / k! (through k = 7, truncation < 3e-7 relative)
-// instead of subtracting two nearly equal numbers.
+// instead of subtracting two nearly equal numbers.  Both forms are evaluated
+// and one selected, which is cheaper than branching per warp.
 __device__ __forceinline__ TD td_of(float x)
 {
     const float a = fabsf(x);
     const float E = ex2_approx(-a * kLog2e);
     const float r = rcp_approx(1.0f + E);
-    float om = 1.0f - E;
-    // warp-uniform test: the series costs nothing in warps without a small input
-    if (__any_sync(0xffffffffu, a < 0.5f)) {
-        float h = fmaf(a, 1.0f / 5040.0f, -1.0f / 720.0f);
-        h = fmaf(a, h, 1.0f / 120.0f);
-        h = fmaf(a, h, -1.0f / 24.0f);
-        h = fmaf(a, h, 1.0f / 6.0f);
-        h = fmaf(a, h, -0.5f);
-        h = fmaf(a, h, 1.0f);
-        if (a < 0.5f) om = a * h;
-    }
+    float h = fmaf(a, 1.0f / 5040.0f, -1.0f / 720.0f);
+    h = fmaf(a, h, 1.0f / 120.0f);
+    h = fmaf(a, h, -1.0f / 24.0f);
+    h = fmaf(a, h, 1.0f / 6.0f);
+    h = fmaf(a, h, -0.5f);
+    h = fmaf(a, h, 1.0f);
+    const float om = (a < 0.5f) ? a * h : 1.0f - E;
     return TD{om * r, (E + E) * r};
 }
 
@@ -95,36 +94,29 @@ __device__ __forceinline__ TD td_of(float x)
 // cancellation.  D = 0 (underflow) gives +inf, which the clamp turns into 30.
 __device__ __forceinline__ float two_atanh(float P, float D)
 {
-    const bool small = P < 0.3f;
-    float y = 0.0f;
-    // both tests are warp-uniform so each branch runs only where some lane needs it
-    if (__any_sync(0xffffffffu, small)) {
-        const float u = P * P;
-        float h = fmaf(u, 1.0f / 13.0f, 1.0f / 11.0f);
-        h = fmaf(u, h, 1.0f / 9.0f);
-        h = fmaf(u, h, 1.0f / 7.0f);
-        h = fmaf(u, h, 1.0f / 5.0f);
-        h = fmaf(u, h, 1.0f / 3.0f);
-        h = fmaf(u, h, 1.0f);
-        y = 2.0f * P * h;
-    }
-    if (__any_sync(0xffffffffu, !small)) {
-        const float big = kLn2 * lg2_approx((1.0f + P) * rcp_approx(D));
-        if (!small) y = big;
-    }
-    return y;
+    const float u = P * P;
+    float h = fmaf(u, 1.0f / 13.0f, 1.0f / 11.0f);
+    h = fmaf(u, h, 1.0f / 9.0f);
+    h = fmaf(u, h, 1.0f / 7.0f);
+    h = fmaf(u, h, 1.0f / 5.0f);
+    h = fmaf(u, h, 1.0f / 3.0f);
+    h = fmaf(u, h, 1.0f);
+    const float series = 2.0f * P * h;
+    const float logv = kLn2 * lg2_approx((1.0f + P) * rcp_approx(D));
+    return (P < 0.3f) ? series : logv;
 }
 
 // Eq. 2 for the four edges of one face: y[j] from the other three inputs and
-// the measurement-variable pair q.
+// the measurement-variable pair q.  The sign of y[j] is (-1)^{s_f} times the
+// product of the other inputs' signs: the XOR of their IEEE sign bits.
 __device__ __forceinline__ void check_node(const float x[4], bool s_neg, TD q, float y[4])
 {
     TD in[4];
-    unsigned neg = s_neg ? 1u : 0u;
+    uint32_t sgn_all = s_neg ? 0x80000000u : 0u;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         in[j] = td_of(x[j]);
-        neg ^= (x[j] < 0.0f) ? 1u : 0u;
+        sgn_all ^= __float_as_uint(x[j]);
     }
     const TD pre1 = td_mul(q, in[0]);
     const TD pre2 = td_mul(pre1, in[1]);
@@ -135,14 +127,14 @@ __device__ __forceinline__ void check_node(const float x[4], bool s_neg, TD q, f
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const float mag = fminf(two_atanh(o[j].t, o[j].d), kMsgClamp);
-        const unsigned sgn = neg ^ ((x[j] < 0.0f) ? 1u : 0u);
-        y[j] = sgn ? -mag : mag;
+        const uint32_t sgn = (sgn_all ^ __float_as_uint(x[j])) & 0x80000000u;
+        y[j] = __uint_as_float(__float_as_uint(mag) | sgn);
     }
 }
 
-// Grid: x covers the L^3 sites of a group, one warp per site handling the
-// three faces at that site (normals x, y, z); y (and z past 65535) is the
-// group.  With r the site and e_a the unit steps, the faces' edges and the
+// Work: per item, one warp per (site, group) of the current chunk handles the
+// three faces at that site (normals x, y, z); an item's local block lb covers
+// 8 consecutive sites of group lb / site_blocks, so sites vary fastest.  With r the site and e_a the unit steps, the faces' edges and the
 // slot each face occupies in its edges' face lists are (edge_faces order):
 //   face n=0: (y,r) slot 2, (y,r+e_z) slot 3, (z,r) slot 2, (z,r+e_y) slot 3
 //   face n=1: (x,r) slot 2, (x,r+e_z) slot 3, (z,r) slot 0, (z,r+e_x) slot 1
@@ -153,11 +145,16 @@ struct SiteWarp {
     int nb[3];  // site + e_x, site + e_y, site + e_z (periodic)
 };
 
-__device__ __forceinline__ bool site_warp(const Lattice& lat, int64_t n_groups, SiteWarp& sw)
+constexpr int kWarpsPerBlock = kBpThreads / 32;
+
+__host__ __device__ __forceinline__ int64_t site_blocks(int L3) { return (L3 + kWarpsPerBlock - 1) / kWarpsPerBlock; }
+
+__device__ __forceinline__ bool site_warp(const Lattice& lat, int64_t lb, SiteWarp& sw)
 {
-    const int site = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
-    sw.g = (int64_t)blockIdx.z * 65535 + blockIdx.y;
-    if (site >= lat.L3 || sw.g >= n_groups) return false;
+    const int64_t sbn = site_blocks(lat.L3);
+    sw.g = lb / sbn;
+    const int site = (int)((lb - sw.g * sbn) * kWarpsPerBlock + (threadIdx.x >> 5));
+    if (site >= lat.L3) return false;
     sw.site = site;
     const Coord r = site_coord(lat, site);
     const int step[3] = {1, lat.L, lat.L2};
@@ -189,13 +186,18 @@ enum SynMode { kSynWords = 0, kSynWordsSave = 1, kSynSaved = 2 };
 // face's own slot, which is not read) and Eq. 2 (check->variable) into msg_out.
 // msg_in == nullptr is the first iteration: every input is the prior l0.
 template <int kSyn>
-__global__ void __launch_bounds__(kBpThreads)
-k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__ s,
-          uint4* __restrict__ syn, float l0, TD q, const float* __restrict__ msg_in,
-          float* __restrict__ msg_out)
+__global__ void __launch_bounds__(kBpThreads, 6)
+k_bp_step(const __grid_constant__ ItemTable tab, float l0, TD q)
 {
+    for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
+    const Lattice lat = d.lat;
+    const int64_t W = d.W;
+    const uint64_t* __restrict__ s = d.s;
+    uint4* __restrict__ syn = d.syn;
+    const float* __restrict__ msg_in = d.msg_in;
+    float* __restrict__ msg_out = d.msg_out;
     SiteWarp sw;
-    if (!site_warp(lat, n_groups, sw)) return;
+    if (!site_warp(lat, lb, sw)) return;
     const int lane = threadIdx.x & 31;
     uint4 sh;
     if (kSyn == kSynSaved) {
@@ -263,6 +265,7 @@ k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__
     PUT(oYr + 0 * kLanes, y[2]);
     PUT(oYx + 1 * kLanes, y[3]);
 #undef PUT
+    });
 }
 
 // Eq. 4 posterior and the hard decision for the three edges at a site (the
@@ -270,12 +273,18 @@ k_bp_step(Lattice lat, int64_t n_groups, int64_t W, const uint64_t* __restrict__
 // The warp XORs d into e at r and, for each face at r, the parity of its four
 // edges' decisions into s (each 32-sample half word has exactly one writer).
 __global__ void __launch_bounds__(kBpThreads)
-k_bp_decide(Lattice lat, int64_t n_groups, int64_t W, int64_t n_samples, float l0,
-            const float* __restrict__ msg, uint32_t* __restrict__ e32, uint32_t* __restrict__ s32,
-            float* __restrict__ llr_out)
+k_bp_decide(const __grid_constant__ ItemTable tab, float l0)
 {
+    for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
+    const Lattice lat = d.lat;
+    const int64_t W = d.W;
+    const int64_t n_samples = d.n_samples;
+    const float* __restrict__ msg = d.msg_in;
+    uint32_t* __restrict__ e32 = reinterpret_cast<uint32_t*>(d.e);
+    uint32_t* __restrict__ s32 = reinterpret_cast<uint32_t*>(d.s);
+    float* __restrict__ llr_out = d.llr;
     SiteWarp sw;
-    if (!site_warp(lat, n_groups, sw)) return;
+    if (!site_warp(lat, lb, sw)) return;
     const int lane = threadIdx.x & 31;
     const int64_t sample = sw.g * kLanes + lane;
     const bool valid = sample < n_samples;
@@ -317,6 +326,7 @@ k_bp_decide(Lattice lat, int64_t n_groups, int64_t W, int64_t n_samples, float l
 #pragma unroll
         for (int d = 0; d < 3; ++d) llr_out[((int64_t)d * lat.L3 + r) * n_samples + sample] = lr[d];
     }
+    });
 }
 
 Lattice make_lattice(int L) { return make_lattice_host(L); }
@@ -335,41 +345,39 @@ float prior(double p) { return (float)std::log((1.0 - p) / p); }
 int64_t group_floats(int L) { return 3LL * L * L * L * 4 * kLanes; }
 int64_t group_syn(int L) { return (int64_t)L * L * L; }  // uint4 per site
 
-dim3 face_grid(int L, int64_t n_groups)
+void set_blocks(ItemTable& tab)
 {
-    const int64_t sites = (int64_t)L * L * L;
-    const int warps_per_block = kBpThreads / 32;
-    return dim3((unsigned)((sites + warps_per_block - 1) / warps_per_block),
-                (unsigned)std::min<int64_t>(n_groups, 65535), (unsigned)((n_groups + 65534) / 65535));
+    for (int i = 0; i < tab.n; ++i) tab.it[i].blocks = site_blocks(tab.it[i].lat.L3) * tab.it[i].groups;
+    finish_table(tab);
 }
 
-t3d_status launch_step(int L, int64_t n_groups, int64_t W, const uint64_t* s, uint4* syn, int mode,
-                       double p, double q_meas, const float* in, float* out, cudaStream_t st)
+t3d_status launch_step(ItemTable& tab, int mode, double p, double q_meas, cudaStream_t st)
 {
-    Lattice lat = make_lattice(L);
+    set_blocks(tab);
+    const int64_t blocks = tab.prefix[tab.n];
     ProfScope prof(T3D_K_BP_STEP, st);
-    const dim3 grid = face_grid(L, n_groups);
     if (mode == kSynWordsSave)
-        k_bp_step<kSynWordsSave><<<grid, kBpThreads, 0, st>>>(lat, n_groups, W, s, syn, prior(p),
-                                                              meas_pair(q_meas), in, out);
+        k_bp_step<kSynWordsSave><<<persistent_grid((const void*)k_bp_step<kSynWordsSave>, kBpThreads,
+                                                   T3D_K_BP_STEP, blocks),
+                                   kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas));
     else if (mode == kSynSaved)
-        k_bp_step<kSynSaved><<<grid, kBpThreads, 0, st>>>(lat, n_groups, W, s, syn, prior(p),
-                                                          meas_pair(q_meas), in, out);
+        k_bp_step<kSynSaved><<<persistent_grid((const void*)k_bp_step<kSynSaved>, kBpThreads, T3D_K_BP_STEP,
+                                               blocks),
+                               kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas));
     else
-        k_bp_step<kSynWords><<<grid, kBpThreads, 0, st>>>(lat, n_groups, W, s, syn, prior(p),
-                                                          meas_pair(q_meas), in, out);
+        k_bp_step<kSynWords><<<persistent_grid((const void*)k_bp_step<kSynWords>, kBpThreads, T3D_K_BP_STEP,
+                                               blocks),
+                               kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas));
     T3D_LAUNCH_CHECK("bp step");
     return T3D_OK;
 }
 
-t3d_status launch_decide(int L, int64_t n_groups, int64_t W, int64_t n_samples, double p,
-                         const float* msg, uint64_t* e, uint64_t* s, float* llr, cudaStream_t st)
+t3d_status launch_decide(ItemTable& tab, double p, cudaStream_t st)
 {
-    Lattice lat = make_lattice(L);
+    set_blocks(tab);
     ProfScope prof(T3D_K_BP_DECIDE, st);
-    k_bp_decide<<<face_grid(L, n_groups), kBpThreads, 0, st>>>(
-        lat, n_groups, W, n_samples, prior(p), msg, reinterpret_cast<uint32_t*>(e),
-        reinterpret_cast<uint32_t*>(s), llr);
+    k_bp_decide<<<persistent_grid((const void*)k_bp_decide, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n]),
+                  kBpThreads, 0, st>>>(tab, prior(p));
     T3D_LAUNCH_CHECK("bp decide");
     return T3D_OK;
 }
@@ -386,31 +394,121 @@ size_t bp_bytes_per_group(int L)
 // The s/e words of chunk c start at group c*chunk_groups, so the kernels see
 // the chunk's slice of the arrays through offset pointers and a local group
 // count (groups are aligned to 64-sample words when chunk_groups is even).
-t3d_status launch_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p, double q_meas,
-                     int iters, float* buf, int64_t chunk_groups, float* llr_out, cudaStream_t st)
+namespace {
+
+// Items' round-r chunks (items with no groups left are dropped); A and B are
+// each chunk's two message buffers.
+int64_t bp_rounds(const ItemTable& items, const int64_t* chunk_groups)
 {
-    const int64_t G = groups_for(n_samples);
-    const int64_t W = words_for(n_samples);
-    float* A = buf;
-    float* B = buf + chunk_groups * group_floats(L);
-    uint4* syn = reinterpret_cast<uint4*>(buf + 2 * chunk_groups * group_floats(L));
-    for (int64_t g0 = 0; g0 < G; g0 += chunk_groups) {
-        const int64_t gc = std::min(chunk_groups, G - g0);
-        // the chunk's words begin at word g0/2 (g0 is even: chunk_groups is even or g0 == 0)
-        const int64_t w0 = g0 / 2;
-        const uint64_t* s_chunk = s + w0;
-        const float* last = nullptr;
+    int64_t rounds = 0;
+    for (int i = 0; i < items.n; ++i) {
+        const int64_t G = groups_for(items.it[i].n_samples);
+        rounds = std::max(rounds, (G + chunk_groups[i] - 1) / chunk_groups[i]);
+    }
+    return rounds;
+}
+
+ItemTable chunk_table(const ItemTable& items, float* const* bufs, const int64_t* chunk_groups, int64_t r,
+                      float* llr_out, float** A, float** B)
+{
+    ItemTable tab;
+    std::memset(&tab, 0, sizeof(tab));
+    for (int i = 0; i < items.n; ++i) {
+        const ItemDesc& src = items.it[i];
+        const int64_t G = groups_for(src.n_samples);
+        const int64_t g0 = r * chunk_groups[i];
+        if (g0 >= G) continue;
+        const int64_t gc = std::min(chunk_groups[i], G - g0);
+        const int64_t w0 = g0 / 2;  // chunks start on 64-sample words (even g0)
+        const int k = tab.n++;
+        ItemDesc& d = tab.it[k];
+        d = src;
+        d.e = src.e + w0;
+        d.s = src.s + w0;
+        d.g0 = g0;
+        d.groups = gc;
+        d.n_samples = std::min<int64_t>(gc * kLanes, src.n_samples - g0 * kLanes);
+        const int64_t fl = chunk_groups[i] * group_floats(src.lat.L);
+        A[k] = bufs[i];
+        B[k] = bufs[i] + fl;
+        d.syn = reinterpret_cast<uint4*>(bufs[i] + 2 * fl);
+        d.llr = (llr_out && items.n == 1) ? llr_out + g0 * kLanes : nullptr;
+    }
+    return tab;
+}
+
+}  // namespace
+
+t3d_status launch_bp(const ItemTable& items, double p, double q_meas, int iters, float* const* bufs,
+                     const int64_t* chunk_groups, float* llr_out, cudaStream_t st)
+{
+    // in round r item i processes groups [r*chunk_i, (r+1)*chunk_i)
+    const int64_t rounds = bp_rounds(items, chunk_groups);
+    for (int64_t r = 0; r < rounds; ++r) {
+        float* A[kMaxItems];
+        float* B[kMaxItems];
+        ItemTable tab = chunk_table(items, bufs, chunk_groups, r, llr_out, A, B);
         for (int it = 0; it < iters; ++it) {
-            T3D_TRY(launch_step(L, gc, W, s_chunk, syn, it == 0 ? kSynWordsSave : kSynSaved, p, q_meas,
-                                last, A, st));
-            last = A;
-            std::swap(A, B);
+            for (int k = 0; k < tab.n; ++k) {
+                tab.it[k].msg_in = it == 0 ? nullptr : B[k];
+                tab.it[k].msg_out = A[k];
+            }
+            T3D_TRY(launch_step(tab, it == 0 ? kSynWordsSave : kSynSaved, p, q_meas, st));
+            for (int k = 0; k < tab.n; ++k) std::swap(A[k], B[k]);
         }
-        const int64_t n_chunk = std::min<int64_t>(gc * kLanes, n_samples - g0 * kLanes);
-        T3D_TRY(launch_decide(L, gc, W, n_chunk, p, last, e + w0, s + w0,
-                              llr_out ? llr_out + g0 * kLanes : nullptr, st));
+        for (int k = 0; k < tab.n; ++k) tab.it[k].msg_in = iters > 0 ? B[k] : nullptr;
+        T3D_TRY(launch_decide(tab, p, st));
     }
     return T3D_OK;
+}
+
+t3d_status autotune_bp(const ItemTable& items, double p, double q_meas, float* const* bufs,
+                       const int64_t* chunk_groups, cudaStream_t st, int* best_cap, float* best_ms)
+{
+    float* A[kMaxItems];
+    float* B[kMaxItems];
+    ItemTable tab = chunk_table(items, bufs, chunk_groups, 0, nullptr, A, B);
+    for (int k = 0; k < tab.n; ++k) {
+        tab.it[k].msg_in = nullptr;
+        tab.it[k].msg_out = A[k];
+    }
+    T3D_TRY(launch_step(tab, kSynWordsSave, p, q_meas, st));  // realistic messages in A
+    for (int k = 0; k < tab.n; ++k) {
+        tab.it[k].msg_in = A[k];
+        tab.it[k].msg_out = B[k];
+    }
+    const int saved = tuned_blocks_per_sm(T3D_K_BP_STEP);
+    const int caps[] = {0, 1, 2, 3, 4, 5, 6, 8};
+    cudaEvent_t ev[2];
+    T3D_CUDA_CHECK(cudaEventCreate(&ev[0]));
+    T3D_CUDA_CHECK(cudaEventCreate(&ev[1]));
+    *best_cap = 0;
+    *best_ms = 1e30f;
+    t3d_status status = T3D_OK;
+    for (int cap : caps) {
+        set_tuned_blocks_per_sm(T3D_K_BP_STEP, cap);
+        status = launch_step(tab, kSynSaved, p, q_meas, st);  // warm-up
+        if (status != T3D_OK) break;
+        cudaEventRecord(ev[0], st);
+        for (int rep = 0; rep < 3 && status == T3D_OK; ++rep) status = launch_step(tab, kSynSaved, p, q_meas, st);
+        cudaEventRecord(ev[1], st);
+        if (status != T3D_OK) break;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess || cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess) {
+            set_error("autotune timing failed");
+            status = T3D_ECUDA;
+            break;
+        }
+        ms /= 3.0f;
+        if (ms < *best_ms) {
+            *best_ms = ms;
+            *best_cap = cap;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    set_tuned_blocks_per_sm(T3D_K_BP_STEP, status == T3D_OK ? *best_cap : saved);
+    return status;
 }
 
 }  // namespace t3d
@@ -451,8 +549,18 @@ extern "C" t3d_status toric3d_bp_step(int L, int64_t n_samples, const uint64_t* 
     T3D_REQUIRE(msg_out != nullptr && aligned(msg_out, 16), "msg_out must be 16-byte aligned");
     T3D_REQUIRE(msg_in == nullptr || aligned(msg_in, 16), "msg_in must be 16-byte aligned");
     T3D_REQUIRE(msg_in != msg_out, "msg_in and msg_out must differ");
-    return launch_step(L, groups_for(n_samples), words_for(n_samples), s, nullptr, kSynWords, p, q_meas,
-                       msg_in, msg_out, as_stream(stream));
+    ItemTable tab;
+    std::memset(&tab, 0, sizeof(tab));
+    tab.n = 1;
+    ItemDesc& d = tab.it[0];
+    d.lat = make_lattice(L);
+    d.W = words_for(n_samples);
+    d.n_samples = n_samples;
+    d.s = const_cast<uint64_t*>(s);
+    d.msg_in = const_cast<float*>(msg_in);
+    d.msg_out = msg_out;
+    d.groups = groups_for(n_samples);
+    return launch_step(tab, kSynWords, p, q_meas, as_stream(stream));
 }
 
 extern "C" t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* msg, double p,
@@ -465,8 +573,19 @@ extern "C" t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* m
     T3D_TRY(check_words(s, "s"));
     T3D_REQUIRE(msg == nullptr || aligned(msg, 16), "msg must be 16-byte aligned");
     T3D_REQUIRE(llr_out == nullptr || aligned(llr_out, 4), "llr_out must be 4-byte aligned");
-    return launch_decide(L, groups_for(n_samples), words_for(n_samples), n_samples, p, msg, e, s,
-                         llr_out, as_stream(stream));
+    ItemTable tab;
+    std::memset(&tab, 0, sizeof(tab));
+    tab.n = 1;
+    ItemDesc& d = tab.it[0];
+    d.lat = make_lattice(L);
+    d.W = words_for(n_samples);
+    d.n_samples = n_samples;
+    d.e = e;
+    d.s = s;
+    d.msg_in = const_cast<float*>(msg);
+    d.llr = llr_out;
+    d.groups = groups_for(n_samples);
+    return launch_decide(tab, p, as_stream(stream));
 }
 
 extern "C" t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p,
@@ -486,6 +605,14 @@ extern "C" t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t
                 toric3d_bp_workspace_bytes(L, 64));
     chunk = std::min(chunk, G);
     T3D_REQUIRE(llr_out == nullptr || chunk >= G, "llr_out requires a workspace for the whole batch");
-    return launch_bp(L, n_samples, e, s, p, q_meas, iters, static_cast<float*>(work), chunk, llr_out,
-                     as_stream(stream));
+    ItemTable items;
+    std::memset(&items, 0, sizeof(items));
+    items.n = 1;
+    items.it[0].lat = make_lattice(L);
+    items.it[0].W = words_for(n_samples);
+    items.it[0].n_samples = n_samples;
+    items.it[0].e = e;
+    items.it[0].s = s;
+    float* buf = static_cast<float*>(work);
+    return launch_bp(items, p, q_meas, iters, &buf, &chunk, llr_out, as_stream(stream));
 }

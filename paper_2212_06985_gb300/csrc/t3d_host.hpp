@@ -80,20 +80,36 @@ struct ProfScope {
 t3d_status check_lattice(int L);
 t3d_status check_words(const void* p, const char* name);
 
-// Kernel launchers used across translation units (no argument validation).
-t3d_status launch_noise(int L, int64_t words, uint64_t* e, uint64_t thr, uint64_t seed,
-                        uint64_t group0, uint32_t cycle, cudaStream_t st);
-t3d_status launch_syndrome(int L, int64_t words, const uint64_t* e, uint64_t* s, uint64_t thr,
-                           uint64_t seed, uint64_t group0, uint32_t cycle, cudaStream_t st);
-t3d_status launch_sweeps(int L, int64_t words, uint64_t* e, uint64_t* s, uint64_t* tmp,
-                         const char* schedule, int slen, int n_apply, uint32_t sweep0,
-                         uint64_t seed, uint64_t group0, uint32_t cycle, cudaStream_t st);
-t3d_status launch_logical(int L, int64_t n_samples, const uint64_t* e, uint8_t* mask,
-                          int64_t* counts8, cudaStream_t st);
+// Persistent grid size for a kernel: SMs x resident blocks of `threads`
+// threads (cached per kernel and device), optionally capped by the tuning
+// table, never more than `blocks`.
+unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks);
+
+// Launch tuning chosen by the autotuner (0 = use the occupancy limit).
+int tuned_blocks_per_sm(int kind);
+void set_tuned_blocks_per_sm(int kind, int blocks_per_sm);
+
+// Kernel launchers over an item table (see t3d_items.cuh).  Each fills the
+// items' `blocks` (and `tx`) for its own kernel; no argument validation.
+struct ItemTable;
+t3d_status launch_noise(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t cycle, cudaStream_t st);
+t3d_status launch_syndrome(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t cycle,
+                           cudaStream_t st);
+// n_apply applications cycling through `schedule`; uses each item's e, s and
+// tmp and leaves the result in s.
+t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_apply,
+                         uint32_t sweep0, uint64_t seed, uint32_t cycle, cudaStream_t st);
+t3d_status launch_logical(ItemTable& tab, cudaStream_t st);
+
 // Bytes of BP workspace per 32-sample group (two message buffers + syndrome copy).
 size_t bp_bytes_per_group(int L);
-t3d_status launch_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p,
-                     double q_meas, int iters, float* buf, int64_t chunk_groups,
-                     float* llr_out, cudaStream_t st);
+// BP over every item (e, s, n_samples, W of each); bufs[i] is item i's chunk
+// workspace holding chunk_groups[i] groups (even unless it covers the item).
+t3d_status launch_bp(const ItemTable& items, double p, double q_meas, int iters, float* const* bufs,
+                     const int64_t* chunk_groups, float* llr_out, cudaStream_t st);
+// Times the BP iteration on the items' first chunks under each blocks-per-SM
+// cap and keeps the fastest in the tuning table (synchronises the stream).
+t3d_status autotune_bp(const ItemTable& items, double p, double q_meas, float* const* bufs,
+                       const int64_t* chunk_groups, cudaStream_t st, int* best_cap, float* best_ms);
 
 }  // namespace t3d

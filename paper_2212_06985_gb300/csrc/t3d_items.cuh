@@ -1,0 +1,71 @@
+// Work items for persistent multi-lattice launches.
+//
+// A batch holds up to kMaxItems independent ensembles, each with its own
+// lattice size L, sample count and buffers.  Every kernel of a run is launched
+// once per step for the whole batch: the item table travels by value in the
+// kernel parameters, each item needs `blocks` thread blocks of work, and a
+// persistent grid (a multiple of the SM count) walks the concatenated block
+// ranges with a grid-stride loop, so uneven lattices share one launch and no
+// SM idles at the tail of a small item.
+#pragma once
+
+#include <cstdint>
+
+#include "t3d_device.cuh"
+
+namespace t3d {
+
+constexpr int kMaxItems = 8;
+
+struct ItemDesc {
+    Lattice lat;
+    int64_t W;            // 64-bit words per bit-sliced row
+    int64_t n_samples;
+    uint64_t group0;      // global index of the item's first 64-sample word
+    uint64_t* e;          // bit-sliced error state [3L^3][W]
+    uint64_t* s;          // bit-sliced syndrome [3L^3][W]
+    uint64_t* tmp;        // ping-pong syndrome for synchronous applications
+    float* msg_in;        // BP messages of the current chunk (nullptr: priors)
+    float* msg_out;
+    uint4* syn;           // BP per-group syndrome words of the current chunk
+    float* llr;           // optional posteriors [3L^3][n_samples]
+    uint8_t* mask;
+    unsigned long long* counts8;
+    int64_t g0;           // BP: first 32-sample group of the current chunk
+    int64_t groups;       // BP: groups in the current chunk
+    int tx;               // bit-sliced kernels: words per thread-block row (power of 2)
+    int64_t blocks;       // thread blocks this item needs in the current launch
+};
+
+struct ItemTable {
+    int n;
+    int64_t prefix[kMaxItems + 1];   // prefix[i] = first block of item i
+    ItemDesc it[kMaxItems];
+};
+
+// Item owning global block b of the concatenated ranges (n <= 8: linear scan).
+__device__ __forceinline__ int item_of(const ItemTable& tab, int64_t b)
+{
+    int i = 0;
+    while (i + 1 < tab.n && b >= tab.prefix[i + 1]) ++i;
+    return i;
+}
+
+// Persistent grid-stride walk over every item's blocks: f(item, local block).
+template <class F>
+__device__ __forceinline__ void for_each_item_block(const ItemTable& tab, F&& f)
+{
+    const int64_t total = tab.prefix[tab.n];
+    for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+        const int i = item_of(tab, b);
+        f(tab.it[i], b - tab.prefix[i]);
+    }
+}
+
+inline void finish_table(ItemTable& tab)
+{
+    tab.prefix[0] = 0;
+    for (int i = 0; i < tab.n; ++i) tab.prefix[i + 1] = tab.prefix[i] + tab.it[i].blocks;
+}
+
+}  // namespace t3d

@@ -1,8 +1,9 @@
 // Whole Monte Carlo runs: T code cycles of noise, noisy measurement and
 // decoding (Sec. 3.1 Fig. 2, Sec. 3.2 schedules, Sec. 4.2 p-BP), an optional
-// noiseless final round, and the logical readout, enqueued on one stream and
-// optionally captured into a CUDA graph that is instantiated once per distinct
-// run and replayed.
+// noiseless final round, and the logical readout.  A run covers a batch of up
+// to eight ensembles of different lattice sizes; every step is one persistent
+// launch over all of them (t3d_items.cuh).  The whole T-cycle sequence can be
+// captured into a CUDA graph, instantiated once per distinct run and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -10,6 +11,7 @@
 #include <mutex>
 
 #include "t3d_host.hpp"
+#include "t3d_items.cuh"
 
 namespace t3d {
 namespace {
@@ -18,27 +20,22 @@ constexpr size_t kAlign = 256;
 
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-size_t state_bytes(const t3d_run_cfg& c)
+size_t state_bytes(int L, int64_t n_samples)
 {
-    return (size_t)3 * c.L * c.L * c.L * (size_t)words_for(c.n_samples) * sizeof(uint64_t);
+    return (size_t)3 * L * L * L * (size_t)words_for(n_samples) * sizeof(uint64_t);
 }
 
-
 struct Plan {
-    uint64_t* s;
-    uint64_t* tmp;
-    float* bp;
-    int64_t chunk_groups;
+    ItemTable items;
+    float* bp[kMaxItems];
+    int64_t chunk[kMaxItems];
 };
 
-t3d_status validate(const t3d_run_cfg* c)
+t3d_status validate_cfg(const t3d_run_cfg* c)
 {
     T3D_REQUIRE(c != nullptr, "cfg is NULL");
-    T3D_TRY(check_lattice(c->L));
     T3D_REQUIRE(c->T >= 0, "T must be >= 0");
     T3D_REQUIRE(c->p >= 0.0 && c->p <= 1.0 && c->q >= 0.0 && c->q <= 1.0, "p, q must lie in [0,1]");
-    T3D_REQUIRE(c->n_samples >= 1 && words_for(c->n_samples) <= 65535LL * 32, "n_samples out of range");
-    T3D_REQUIRE(c->sample0 % 64 == 0, "sample0 must be a multiple of 64");
     T3D_REQUIRE(c->n_apply >= 0, "n_apply must be >= 0");
     size_t slen = strnlen(c->schedule, sizeof(c->schedule));
     T3D_REQUIRE(slen < sizeof(c->schedule), "schedule must be NUL-terminated");
@@ -55,71 +52,142 @@ t3d_status validate(const t3d_run_cfg* c)
     return T3D_OK;
 }
 
-t3d_status plan_workspace(const t3d_run_cfg& c, void* work, size_t work_bytes, Plan& pl)
+t3d_status validate_items(const t3d_run_cfg* c, const t3d_batch_item* items, int n_items)
 {
-    const size_t sb = round_up(state_bytes(c));
-    T3D_REQUIRE(work != nullptr && aligned(work, kAlign), "work must be a 256-byte aligned device pointer");
-    T3D_REQUIRE(work_bytes >= 2 * sb, "workspace too small: %zu < %zu", work_bytes, 2 * sb);
-    char* base = static_cast<char*>(work);
-    pl.s = reinterpret_cast<uint64_t*>(base);
-    pl.tmp = reinterpret_cast<uint64_t*>(base + sb);
-    pl.bp = nullptr;
-    pl.chunk_groups = 0;
-    if (c.use_bp && c.bp_iters > 0) {
-        const int64_t G = groups_for(c.n_samples);
-        int64_t chunk = (int64_t)((work_bytes - 2 * sb) / bp_bytes_per_group(c.L));
-        if (c.bp_chunk_samples > 0) chunk = std::min(chunk, groups_for(c.bp_chunk_samples));
-        if (chunk < G) chunk &= ~1LL;
-        T3D_REQUIRE(chunk >= 1, "workspace too small for one BP chunk");
-        pl.chunk_groups = std::min(chunk, G);
-        pl.bp = reinterpret_cast<float*>(base + 2 * sb);
+    T3D_REQUIRE(items != nullptr && n_items >= 1 && n_items <= kMaxItems, "need 1..%d batch items", kMaxItems);
+    for (int i = 0; i < n_items; ++i) {
+        const t3d_batch_item& it = items[i];
+        T3D_TRY(check_lattice(it.L));
+        T3D_REQUIRE(!c->use_bp || it.L <= 128, "BP supports L <= 128 (item %d has L=%d)", i, it.L);
+        T3D_REQUIRE(it.n_samples >= 1 && words_for(it.n_samples) <= (1LL << 31), "item %d: n_samples out of range", i);
+        T3D_REQUIRE(it.sample0 % 64 == 0, "item %d: sample0 must be a multiple of 64", i);
+        T3D_TRY(check_words(it.e, "item e"));
+        T3D_REQUIRE(it.counts8 == nullptr || aligned(it.counts8, 8), "item %d: counts8 must be 8-byte aligned", i);
     }
     return T3D_OK;
 }
 
-t3d_status enqueue_run(const t3d_run_cfg& c, uint64_t* e, const Plan& pl, uint8_t* mask,
-                       int64_t* counts8, cudaStream_t st)
+// Groups per BP chunk for every item: all groups (one round) when the
+// workspace allows, else the fewest rounds that fit; chunks hold whole
+// 64-sample words unless they cover the item.
+bool bp_chunks(const t3d_run_cfg& c, const t3d_batch_item* items, int n, size_t avail, int64_t* chunk)
 {
-    const int L = c.L;
-    const int64_t W = words_for(c.n_samples);
-    const uint64_t group0 = c.sample0 / 64;
+    int64_t max_groups = 0;
+    for (int i = 0; i < n; ++i) max_groups = std::max(max_groups, groups_for(items[i].n_samples));
+    for (int64_t rounds = 1; rounds <= max_groups; ++rounds) {
+        size_t need = 0;
+        for (int i = 0; i < n; ++i) {
+            const int64_t G = groups_for(items[i].n_samples);
+            int64_t g = (G + rounds - 1) / rounds;
+            if (c.bp_chunk_samples > 0) g = std::min(g, groups_for(c.bp_chunk_samples));
+            if (g < G) g = std::max<int64_t>(2, g + (g & 1));
+            g = std::min(g, G);
+            chunk[i] = g;
+            need += round_up((size_t)g * bp_bytes_per_group(items[i].L));
+        }
+        if (need <= avail) return true;
+    }
+    return false;
+}
+
+size_t batch_workspace_bytes(const t3d_run_cfg& c, const t3d_batch_item* items, int n)
+{
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) total += 2 * round_up(state_bytes(items[i].L, items[i].n_samples));
+    if (c.use_bp && c.bp_iters > 0) {
+        for (int i = 0; i < n; ++i) {
+            const int64_t G = groups_for(items[i].n_samples);
+            int64_t g = c.bp_chunk_samples > 0 ? std::min(G, groups_for(c.bp_chunk_samples)) : G;
+            if (g < G) g = std::max<int64_t>(2, g + (g & 1));
+            g = std::min(g, G);
+            total += round_up((size_t)g * bp_bytes_per_group(items[i].L));
+        }
+    }
+    return total;
+}
+
+t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int n, void* work,
+                          size_t work_bytes, Plan& pl)
+{
+    T3D_REQUIRE(work != nullptr && aligned(work, kAlign), "work must be a 256-byte aligned device pointer");
+    std::memset(&pl, 0, sizeof(pl));
+    char* base = static_cast<char*>(work);
+    size_t used = 0;
+    pl.items.n = n;
+    for (int i = 0; i < n; ++i) {
+        const size_t sb = round_up(state_bytes(items[i].L, items[i].n_samples));
+        T3D_REQUIRE(used + 2 * sb <= work_bytes, "workspace too small: %zu bytes", work_bytes);
+        ItemDesc& d = pl.items.it[i];
+        d.lat = make_lattice_host(items[i].L);
+        d.W = words_for(items[i].n_samples);
+        d.n_samples = items[i].n_samples;
+        d.group0 = items[i].sample0 / 64;
+        d.e = items[i].e;
+        d.s = reinterpret_cast<uint64_t*>(base + used);
+        d.tmp = reinterpret_cast<uint64_t*>(base + used + sb);
+        d.mask = items[i].mask;
+        d.counts8 = reinterpret_cast<unsigned long long*>(items[i].counts8);
+        used += 2 * sb;
+    }
+    if (c.use_bp && c.bp_iters > 0) {
+        T3D_REQUIRE(bp_chunks(c, items, n, work_bytes - used, pl.chunk), "workspace too small for BP chunks");
+        for (int i = 0; i < n; ++i) {
+            pl.bp[i] = reinterpret_cast<float*>(base + used);
+            used += round_up((size_t)pl.chunk[i] * bp_bytes_per_group(items[i].L));
+        }
+    } else if (c.use_bp) {
+        for (int i = 0; i < n; ++i) pl.chunk[i] = std::max<int64_t>(1, groups_for(items[i].n_samples));
+    }
+    return T3D_OK;
+}
+
+t3d_status enqueue_run(const t3d_run_cfg& c, const Plan& pl, cudaStream_t st)
+{
     const uint64_t thr_p = prob_threshold(c.p), thr_q = prob_threshold(c.q);
     const int slen = (int)strnlen(c.schedule, sizeof(c.schedule));
+    ItemTable tab;
     for (int t = 1; t <= c.T; ++t) {
         const uint32_t cycle = c.cycle0 + (uint32_t)t;
-        T3D_TRY(launch_noise(L, W, e, thr_p, c.seed, group0, cycle, st));
-        T3D_TRY(launch_syndrome(L, W, e, pl.s, thr_q, c.seed, group0, cycle, st));
+        tab = pl.items;
+        T3D_TRY(launch_noise(tab, thr_p, c.seed, cycle, st));
+        tab = pl.items;
+        T3D_TRY(launch_syndrome(tab, thr_q, c.seed, cycle, st));
         if (c.use_bp)
-            T3D_TRY(launch_bp(L, c.n_samples, e, pl.s, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters,
-                              pl.bp, pl.chunk_groups, nullptr, st));
-        if (c.n_apply > 0)
-            T3D_TRY(launch_sweeps(L, W, e, pl.s, pl.tmp, c.schedule, slen, c.n_apply, 0, c.seed,
-                                  group0, cycle, st));
+            T3D_TRY(launch_bp(pl.items, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, pl.bp, pl.chunk,
+                              nullptr, st));
+        if (c.n_apply > 0) {
+            tab = pl.items;
+            T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
+        }
     }
     if (c.perfect_round) {
         const uint32_t cycle = c.cycle0 + (uint32_t)c.T + 1;
-        T3D_TRY(launch_syndrome(L, W, e, pl.s, 0, c.seed, group0, cycle, st));
-        if (c.perfect_max_sweeps > 0)
-            T3D_TRY(launch_sweeps(L, W, e, pl.s, pl.tmp, "F", 1, c.perfect_max_sweeps, 0, c.seed,
-                                  group0, cycle, st));
+        tab = pl.items;
+        T3D_TRY(launch_syndrome(tab, 0, c.seed, cycle, st));
+        if (c.perfect_max_sweeps > 0) {
+            tab = pl.items;
+            T3D_TRY(launch_sweeps(tab, "F", 1, c.perfect_max_sweeps, 0, c.seed, cycle, st));
+        }
     }
-    if (mask || counts8) T3D_TRY(launch_logical(L, c.n_samples, e, mask, counts8, st));
+    bool readout = false;
+    for (int i = 0; i < pl.items.n; ++i) readout |= pl.items.it[i].mask || pl.items.it[i].counts8;
+    if (readout) {
+        tab = pl.items;
+        T3D_TRY(launch_logical(tab, st));
+    }
     return T3D_OK;
 }
 
 // ------------------------------------------------------------ graph cache
 struct GraphKey {
     t3d_run_cfg cfg;
-    const void* e;
+    t3d_batch_item items[kMaxItems];
+    int n_items;
     const void* work;
     size_t work_bytes;
-    const void* mask;
-    const void* counts8;
     cudaStream_t stream;
     int device;
 };
-
-bool same_key(const GraphKey& a, const GraphKey& b) { return std::memcmp(&a, &b, sizeof(GraphKey)) == 0; }
 
 struct GraphEntry {
     GraphKey key;
@@ -132,29 +200,28 @@ GraphEntry g_graphs[kGraphCache];
 int g_graph_next = 0;
 std::mutex g_graph_mutex;
 
-t3d_status run_with_graph(const t3d_run_cfg& c, uint64_t* e, const Plan& pl, void* work,
-                          size_t work_bytes, uint8_t* mask, int64_t* counts8, cudaStream_t st)
+t3d_status run_with_graph(const t3d_run_cfg& c, const t3d_batch_item* items, int n, const Plan& pl,
+                          void* work, size_t work_bytes, cudaStream_t st)
 {
     T3D_REQUIRE(st != nullptr, "use_graph needs a non-default stream");
     GraphKey key;
     std::memset(&key, 0, sizeof(key));
     key.cfg = c;
-    key.e = e;
+    std::memcpy(key.items, items, sizeof(t3d_batch_item) * n);
+    key.n_items = n;
     key.work = work;
     key.work_bytes = work_bytes;
-    key.mask = mask;
-    key.counts8 = counts8;
     key.stream = st;
     T3D_CUDA_CHECK(cudaGetDevice(&key.device));
     std::lock_guard<std::mutex> lock(g_graph_mutex);
     for (auto& g : g_graphs) {
-        if (g.used && same_key(g.key, key)) {
+        if (g.used && std::memcmp(&g.key, &key, sizeof(GraphKey)) == 0) {
             T3D_CUDA_CHECK(cudaGraphLaunch(g.exec, st));
             return T3D_OK;
         }
     }
     T3D_CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    t3d_status stq = enqueue_run(c, e, pl, mask, counts8, st);
+    t3d_status stq = enqueue_run(c, pl, st);
     cudaGraph_t graph = nullptr;
     cudaError_t end = cudaStreamEndCapture(st, &graph);
     if (stq != T3D_OK) {
@@ -186,23 +253,79 @@ t3d_status run_with_graph(const t3d_run_cfg& c, uint64_t* e, const Plan& pl, voi
     return T3D_OK;
 }
 
+t3d_status run_batch(const t3d_run_cfg* cfg, const t3d_batch_item* items, int n_items, void* work,
+                     size_t work_bytes, t3d_stream stream)
+{
+    T3D_TRY(validate_cfg(cfg));
+    T3D_TRY(validate_items(cfg, items, n_items));
+    Plan pl;
+    T3D_TRY(plan_workspace(*cfg, items, n_items, work, work_bytes, pl));
+    cudaStream_t st = as_stream(stream);
+    if (cfg->use_graph) return run_with_graph(*cfg, items, n_items, pl, work, work_bytes, st);
+    return enqueue_run(*cfg, pl, st);
+}
+
+t3d_batch_item single(const t3d_run_cfg* cfg, uint64_t* e, uint8_t* mask, int64_t* counts8)
+{
+    t3d_batch_item it;
+    std::memset(&it, 0, sizeof(it));
+    it.L = cfg->L;
+    it.n_samples = cfg->n_samples;
+    it.sample0 = cfg->sample0;
+    it.e = e;
+    it.mask = mask;
+    it.counts8 = counts8;
+    return it;
+}
+
 }  // namespace
 }  // namespace t3d
 
 using namespace t3d;
 
+extern "C" size_t toric3d_run_batch_workspace_bytes(const t3d_run_cfg* cfg, const t3d_batch_item* items,
+                                                    int n_items)
+{
+    if (validate_cfg(cfg) != T3D_OK || items == nullptr || n_items < 1 || n_items > kMaxItems) return 0;
+    for (int i = 0; i < n_items; ++i)
+        if (items[i].L < 2 || items[i].L > kMaxL || items[i].n_samples < 1) return 0;
+    return batch_workspace_bytes(*cfg, items, n_items);
+}
+
+extern "C" t3d_status toric3d_run_batch(const t3d_run_cfg* cfg, const t3d_batch_item* items, int n_items,
+                                        void* work, size_t work_bytes, t3d_stream stream)
+{
+    clear_error();
+    return run_batch(cfg, items, n_items, work, work_bytes, stream);
+}
+
+extern "C" t3d_status toric3d_autotune_batch(const t3d_run_cfg* cfg, const t3d_batch_item* items,
+                                             int n_items, void* work, size_t work_bytes,
+                                             int* bp_blocks_per_sm, float* bp_ms, t3d_stream stream)
+{
+    clear_error();
+    T3D_TRY(validate_cfg(cfg));
+    T3D_TRY(validate_items(cfg, items, n_items));
+    T3D_REQUIRE(cfg->use_bp && cfg->bp_iters > 0, "autotuning needs a BP decoder");
+    Plan pl;
+    T3D_TRY(plan_workspace(*cfg, items, n_items, work, work_bytes, pl));
+    cudaStream_t st = as_stream(stream);
+    ItemTable tab = pl.items;
+    // a realistic noisy syndrome in the workspace (the states e are only read)
+    T3D_TRY(launch_syndrome(tab, prob_threshold(cfg->q), cfg->seed, cfg->cycle0 + 1, st));
+    int cap = 0;
+    float ms = 0.0f;
+    T3D_TRY(autotune_bp(pl.items, cfg->p, cfg->bp_meas_nodes ? cfg->q : 0.0, pl.bp, pl.chunk, st, &cap, &ms));
+    if (bp_blocks_per_sm) *bp_blocks_per_sm = cap;
+    if (bp_ms) *bp_ms = ms;
+    return T3D_OK;
+}
+
 extern "C" size_t toric3d_run_workspace_bytes(const t3d_run_cfg* cfg)
 {
-    if (validate(cfg) != T3D_OK) return 0;
-    size_t total = 2 * round_up(state_bytes(*cfg));
-    if (cfg->use_bp && cfg->bp_iters > 0) {
-        int64_t n = cfg->bp_chunk_samples > 0 ? std::min(cfg->bp_chunk_samples, cfg->n_samples)
-                                              : cfg->n_samples;
-        int64_t g = groups_for(n);
-        if (g < groups_for(cfg->n_samples)) g += g & 1;
-        total += (size_t)g * bp_bytes_per_group(cfg->L);
-    }
-    return total;
+    if (validate_cfg(cfg) != T3D_OK || cfg->L < 2 || cfg->L > kMaxL || cfg->n_samples < 1) return 0;
+    t3d_batch_item it = single(cfg, nullptr, nullptr, nullptr);
+    return batch_workspace_bytes(*cfg, &it, 1);
 }
 
 extern "C" t3d_status toric3d_run_cycles(const t3d_run_cfg* cfg, uint64_t* e, void* work,
@@ -210,12 +333,7 @@ extern "C" t3d_status toric3d_run_cycles(const t3d_run_cfg* cfg, uint64_t* e, vo
                                          t3d_stream stream)
 {
     clear_error();
-    T3D_TRY(validate(cfg));
-    T3D_TRY(check_words(e, "e"));
-    T3D_REQUIRE(counts8 == nullptr || aligned(counts8, 8), "counts8 must be 8-byte aligned");
-    Plan pl;
-    T3D_TRY(plan_workspace(*cfg, work, work_bytes, pl));
-    cudaStream_t st = as_stream(stream);
-    if (cfg->use_graph) return run_with_graph(*cfg, e, pl, work, work_bytes, mask, counts8, st);
-    return enqueue_run(*cfg, e, pl, mask, counts8, st);
+    T3D_REQUIRE(cfg != nullptr, "cfg is NULL");
+    t3d_batch_item it = single(cfg, e, mask, counts8);
+    return run_batch(cfg, &it, 1, work, work_bytes, stream);
 }

@@ -92,3 +92,33 @@ def test_table1_schedule_matches_paper():
     g = json.load(open(os.path.join(ROOT, "tests", "golden", "schedules.json")))
     for row in g["table1"]:
         assert t3d.table1_schedule(row["n_A"], row["lambda_p"]) == row["schedule"]
+
+
+def test_batch_validation():
+    lib = t3d.lib()
+    cfg = t3d.make_run_cfg(4, 2, 0.01, 0.01, 0, 1, schedule="F", n_apply=1)
+    items = (t3d.BatchItem * 9)()
+    for it in items:
+        it.L, it.n_samples, it.e = 4, 64, 0x10000
+    assert lib.toric3d_run_batch(ctypes.byref(cfg), items, 9, FAKE, 1 << 30, None) == EINVAL
+    assert lib.toric3d_run_batch(ctypes.byref(cfg), items, 0, FAKE, 1 << 30, None) == EINVAL
+    items[1].L = 1
+    assert lib.toric3d_run_batch(ctypes.byref(cfg), items, 2, FAKE, 1 << 30, None) == EINVAL
+    assert "L=1" in _err()
+    items[1].L = 5
+    items[1].sample0 = 3
+    assert lib.toric3d_run_batch(ctypes.byref(cfg), items, 2, FAKE, 1 << 30, None) == EINVAL
+    items[1].sample0 = 0
+    assert t3d.toric3d_run_batch_workspace_bytes(cfg, items[:2]) == sum(
+        2 * ((3 * L ** 3 * 8 + 255) // 256 * 256) for L in (4, 5))
+    bp = t3d.make_run_cfg(4, 2, 0.04, 0.04, 0, 1, use_bp=True, bp_iters=4, schedule="F", n_apply=1)
+    items[0].L = 130
+    assert lib.toric3d_run_batch(ctypes.byref(bp), items, 1, FAKE, 1 << 40, None) == EINVAL
+    assert "L <= 128" in _err()
+
+
+def test_tuning_table_roundtrip():
+    t3d.toric3d_set_blocks_per_sm("bp_step", 3)
+    assert t3d.toric3d_get_blocks_per_sm("bp_step") == 3
+    t3d.toric3d_set_blocks_per_sm("bp_step", 0)
+    assert t3d.toric3d_get_blocks_per_sm("bp_step") == 0

@@ -84,6 +84,11 @@ class Workload:
     bp_meas_nodes: bool = True
     perfect_round: bool = False
     perfect_max_sweeps: int = 0
+    extra_L: tuple = ()         # further lattice sizes decoded in the same launches
+
+    @property
+    def sizes(self):
+        return (self.L,) + tuple(self.extra_L)
 
 
 # Workload recipes (phenomenological noise with p = q throughout, as in the
@@ -98,6 +103,9 @@ WORKLOADS = {
     # BP (16 FP32 iterations) + 32 applications cycling PFFPFF, T=L
     "bp_pflip_L16": Workload("bp_pflip_L16", 16, 0.04, 0.04, 16, 100_000, 7, "bp_pflip",
                              "PFFPFF", 32, bp_iters=16),
+    # L=16 and L=24 mixed in one persistent launch per step, 10^5 samples each
+    "bp_pflip_L16_L24": Workload("bp_pflip_L16_L24", 16, 0.04, 0.04, 16, 100_000, 7, "bp_pflip",
+                                 "PFFPFF", 32, bp_iters=16, extra_L=(24,)),
     # throughput point: L=32, p=q=4%, T=L, 10^5 samples, BP16 + 32 x PFFPFF
     "bp_pflip_L32": Workload("bp_pflip_L32", 32, 0.04, 0.04, 32, 100_000, 11, "bp_pflip",
                              "PFFPFF", 32, bp_iters=16),
