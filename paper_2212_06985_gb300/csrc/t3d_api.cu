@@ -4,6 +4,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -78,6 +79,10 @@ void set_tuned_blocks_per_sm(int kind, int blocks_per_sm)
 
 unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks)
 {
+    const int64_t max_grid = 0x7fffffffLL;
+    if (blocks < 1) return 1;
+    const int cap = tuned_blocks_per_sm(kind);
+    if (cap <= 0) return (unsigned)std::min(blocks, max_grid);  // one block per work unit
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_grid_mutex);
@@ -97,12 +102,9 @@ unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t bloc
         g_grids.push_back(GridEntry{kernel, threads, dev, n});
         per_sm = n;
     }
-    if (kind >= 0 && kind < T3D_K_COUNT && g_tuned[kind] > 0 && g_tuned[kind] < per_sm)
-        per_sm = g_tuned[kind];
-    int64_t grid = (int64_t)per_sm * g_sms[dev];
-    if (grid > blocks) grid = blocks;
-    if (grid < 1) grid = 1;
-    return (unsigned)grid;
+    per_sm = std::min(per_sm, cap);
+    const int64_t grid = (int64_t)per_sm * g_sms[dev];
+    return (unsigned)std::max<int64_t>(1, std::min(grid, blocks));
 }
 
 // ------------------------------------------------------------ kernel timing

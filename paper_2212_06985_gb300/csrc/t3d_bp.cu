@@ -69,41 +69,34 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
 // (tanh(|x|/2), 1 - tanh(|x|/2)) = ((1 - E), 2E) / (1 + E) with E = e^{-|x|}.
-// For |x| < 1/2 the difference 1 - E is taken from its Taylor series
-// sum_{k>=1} (-1)^{k+1} |x|^k / k! (through k = 7, truncation < 3e-7 relative)
-// instead of subtracting two nearly equal numbers.  Both forms are evaluated
-// and one selected, which is cheaper than branching per warp.
+// For |x| < 0.1 the difference 1 - E is taken from its Taylor series
+// |x| - |x|^2/2 + |x|^3/6 - |x|^4/24 (truncation < 1e-6 relative) instead of
+// subtracting two nearly equal numbers; above 0.1 the subtraction loses at
+// most a factor E/(1-E) < 10 on E's few-ulp error.  Both forms are evaluated
+// and one selected.
 __device__ __forceinline__ TD td_of(float x)
 {
     const float a = fabsf(x);
     const float E = ex2_approx(-a * kLog2e);
     const float r = rcp_approx(1.0f + E);
-    float h = fmaf(a, 1.0f / 5040.0f, -1.0f / 720.0f);
-    h = fmaf(a, h, 1.0f / 120.0f);
-    h = fmaf(a, h, -1.0f / 24.0f);
-    h = fmaf(a, h, 1.0f / 6.0f);
+    float h = fmaf(a, -1.0f / 24.0f, 1.0f / 6.0f);
     h = fmaf(a, h, -0.5f);
     h = fmaf(a, h, 1.0f);
-    const float om = (a < 0.5f) ? a * h : 1.0f - E;
+    const float om = (a < 0.1f) ? a * h : 1.0f - E;
     return TD{om * r, (E + E) * r};
 }
 
-// 2 atanh(P) for P = prod t, D = 1 - P: for P < 0.3 the odd series
-// 2 sum_k P^{2k+1}/(2k+1) (through P^13, truncation < 1e-8 relative); above it
-// log((1 + P) / D), whose argument exceeds 1.85 so the logarithm carries no
-// cancellation.  D = 0 (underflow) gives +inf, which the clamp turns into 30.
+// 2 atanh(P) for P = prod t, D = 1 - P: for P < 0.05 the odd series
+// 2P (1 + P^2/3 + P^4/5) (truncation < 3e-10 relative); above it
+// log((1 + P) / D), whose argument exceeds 1.1 so the approximate logarithm's
+// absolute error stays below 2e-6 of the result.  D = 0 (underflow) gives +inf,
+// which the clamp turns into 30.
 __device__ __forceinline__ float two_atanh(float P, float D)
 {
     const float u = P * P;
-    float h = fmaf(u, 1.0f / 13.0f, 1.0f / 11.0f);
-    h = fmaf(u, h, 1.0f / 9.0f);
-    h = fmaf(u, h, 1.0f / 7.0f);
-    h = fmaf(u, h, 1.0f / 5.0f);
-    h = fmaf(u, h, 1.0f / 3.0f);
-    h = fmaf(u, h, 1.0f);
-    const float series = 2.0f * P * h;
+    const float series = 2.0f * P * fmaf(u, fmaf(u, 1.0f / 5.0f, 1.0f / 3.0f), 1.0f);
     const float logv = kLn2 * lg2_approx((1.0f + P) * rcp_approx(D));
-    return (P < 0.3f) ? series : logv;
+    return (P < 0.05f) ? series : logv;
 }
 
 // Eq. 2 for the four edges of one face: y[j] from the other three inputs and
@@ -478,7 +471,7 @@ t3d_status autotune_bp(const ItemTable& items, double p, double q_meas, float* c
         tab.it[k].msg_out = B[k];
     }
     const int saved = tuned_blocks_per_sm(T3D_K_BP_STEP);
-    const int caps[] = {0, 1, 2, 3, 4, 5, 6, 8};
+    const int caps[] = {0, 1, 2, 4, 6, 8};
     cudaEvent_t ev[2];
     T3D_CUDA_CHECK(cudaEventCreate(&ev[0]));
     T3D_CUDA_CHECK(cudaEventCreate(&ev[1]));

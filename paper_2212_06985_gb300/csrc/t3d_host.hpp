@@ -80,9 +80,9 @@ struct ProfScope {
 t3d_status check_lattice(int L);
 t3d_status check_words(const void* p, const char* name);
 
-// Persistent grid size for a kernel: SMs x resident blocks of `threads`
-// threads (cached per kernel and device), optionally capped by the tuning
-// table, never more than `blocks`.
+// Grid size for a grid-stride kernel with `blocks` work units: one block per
+// unit by default; with a tuned cap of c blocks per SM, a persistent grid of
+// SMs x min(c, resident blocks) that walks the units.
 unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks);
 
 // Launch tuning chosen by the autotuner (0 = use the occupancy limit).

@@ -42,7 +42,7 @@ def _batch(kw, specs, ws_bytes=None, use_graph=False, tune=False):
     with torch.cuda.stream(stream):
         if tune:
             cap, ms = t3d.toric3d_autotune_batch(cfg, batch, work)
-            assert cap in (0, 1, 2, 3, 4, 5, 6, 8) and ms > 0
+            assert cap in (0, 1, 2, 4, 6, 8) and ms > 0
         t3d.toric3d_run_batch(cfg, batch, work)
     stream.synchronize()
     return [(download_bits(b[0], S), b[1].cpu().numpy(), b[2].cpu().numpy())
