@@ -100,6 +100,24 @@ t3d_status toric3d_flip(int L, int64_t words, uint64_t* e, uint64_t* s, int swee
                         size_t work_bytes, t3d_stream stream);
 
 /*
+ * toric3d_flip without a workspace argument, for callers that cannot give the
+ * library device memory: a decoder in a control loop whose device memory is
+ * fixed at start-up, a plugin whose host application owns every device
+ * allocation, or a latency-critical caller that cannot risk the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.  The paper has no
+ * counterpart; it is the same computation as toric3d_flip.  The scratch
+ * syndrome copy lives in a 32 MiB array inside the library (held on every GPU
+ * that loads the library until the process exits), so this call allocates
+ * nothing.  It rejects (T3D_EINVAL) any L, words with 3 L^3 * words * 8 bytes
+ * above 32 MiB.  The first call on a device looks up the array's address with
+ * that device current; make it before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race, so order them.  Nothing in
+ * the array needs clearing between calls.
+ */
+t3d_status toric3d_flip_noalloc(int L, int64_t words, uint64_t* e, uint64_t* s, int sweeps,
+                                t3d_stream stream);
+
+/*
  * flip + p-flip on a schedule (Sec. 3.2 p-flip rule and schedule list,
  * Table 1 footnote, Sec. 4.2): n_apply synchronous applications whose kinds
  * cycle through `schedule`, a host string over {'F','P'} of length 1..63.  A

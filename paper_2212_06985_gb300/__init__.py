@@ -30,7 +30,7 @@ __all__ = [
     "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "KERNEL_KINDS",
     "EXPORTED_SYMBOLS", "replica_sample0", "BatchItem", "make_batch", "toric3d_run_batch",
     "toric3d_run_batch_workspace_bytes", "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm",
-    "toric3d_autotune_batch",
+    "toric3d_autotune_batch", "toric3d_flip_noalloc",
 ]
 
 EXPORTED_SYMBOLS = [
@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = [
     "toric3d_logical", "toric3d_pack", "toric3d_unpack", "toric3d_run_workspace_bytes",
     "toric3d_run_cycles", "toric3d_run_batch_workspace_bytes", "toric3d_run_batch",
     "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm", "toric3d_autotune_batch",
-    "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read",
+    "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "toric3d_flip_noalloc",
 ]
 
 KERNEL_KINDS = {"noise": 0, "syndrome": 1, "flip": 2, "pflip": 3, "bp_step": 4, "bp_decide": 5,
@@ -119,6 +119,7 @@ def _declare(h):
         "toric3d_syndrome": (i32, [i32, i64, _P, _P, dbl, u64, u64, u32, _P]),
         "toric3d_flip_workspace_bytes": (sz, [i32, i64]),
         "toric3d_flip": (i32, [i32, i64, _P, _P, i32, _P, sz, _P]),
+        "toric3d_flip_noalloc": (i32, [i32, i64, _P, _P, i32, _P]),
         "toric3d_pflip": (i32, [i32, i64, _P, _P, ctypes.c_char_p, i32, u32, u64, u64, u32, _P, sz, _P]),
         "toric3d_bp_message_bytes": (sz, [i32, i64]),
         "toric3d_bp_step": (i32, [i32, i64, _P, dbl, dbl, _P, _P, _P]),
@@ -217,6 +218,12 @@ def toric3d_syndrome(L, e, s, q, seed, sample0, cycle, stream=None):
 def toric3d_flip(L, e, s, sweeps, work, stream=None):
     _check(lib().toric3d_flip(L, e.shape[-1], _ptr(e), _ptr(s), sweeps, _ptr(work),
                               work.numel() * work.element_size(), _stream(stream)))
+
+
+def toric3d_flip_noalloc(L, e, s, sweeps, stream=None):
+    """toric3d_flip with the library's built-in 32 MiB scratch instead of a
+    caller workspace (no device allocation anywhere in the call)."""
+    _check(lib().toric3d_flip_noalloc(L, e.shape[-1], _ptr(e), _ptr(s), sweeps, _stream(stream)))
 
 
 def toric3d_pflip(L, e, s, schedule, n_apply, sweep0, seed, sample0, cycle, work, stream=None):
