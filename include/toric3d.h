@@ -130,10 +130,11 @@ t3d_status toric3d_pflip(int L, int64_t words, uint64_t* e, uint64_t* s, const c
                          uint32_t cycle, void* work, size_t work_bytes, t3d_stream stream);
 
 /*
- * Belief propagation messages.  Samples are processed in groups of 32
- * (sample 32g + lane).  A message buffer for n samples is
- * float[ceil(n/32)][L^3][3][4][32]: entry (g, site, d, k, lane) is the
- * check->variable message M_{f->v} into edge v = (d, site) from its k-th face.
+ * Belief propagation messages.  Samples are processed in rows of 64, the
+ * samples of one bit-sliced word.  A message buffer for n samples is
+ * float[ceil(n/64)][L^3][3][4][64]: entry (w, site, d, k, i) is the
+ * check->variable message M_{f->v} for sample 64w + i into edge v = (d, site)
+ * from its k-th face.
  * For an edge along axis a at r, with c0 < c1 the two other axes, its faces
  * are k = 0: normal 3-a-c0 at r; k = 1: that face at r - e_c0; k = 2: normal
  * 3-a-c1 at r; k = 3: that face at r - e_c1.
@@ -171,8 +172,9 @@ size_t toric3d_bp_workspace_bytes(int L, int64_t chunk_samples);
 /*
  * Local BP decoder (Sec. 4.1): `iters` flooding iterations from the priors,
  * then the hard decision applied to e and s.  Samples are processed in chunks
- * as large as the workspace allows (at least 32 samples must fit; see
- * toric3d_bp_workspace_bytes).  llr_out as for toric3d_bp_decide.
+ * of whole 64-sample words, as large as the workspace allows (at least one
+ * word must fit; see toric3d_bp_workspace_bytes).  llr_out as for
+ * toric3d_bp_decide; it needs a workspace for the whole batch.
  */
 t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p,
                       double q_meas, int iters, void* work, size_t work_bytes, float* llr_out,
@@ -248,7 +250,7 @@ t3d_status toric3d_run_cycles(const t3d_run_cfg* cfg, uint64_t* e, void* work, s
  * paper's multi-size threshold plots, Fig. 2, 6, 7).  Up to 8 independent
  * ensembles, each with its own L, sample range and state, advance through the
  * same cycles with the decoder settings of `cfg` (its L, n_samples and sample0
- * are ignored); every step is one persistent launch over all ensembles.  e,
+ * are ignored); every step is one launch over all ensembles.  e,
  * mask and counts8 of each item are as for toric3d_run_cycles.  BP chunks are
  * sized per item so the workspace holds one chunk of every item (rounds are
  * added until it does).

@@ -1,10 +1,12 @@
 // Product-sum belief propagation on the face Tanner graph of the 3D toric
 // code (Sec. 4.1 of arXiv:2212.06985, Eqs. 1-4), FP32, one sample per thread.
 //
-// Layout: a message buffer is float[groups][L^3][3][4][32]; entry
-// (g, site, d, k, lane) is M_{f->v} into edge v = (d, site) from its k-th face
-// (slot order of edge_faces()) for sample 32 g + lane.  A warp handles one
-// face for 32 samples, so every message access is a coalesced 128-byte row.
+// Layout: a message buffer is float[words][L^3][3][4][64]; entry
+// (w, site, d, k, i) is M_{f->v} into edge v = (d, site) from its k-th face
+// (slot order of edge_faces()) for sample 64 w + i -- the same 64 samples as
+// one word of the bit-sliced state.  A warp handles one site for 64 samples,
+// lane l holding samples 2l and 2l+1 as a float2, so every message access is
+// a coalesced 256-byte row.
 //
 // Check-node arithmetic.  For inputs x_i (variable->check messages) let
 // t_i = tanh(|x_i|/2) and d_i = 1 - t_i = 2 e^{-|x_i|} / (1 + e^{-|x_i|}).
@@ -29,9 +31,9 @@ namespace t3d {
 namespace {
 
 constexpr int kBpThreads = 256;
-constexpr int kLanes = 32;
+constexpr int kWord = 64;  // samples per message row (one bit-sliced word)
 constexpr float kMsgClamp = 30.0f;
-// Message offsets within one group, 3 L^3 * 128 floats, stay below 2^31.
+// Message offsets within one word-row block, 3 L^3 * 256 floats, stay below 2^31.
 constexpr int kMaxBpL = 128;
 
 struct TD {
@@ -125,15 +127,17 @@ __device__ __forceinline__ void check_node(const float x[4], bool s_neg, TD q, f
     }
 }
 
-// Work: per item, one warp per (site, group) of the current chunk handles the
-// three faces at that site (normals x, y, z); an item's local block lb covers
-// 8 consecutive sites of group lb / site_blocks, so sites vary fastest.  With r the site and e_a the unit steps, the faces' edges and the
-// slot each face occupies in its edges' face lists are (edge_faces order):
+// Work: per item, one warp per (site, word) of the current chunk handles the
+// three faces at that site (normals x, y, z) for the word's 64 samples; an
+// item's local block lb covers 8 consecutive sites of word lb / site_blocks,
+// so sites vary fastest.  With r the site and e_a the unit steps, the faces'
+// edges and the slot each face occupies in its edges' face lists are
+// (edge_faces order):
 //   face n=0: (y,r) slot 2, (y,r+e_z) slot 3, (z,r) slot 2, (z,r+e_y) slot 3
 //   face n=1: (x,r) slot 2, (x,r+e_z) slot 3, (z,r) slot 0, (z,r+e_x) slot 1
 //   face n=2: (x,r) slot 0, (x,r+e_y) slot 1, (y,r) slot 0, (y,r+e_x) slot 1
 struct SiteWarp {
-    int64_t g;
+    int64_t w;  // word (64-sample group) within the chunk
     int site;
     int nb[3];  // site + e_x, site + e_y, site + e_z (periodic)
 };
@@ -145,8 +149,8 @@ __host__ __device__ __forceinline__ int64_t site_blocks(int L3) { return (L3 + k
 __device__ __forceinline__ bool site_warp(const Lattice& lat, int64_t lb, SiteWarp& sw)
 {
     const int64_t sbn = site_blocks(lat.L3);
-    sw.g = lb / sbn;
-    const int site = (int)((lb - sw.g * sbn) * kWarpsPerBlock + (threadIdx.x >> 5));
+    sw.w = lb / sbn;
+    const int site = (int)((lb - sw.w * sbn) * kWarpsPerBlock + (threadIdx.x >> 5));
     if (site >= lat.L3) return false;
     sw.site = site;
     const Coord r = site_coord(lat, site);
@@ -157,167 +161,223 @@ __device__ __forceinline__ bool site_warp(const Lattice& lat, int64_t lb, SiteWa
     return true;
 }
 
-// Offset of edge (d, site)'s 4x32 message block within a group.
-__device__ __forceinline__ int msg_off(int site, int d) { return (site * 3 + d) * (4 * kLanes); }
-
-// The 32-sample half word of face (n, site)'s syndrome for group g.
-__device__ __forceinline__ uint32_t syndrome_half(const uint64_t* s, const Lattice& lat, int64_t W,
-                                                  int n, int site, int64_t g)
-{
-    const uint64_t w = s[((int64_t)n * lat.L3 + site) * W + (g >> 1)];
-    return (uint32_t)(w >> ((g & 1) * 32));
-}
+// Offset of edge (d, site)'s 4x64 message block within a word-row block.
+__device__ __forceinline__ int msg_off(int site, int d) { return (site * 3 + d) * (4 * kWord); }
 
 // Where an iteration takes the syndrome from: the caller's bit-sliced words
-// (kSynWords), the same and also a per-group copy for later iterations
-// (kSynWordsSave: uint4 per site and group, faces 0..2 in .x .y .z), or that
-// copy (kSynSaved), which puts the three faces' bits in one 16-byte load.
+// (kSynWords), the same and also a per-word copy for later iterations
+// (kSynWordsSave: the three faces' words of a site side by side), or that
+// copy (kSynSaved), which brings a site's syndrome in one 32-byte load.
 enum SynMode { kSynWords = 0, kSynWordsSave = 1, kSynSaved = 2 };
+
+struct __align__(32) Syn3 {
+    uint64_t f[4];  // faces 0..2, padding
+};
+
+// The two syndrome bits of this lane's samples (2 lane, 2 lane + 1).
+__device__ __forceinline__ bool sbit(uint64_t word, int lane, int j) { return (word >> (2 * lane + j)) & 1ULL; }
 
 // One flooding iteration for the three faces of a site: Eq. 3 (variable->check
 // inputs, each the prior plus the three messages of its edge other than the
 // face's own slot, which is not read) and Eq. 2 (check->variable) into msg_out.
-// msg_in == nullptr is the first iteration: every input is the prior l0.
+// msg_in == nullptr is the first iteration: every input is the prior l0, so
+// every output is (-1)^{s_f} m1 with m1 = 2 atanh(tq tanh(l0/2)^3) computed
+// once on the host, and the launch only writes.
 template <int kSyn>
-__global__ void __launch_bounds__(kBpThreads, 6)
-k_bp_step(const __grid_constant__ ItemTable tab, float l0, TD q)
+__global__ void __launch_bounds__(kBpThreads, 4)
+k_bp_step(const __grid_constant__ ItemTable tab, float l0, TD q, float m1)
 {
     for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
     const Lattice lat = d.lat;
     const int64_t W = d.W;
-    const uint64_t* __restrict__ s = d.s;
-    uint4* __restrict__ syn = d.syn;
-    const float* __restrict__ msg_in = d.msg_in;
-    float* __restrict__ msg_out = d.msg_out;
     SiteWarp sw;
     if (!site_warp(lat, lb, sw)) return;
     const int lane = threadIdx.x & 31;
-    uint4 sh;
+    Syn3* __restrict__ syn = reinterpret_cast<Syn3*>(d.syn);
+    uint64_t s0, s1, s2;
     if (kSyn == kSynSaved) {
-        sh = syn[sw.g * lat.L3 + sw.site];
+        const Syn3 v = syn[sw.w * lat.L3 + sw.site];
+        s0 = v.f[0];
+        s1 = v.f[1];
+        s2 = v.f[2];
     } else {
-        sh.x = syndrome_half(s, lat, W, 0, sw.site, sw.g);
-        sh.y = syndrome_half(s, lat, W, 1, sw.site, sw.g);
-        sh.z = syndrome_half(s, lat, W, 2, sw.site, sw.g);
-        sh.w = 0;
-        if (kSyn == kSynWordsSave && lane == 0) syn[sw.g * lat.L3 + sw.site] = sh;
+        s0 = d.s[((int64_t)0 * lat.L3 + sw.site) * W + sw.w];
+        s1 = d.s[((int64_t)1 * lat.L3 + sw.site) * W + sw.w];
+        s2 = d.s[((int64_t)2 * lat.L3 + sw.site) * W + sw.w];
+        if (kSyn == kSynWordsSave && lane == 0) {
+            Syn3 v;
+            v.f[0] = s0;
+            v.f[1] = s1;
+            v.f[2] = s2;
+            v.f[3] = 0;
+            syn[sw.w * lat.L3 + sw.site] = v;
+        }
     }
-    const int64_t gbase = sw.g * (int64_t)lat.L3 * (3 * 4 * kLanes) + lane;
+    const int64_t wbase = sw.w * (int64_t)lat.L3 * (3 * 4 * kWord) + 2 * lane;
     const int r = sw.site, rx = sw.nb[0], ry = sw.nb[1], rz = sw.nb[2];
     // message blocks: edges at r (x, y, z) and the six neighbours used
     const int oXr = msg_off(r, 0), oYr = msg_off(r, 1), oZr = msg_off(r, 2);
     const int oXy = msg_off(ry, 0), oXz = msg_off(rz, 0);
     const int oYx = msg_off(rx, 1), oYz = msg_off(rz, 1);
     const int oZx = msg_off(rx, 2), oZy = msg_off(ry, 2);
-    // inputs x[face][edge] in face_edges order
-    float in0[4], in1[4], in2[4];
-    if (msg_in) {
-        const float* m = msg_in + gbase;
-#define MSG(o, k) m[(o) + (k) * kLanes]
-        const float xr0 = MSG(oXr, 0), xr1 = MSG(oXr, 1), xr2 = MSG(oXr, 2), xr3 = MSG(oXr, 3);
-        const float yr0 = MSG(oYr, 0), yr1 = MSG(oYr, 1), yr2 = MSG(oYr, 2), yr3 = MSG(oYr, 3);
-        const float zr0 = MSG(oZr, 0), zr1 = MSG(oZr, 1), zr2 = MSG(oZr, 2), zr3 = MSG(oZr, 3);
-        const float xs = l0 + xr1 + xr3, ys = l0 + yr1 + yr3, zs = l0 + zr1 + zr3;
-        // face 0: (y,r) excl 2, (y,r+z) excl 3, (z,r) excl 2, (z,r+y) excl 3
-        in0[0] = ys + yr0;
-        in0[1] = l0 + MSG(oYz, 0) + MSG(oYz, 1) + MSG(oYz, 2);
-        in0[2] = zs + zr0;
-        in0[3] = l0 + MSG(oZy, 0) + MSG(oZy, 1) + MSG(oZy, 2);
-        // face 1: (x,r) excl 2, (x,r+z) excl 3, (z,r) excl 0, (z,r+x) excl 1
-        in1[0] = xs + xr0;
-        in1[1] = l0 + MSG(oXz, 0) + MSG(oXz, 1) + MSG(oXz, 2);
-        in1[2] = zs + zr2;
-        in1[3] = l0 + MSG(oZx, 0) + MSG(oZx, 2) + MSG(oZx, 3);
-        // face 2: (x,r) excl 0, (x,r+y) excl 1, (y,r) excl 0, (y,r+x) excl 1
-        in2[0] = xs + xr2;
-        in2[1] = l0 + MSG(oXy, 0) + MSG(oXy, 2) + MSG(oXy, 3);
-        in2[2] = ys + yr2;
-        in2[3] = l0 + MSG(oYx, 0) + MSG(oYx, 2) + MSG(oYx, 3);
-#undef MSG
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) in0[j] = in1[j] = in2[j] = l0;
+    if (!d.msg_in) {
+        float* o = d.msg_out + wbase;
+        auto PUT1 = [&](int off, uint64_t sw) {
+            const float a = sbit(sw, lane, 0) ? -m1 : m1, b = sbit(sw, lane, 1) ? -m1 : m1;
+            __stcs(reinterpret_cast<float2*>(o + off), make_float2(a, b));
+        };
+        PUT1(oYr + 2 * kWord, s0);
+        PUT1(oYz + 3 * kWord, s0);
+        PUT1(oZr + 2 * kWord, s0);
+        PUT1(oZy + 3 * kWord, s0);
+        PUT1(oXr + 2 * kWord, s1);
+        PUT1(oXz + 3 * kWord, s1);
+        PUT1(oZr + 0 * kWord, s1);
+        PUT1(oZx + 1 * kWord, s1);
+        PUT1(oXr + 0 * kWord, s2);
+        PUT1(oXy + 1 * kWord, s2);
+        PUT1(oYr + 0 * kWord, s2);
+        PUT1(oYx + 1 * kWord, s2);
+        return;
     }
-    float y[4];
-    float* o = msg_out + gbase;
+    // inputs [sample j][face][edge], edges in face_edges order
+    float in[2][3][4];
+    {
+        const float* m = d.msg_in + wbase;
+        auto M = [&](int o, int k) { return *reinterpret_cast<const float2*>(m + o + k * kWord); };
+        const float2 xr0 = M(oXr, 0), xr1 = M(oXr, 1), xr2 = M(oXr, 2), xr3 = M(oXr, 3);
+        const float2 yr0 = M(oYr, 0), yr1 = M(oYr, 1), yr2 = M(oYr, 2), yr3 = M(oYr, 3);
+        const float2 zr0 = M(oZr, 0), zr1 = M(oZr, 1), zr2 = M(oZr, 2), zr3 = M(oZr, 3);
+        const float2 yz0 = M(oYz, 0), yz1 = M(oYz, 1), yz2 = M(oYz, 2);
+        const float2 zy0 = M(oZy, 0), zy1 = M(oZy, 1), zy2 = M(oZy, 2);
+        const float2 xz0 = M(oXz, 0), xz1 = M(oXz, 1), xz2 = M(oXz, 2);
+        const float2 zx0 = M(oZx, 0), zx2 = M(oZx, 2), zx3 = M(oZx, 3);
+        const float2 xy0 = M(oXy, 0), xy2 = M(oXy, 2), xy3 = M(oXy, 3);
+        const float2 yx0 = M(oYx, 0), yx2 = M(oYx, 2), yx3 = M(oYx, 3);
+#define INPUTS(c, j)                                                   \
+    {                                                                  \
+        const float xs = l0 + xr1.c + xr3.c, ys = l0 + yr1.c + yr3.c;  \
+        const float zs = l0 + zr1.c + zr3.c;                           \
+        /* face 0: (y,r) excl 2, (y,r+z) excl 3, (z,r) excl 2, (z,r+y) excl 3 */ \
+        in[j][0][0] = ys + yr0.c;                                      \
+        in[j][0][1] = l0 + yz0.c + yz1.c + yz2.c;                      \
+        in[j][0][2] = zs + zr0.c;                                      \
+        in[j][0][3] = l0 + zy0.c + zy1.c + zy2.c;                      \
+        /* face 1: (x,r) excl 2, (x,r+z) excl 3, (z,r) excl 0, (z,r+x) excl 1 */ \
+        in[j][1][0] = xs + xr0.c;                                      \
+        in[j][1][1] = l0 + xz0.c + xz1.c + xz2.c;                      \
+        in[j][1][2] = zs + zr2.c;                                      \
+        in[j][1][3] = l0 + zx0.c + zx2.c + zx3.c;                      \
+        /* face 2: (x,r) excl 0, (x,r+y) excl 1, (y,r) excl 0, (y,r+x) excl 1 */ \
+        in[j][2][0] = xs + xr2.c;                                      \
+        in[j][2][1] = l0 + xy0.c + xy2.c + xy3.c;                      \
+        in[j][2][2] = ys + yr2.c;                                      \
+        in[j][2][3] = l0 + yx0.c + yx2.c + yx3.c;                      \
+    }
+        INPUTS(x, 0)
+        INPUTS(y, 1)
+#undef INPUTS
+    }
+    float* o = d.msg_out + wbase;
     // the new messages are not read again in this launch: store them evict-first
-#define PUT(off, v) __stcs(o + (off), (v))
-    check_node(in0, (sh.x >> lane) & 1u, q, y);
-    PUT(oYr + 2 * kLanes, y[0]);
-    PUT(oYz + 3 * kLanes, y[1]);
-    PUT(oZr + 2 * kLanes, y[2]);
-    PUT(oZy + 3 * kLanes, y[3]);
-    check_node(in1, (sh.y >> lane) & 1u, q, y);
-    PUT(oXr + 2 * kLanes, y[0]);
-    PUT(oXz + 3 * kLanes, y[1]);
-    PUT(oZr + 0 * kLanes, y[2]);
-    PUT(oZx + 1 * kLanes, y[3]);
-    check_node(in2, (sh.z >> lane) & 1u, q, y);
-    PUT(oXr + 0 * kLanes, y[0]);
-    PUT(oXy + 1 * kLanes, y[1]);
-    PUT(oYr + 0 * kLanes, y[2]);
-    PUT(oYx + 1 * kLanes, y[3]);
-#undef PUT
+    auto PUT = [&](int off, float a, float b) { __stcs(reinterpret_cast<float2*>(o + off), make_float2(a, b)); };
+    float ya[4], yb[4];
+    check_node(in[0][0], sbit(s0, lane, 0), q, ya);
+    check_node(in[1][0], sbit(s0, lane, 1), q, yb);
+    PUT(oYr + 2 * kWord, ya[0], yb[0]);
+    PUT(oYz + 3 * kWord, ya[1], yb[1]);
+    PUT(oZr + 2 * kWord, ya[2], yb[2]);
+    PUT(oZy + 3 * kWord, ya[3], yb[3]);
+    check_node(in[0][1], sbit(s1, lane, 0), q, ya);
+    check_node(in[1][1], sbit(s1, lane, 1), q, yb);
+    PUT(oXr + 2 * kWord, ya[0], yb[0]);
+    PUT(oXz + 3 * kWord, ya[1], yb[1]);
+    PUT(oZr + 0 * kWord, ya[2], yb[2]);
+    PUT(oZx + 1 * kWord, ya[3], yb[3]);
+    check_node(in[0][2], sbit(s2, lane, 0), q, ya);
+    check_node(in[1][2], sbit(s2, lane, 1), q, yb);
+    PUT(oXr + 0 * kWord, ya[0], yb[0]);
+    PUT(oXy + 1 * kWord, ya[1], yb[1]);
+    PUT(oYr + 0 * kWord, ya[2], yb[2]);
+    PUT(oYx + 1 * kWord, ya[3], yb[3]);
     });
+}
+
+// 32 ballot bits b_l -> 64-bit word with b_l at bit 2l (the even bits).
+__device__ __forceinline__ uint64_t spread_even(uint32_t x)
+{
+    uint64_t v = x;
+    v = (v | (v << 16)) & 0x0000FFFF0000FFFFULL;
+    v = (v | (v << 8)) & 0x00FF00FF00FF00FFULL;
+    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0FULL;
+    v = (v | (v << 2)) & 0x3333333333333333ULL;
+    v = (v | (v << 1)) & 0x5555555555555555ULL;
+    return v;
 }
 
 // Eq. 4 posterior and the hard decision for the three edges at a site (the
 // edges this site's faces own): l = l0 + the four incoming messages, d = [l < 0].
 // The warp XORs d into e at r and, for each face at r, the parity of its four
-// edges' decisions into s (each 32-sample half word has exactly one writer).
+// edges' decisions into s (each 64-sample word has exactly one writer).
 __global__ void __launch_bounds__(kBpThreads)
 k_bp_decide(const __grid_constant__ ItemTable tab, float l0)
 {
     for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
     const Lattice lat = d.lat;
     const int64_t W = d.W;
-    const int64_t n_samples = d.n_samples;
-    const float* __restrict__ msg = d.msg_in;
-    uint32_t* __restrict__ e32 = reinterpret_cast<uint32_t*>(d.e);
-    uint32_t* __restrict__ s32 = reinterpret_cast<uint32_t*>(d.s);
-    float* __restrict__ llr_out = d.llr;
     SiteWarp sw;
     if (!site_warp(lat, lb, sw)) return;
     const int lane = threadIdx.x & 31;
-    const int64_t sample = sw.g * kLanes + lane;
-    const bool valid = sample < n_samples;
-    const int64_t gbase = sw.g * (int64_t)lat.L3 * (3 * 4 * kLanes) + lane;
-    auto post = [&](int site, int d) {
-        float l = l0;
-        if (msg) {
-            const float* m = msg + gbase + msg_off(site, d);
-            l += m[0];
-            l += m[kLanes];
-            l += m[2 * kLanes];
-            l += m[3 * kLanes];
+    const int64_t sample0 = sw.w * kWord + 2 * lane;
+    const bool valid0 = sample0 < d.n_samples, valid1 = sample0 + 1 < d.n_samples;
+    const int64_t wbase = sw.w * (int64_t)lat.L3 * (3 * 4 * kWord) + 2 * lane;
+    auto post = [&](int site, int dd) {
+        float2 l = make_float2(l0, l0);
+        if (d.msg_in) {
+            const float* m = d.msg_in + wbase + msg_off(site, dd);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 v = *reinterpret_cast<const float2*>(m + k * kWord);
+                l.x += v.x;
+                l.y += v.y;
+            }
         }
         return l;
     };
+    auto decide = [&](float2 l) {
+        const uint32_t b0 = __ballot_sync(0xffffffffu, valid0 && l.x < 0.0f);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, valid1 && l.y < 0.0f);
+        return spread_even(b0) | (spread_even(b1) << 1);
+    };
     const int r = sw.site;
-    float lr[3];
-    unsigned dr[3];
+    float2 lr[3];
+    uint64_t dr[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        lr[d] = post(r, d);
-        dr[d] = __ballot_sync(0xffffffffu, valid && lr[d] < 0.0f);
+    for (int dd = 0; dd < 3; ++dd) {
+        lr[dd] = post(r, dd);
+        dr[dd] = decide(lr[dd]);
     }
-    const unsigned dXy = __ballot_sync(0xffffffffu, valid && post(sw.nb[1], 0) < 0.0f);
-    const unsigned dXz = __ballot_sync(0xffffffffu, valid && post(sw.nb[2], 0) < 0.0f);
-    const unsigned dYx = __ballot_sync(0xffffffffu, valid && post(sw.nb[0], 1) < 0.0f);
-    const unsigned dYz = __ballot_sync(0xffffffffu, valid && post(sw.nb[2], 1) < 0.0f);
-    const unsigned dZx = __ballot_sync(0xffffffffu, valid && post(sw.nb[0], 2) < 0.0f);
-    const unsigned dZy = __ballot_sync(0xffffffffu, valid && post(sw.nb[1], 2) < 0.0f);
-    const unsigned par[3] = {dr[1] ^ dYz ^ dr[2] ^ dZy, dr[0] ^ dXz ^ dr[2] ^ dZx,
-                             dr[0] ^ dXy ^ dr[1] ^ dYx};
-    const int64_t half = 2 * (sw.g >> 1) + (sw.g & 1);
+    const uint64_t dXy = decide(post(sw.nb[1], 0)), dXz = decide(post(sw.nb[2], 0));
+    const uint64_t dYx = decide(post(sw.nb[0], 1)), dYz = decide(post(sw.nb[2], 1));
+    const uint64_t dZx = decide(post(sw.nb[0], 2)), dZy = decide(post(sw.nb[1], 2));
+    const uint64_t par0 = dr[1] ^ dYz ^ dr[2] ^ dZy;
+    const uint64_t par1 = dr[0] ^ dXz ^ dr[2] ^ dZx;
+    const uint64_t par2 = dr[0] ^ dXy ^ dr[1] ^ dYx;
     if (lane < 3) {
-        const int64_t idx = 2 * ((int64_t)lane * lat.L3 + r) * W + half;
-        if (par[lane]) s32[idx] ^= par[lane];
-        if (dr[lane]) e32[idx] ^= dr[lane];
+        // lane n writes face n's syndrome word and edge n's error word at r
+        const uint64_t par = lane == 0 ? par0 : (lane == 1 ? par1 : par2);
+        const uint64_t dec = lane == 0 ? dr[0] : (lane == 1 ? dr[1] : dr[2]);
+        const int64_t idx = ((int64_t)lane * lat.L3 + r) * W + sw.w;
+        if (par) d.s[idx] ^= par;
+        if (dec) d.e[idx] ^= dec;
     }
-    if (llr_out && valid) {
+    if (d.llr) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) llr_out[((int64_t)d * lat.L3 + r) * n_samples + sample] = lr[d];
+        for (int dd = 0; dd < 3; ++dd) {
+            float* row = d.llr + ((int64_t)dd * lat.L3 + r) * d.n_samples;
+            if (valid0) row[sample0] = lr[dd].x;
+            if (valid1) row[sample0 + 1] = lr[dd].y;
+        }
     }
     });
 }
@@ -335,12 +395,24 @@ TD meas_pair(double q_meas)
 
 float prior(double p) { return (float)std::log((1.0 - p) / p); }
 
-int64_t group_floats(int L) { return 3LL * L * L * L * 4 * kLanes; }
-int64_t group_syn(int L) { return (int64_t)L * L * L; }  // uint4 per site
+// First-iteration message magnitude (signed): 2 atanh(tq tanh(l0/2)^3), Eq. 2
+// with every input equal to the prior, clamped like every message.
+float first_message(double p, double q_meas)
+{
+    const double l0 = std::log((1.0 - p) / p);
+    const double tq = q_meas > 0.0 ? std::tanh(std::log((1.0 - q_meas) / q_meas) / 2.0) : 1.0;
+    const double t0 = std::tanh(l0 / 2.0);
+    double m = 2.0 * std::atanh(std::max(-1.0 + 1e-15, std::min(1.0 - 1e-15, tq * t0 * t0 * t0)));
+    m = std::max(-30.0, std::min(30.0, m));
+    return (float)m;
+}
+
+int64_t word_floats(int L) { return 3LL * L * L * L * 4 * kWord; }
+int64_t word_syn_bytes(int L) { return (int64_t)L * L * L * (int64_t)sizeof(Syn3); }
 
 void set_blocks(ItemTable& tab)
 {
-    for (int i = 0; i < tab.n; ++i) tab.it[i].blocks = site_blocks(tab.it[i].lat.L3) * tab.it[i].groups;
+    for (int i = 0; i < tab.n; ++i) tab.it[i].blocks = site_blocks(tab.it[i].lat.L3) * tab.it[i].words;
     finish_table(tab);
 }
 
@@ -352,15 +424,15 @@ t3d_status launch_step(ItemTable& tab, int mode, double p, double q_meas, cudaSt
     if (mode == kSynWordsSave)
         k_bp_step<kSynWordsSave><<<persistent_grid((const void*)k_bp_step<kSynWordsSave>, kBpThreads,
                                                    T3D_K_BP_STEP, blocks),
-                                   kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas));
+                                   kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas), first_message(p, q_meas));
     else if (mode == kSynSaved)
         k_bp_step<kSynSaved><<<persistent_grid((const void*)k_bp_step<kSynSaved>, kBpThreads, T3D_K_BP_STEP,
                                                blocks),
-                               kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas));
+                               kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas), first_message(p, q_meas));
     else
         k_bp_step<kSynWords><<<persistent_grid((const void*)k_bp_step<kSynWords>, kBpThreads, T3D_K_BP_STEP,
                                                blocks),
-                               kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas));
+                               kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas), first_message(p, q_meas));
     T3D_LAUNCH_CHECK("bp step");
     return T3D_OK;
 }
@@ -377,55 +449,52 @@ t3d_status launch_decide(ItemTable& tab, double p, cudaStream_t st)
 
 }  // namespace
 
-size_t bp_bytes_per_group(int L)
+size_t bp_bytes_per_word(int L)
 {
-    return 2 * (size_t)group_floats(L) * sizeof(float) + (size_t)group_syn(L) * sizeof(uint4);
+    return 2 * (size_t)word_floats(L) * sizeof(float) + (size_t)word_syn_bytes(L);
 }
 
-// Chunks of chunk_groups groups; buf holds two chunk-sized message buffers
-// followed by the chunk's saved syndrome words.
-// The s/e words of chunk c start at group c*chunk_groups, so the kernels see
-// the chunk's slice of the arrays through offset pointers and a local group
-// count (groups are aligned to 64-sample words when chunk_groups is even).
+// Chunks of chunk_words 64-sample words; an item's buffer holds two
+// chunk-sized message buffers followed by the chunk's saved syndrome words.
+// The kernels see a chunk's slice of e and s through offset pointers (the row
+// stride W stays the whole batch's).
 namespace {
 
-// Items' round-r chunks (items with no groups left are dropped); A and B are
-// each chunk's two message buffers.
-int64_t bp_rounds(const ItemTable& items, const int64_t* chunk_groups)
+int64_t bp_rounds(const ItemTable& items, const int64_t* chunk_words)
 {
     int64_t rounds = 0;
     for (int i = 0; i < items.n; ++i) {
-        const int64_t G = groups_for(items.it[i].n_samples);
-        rounds = std::max(rounds, (G + chunk_groups[i] - 1) / chunk_groups[i]);
+        const int64_t W = items.it[i].W;
+        rounds = std::max(rounds, (W + chunk_words[i] - 1) / chunk_words[i]);
     }
     return rounds;
 }
 
-ItemTable chunk_table(const ItemTable& items, float* const* bufs, const int64_t* chunk_groups, int64_t r,
+// Items' round-r chunks (items with no words left are dropped); A and B are
+// each chunk's two message buffers.
+ItemTable chunk_table(const ItemTable& items, float* const* bufs, const int64_t* chunk_words, int64_t r,
                       float* llr_out, float** A, float** B)
 {
     ItemTable tab;
     std::memset(&tab, 0, sizeof(tab));
     for (int i = 0; i < items.n; ++i) {
         const ItemDesc& src = items.it[i];
-        const int64_t G = groups_for(src.n_samples);
-        const int64_t g0 = r * chunk_groups[i];
-        if (g0 >= G) continue;
-        const int64_t gc = std::min(chunk_groups[i], G - g0);
-        const int64_t w0 = g0 / 2;  // chunks start on 64-sample words (even g0)
+        const int64_t w0 = r * chunk_words[i];
+        if (w0 >= src.W) continue;
+        const int64_t wc = std::min(chunk_words[i], src.W - w0);
         const int k = tab.n++;
         ItemDesc& d = tab.it[k];
         d = src;
         d.e = src.e + w0;
         d.s = src.s + w0;
-        d.g0 = g0;
-        d.groups = gc;
-        d.n_samples = std::min<int64_t>(gc * kLanes, src.n_samples - g0 * kLanes);
-        const int64_t fl = chunk_groups[i] * group_floats(src.lat.L);
+        d.w0 = w0;
+        d.words = wc;
+        d.n_samples = std::min<int64_t>(wc * kWord, src.n_samples - w0 * kWord);
+        const int64_t fl = chunk_words[i] * word_floats(src.lat.L);
         A[k] = bufs[i];
         B[k] = bufs[i] + fl;
         d.syn = reinterpret_cast<uint4*>(bufs[i] + 2 * fl);
-        d.llr = (llr_out && items.n == 1) ? llr_out + g0 * kLanes : nullptr;
+        d.llr = (llr_out && items.n == 1) ? llr_out + w0 * kWord : nullptr;
     }
     return tab;
 }
@@ -433,14 +502,14 @@ ItemTable chunk_table(const ItemTable& items, float* const* bufs, const int64_t*
 }  // namespace
 
 t3d_status launch_bp(const ItemTable& items, double p, double q_meas, int iters, float* const* bufs,
-                     const int64_t* chunk_groups, float* llr_out, cudaStream_t st)
+                     const int64_t* chunk_words, float* llr_out, cudaStream_t st)
 {
-    // in round r item i processes groups [r*chunk_i, (r+1)*chunk_i)
-    const int64_t rounds = bp_rounds(items, chunk_groups);
+    // in round r item i processes words [r*chunk_i, (r+1)*chunk_i)
+    const int64_t rounds = bp_rounds(items, chunk_words);
     for (int64_t r = 0; r < rounds; ++r) {
         float* A[kMaxItems];
         float* B[kMaxItems];
-        ItemTable tab = chunk_table(items, bufs, chunk_groups, r, llr_out, A, B);
+        ItemTable tab = chunk_table(items, bufs, chunk_words, r, llr_out, A, B);
         for (int it = 0; it < iters; ++it) {
             for (int k = 0; k < tab.n; ++k) {
                 tab.it[k].msg_in = it == 0 ? nullptr : B[k];
@@ -456,11 +525,11 @@ t3d_status launch_bp(const ItemTable& items, double p, double q_meas, int iters,
 }
 
 t3d_status autotune_bp(const ItemTable& items, double p, double q_meas, float* const* bufs,
-                       const int64_t* chunk_groups, cudaStream_t st, int* best_cap, float* best_ms)
+                       const int64_t* chunk_words, cudaStream_t st, int* best_cap, float* best_ms)
 {
     float* A[kMaxItems];
     float* B[kMaxItems];
-    ItemTable tab = chunk_table(items, bufs, chunk_groups, 0, nullptr, A, B);
+    ItemTable tab = chunk_table(items, bufs, chunk_words, 0, nullptr, A, B);
     for (int k = 0; k < tab.n; ++k) {
         tab.it[k].msg_in = nullptr;
         tab.it[k].msg_out = A[k];
@@ -511,15 +580,13 @@ using namespace t3d;
 extern "C" size_t toric3d_bp_message_bytes(int L, int64_t n_samples)
 {
     if (L < 2 || L > kMaxL || n_samples < 1) return 0;
-    return (size_t)groups_for(n_samples) * (size_t)group_floats(L) * sizeof(float);
+    return (size_t)words_for(n_samples) * (size_t)word_floats(L) * sizeof(float);
 }
 
 extern "C" size_t toric3d_bp_workspace_bytes(int L, int64_t chunk_samples)
 {
     if (L < 2 || L > kMaxL || chunk_samples < 1) return 0;
-    int64_t g = groups_for(chunk_samples);
-    g += g & 1;  // chunks hold whole 64-sample words
-    return (size_t)g * bp_bytes_per_group(L);
+    return (size_t)words_for(chunk_samples) * bp_bytes_per_word(L);
 }
 
 static t3d_status bp_common_checks(int L, int64_t n_samples, double p, double q_meas)
@@ -552,7 +619,7 @@ extern "C" t3d_status toric3d_bp_step(int L, int64_t n_samples, const uint64_t* 
     d.s = const_cast<uint64_t*>(s);
     d.msg_in = const_cast<float*>(msg_in);
     d.msg_out = msg_out;
-    d.groups = groups_for(n_samples);
+    d.words = words_for(n_samples);
     return launch_step(tab, kSynWords, p, q_meas, as_stream(stream));
 }
 
@@ -577,7 +644,7 @@ extern "C" t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* m
     d.s = s;
     d.msg_in = const_cast<float*>(msg);
     d.llr = llr_out;
-    d.groups = groups_for(n_samples);
+    d.words = words_for(n_samples);
     return launch_decide(tab, p, as_stream(stream));
 }
 
@@ -591,9 +658,8 @@ extern "C" t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t
     T3D_TRY(check_words(s, "s"));
     T3D_REQUIRE(iters >= 0, "iters must be >= 0");
     T3D_REQUIRE(work != nullptr && aligned(work, 16), "work must be a 16-byte aligned device pointer");
-    int64_t chunk = (int64_t)(work_bytes / bp_bytes_per_group(L));
-    const int64_t G = groups_for(n_samples);
-    if (chunk < G) chunk &= ~1LL;  // partial chunks must cover whole 64-sample words
+    int64_t chunk = (int64_t)(work_bytes / bp_bytes_per_word(L));
+    const int64_t G = words_for(n_samples);
     T3D_REQUIRE(chunk >= 1, "workspace too small: %zu bytes, need at least %zu", work_bytes,
                 toric3d_bp_workspace_bytes(L, 64));
     chunk = std::min(chunk, G);

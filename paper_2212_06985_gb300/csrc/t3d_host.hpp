@@ -101,15 +101,15 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
                          uint32_t sweep0, uint64_t seed, uint32_t cycle, cudaStream_t st);
 t3d_status launch_logical(ItemTable& tab, cudaStream_t st);
 
-// Bytes of BP workspace per 32-sample group (two message buffers + syndrome copy).
-size_t bp_bytes_per_group(int L);
+// Bytes of BP workspace per 64-sample word (two message buffers + syndrome copy).
+size_t bp_bytes_per_word(int L);
 // BP over every item (e, s, n_samples, W of each); bufs[i] is item i's chunk
-// workspace holding chunk_groups[i] groups (even unless it covers the item).
+// workspace holding chunk_words[i] words.
 t3d_status launch_bp(const ItemTable& items, double p, double q_meas, int iters, float* const* bufs,
-                     const int64_t* chunk_groups, float* llr_out, cudaStream_t st);
+                     const int64_t* chunk_words, float* llr_out, cudaStream_t st);
 // Times the BP iteration on the items' first chunks under each blocks-per-SM
 // cap and keeps the fastest in the tuning table (synchronises the stream).
 t3d_status autotune_bp(const ItemTable& items, double p, double q_meas, float* const* bufs,
-                       const int64_t* chunk_groups, cudaStream_t st, int* best_cap, float* best_ms);
+                       const int64_t* chunk_words, cudaStream_t st, int* best_cap, float* best_ms);
 
 }  // namespace t3d

@@ -27,12 +27,12 @@ struct ItemDesc {
     uint64_t* tmp;        // ping-pong syndrome for synchronous applications
     float* msg_in;        // BP messages of the current chunk (nullptr: priors)
     float* msg_out;
-    uint4* syn;           // BP per-group syndrome words of the current chunk
+    uint4* syn;           // BP per-word syndrome copy of the current chunk
     float* llr;           // optional posteriors [3L^3][n_samples]
     uint8_t* mask;
     unsigned long long* counts8;
-    int64_t g0;           // BP: first 32-sample group of the current chunk
-    int64_t groups;       // BP: groups in the current chunk
+    int64_t w0;           // BP: first 64-sample word of the current chunk
+    int64_t words;        // BP: words in the current chunk
     int tx;               // bit-sliced kernels: words per thread-block row (power of 2)
     int64_t blocks;       // thread blocks this item needs in the current launch
 };

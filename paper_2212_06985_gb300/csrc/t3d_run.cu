@@ -67,23 +67,20 @@ t3d_status validate_items(const t3d_run_cfg* c, const t3d_batch_item* items, int
     return T3D_OK;
 }
 
-// Groups per BP chunk for every item: all groups (one round) when the
-// workspace allows, else the fewest rounds that fit; chunks hold whole
-// 64-sample words unless they cover the item.
+// 64-sample words per BP chunk for every item: all words (one round) when the
+// workspace allows, else the fewest rounds that fit.
 bool bp_chunks(const t3d_run_cfg& c, const t3d_batch_item* items, int n, size_t avail, int64_t* chunk)
 {
-    int64_t max_groups = 0;
-    for (int i = 0; i < n; ++i) max_groups = std::max(max_groups, groups_for(items[i].n_samples));
-    for (int64_t rounds = 1; rounds <= max_groups; ++rounds) {
+    int64_t max_words = 0;
+    for (int i = 0; i < n; ++i) max_words = std::max(max_words, words_for(items[i].n_samples));
+    for (int64_t rounds = 1; rounds <= max_words; ++rounds) {
         size_t need = 0;
         for (int i = 0; i < n; ++i) {
-            const int64_t G = groups_for(items[i].n_samples);
-            int64_t g = (G + rounds - 1) / rounds;
-            if (c.bp_chunk_samples > 0) g = std::min(g, groups_for(c.bp_chunk_samples));
-            if (g < G) g = std::max<int64_t>(2, g + (g & 1));
-            g = std::min(g, G);
-            chunk[i] = g;
-            need += round_up((size_t)g * bp_bytes_per_group(items[i].L));
+            const int64_t Wi = words_for(items[i].n_samples);
+            int64_t w = (Wi + rounds - 1) / rounds;
+            if (c.bp_chunk_samples > 0) w = std::min(w, words_for(c.bp_chunk_samples));
+            chunk[i] = w;
+            need += round_up((size_t)w * bp_bytes_per_word(items[i].L));
         }
         if (need <= avail) return true;
     }
@@ -96,11 +93,9 @@ size_t batch_workspace_bytes(const t3d_run_cfg& c, const t3d_batch_item* items, 
     for (int i = 0; i < n; ++i) total += 2 * round_up(state_bytes(items[i].L, items[i].n_samples));
     if (c.use_bp && c.bp_iters > 0) {
         for (int i = 0; i < n; ++i) {
-            const int64_t G = groups_for(items[i].n_samples);
-            int64_t g = c.bp_chunk_samples > 0 ? std::min(G, groups_for(c.bp_chunk_samples)) : G;
-            if (g < G) g = std::max<int64_t>(2, g + (g & 1));
-            g = std::min(g, G);
-            total += round_up((size_t)g * bp_bytes_per_group(items[i].L));
+            const int64_t Wi = words_for(items[i].n_samples);
+            const int64_t w = c.bp_chunk_samples > 0 ? std::min(Wi, words_for(c.bp_chunk_samples)) : Wi;
+            total += round_up((size_t)w * bp_bytes_per_word(items[i].L));
         }
     }
     return total;
@@ -133,10 +128,10 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
         T3D_REQUIRE(bp_chunks(c, items, n, work_bytes - used, pl.chunk), "workspace too small for BP chunks");
         for (int i = 0; i < n; ++i) {
             pl.bp[i] = reinterpret_cast<float*>(base + used);
-            used += round_up((size_t)pl.chunk[i] * bp_bytes_per_group(items[i].L));
+            used += round_up((size_t)pl.chunk[i] * bp_bytes_per_word(items[i].L));
         }
     } else if (c.use_bp) {
-        for (int i = 0; i < n; ++i) pl.chunk[i] = std::max<int64_t>(1, groups_for(items[i].n_samples));
+        for (int i = 0; i < n; ++i) pl.chunk[i] = std::max<int64_t>(1, words_for(items[i].n_samples));
     }
     return T3D_OK;
 }

@@ -31,8 +31,8 @@ def workspace(nbytes: int) -> torch.Tensor:
 
 def message_index(L: int, face_edges) -> np.ndarray:
     """For every oracle Tanner edge 4f + j (face f -> its j-th edge in the
-    oracle's face order), the flat offset within one 32-sample group of the
-    library's message buffer float[groups][L^3][3][4][32] (lane 0)."""
+    oracle's face order), the flat offset within one 64-sample word row of the
+    library's message buffer float[words][L^3][3][4][64] (sample 0 of the row)."""
     L3 = L ** 3
     n = 3 * L3
     out = np.zeros(4 * n, dtype=np.int64)
@@ -43,15 +43,15 @@ def message_index(L: int, face_edges) -> np.ndarray:
         for j in range(4):
             v = int(face_edges[f][j])
             d, site = v // L3, v % L3
-            out[4 * f + j] = ((site * 3 + d) * 4 + slots[j]) * 32
+            out[4 * f + j] = ((site * 3 + d) * 4 + slots[j]) * 64
     return out
 
 
 def gpu_messages_to_oracle(msg: torch.Tensor, L: int, n_samples: int, idx: np.ndarray) -> np.ndarray:
     """Library message buffer -> [S][4*3L^3] float64 in oracle Tanner-edge order."""
-    per_group = 3 * L ** 3 * 4 * 32
-    m = msg.detach().cpu().numpy().astype(np.float64).reshape(-1, per_group)
+    per_word = 3 * L ** 3 * 4 * 64
+    m = msg.detach().cpu().numpy().astype(np.float64).reshape(-1, per_word)
     out = np.empty((n_samples, len(idx)))
     for s in range(n_samples):
-        out[s] = m[s // 32, idx + (s % 32)]
+        out[s] = m[s // 64, idx + (s % 64)]
     return out

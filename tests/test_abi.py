@@ -37,8 +37,8 @@ def test_workspace_sizes():
     L, W = 4, 157
     assert t3d.toric3d_flip_workspace_bytes(L, W) == 3 * 64 * W * 8
     assert t3d.toric3d_flip_workspace_bytes(1, W) == 0
-    assert t3d.toric3d_bp_message_bytes(4, 100) == 4 * 3 * 64 * 4 * 32 * 4
-    assert t3d.toric3d_bp_workspace_bytes(4, 100) == 4 * (2 * 3 * 64 * 4 * 32 * 4 + 64 * 16)
+    assert t3d.toric3d_bp_message_bytes(4, 100) == 2 * 3 * 64 * 4 * 64 * 4
+    assert t3d.toric3d_bp_workspace_bytes(4, 100) == 2 * (2 * 3 * 64 * 4 * 64 * 4 + 64 * 32)
     cfg = t3d.make_run_cfg(4, 4, 0.01, 0.01, 0, 10_000, schedule="F", n_apply=32)
     assert t3d.toric3d_run_workspace_bytes(cfg) == 2 * ((3 * 64 * 157 * 8 + 255) // 256 * 256)
     bad = t3d.make_run_cfg(4, 4, 0.01, 0.01, 0, 10_000, schedule="FX", n_apply=2)

@@ -70,9 +70,9 @@ def test_batch_bp_chunk_rounds_are_invisible():
     specs = [(4, 1000, 0), (6, 700, 0)]
     full = _batch(kw, specs)
     cfg = t3d.make_run_cfg(8, 1, 0.04, 0.04, 5, 1, use_bp=True, bp_iters=6, schedule="PFFPFF", n_apply=6)
-    # just enough for the two states and one 64-sample chunk per item: many rounds
+    # just enough for the two states and one 64-sample word per item: many rounds
     tight = sum(2 * ((3 * L ** 3 * inp.words_for(S) * 8 + 255) // 256 * 256) for L, S, _ in specs)
-    tight += sum((2 * (2 * 3 * L ** 3 * 128 * 4 + L ** 3 * 16) + 255) // 256 * 256 for L, _, _ in specs)
+    tight += sum((2 * 3 * L ** 3 * 4 * 64 * 4 + L ** 3 * 32 + 255) // 256 * 256 for L, _, _ in specs)
     small = _batch(kw, specs, ws_bytes=tight)
     for a, b in zip(full, small):
         assert all(np.array_equal(x, y) for x, y in zip(a, b))

@@ -125,7 +125,7 @@ def test_bp_chunking_is_invisible():
     L, S, p = 4, 300, 0.04
     ebits, sbits = _noisy_syndromes(L, S, p, p, seed=9)
     outs = []
-    for chunk in (64, 128, S):
+    for chunk in (64, 128, 192, S):
         e, s = upload_bits(ebits), upload_bits(sbits)
         t3d.toric3d_bp(L, S, e, s, p, p, 12, workspace(t3d.toric3d_bp_workspace_bytes(L, chunk)))
         outs.append((download_bits(e, S), download_bits(s, S)))
