@@ -161,10 +161,13 @@ t3d_status toric3d_bp_step(int L, int64_t n_samples, const uint64_t* s, double p
  * BP hard decision (Sec. 4.1, after Eq. 4): posterior l_v = l0 + sum of the
  * four incoming messages (msg NULL: l_v = l0); every qubit with l_v < 0 is
  * corrected, e ^= d and s ^= H d.  llr_out (nullable) receives l_v as
- * float[3L^3][n_samples].
+ * float[3L^3][n_samples].  work: >= toric3d_bp_decide_workspace_bytes(L,
+ * n_samples) bytes of 32-byte aligned device scratch for the decision words.
  */
+size_t toric3d_bp_decide_workspace_bytes(int L, int64_t n_samples);
 t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* msg, double p, uint64_t* e,
-                             uint64_t* s, float* llr_out, t3d_stream stream);
+                             uint64_t* s, float* llr_out, void* work, size_t work_bytes,
+                             t3d_stream stream);
 
 /* Workspace for toric3d_bp processing `chunk_samples` samples at a time. */
 size_t toric3d_bp_workspace_bytes(int L, int64_t chunk_samples);

@@ -23,7 +23,7 @@ from . import build as _build
 __all__ = [
     "T3DError", "RunCfg", "lib", "n_bits", "words_for", "table1_schedule",
     "toric3d_noise", "toric3d_syndrome", "toric3d_flip", "toric3d_pflip",
-    "toric3d_bp_step", "toric3d_bp_decide", "toric3d_bp", "toric3d_logical",
+    "toric3d_bp_step", "toric3d_bp_decide", "toric3d_bp_decide_workspace_bytes", "toric3d_bp", "toric3d_logical",
     "toric3d_pack", "toric3d_unpack", "toric3d_run_cycles",
     "toric3d_flip_workspace_bytes", "toric3d_bp_message_bytes",
     "toric3d_bp_workspace_bytes", "toric3d_run_workspace_bytes", "make_run_cfg",
@@ -36,7 +36,8 @@ __all__ = [
 EXPORTED_SYMBOLS = [
     "toric3d_last_error", "toric3d_abi_version", "toric3d_noise", "toric3d_syndrome",
     "toric3d_flip_workspace_bytes", "toric3d_flip", "toric3d_pflip", "toric3d_bp_message_bytes",
-    "toric3d_bp_step", "toric3d_bp_decide", "toric3d_bp_workspace_bytes", "toric3d_bp",
+    "toric3d_bp_step", "toric3d_bp_decide_workspace_bytes", "toric3d_bp_decide",
+    "toric3d_bp_workspace_bytes", "toric3d_bp",
     "toric3d_logical", "toric3d_pack", "toric3d_unpack", "toric3d_run_workspace_bytes",
     "toric3d_run_cycles", "toric3d_run_batch_workspace_bytes", "toric3d_run_batch",
     "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm", "toric3d_autotune_batch",
@@ -123,7 +124,8 @@ def _declare(h):
         "toric3d_pflip": (i32, [i32, i64, _P, _P, ctypes.c_char_p, i32, u32, u64, u64, u32, _P, sz, _P]),
         "toric3d_bp_message_bytes": (sz, [i32, i64]),
         "toric3d_bp_step": (i32, [i32, i64, _P, dbl, dbl, _P, _P, _P]),
-        "toric3d_bp_decide": (i32, [i32, i64, _P, dbl, _P, _P, _P, _P]),
+        "toric3d_bp_decide_workspace_bytes": (sz, [i32, i64]),
+        "toric3d_bp_decide": (i32, [i32, i64, _P, dbl, _P, _P, _P, _P, sz, _P]),
         "toric3d_bp_workspace_bytes": (sz, [i32, i64]),
         "toric3d_bp": (i32, [i32, i64, _P, _P, dbl, dbl, i32, _P, sz, _P, _P]),
         "toric3d_logical": (i32, [i32, i64, _P, _P, _P, _P]),
@@ -237,9 +239,14 @@ def toric3d_bp_step(L, n_samples, s, p, q_meas, msg_in, msg_out, stream=None):
                                  _ptr(msg_out), _stream(stream)))
 
 
-def toric3d_bp_decide(L, n_samples, msg, p, e, s, llr_out=None, stream=None):
+def toric3d_bp_decide_workspace_bytes(L: int, n_samples: int) -> int:
+    return int(lib().toric3d_bp_decide_workspace_bytes(L, n_samples))
+
+
+def toric3d_bp_decide(L, n_samples, msg, p, e, s, work, llr_out=None, stream=None):
     _check(lib().toric3d_bp_decide(L, n_samples, _ptr(msg), float(p), _ptr(e), _ptr(s),
-                                   _ptr(llr_out), _stream(stream)))
+                                   _ptr(llr_out), _ptr(work), work.numel() * work.element_size(),
+                                   _stream(stream)))
 
 
 def toric3d_bp(L, n_samples, e, s, p, q_meas, iters, work, llr_out=None, stream=None):

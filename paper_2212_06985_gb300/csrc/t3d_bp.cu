@@ -315,10 +315,11 @@ __device__ __forceinline__ uint64_t spread_even(uint32_t x)
     return v;
 }
 
-// Eq. 4 posterior and the hard decision for the three edges at a site (the
-// edges this site's faces own): l = l0 + the four incoming messages, d = [l < 0].
-// The warp XORs d into e at r and, for each face at r, the parity of its four
-// edges' decisions into s (each 64-sample word has exactly one writer).
+// Eq. 4 posterior and the hard decision, pass 1: for the three edges at a
+// site, l = l0 + the four incoming messages and d = [l < 0]; the warp XORs d
+// into e at the site (each 64-sample word has exactly one writer) and leaves
+// the three decision words in the chunk's syndrome-copy slot of the site,
+// which the iterations no longer need.  Every message is read once.
 __global__ void __launch_bounds__(kBpThreads)
 k_bp_decide(const __grid_constant__ ItemTable tab, float l0)
 {
@@ -331,54 +332,85 @@ k_bp_decide(const __grid_constant__ ItemTable tab, float l0)
     const int64_t sample0 = sw.w * kWord + 2 * lane;
     const bool valid0 = sample0 < d.n_samples, valid1 = sample0 + 1 < d.n_samples;
     const int64_t wbase = sw.w * (int64_t)lat.L3 * (3 * 4 * kWord) + 2 * lane;
-    auto post = [&](int site, int dd) {
-        float2 l = make_float2(l0, l0);
+    const int r = sw.site;
+    float2 l[3];
+    uint64_t dec[3];
+#pragma unroll
+    for (int dd = 0; dd < 3; ++dd) {
+        l[dd] = make_float2(l0, l0);
         if (d.msg_in) {
-            const float* m = d.msg_in + wbase + msg_off(site, dd);
+            const float* m = d.msg_in + wbase + msg_off(r, dd);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float2 v = *reinterpret_cast<const float2*>(m + k * kWord);
-                l.x += v.x;
-                l.y += v.y;
+                l[dd].x += v.x;
+                l[dd].y += v.y;
             }
         }
-        return l;
-    };
-    auto decide = [&](float2 l) {
-        const uint32_t b0 = __ballot_sync(0xffffffffu, valid0 && l.x < 0.0f);
-        const uint32_t b1 = __ballot_sync(0xffffffffu, valid1 && l.y < 0.0f);
-        return spread_even(b0) | (spread_even(b1) << 1);
-    };
-    const int r = sw.site;
-    float2 lr[3];
-    uint64_t dr[3];
-#pragma unroll
-    for (int dd = 0; dd < 3; ++dd) {
-        lr[dd] = post(r, dd);
-        dr[dd] = decide(lr[dd]);
+        const uint32_t b0 = __ballot_sync(0xffffffffu, valid0 && l[dd].x < 0.0f);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, valid1 && l[dd].y < 0.0f);
+        dec[dd] = spread_even(b0) | (spread_even(b1) << 1);
     }
-    const uint64_t dXy = decide(post(sw.nb[1], 0)), dXz = decide(post(sw.nb[2], 0));
-    const uint64_t dYx = decide(post(sw.nb[0], 1)), dYz = decide(post(sw.nb[2], 1));
-    const uint64_t dZx = decide(post(sw.nb[0], 2)), dZy = decide(post(sw.nb[1], 2));
-    const uint64_t par0 = dr[1] ^ dYz ^ dr[2] ^ dZy;
-    const uint64_t par1 = dr[0] ^ dXz ^ dr[2] ^ dZx;
-    const uint64_t par2 = dr[0] ^ dXy ^ dr[1] ^ dYx;
     if (lane < 3) {
-        // lane n writes face n's syndrome word and edge n's error word at r
-        const uint64_t par = lane == 0 ? par0 : (lane == 1 ? par1 : par2);
-        const uint64_t dec = lane == 0 ? dr[0] : (lane == 1 ? dr[1] : dr[2]);
-        const int64_t idx = ((int64_t)lane * lat.L3 + r) * W + sw.w;
-        if (par) d.s[idx] ^= par;
-        if (dec) d.e[idx] ^= dec;
+        const uint64_t v = lane == 0 ? dec[0] : (lane == 1 ? dec[1] : dec[2]);
+        if (v) d.e[((int64_t)lane * lat.L3 + r) * W + sw.w] ^= v;
+    }
+    if (lane == 0) {
+        Syn3 out;
+        out.f[0] = dec[0];
+        out.f[1] = dec[1];
+        out.f[2] = dec[2];
+        out.f[3] = 0;
+        reinterpret_cast<Syn3*>(d.syn)[sw.w * lat.L3 + r] = out;
     }
     if (d.llr) {
 #pragma unroll
         for (int dd = 0; dd < 3; ++dd) {
             float* row = d.llr + ((int64_t)dd * lat.L3 + r) * d.n_samples;
-            if (valid0) row[sample0] = lr[dd].x;
-            if (valid1) row[sample0 + 1] = lr[dd].y;
+            if (valid0) row[sample0] = l[dd].x;
+            if (valid1) row[sample0 + 1] = l[dd].y;
         }
     }
+    });
+}
+
+// Pass 2: s ^= H d.  One thread per (site, word); a warp covers 32 words of
+// one site, so the syndrome rows are read and written coalesced.  Face n at r
+// holds the edges listed at the top of this file, so its parity is
+//   n=0: d(y,r) ^ d(y,r+e_z) ^ d(z,r) ^ d(z,r+e_y)
+//   n=1: d(x,r) ^ d(x,r+e_z) ^ d(z,r) ^ d(z,r+e_x)
+//   n=2: d(x,r) ^ d(x,r+e_y) ^ d(y,r) ^ d(y,r+e_x).
+constexpr int kSynWordsPerRow = 32;
+constexpr int kSynSitesPerBlock = kBpThreads / kSynWordsPerRow;
+
+__host__ __device__ __forceinline__ int64_t syn_blocks(int L3, int64_t words)
+{
+    return ((L3 + kSynSitesPerBlock - 1) / kSynSitesPerBlock) *
+           ((words + kSynWordsPerRow - 1) / kSynWordsPerRow);
+}
+
+__global__ void __launch_bounds__(kBpThreads)
+k_bp_syndrome(const __grid_constant__ ItemTable tab)
+{
+    for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
+    const Lattice lat = d.lat;
+    const int64_t site_tiles = (lat.L3 + kSynSitesPerBlock - 1) / kSynSitesPerBlock;
+    const int64_t word_tile = lb / site_tiles;
+    const int r = (int)((lb - word_tile * site_tiles) * kSynSitesPerBlock + (threadIdx.x / kSynWordsPerRow));
+    const int64_t w = word_tile * kSynWordsPerRow + (threadIdx.x % kSynWordsPerRow);
+    if (r >= lat.L3 || w >= d.words) return;
+    const Coord rc = site_coord(lat, r);
+    const int step[3] = {1, lat.L, lat.L2};
+    int nb[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) nb[a] = r + ((rc.x[a] + 1 == lat.L) ? step[a] * (1 - lat.L) : step[a]);
+    const Syn3* D = reinterpret_cast<const Syn3*>(d.syn) + w * lat.L3;
+    const Syn3 dr = D[r], dx = D[nb[0]], dy = D[nb[1]], dz = D[nb[2]];
+    const uint64_t par[3] = {dr.f[1] ^ dz.f[1] ^ dr.f[2] ^ dy.f[2], dr.f[0] ^ dz.f[0] ^ dr.f[2] ^ dx.f[2],
+                             dr.f[0] ^ dy.f[0] ^ dr.f[1] ^ dx.f[1]};
+#pragma unroll
+    for (int n = 0; n < 3; ++n)
+        if (par[n]) d.s[((int64_t)n * lat.L3 + r) * d.W + w] ^= par[n];
     });
 }
 
@@ -440,10 +472,18 @@ t3d_status launch_step(ItemTable& tab, int mode, double p, double q_meas, cudaSt
 t3d_status launch_decide(ItemTable& tab, double p, cudaStream_t st)
 {
     set_blocks(tab);
+    {
+        ProfScope prof(T3D_K_BP_DECIDE, st);
+        k_bp_decide<<<persistent_grid((const void*)k_bp_decide, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n]),
+                      kBpThreads, 0, st>>>(tab, prior(p));
+        T3D_LAUNCH_CHECK("bp decide");
+    }
+    for (int i = 0; i < tab.n; ++i) tab.it[i].blocks = syn_blocks(tab.it[i].lat.L3, tab.it[i].words);
+    finish_table(tab);
     ProfScope prof(T3D_K_BP_DECIDE, st);
-    k_bp_decide<<<persistent_grid((const void*)k_bp_decide, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n]),
-                  kBpThreads, 0, st>>>(tab, prior(p));
-    T3D_LAUNCH_CHECK("bp decide");
+    k_bp_syndrome<<<persistent_grid((const void*)k_bp_syndrome, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n]),
+                    kBpThreads, 0, st>>>(tab);
+    T3D_LAUNCH_CHECK("bp syndrome update");
     return T3D_OK;
 }
 
@@ -623,9 +663,15 @@ extern "C" t3d_status toric3d_bp_step(int L, int64_t n_samples, const uint64_t* 
     return launch_step(tab, kSynWords, p, q_meas, as_stream(stream));
 }
 
+extern "C" size_t toric3d_bp_decide_workspace_bytes(int L, int64_t n_samples)
+{
+    if (L < 2 || L > kMaxL || n_samples < 1) return 0;
+    return (size_t)words_for(n_samples) * (size_t)word_syn_bytes(L);
+}
+
 extern "C" t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* msg, double p,
-                                        uint64_t* e, uint64_t* s, float* llr_out,
-                                        t3d_stream stream)
+                                        uint64_t* e, uint64_t* s, float* llr_out, void* work,
+                                        size_t work_bytes, t3d_stream stream)
 {
     clear_error();
     T3D_TRY(bp_common_checks(L, n_samples, p, 0.0));
@@ -633,6 +679,9 @@ extern "C" t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* m
     T3D_TRY(check_words(s, "s"));
     T3D_REQUIRE(msg == nullptr || aligned(msg, 16), "msg must be 16-byte aligned");
     T3D_REQUIRE(llr_out == nullptr || aligned(llr_out, 4), "llr_out must be 4-byte aligned");
+    T3D_REQUIRE(work != nullptr && aligned(work, 32), "work must be a 32-byte aligned device pointer");
+    T3D_REQUIRE(work_bytes >= toric3d_bp_decide_workspace_bytes(L, n_samples), "workspace too small: %zu < %zu",
+                work_bytes, toric3d_bp_decide_workspace_bytes(L, n_samples));
     ItemTable tab;
     std::memset(&tab, 0, sizeof(tab));
     tab.n = 1;
@@ -644,6 +693,7 @@ extern "C" t3d_status toric3d_bp_decide(int L, int64_t n_samples, const float* m
     d.s = s;
     d.msg_in = const_cast<float*>(msg);
     d.llr = llr_out;
+    d.syn = static_cast<uint4*>(work);
     d.words = words_for(n_samples);
     return launch_decide(tab, p, as_stream(stream));
 }

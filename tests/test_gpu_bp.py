@@ -138,8 +138,31 @@ def test_bp_decide_without_messages_uses_prior():
     n = 3 * L ** 3
     ebits = inp.random_bits(S, n, 0.2, 1)
     e, s = upload_bits(ebits), upload_bits(np.zeros_like(ebits))
-    t3d.toric3d_bp_decide(L, S, None, 0.3, e, s)     # l0 > 0: no correction
+    work = workspace(t3d.toric3d_bp_decide_workspace_bytes(L, S))
+    t3d.toric3d_bp_decide(L, S, None, 0.3, e, s, work)     # l0 > 0: no correction
     assert np.array_equal(download_bits(e, S), ebits)
-    t3d.toric3d_bp_decide(L, S, None, 0.7, e, s)     # l0 < 0: flip every qubit
+    t3d.toric3d_bp_decide(L, S, None, 0.7, e, s, work)     # l0 < 0: flip every qubit
     assert np.array_equal(download_bits(e, S), ebits ^ 1)
     assert download_bits(s, S).sum() == 0            # H applied to all-ones is zero (4 edges per face)
+
+
+def test_bp_decide_api_from_stepped_messages():
+    L, S, p, iters = 4, 150, 0.04, 5
+    ebits, sbits = _noisy_syndromes(L, S, p, p, seed=21)
+    e, s = upload_bits(ebits), upload_bits(sbits)
+    nfl = t3d.toric3d_bp_message_bytes(L, S) // 4
+    A = torch.zeros(nfl, dtype=torch.float32, device=dev())
+    B = torch.zeros_like(A)
+    t3d.toric3d_bp_step(L, S, s, p, p, None, A)
+    for _ in range(iters - 1):
+        t3d.toric3d_bp_step(L, S, s, p, p, A, B)
+        A, B = B, A
+    n = 3 * L ** 3
+    llr = torch.zeros((n, S), dtype=torch.float32, device=dev())
+    t3d.toric3d_bp_decide(L, S, A, p, e, s, workspace(t3d.toric3d_bp_decide_workspace_bytes(L, S)), llr)
+    g = llr.cpu().numpy().T.astype(np.float64)
+    _, ref = oracle.bp_batch(L, sbits, p, p, True, iters)
+    assert np.abs(g - ref).max() < 1e-3
+    d = (g < 0).astype(np.uint8)
+    assert np.array_equal(download_bits(e, S), ebits ^ d)
+    assert np.array_equal(download_bits(s, S), sbits ^ oracle.syndrome_batch(L, d))
