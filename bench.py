@@ -34,10 +34,12 @@ import toric3d_inputs as inp  # noqa: E402
 
 METRIC = "qubit-cycles decoded/s at L=32 p=4%: BP+p-flip"
 
-# DRAM bytes (read + write) per launch of the dominant kernel from an ncu
-# capture of the current kernel, scaled to a full launch by the units
-# processed (profiles/ has the capture); None until one exists.
-TRAFFIC = {}
+# DRAM bytes (read + write) per edge-sample of the dominant kernel from one
+# ncu capture of the current k_bp_step (L = 32, 1024 samples; traffic grows in
+# proportion to the samples a launch covers, so it scales to full launches):
+# profiles/k_bp_step_bp_pflip_L32_1024samples.md.  Set to None when the kernel
+# changes until it is captured again.
+BP_STEP_TRAFFIC = {"first_iteration": 15.72, "full_iteration": 31.94}
 UNIT = "qubit-cycles/s"
 
 
@@ -276,8 +278,12 @@ def cuda_arm(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / (bp_ms / 1e3) / 1e9 if bp_ms > 0 else 0.0
+    traffic = None
+    if BP_STEP_TRAFFIC and bp_launches:
+        traffic = qubits * S * args.steps * (BP_STEP_TRAFFIC["first_iteration"] +
+                                             BP_STEP_TRAFFIC["full_iteration"] * (w.bp_iters - 1)) / bp_launches
     roofline = {"kernel": "k_bp_step", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": TRAFFIC.get(args.workload),
+                "frac": achieved / hbm_peak, "traffic": traffic,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
                 "launches": bp_launches, "avg_launch_ms": bp_ms / max(bp_launches, 1),
                 "share_of_step": bp_ms / ms if ms else None,
