@@ -249,6 +249,46 @@ t3d_status toric3d_run_cycles(const t3d_run_cfg* cfg, uint64_t* e, void* work, s
                               uint8_t* mask, int64_t* counts8, t3d_stream stream);
 
 /*
+ * Learned local pre-decoder (not in the paper; it stands in for BP ahead of
+ * the flip / p-flip schedule).  A periodic 3-D convolutional network:
+ * conv 3x3x3 (6 -> 16) + ReLU, conv 3x3x3 (16 -> 16) + ReLU, conv 3x3x3
+ * (16 -> 16) + ReLU, 1x1x1 head (16 -> 3), sigmoid.  The six input channels of
+ * site r are s_prev(n, r) and s(n, r) for the face normals n = 0, 1, 2 (0/1);
+ * output d of site r is the flip probability of edge (d, r).  Parameters are
+ * FP32 in PyTorch order: conv1.weight [16][6][3][3][3], conv1.bias [16],
+ * conv2.weight [16][16][3][3][3], conv2.bias, conv3.weight, conv3.bias,
+ * head.weight [3][16], head.bias [3] (toric3d_cnn_param_count() = 16,515);
+ * kernel index (kz, ky, kx) reads the neighbour at (x+kx-1, y+ky-1, z+kz-1),
+ * periodic.  Kernels use BF16 weights and activations with FP32 accumulation
+ * on the tensor cores; hidden activations are rounded to BF16 between layers.
+ *
+ * toric3d_cnn_prepare: params (device FP32) -> blob (toric3d_cnn_blob_bytes(),
+ * device, 16-byte aligned) in the kernels' layouts.
+ * toric3d_cnn_decode: logits from (s_prev, s), corrections d = [logit > 0]
+ * applied as e ^= d and s ^= H d.  logits_out (nullable) receives
+ * float[3][L^3][n_samples].  work: toric3d_cnn_workspace_bytes(L, n).
+ * toric3d_cnn_train_step: one Adam step (lr > 0) of mean binary cross-entropy
+ * between the logits and the labels e_label (bit-sliced, the error before
+ * decoding) on this batch; params, adam_m, adam_v (device FP32) are updated in
+ * place and blob re-prepared; grads_out (nullable, FP32 [param_count])
+ * receives the gradient; loss_out (device float) the summed loss.  lr = 0
+ * computes gradient and loss only.  work: toric3d_cnn_train_workspace_bytes.
+ */
+int toric3d_cnn_param_count(void);
+size_t toric3d_cnn_blob_bytes(void);
+t3d_status toric3d_cnn_prepare(const float* params, void* blob, t3d_stream stream);
+size_t toric3d_cnn_workspace_bytes(int L, int64_t n_samples);
+t3d_status toric3d_cnn_decode(int L, int64_t n_samples, const uint64_t* s_prev, uint64_t* s,
+                              uint64_t* e, const void* blob, float* logits_out, void* work,
+                              size_t work_bytes, t3d_stream stream);
+size_t toric3d_cnn_train_workspace_bytes(int L, int64_t n_samples);
+t3d_status toric3d_cnn_train_step(int L, int64_t n_samples, const uint64_t* s_prev,
+                                  const uint64_t* s, const uint64_t* e_label, float* params,
+                                  float* adam_m, float* adam_v, int step, float lr, void* blob,
+                                  float* grads_out, float* loss_out, void* work, size_t work_bytes,
+                                  t3d_stream stream);
+
+/*
  * Batched runs over lattices of different sizes (measurement support for the
  * paper's multi-size threshold plots, Fig. 2, 6, 7).  Up to 8 independent
  * ensembles, each with its own L, sample range and state, advance through the
@@ -307,7 +347,8 @@ typedef enum {
     T3D_K_BP_DECIDE = 5,
     T3D_K_LOGICAL = 6,
     T3D_K_LAYOUT = 7,
-    T3D_K_COUNT = 8
+    T3D_K_CNN = 8,
+    T3D_K_COUNT = 9
 } t3d_kernel_kind;
 
 void toric3d_profile_enable(int on);

@@ -42,10 +42,12 @@ EXPORTED_SYMBOLS = [
     "toric3d_run_cycles", "toric3d_run_batch_workspace_bytes", "toric3d_run_batch",
     "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm", "toric3d_autotune_batch",
     "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "toric3d_flip_noalloc",
+    "toric3d_cnn_param_count", "toric3d_cnn_blob_bytes", "toric3d_cnn_prepare", "toric3d_cnn_workspace_bytes",
+    "toric3d_cnn_decode", "toric3d_cnn_train_workspace_bytes", "toric3d_cnn_train_step",
 ]
 
 KERNEL_KINDS = {"noise": 0, "syndrome": 1, "flip": 2, "pflip": 3, "bp_step": 4, "bp_decide": 5,
-                "logical": 6, "layout": 7}
+                "logical": 6, "layout": 7, "cnn": 8}
 
 
 class T3DError(RuntimeError):
@@ -139,6 +141,14 @@ def _declare(h):
         "toric3d_get_blocks_per_sm": (i32, [i32]),
         "toric3d_autotune_batch": (i32, [ctypes.POINTER(RunCfg), ctypes.POINTER(BatchItem), i32, _P, sz,
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), _P]),
+        "toric3d_cnn_param_count": (i32, []),
+        "toric3d_cnn_blob_bytes": (sz, []),
+        "toric3d_cnn_prepare": (i32, [_P, _P, _P]),
+        "toric3d_cnn_workspace_bytes": (sz, [i32, i64]),
+        "toric3d_cnn_decode": (i32, [i32, i64, _P, _P, _P, _P, _P, _P, sz, _P]),
+        "toric3d_cnn_train_workspace_bytes": (sz, [i32, i64]),
+        "toric3d_cnn_train_step": (i32, [i32, i64, _P, _P, _P, _P, _P, _P, i32, ctypes.c_float, _P, _P, _P,
+                                         _P, sz, _P]),
         "toric3d_profile_enable": (None, [i32]),
         "toric3d_profile_reset": (None, []),
         "toric3d_profile_read": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
@@ -365,3 +375,38 @@ def replica_sample0(rank: int, samples_per_rank: int) -> int:
     64-sample word boundaries, so every replica draws exactly the random
     numbers one large batch would (the generator is keyed by global sample)."""
     return rank * ((samples_per_rank + 63) // 64 * 64)
+
+
+# ------------------------------------------------------------------ learned pre-decoder
+def toric3d_cnn_param_count() -> int:
+    return int(lib().toric3d_cnn_param_count())
+
+
+def toric3d_cnn_blob_bytes() -> int:
+    return int(lib().toric3d_cnn_blob_bytes())
+
+
+def toric3d_cnn_prepare(params, blob, stream=None):
+    _check(lib().toric3d_cnn_prepare(_ptr(params), _ptr(blob), _stream(stream)))
+
+
+def toric3d_cnn_workspace_bytes(L: int, n_samples: int) -> int:
+    return int(lib().toric3d_cnn_workspace_bytes(L, n_samples))
+
+
+def toric3d_cnn_decode(L, n_samples, s_prev, s, e, blob, work, logits_out=None, stream=None):
+    _check(lib().toric3d_cnn_decode(L, n_samples, _ptr(s_prev), _ptr(s), _ptr(e), _ptr(blob),
+                                    _ptr(logits_out), _ptr(work), work.numel() * work.element_size(),
+                                    _stream(stream)))
+
+
+def toric3d_cnn_train_workspace_bytes(L: int, n_samples: int) -> int:
+    return int(lib().toric3d_cnn_train_workspace_bytes(L, n_samples))
+
+
+def toric3d_cnn_train_step(L, n_samples, s_prev, s, e_label, params, adam_m, adam_v, step, lr, blob,
+                           work, loss_out, grads_out=None, stream=None):
+    _check(lib().toric3d_cnn_train_step(L, n_samples, _ptr(s_prev), _ptr(s), _ptr(e_label), _ptr(params),
+                                        _ptr(adam_m), _ptr(adam_v), int(step), float(lr), _ptr(blob),
+                                        _ptr(grads_out), _ptr(loss_out), _ptr(work),
+                                        work.numel() * work.element_size(), _stream(stream)))
