@@ -184,6 +184,17 @@ t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double
                       t3d_stream stream);
 
 /*
+ * Fallback gate of the learned pre-decoder (no counterpart in the paper,
+ * whose decoders have no fallback): gate[w] = 1 iff some sample of word w has
+ * more than max_weight unsatisfied checks in s (s: uint64_t[3L^3][words],
+ * gate: uint8_t[words], device).  n_flagged (device, nullable) += the number
+ * of flagged words.  work: device scratch of toric3d_gate_workspace_bytes.
+ */
+size_t toric3d_gate_workspace_bytes(int L, int64_t words);
+t3d_status toric3d_gate(int L, int64_t words, const uint64_t* s, uint32_t max_weight, uint8_t* gate,
+                        int64_t* n_flagged, void* work, size_t work_bytes, t3d_stream stream);
+
+/*
  * Logical readout (Sec. 3.1 and its footnote, Fig. 2 caption, App. A.2): for
  * each axis d the L^2 straight lines of d-edges are a complete set of
  * disjoint logical Z operators; the number c_d of lines with odd residual
@@ -232,7 +243,12 @@ typedef struct {
     int32_t perfect_max_sweeps;
     uint32_t cycle0;
     int32_t use_graph;         /* 1: capture the T cycles in a CUDA graph and launch it once */
-    int64_t bp_chunk_samples;  /* BP chunk size; 0 = as large as the workspace allows */
+    int64_t bp_chunk_samples;  /* BP (and pre-decoder) chunk size; 0 = as large as the workspace allows */
+    const void* cnn_blob;      /* learned pre-decoder (toric3d_cnn_prepare) decoding in place of BP
+                                  (use_bp must be 0; toric3d_run_batch only, items carry s_prev); NULL = none */
+    int32_t fallback_max_weight; /* with cnn_blob: after the schedule, every 64-sample word in which a sample
+                                    keeps more than this many unsatisfied checks is decoded again by BP
+                                    (bp_iters) + the schedule; -1 = no fallback */
 } t3d_run_cfg;
 
 /* Workspace toric3d_run_cycles needs for `cfg` (uses cfg->bp_chunk_samples, 0 = all). */
@@ -281,6 +297,10 @@ size_t toric3d_cnn_workspace_bytes(int L, int64_t n_samples);
 t3d_status toric3d_cnn_decode(int L, int64_t n_samples, const uint64_t* s_prev, uint64_t* s,
                               uint64_t* e, const void* blob, float* logits_out, void* work,
                               size_t work_bytes, t3d_stream stream);
+/* T3D_OK, or T3D_ETIMEOUT if a tensor-core pre-decoder kernel gave up one of
+ * its bounded waits (its results are then invalid) since the last call.
+ * Reads and clears the device flag; synchronises the device. */
+t3d_status toric3d_cnn_status(void);
 size_t toric3d_cnn_train_workspace_bytes(int L, int64_t n_samples);
 t3d_status toric3d_cnn_train_step(int L, int64_t n_samples, const uint64_t* s_prev,
                                   const uint64_t* s, const uint64_t* e_label, float* params,
@@ -305,6 +325,9 @@ typedef struct {
     uint64_t* e;               /* device, uint64_t[3L^3][ceil(n_samples/64)], in/out */
     uint8_t* mask;             /* device, uint8_t[n_samples], nullable */
     int64_t* counts8;          /* device, int64_t[8], nullable */
+    uint64_t* s_prev;          /* learned decoder: device, like e, the previous cycle's measured syndrome
+                                  (zero for a fresh run), in/out; otherwise unused */
+    int64_t* fallback_words;   /* learned decoder: device counter, nullable, += words sent to the fallback */
 } t3d_batch_item;
 
 size_t toric3d_run_batch_workspace_bytes(const t3d_run_cfg* cfg, const t3d_batch_item* items,

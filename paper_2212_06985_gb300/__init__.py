@@ -30,7 +30,7 @@ __all__ = [
     "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "KERNEL_KINDS",
     "EXPORTED_SYMBOLS", "replica_sample0", "BatchItem", "make_batch", "toric3d_run_batch",
     "toric3d_run_batch_workspace_bytes", "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm",
-    "toric3d_autotune_batch", "toric3d_flip_noalloc",
+    "toric3d_autotune_batch", "toric3d_flip_noalloc", "toric3d_gate_workspace_bytes", "toric3d_gate",
 ]
 
 EXPORTED_SYMBOLS = [
@@ -44,6 +44,7 @@ EXPORTED_SYMBOLS = [
     "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "toric3d_flip_noalloc",
     "toric3d_cnn_param_count", "toric3d_cnn_blob_bytes", "toric3d_cnn_prepare", "toric3d_cnn_workspace_bytes",
     "toric3d_cnn_decode", "toric3d_cnn_train_workspace_bytes", "toric3d_cnn_train_step",
+    "toric3d_gate_workspace_bytes", "toric3d_gate", "toric3d_cnn_status",
 ]
 
 KERNEL_KINDS = {"noise": 0, "syndrome": 1, "flip": 2, "pflip": 3, "bp_step": 4, "bp_decide": 5,
@@ -79,6 +80,8 @@ class RunCfg(ctypes.Structure):
         ("cycle0", ctypes.c_uint32),
         ("use_graph", ctypes.c_int32),
         ("bp_chunk_samples", ctypes.c_int64),
+        ("cnn_blob", ctypes.c_void_p),
+        ("fallback_max_weight", ctypes.c_int32),
     ]
 
 
@@ -92,6 +95,8 @@ class BatchItem(ctypes.Structure):
         ("e", ctypes.c_void_p),
         ("mask", ctypes.c_void_p),
         ("counts8", ctypes.c_void_p),
+        ("s_prev", ctypes.c_void_p),
+        ("fallback_words", ctypes.c_void_p),
     ]
 
 
@@ -131,6 +136,9 @@ def _declare(h):
         "toric3d_bp_workspace_bytes": (sz, [i32, i64]),
         "toric3d_bp": (i32, [i32, i64, _P, _P, dbl, dbl, i32, _P, sz, _P, _P]),
         "toric3d_logical": (i32, [i32, i64, _P, _P, _P, _P]),
+        "toric3d_gate_workspace_bytes": (ctypes.c_size_t, [i32, i64]),
+        "toric3d_cnn_status": (i32, []),
+        "toric3d_gate": (i32, [i32, i64, _P, ctypes.c_uint32, _P, _P, _P, ctypes.c_size_t, _P]),
         "toric3d_pack": (i32, [i64, i64, _P, _P, _P]),
         "toric3d_unpack": (i32, [i64, i64, _P, _P, _P]),
         "toric3d_run_workspace_bytes": (sz, [ctypes.POINTER(RunCfg)]),
@@ -277,9 +285,19 @@ def toric3d_unpack(n_bits_, n_samples, words, bits, stream=None):
     _check(lib().toric3d_unpack(n_bits_, n_samples, _ptr(words), _ptr(bits), _stream(stream)))
 
 
+def toric3d_gate_workspace_bytes(L, words) -> int:
+    return int(lib().toric3d_gate_workspace_bytes(L, words))
+
+
+def toric3d_gate(L, s, max_weight, gate, work, n_flagged=None, stream=None):
+    _check(lib().toric3d_gate(L, s.shape[1], _ptr(s), max_weight, _ptr(gate), _ptr(n_flagged), _ptr(work),
+                              work.numel() * work.element_size(), _stream(stream)))
+
+
 def make_run_cfg(L, T, p, q, seed, n_samples, *, sample0=0, use_bp=False, bp_iters=0,
                  bp_meas_nodes=True, schedule="", n_apply=None, perfect_round=False,
-                 perfect_max_sweeps=0, cycle0=0, use_graph=False, bp_chunk_samples=0) -> RunCfg:
+                 perfect_max_sweeps=0, cycle0=0, use_graph=False, bp_chunk_samples=0, cnn_blob=None,
+                 fallback_max_weight=-1) -> RunCfg:
     c = RunCfg()
     c.L, c.T, c.p, c.q, c.seed = L, T, float(p), float(q), seed
     c.sample0, c.n_samples = sample0, n_samples
@@ -288,6 +306,7 @@ def make_run_cfg(L, T, p, q, seed, n_samples, *, sample0=0, use_bp=False, bp_ite
     c.schedule = schedule.encode()
     c.perfect_round, c.perfect_max_sweeps = int(perfect_round), perfect_max_sweeps
     c.cycle0, c.use_graph, c.bp_chunk_samples = cycle0, int(use_graph), bp_chunk_samples
+    c.cnn_blob, c.fallback_max_weight = _ptr(cnn_blob), fallback_max_weight
     return c
 
 
@@ -300,7 +319,7 @@ def toric3d_run_cycles(cfg: RunCfg, e, work, mask=None, counts8=None, stream=Non
 # ------------------------------------------------------------------ batches of lattices
 def make_batch(items):
     """items: iterable of dicts with L, n_samples, e (device int64 tensor) and
-    optional sample0, mask, counts8 -> ctypes array of BatchItem."""
+    optional sample0, mask, counts8, s_prev, fallback_words -> ctypes array of BatchItem."""
     items = list(items)
     arr = (BatchItem * len(items))()
     for a, it in zip(arr, items):
@@ -309,6 +328,8 @@ def make_batch(items):
         a.e = _ptr(it["e"])
         a.mask = _ptr(it.get("mask"))
         a.counts8 = _ptr(it.get("counts8"))
+        a.s_prev = _ptr(it.get("s_prev"))
+        a.fallback_words = _ptr(it.get("fallback_words"))
     return arr
 
 
@@ -398,6 +419,11 @@ def toric3d_cnn_decode(L, n_samples, s_prev, s, e, blob, work, logits_out=None, 
     _check(lib().toric3d_cnn_decode(L, n_samples, _ptr(s_prev), _ptr(s), _ptr(e), _ptr(blob),
                                     _ptr(logits_out), _ptr(work), work.numel() * work.element_size(),
                                     _stream(stream)))
+
+
+def toric3d_cnn_status():
+    """Raise T3DError if a tensor-core pre-decoder kernel gave up a bounded wait."""
+    _check(lib().toric3d_cnn_status())
 
 
 def toric3d_cnn_train_workspace_bytes(L: int, n_samples: int) -> int:

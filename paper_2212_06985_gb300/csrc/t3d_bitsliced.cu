@@ -141,6 +141,12 @@ k_sweep(const __grid_constant__ ItemTable tab, uint64_t seed, uint32_t cycle, ui
         uint64_t* __restrict__ s_out = d.tmp;
         uint64_t* __restrict__ e = d.e;
         const int64_t W = d.W;
+        if (d.gate && !d.gate[w]) {
+            // word not decoded: carry its syndrome into the other buffer unchanged
+#pragma unroll
+            for (int n = 0; n < 3; ++n) s_out[((int64_t)n * lat.L3 + r) * W + w] = s_in[((int64_t)n * lat.L3 + r) * W + w];
+            return;
+        }
         const Moves mv = site_moves(lat, r);
         const int rx = r + mv.plus[0], ry = r + mv.plus[1], rz = r + mv.plus[2];
         const int64_t L3 = lat.L3;
@@ -274,6 +280,89 @@ k_logical(const __grid_constant__ ItemTable tab)
     });
 }
 
+// Fallback gate: flag every word in which some sample's syndrome has more
+// than max_weight unsatisfied checks.  Two passes.  k_gate_count: block
+// (32, 8) over a 32-word tile and one of Y face ranges (blockIdx.y);
+// threadIdx.y splits the range further; per-lane counts are bit-sliced and
+// the block's partial count goes to part[y][bit][w].  k_gate_decide: one
+// thread per word adds the Y partials and compares.
+constexpr int kWeightBits = 23;  // 3 L^3 <= 3 * 128^3 < 2^23
+
+__device__ __forceinline__ void add_sliced(uint64_t (&tot)[kWeightBits], const uint64_t* x, int64_t stride)
+{
+    uint64_t carry = 0;
+#pragma unroll
+    for (int b = 0; b < kWeightBits; ++b) {
+        const uint64_t v = x[b * stride];
+        const uint64_t sum = tot[b] ^ v ^ carry;
+        carry = (tot[b] & v) | (carry & (tot[b] ^ v));
+        tot[b] = sum;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_gate_count(Lattice lat, int64_t W, const uint64_t* __restrict__ s, int64_t faces_per_y,
+             uint64_t* __restrict__ part)
+{
+    __shared__ uint64_t red[kLineSplit][kWeightBits][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t f0 = (int64_t)blockIdx.y * faces_per_y;
+    const int64_t f1 = min(f0 + faces_per_y, (int64_t)3 * lat.L3);
+    uint64_t cnt[kWeightBits];
+#pragma unroll
+    for (int b = 0; b < kWeightBits; ++b) cnt[b] = 0;
+    if (w < W) {
+        for (int64_t f = f0 + ty; f < f1; f += kLineSplit) {
+            uint64_t bit = __ldcs(&s[f * W + w]);
+#pragma unroll
+            for (int b = 0; b < kWeightBits; ++b) {
+                const uint64_t carry = cnt[b] & bit;
+                cnt[b] ^= bit;
+                bit = carry;
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < kWeightBits; ++b) red[ty][b][tx] = cnt[b];
+    __syncthreads();
+    if (ty == 0 && w < W) {
+        uint64_t tot[kWeightBits];
+#pragma unroll
+        for (int b = 0; b < kWeightBits; ++b) tot[b] = red[0][b][tx];
+        for (int k = 1; k < kLineSplit; ++k) add_sliced(tot, &red[k][0][tx], 32);
+        uint64_t* out = part + (int64_t)blockIdx.y * kWeightBits * W + w;
+#pragma unroll
+        for (int b = 0; b < kWeightBits; ++b) out[b * W] = tot[b];
+    }
+}
+
+__global__ void k_gate_decide(int64_t W, int Y, const uint64_t* __restrict__ part, uint32_t max_weight,
+                              uint8_t* __restrict__ gate, unsigned long long* __restrict__ n_flagged)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    uint64_t tot[kWeightBits];
+#pragma unroll
+    for (int b = 0; b < kWeightBits; ++b) tot[b] = part[b * W + w];
+    for (int y = 1; y < Y; ++y) add_sliced(tot, part + (int64_t)y * kWeightBits * W + w, W);
+    // lanes with count > max_weight, i.e. count >= max_weight + 1 (MSB-first comparison)
+    const uint64_t need = (uint64_t)max_weight + 1;
+    uint64_t gt = 0, eq = ~0ULL;
+#pragma unroll
+    for (int b = kWeightBits - 1; b >= 0; --b) {
+        if ((need >> b) & 1u) {
+            eq &= tot[b];
+        } else {
+            gt |= eq & tot[b];
+            eq &= ~tot[b];
+        }
+    }
+    const bool flag = (need >> kWeightBits) == 0 && (gt | eq) != 0;
+    gate[w] = flag ? 1 : 0;
+    if (flag && n_flagged) atomicAdd(n_flagged, 1ULL);
+}
+
 __global__ void k_pack(int64_t n_bits, int64_t n_samples, int64_t W, const uint8_t* __restrict__ bits,
                        uint64_t* __restrict__ words)
 {
@@ -382,6 +471,34 @@ t3d_status launch_logical(ItemTable& tab, cudaStream_t st)
     return T3D_OK;
 }
 
+int gate_splits(int L, int64_t W)
+{
+    const int64_t faces = 3LL * L * L * L;
+    const int64_t tiles = (W + 31) / 32;
+    int64_t y = (4 * 152 + tiles - 1) / tiles;              // about four blocks per SM
+    y = std::min<int64_t>(y, (faces + 8 * 64 - 1) / (8 * 64));  // at least 64 faces per warp
+    return (int)std::max<int64_t>(1, std::min<int64_t>(y, 64));
+}
+
+size_t gate_scratch_bytes(int L, int64_t W)
+{
+    return (size_t)gate_splits(L, W) * kWeightBits * (size_t)W * sizeof(uint64_t);
+}
+
+t3d_status launch_gate(const Lattice& lat, int64_t W, const uint64_t* s, uint32_t max_weight, uint8_t* gate,
+                       unsigned long long* n_flagged, uint64_t* scratch, cudaStream_t st)
+{
+    ProfScope prof(T3D_K_LOGICAL, st);
+    const int Y = gate_splits(lat.L, W);
+    const int64_t faces = 3LL * lat.L3;
+    const int64_t per_y = (faces + Y - 1) / Y;
+    k_gate_count<<<dim3((unsigned)((W + 31) / 32), (unsigned)Y), 256, 0, st>>>(lat, W, s, per_y, scratch);
+    T3D_LAUNCH_CHECK("fallback gate count");
+    k_gate_decide<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(W, Y, scratch, max_weight, gate, n_flagged);
+    T3D_LAUNCH_CHECK("fallback gate decide");
+    return T3D_OK;
+}
+
 namespace {
 
 // A one-item table for the single-lattice entry points.
@@ -408,6 +525,29 @@ ItemTable single_item(int L, int64_t words, int64_t n_samples, uint64_t group0, 
 using namespace t3d;
 
 // ----------------------------------------------------------------- C ABI
+extern "C" size_t toric3d_gate_workspace_bytes(int L, int64_t words)
+{
+    if (L < 2 || L > 1024 || words < 1) return 0;
+    return gate_scratch_bytes(L, words);
+}
+
+extern "C" t3d_status toric3d_gate(int L, int64_t words, const uint64_t* s, uint32_t max_weight, uint8_t* gate,
+                                   int64_t* n_flagged, void* work, size_t work_bytes, t3d_stream stream)
+{
+    clear_error();
+    T3D_TRY(check_lattice(L));
+    T3D_REQUIRE(words >= 1 && words <= 65535LL * 32, "words=%lld out of range", (long long)words);
+    T3D_TRY(check_words(s, "s"));
+    T3D_REQUIRE(gate != nullptr, "gate is NULL");
+    T3D_REQUIRE(n_flagged == nullptr || aligned(n_flagged, 8), "n_flagged must be 8-byte aligned");
+    T3D_TRY(check_words(static_cast<const uint64_t*>(work), "work"));
+    T3D_REQUIRE(work_bytes >= gate_scratch_bytes(L, words), "workspace %zu bytes < %zu needed", work_bytes,
+                gate_scratch_bytes(L, words));
+    return launch_gate(make_lattice_host(L), words, s, max_weight, gate,
+                       reinterpret_cast<unsigned long long*>(n_flagged), static_cast<uint64_t*>(work),
+                       as_stream(stream));
+}
+
 extern "C" t3d_status toric3d_noise(int L, int64_t words, uint64_t* e, double p, uint64_t seed,
                                     uint64_t sample0, uint32_t cycle, t3d_stream stream)
 {

@@ -192,6 +192,7 @@ k_bp_step(const __grid_constant__ ItemTable tab, float l0, TD q, float m1)
     const int64_t W = d.W;
     SiteWarp sw;
     if (!site_warp(lat, lb, sw)) return;
+    if (d.gate && !d.gate[d.w0 + sw.w]) return;
     const int lane = threadIdx.x & 31;
     Syn3* __restrict__ syn = reinterpret_cast<Syn3*>(d.syn);
     uint64_t s0, s1, s2;
@@ -328,6 +329,7 @@ k_bp_decide(const __grid_constant__ ItemTable tab, float l0)
     const int64_t W = d.W;
     SiteWarp sw;
     if (!site_warp(lat, lb, sw)) return;
+    if (d.gate && !d.gate[d.w0 + sw.w]) return;
     const int lane = threadIdx.x & 31;
     const int64_t sample0 = sw.w * kWord + 2 * lane;
     const bool valid0 = sample0 < d.n_samples, valid1 = sample0 + 1 < d.n_samples;
@@ -399,6 +401,7 @@ k_bp_syndrome(const __grid_constant__ ItemTable tab)
     const int r = (int)((lb - word_tile * site_tiles) * kSynSitesPerBlock + (threadIdx.x / kSynWordsPerRow));
     const int64_t w = word_tile * kSynWordsPerRow + (threadIdx.x % kSynWordsPerRow);
     if (r >= lat.L3 || w >= d.words) return;
+    if (d.gate && !d.gate[d.w0 + w]) return;
     const Coord rc = site_coord(lat, r);
     const int step[3] = {1, lat.L, lat.L2};
     int nb[3];

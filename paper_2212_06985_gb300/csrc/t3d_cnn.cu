@@ -28,37 +28,15 @@
 #include <cmath>
 #include <cstring>
 
+#include "t3d_cnn.cuh"
 #include "t3d_device.cuh"
 #include "t3d_host.hpp"
 
 namespace t3d {
 namespace cnn {
 
-constexpr int kC = 16;          // channels of every hidden layer
-constexpr int kInC = 6;         // input channels
-constexpr int kOff = 27;        // 3x3x3 offsets, k = (kz*3 + ky)*3 + kx, displacement (k? - 1)
 constexpr int kThreads = 256;   // 8 warps
 constexpr int kTile = 32;       // samples per warp tile
-
-// Master parameters (FP32), PyTorch order.
-constexpr int P_W1 = 0;                          // [16][6][27]
-constexpr int P_B1 = P_W1 + kC * kInC * kOff;    // [16]
-constexpr int P_W2 = P_B1 + kC;                  // [16][16][27]
-constexpr int P_B2 = P_W2 + kC * kC * kOff;
-constexpr int P_W3 = P_B2 + kC;
-constexpr int P_B3 = P_W3 + kC * kC * kOff;
-constexpr int P_W4 = P_B3 + kC;                  // [3][16]
-constexpr int P_B4 = P_W4 + 3 * kC;              // [3]
-constexpr int kParams = P_B4 + 3;                // 16,515
-
-// Prepared device blob.
-struct Blob {
-    __nv_bfloat16 wf[3][kOff][kC][kC];   // forward: [layer][k][co][ci] (layer 1: ci >= 6 zero)
-    __nv_bfloat16 wt[3][kOff][kC][kC];   // backward data: [layer][k][ci][co] = wf[layer][26-k][co][ci]
-    float bias[3][kC];
-    float w4[3][kC];
-    float b4[3];
-};
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -535,10 +513,16 @@ extern "C" t3d_status toric3d_cnn_prepare(const float* params, void* blob, t3d_s
     return T3D_OK;
 }
 
+extern "C" t3d_status toric3d_cnn_status(void)
+{
+    clear_error();
+    return tc_status();
+}
+
 extern "C" size_t toric3d_cnn_workspace_bytes(int L, int64_t n_samples)
 {
     if (L < 2 || L > 128 || n_samples < 1) return 0;
-    return 2 * round256(act_bytes(L, n_samples)) + round256((size_t)words_for(n_samples) * L * L * L * 32);
+    return cnn_workspace_bytes(L, n_samples);
 }
 
 static t3d_status cnn_checks(int L, int64_t n_samples)
@@ -548,6 +532,35 @@ static t3d_status cnn_checks(int L, int64_t n_samples)
     T3D_REQUIRE(n_samples >= 1 && padded(n_samples) / kTile <= 65535, "n_samples out of range");
     return T3D_OK;
 }
+
+namespace t3d {
+
+// The decode pass on n_samples samples whose bit-sliced rows have stride W
+// words (a chunk of a larger batch when the pointers are offset).
+t3d_status launch_cnn_decode(int L, int64_t n_samples, int64_t W, const uint64_t* s_prev, uint64_t* s,
+                             uint64_t* e, const void* blob, float* logits_out, void* work, cudaStream_t st)
+{
+    using namespace t3d::cnn;
+    const int64_t words = words_for(n_samples);
+    uint64_t* dec = reinterpret_cast<uint64_t*>(work);
+    void* fwd = static_cast<char*>(work) + round256((size_t)words * L * L * L * 32);
+    T3D_TRY(launch_forward_tc(L, n_samples, W, s_prev, s, e, dec, static_cast<const Blob*>(blob), logits_out, fwd,
+                              st));
+    ProfScope prof(T3D_K_CNN, st);
+    const Lattice lat = make_lattice_host(L);
+    dim3 sg((unsigned)((L * L * L + 7) / 8), (unsigned)((words + 31) / 32));
+    k_dec_syndrome<<<sg, 256, 0, st>>>(lat, W, words, dec, s);
+    T3D_LAUNCH_CHECK("cnn syndrome update");
+    return T3D_OK;
+}
+
+size_t cnn_workspace_bytes(int L, int64_t n_samples)
+{
+    using namespace t3d::cnn;
+    return round256((size_t)words_for(n_samples) * L * L * L * 32) + tc_workspace_bytes(L, n_samples);
+}
+
+}  // namespace t3d
 
 extern "C" t3d_status toric3d_cnn_decode(int L, int64_t n_samples, const uint64_t* s_prev, uint64_t* s,
                                          uint64_t* e, const void* blob, float* logits_out, void* work,
@@ -562,60 +575,8 @@ extern "C" t3d_status toric3d_cnn_decode(int L, int64_t n_samples, const uint64_
     T3D_REQUIRE(work != nullptr && aligned(work, 256), "work must be 256-byte aligned");
     T3D_REQUIRE(work_bytes >= toric3d_cnn_workspace_bytes(L, n_samples), "workspace too small: %zu < %zu",
                 work_bytes, toric3d_cnn_workspace_bytes(L, n_samples));
-    cudaStream_t st = as_stream(stream);
-    const Blob* b = static_cast<const Blob*>(blob);
-    char* base = static_cast<char*>(work);
-    const size_t ab = round256(act_bytes(L, n_samples));
-    uint32_t* act0 = reinterpret_cast<uint32_t*>(base);
-    uint32_t* act1 = reinterpret_cast<uint32_t*>(base + ab);
-    uint64_t* dec = reinterpret_cast<uint64_t*>(base + 2 * ab);
-    ConvArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.lat = make_lattice_host(L);
-    a.Sp = padded(n_samples);
-    a.n_samples = n_samples;
-    a.W = words_for(n_samples);
-    a.s_prev = s_prev;
-    a.s_cur = s;
-    const dim3 grid = conv_grid(L, n_samples);
-    // decision words of sample lanes past the last tile stay zero
-    T3D_CUDA_CHECK(cudaMemsetAsync(dec, 0, (size_t)a.W * L * L * L * 32, st));
-    {
-        ProfScope prof(T3D_K_CNN, st);
-        a.w = &b->wf[0][0][0][0];
-        a.bias = b->bias[0];
-        a.y = act0;
-        k_conv<kInBits, kOutRelu><<<grid, kThreads, 0, st>>>(a);
-        T3D_LAUNCH_CHECK("cnn layer 1");
-    }
-    {
-        ProfScope prof(T3D_K_CNN, st);
-        a.x = act0;
-        a.w = &b->wf[1][0][0][0];
-        a.bias = b->bias[1];
-        a.y = act1;
-        k_conv<kInAct, kOutRelu><<<grid, kThreads, 0, st>>>(a);
-        T3D_LAUNCH_CHECK("cnn layer 2");
-    }
-    {
-        ProfScope prof(T3D_K_CNN, st);
-        a.x = act1;
-        a.w = &b->wf[2][0][0][0];
-        a.bias = b->bias[2];
-        a.w4 = &b->w4[0][0];
-        a.b4 = b->b4;
-        a.y = nullptr;
-        a.e32 = reinterpret_cast<uint32_t*>(e);
-        a.dec32 = reinterpret_cast<uint32_t*>(dec);
-        a.logits = logits_out;
-        k_conv<kInAct, kOutHeadDecide><<<grid, kThreads, 0, st>>>(a);
-        T3D_LAUNCH_CHECK("cnn layer 3 + head");
-    }
-    ProfScope prof(T3D_K_CNN, st);
-    dim3 sg((unsigned)((L * L * L + 7) / 8), (unsigned)((a.W + 31) / 32));
-    k_dec_syndrome<<<sg, 256, 0, st>>>(a.lat, a.W, a.W, dec, s);
-    T3D_LAUNCH_CHECK("cnn syndrome update");
-    return T3D_OK;
+    return launch_cnn_decode(L, n_samples, words_for(n_samples), s_prev, s, e, blob, logits_out, work,
+                             as_stream(stream));
 }
 
 extern "C" size_t toric3d_cnn_train_workspace_bytes(int L, int64_t n_samples)

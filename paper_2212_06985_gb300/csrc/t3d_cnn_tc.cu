@@ -1,0 +1,668 @@
+// Inference forward pass of the learned pre-decoder on the fifth-generation
+// tensor cores (tcgen05 MMA with TMEM accumulators, operands staged in shared
+// memory by bulk asynchronous copies).
+//
+// A 3x3x3 convolution with 16 output channels has a small GEMM N (16), and a
+// tcgen05.mma with M = 128, K = 16 takes as long for N = 16 as for N = 128
+// (measured on GB300: about 53 cycles from one issuing thread at N = 16, 64 at
+// N = 128, 128 at N = 256, the last two at the tensor peak).  So every MMA here
+// computes 8 output sites at once:
+//   D[sample][(r, co)] += A_i[sample][ci] . B[(r, co)][ci],   M = N = 128, K = 16,
+// where A_i is the 128-sample activation tile of one input site i, the 128
+// columns of D are 8 consecutive output sites along x (r = 7 - (x - x0)) times 16
+// channels, and B stacks, for each of the 8 outputs, the weights of the offset
+// that connects it to i (zero where i is not its neighbour).  For a fixed
+// (dy, dz) these stacks are strided views of one zero-padded strip of weight
+// blocks [0 x 7, W(dx=-1), W(0), W(+1), 0 x 7]: the view for input offset
+// a = x_i - x0 starts a blocks further along the strip.  Nine strips (one per
+// (dy, dz), sharing their zero padding) take 97 blocks of 512 bytes.
+//
+// Work unit: one 128-sample tile x one line of 8 output sites (x0..x0+7, y)
+// running through all L planes in z.  The CTA streams the unit's input tiles
+// plane by plane (input planes z = -1 .. L, each with the 10 x 3 sites
+// (x0-1..x0+8, y-1..y+1) around the line, periodic wrap); each input tile is
+// loaded into shared memory once and multiplied into the (up to) three output
+// planes z-1, z, z+1 it touches, one MMA each.  TMEM holds the accumulators of
+// four output planes (4 x 128 columns): while input plane z is multiplied,
+// outputs z-1, z, z+1 accumulate and the epilogue drains plane z-2.
+//
+// Warp roles (192 threads, one CTA per SM):
+//   warps 0-3  epilogue: tcgen05.ld of a finished plane (warp w reads TMEM lanes
+//              32w..32w+31 = samples), bias + ReLU + BF16 store of the next
+//              layer's input, or for the last layer the 16 -> 3 head and the
+//              hard decisions;
+//   warp 4     producer: one thread issues the bulk copies of input tiles into
+//              a ring of shared-memory slots;
+//   warp 5     MMA issuer: one thread issues the MMAs and commits their
+//              completion to the slot's "empty" barrier and to the plane's
+//              "accumulators full" barrier.
+// Every wait is bounded (one second); a wait that gives up sets the device
+// error flag and the CTA winds down (waiting, again bounded, for its copies and
+// MMAs in flight, and freeing its TMEM) so the context stays usable.
+//
+// Shared-memory operand layout ("no swizzle", K-major): core matrices of 8 rows
+// x 16 bytes stored contiguously.  Hidden activations in global memory use the
+// same layout, [site][sample/8][channel/8][8 samples][8 channels] BF16, so a
+// tile (site, 128 samples) is one contiguous 4 KiB block: K-direction core
+// matrix stride (LBO) 128 B, M-direction stride (SBO) 256 B.  The first
+// layer's input (6 of 16 channels used) is stored as [site][sample][8]
+// (2 KiB per tile, SBO 128 B); its channels 8..15 come from a zero block that
+// sits 2 KiB after the tile in every ring slot (LBO 2 KiB).  Weight blocks:
+// [co/8][ci/8][co%8][ci%8] (512 B, LBO 128 B, SBO 256 B).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "t3d_cnn.cuh"
+#include "t3d_device.cuh"
+#include "t3d_host.hpp"
+
+namespace t3d {
+namespace cnn {
+namespace {
+
+constexpr int kTileM = 128;                         // samples per tile (MMA M)
+constexpr int kLine = 8;                            // output sites per MMA (N = 8 x 16)
+constexpr int kN = kLine * kC;                      // 128
+constexpr int kPlanes = 4;                          // output planes resident in TMEM
+constexpr uint32_t kTmemCols = kPlanes * kN;        // 512
+constexpr int kRowSlots = kLine + 2;                // input tiles of one row (x0-1 .. x0+8)
+constexpr int kGroups = 4;                          // rows in flight; each row has one full / empty barrier
+constexpr int kRing = kRowSlots * kGroups;          // 40 shared-memory input slots
+constexpr int kSlotBytes = 4096;
+constexpr int kStripPad = 7;                        // zero blocks between strips
+constexpr int kStripBlocks = kStripPad + 9 * (3 + kStripPad);   // 97
+constexpr int kWBytes = kStripBlocks * 512;         // 49,664 B
+constexpr int kEpiWarps = 4;
+constexpr int kProducerWarp = 4;
+constexpr int kIssuerWarp = 5;
+constexpr int kTcThreads = 192;
+constexpr uint64_t kWaitNs = 1000000000ull;         // bound of every wait
+
+// Dynamic shared memory: ring | weight strips | barriers | misc.
+constexpr int kOffW = kRing * kSlotBytes;
+constexpr int kOffBar = kOffW + kWBytes;
+constexpr int kNumBars = 2 * kGroups + 2 * kPlanes + 1;   // full, empty, acc_full, acc_empty, done
+constexpr int kOffMisc = kOffBar + kNumBars * 8;
+constexpr int kSmemBytes = kOffMisc + 16 + 1024;        // + alignment slack
+static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+
+// Block index of W(dx = -1, dy, dz) in the strips; s = (dz + 1) * 3 + (dy + 1).
+__host__ __device__ constexpr int strip_start(int s) { return kStripPad + s * (3 + kStripPad); }
+
+// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ unsigned int g_tc_error;   // bit 0: a bounded wait gave up
+
+struct TcArgs {
+    int L, L3;
+    int64_t Sp;                 // padded samples of the activation buffers (multiple of 128)
+    int64_t n_samples;
+    int64_t W;                  // row stride of the bit-sliced arrays (words)
+    int64_t words;              // words of this pass
+    int nbx;                    // lines of 8 sites along x
+    int64_t n_units;
+    const uint8_t* in;          // input activations
+    uint8_t* out;               // hidden layers: output activations
+    const __nv_bfloat16* w;     // [27][co][ci]
+    const float* bias;          // [16]
+    const float* w4;            // head [3][16]
+    const float* b4;            // [3]
+    uint32_t* e32;              // head: error words as 32-bit halves
+    uint32_t* dec32;            // head: decision words [word][site][8] 32-bit halves
+    float* logits;              // head: optional [3][L^3][n_samples]
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity.  Gives up after kWaitNs, or
+// early once another role of the CTA has given up (abort flag), unless
+// ignore_abort (the final drain of work in flight).
+__device__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag, bool ignore_abort = false)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (!ignore_abort && *abort_flag) return false;
+        if (global_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicOr(&g_tc_error, 1u);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Whole warp: allocate ncols TMEM columns; the base address goes to smem.
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1 (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// D (+)= A . B^T; accumulate = 0 overwrites D.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n"
+        ".reg .pred pa;\n"
+        "setp.ne.b32 pa, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on the barrier once every MMA this thread issued so far has completed.
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// Warp: 32 TMEM lanes x 16 consecutive 32-bit columns, one lane per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// ------------------------------------------------------------------ schedule
+struct Unit {
+    int64_t m0;      // first sample of the tile
+    int x0, y;       // line origin
+    int fx;          // line length (clipped at the lattice edge)
+};
+
+__device__ __forceinline__ Unit unit_of(const TcArgs& a, int64_t u)
+{
+    const int64_t lines = (int64_t)a.nbx * a.L;
+    const int64_t tile = u / lines;
+    const int rem = (int)(u - tile * lines);
+    Unit t;
+    t.m0 = tile * kTileM;
+    t.y = rem / a.nbx;
+    t.x0 = (rem % a.nbx) * kLine;
+    t.fx = min(kLine, a.L - t.x0);
+    return t;
+}
+
+// v in [-L, 2L): periodic coordinate
+__device__ __forceinline__ int wrap(int v, int L)
+{
+    return v < 0 ? v + L : (v >= L ? v - L : v);
+}
+
+// ------------------------------------------------------------------ kernel
+template <bool kHead, bool kBitsIn>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant__ TcArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t ring = smem_u32(sm);
+    const uint32_t wsm = ring + kOffW;
+    const uint32_t bars = ring + kOffBar;
+    auto full_bar = [&](int i) { return bars + 8u * (uint32_t)i; };
+    auto empty_bar = [&](int i) { return bars + 8u * (uint32_t)(kGroups + i); };
+    auto accf_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kGroups + i); };
+    auto acce_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kGroups + kPlanes + i); };
+    const uint32_t done_bar = bars + 8u * (uint32_t)(2 * kGroups + 2 * kPlanes);
+    uint32_t* misc = reinterpret_cast<uint32_t*>(sm + kOffMisc);   // [0] TMEM base, [1] abort flag
+    volatile uint32_t* abort_flag = misc + 1;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // weight strips: zero everything, then W(dx, dy, dz) at block strip_start(s) + dx + 1 in the
+    // B-operand layout [co/8][ci/8][co%8][ci%8]
+    for (int i = threadIdx.x; i < kWBytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(sm + kOffW)[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kOff * kC * kC; i += blockDim.x) {
+        const int k = i >> 8, co = (i >> 4) & 15, ci = i & 15;
+        const int blk = strip_start(k / 3) + k % 3;   // k / 3 = (dz + 1) * 3 + (dy + 1), k % 3 = dx + 1
+        const int off = blk * 512 + (co >> 3) * 256 + (ci >> 3) * 128 + (co & 7) * 16 + (ci & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(sm + kOffW + off) = a.w[i];
+    }
+    if (kBitsIn) {   // zero block 2 KiB after the tile in every slot: channels 8..15 of layer 1
+        for (int i = threadIdx.x; i < kRing * 128; i += blockDim.x) {
+            const int slot = i >> 7, j = i & 127;
+            reinterpret_cast<uint4*>(sm + slot * kSlotBytes + 2048)[j] = make_uint4(0, 0, 0, 0);
+        }
+    }
+    fence_proxy_async_smem();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kGroups; ++i) {
+            mbar_init(full_bar(i), 1);
+            mbar_init(empty_bar(i), 1);
+        }
+        for (int i = 0; i < kPlanes; ++i) {
+            mbar_init(accf_bar(i), 1);
+            mbar_init(acce_bar(i), kEpiWarps);
+        }
+        mbar_init(done_bar, 1);
+        misc[1] = 0;
+        fence_mbar_init();
+    }
+    if (warp == kIssuerWarp) tmem_alloc(smem_u32(misc), kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = misc[0];
+
+    const int L = a.L;
+    const uint32_t in_row = kBitsIn ? 16u : 32u;
+    const uint32_t tile_bytes = kTileM * in_row;
+
+    if (warp == kProducerWarp) {
+        if (lane == 0) {
+            // one row (fixed input y and z, x = x0-1 .. x0+fx) per slot group, one barrier phase each
+            uint32_t gseq = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+                const Unit t = unit_of(a, u);
+                for (int zi = -1; zi <= L && ok; ++zi) {
+                    const int zw = wrap(zi, L);
+                    for (int yi = t.y - 1; yi <= t.y + 1; ++yi) {
+                        const int g = (int)(gseq % kGroups);
+                        const uint32_t use = gseq / kGroups;
+                        if (use > 0 && !wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        const int64_t row = ((int64_t)zw * L + wrap(yi, L)) * L;
+                        mbar_arrive_expect_tx(full_bar(g), (uint32_t)(t.fx + 2) * tile_bytes);
+                        const uint32_t dst = ring + (uint32_t)(g * kRowSlots) * kSlotBytes;
+                        for (int xa = -1; xa <= t.fx; ++xa) {
+                            const int64_t site = row + wrap(t.x0 + xa, L);
+                            bulk_load(dst + (uint32_t)(xa + 1) * kSlotBytes, a.in + (site * a.Sp + t.m0) * in_row,
+                                      tile_bytes, full_bar(g));
+                        }
+                        ++gseq;
+                    }
+                }
+            }
+            // copies still in flight land before the CTA exits
+            const uint32_t last = gseq < (uint32_t)kGroups ? gseq : (uint32_t)kGroups;
+            for (uint32_t g = 0; g < last; ++g) {
+                // the latest row issued on this group: the largest q < gseq with q % kGroups == g
+                const uint32_t q = gseq - 1 - ((gseq - 1 - g) % kGroups);
+                wait_bar(full_bar((int)g), (q / kGroups) & 1u, abort_flag, true);
+            }
+        }
+        __syncwarp();
+    } else if (warp == kIssuerWarp) {
+        if (lane == 0) {
+            uint32_t gseq = 0;
+            int64_t qbase = 0;
+            bool ok = true;
+            const uint32_t a_lbo = kBitsIn ? 2048u : 128u, a_sbo = kBitsIn ? 128u : 256u;
+            const uint64_t bdesc0 = smem_desc(wsm, 128u, 256u);   // + 32 per 512-byte block
+            for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+                const Unit t = unit_of(a, u);
+                const bool full = t.fx == kLine;
+                for (int zi = -1; zi <= L && ok; ++zi) {
+                    // output plane zi + 1 is first written by this input plane
+                    if (zi + 1 <= L - 1) {
+                        const int64_t q = qbase + zi + 1;
+                        const uint32_t v = (uint32_t)(q >> 2);
+                        if (v > 0 && !wait_bar(acce_bar((int)(q & 3)), (v - 1) & 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    // TMEM column of output plane zi - dz (i = dz + 1), or -1 outside [0, L)
+                    int colb[3];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const int zo = zi - (i - 1);
+                        colb[i] = (zo >= 0 && zo < L) ? (int)((qbase + zo) & 3) * kN : -1;
+                    }
+                    // one tile: input offset xa = x_i - x0 in [-1, 8], dy; the MMA into plane
+                    // zi + 1 from the plane's first tile (xa = -1, dy = -1) overwrites D.
+                    auto tile_mmas = [&](int xa, int dyi, uint64_t adesc) {
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            if (colb[i] < 0) continue;
+                            const int blk = strip_start(i * 3 + dyi) + xa - 6;
+                            const uint32_t acc = (i == 0 && dyi == 0 && xa == -1) ? 0u : 1u;
+                            mma_bf16(tmem + (uint32_t)colb[i], adesc, bdesc0 + (uint64_t)(32 * blk), acc);
+                        }
+                    };
+                    // the three rows of the plane, each one slot group behind one barrier
+                    auto row_mmas = [&](int dyi) {
+                        const int g = (int)(gseq % kGroups);
+                        if (ok && !wait_bar(full_bar(g), (gseq / kGroups) & 1u, abort_flag)) ok = false;
+                        if (!ok) return;
+                        tc_fence_after();
+                        const uint64_t adesc0 =
+                            smem_desc(ring + (uint32_t)(g * kRowSlots) * kSlotBytes, a_lbo, a_sbo);
+                        if (full) {
+#pragma unroll
+                            for (int xa = -1; xa <= kLine; ++xa)
+                                tile_mmas(xa, dyi, adesc0 + (uint64_t)((xa + 1) * (kSlotBytes >> 4)));
+                        } else {
+                            for (int xa = -1; xa <= t.fx; ++xa)
+                                tile_mmas(xa, dyi, adesc0 + (uint64_t)((xa + 1) * (kSlotBytes >> 4)));
+                        }
+                        mma_commit(empty_bar(g));
+                        ++gseq;
+                    };
+                    row_mmas(0);
+                    row_mmas(1);
+                    row_mmas(2);
+                    if (!ok) break;
+                    // output plane zi - 1 has received its last contribution
+                    if (zi - 1 >= 0 && zi - 1 <= L - 1) mma_commit(accf_bar((int)((qbase + zi - 1) & 3)));
+                }
+                qbase += L;
+            }
+            // every MMA issued has completed before TMEM is released
+            mma_commit(done_bar);
+            wait_bar(done_bar, 0, abort_flag, true);
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warp w owns TMEM lanes (= tile rows = samples) 32w .. 32w + 31
+        const int r = warp * 32 + lane;
+        float bias[kC];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) bias[c] = a.bias[c];
+        float w4[kHead ? 3 * kC : 1];
+        float b4[3] = {0.0f, 0.0f, 0.0f};
+        if (kHead) {
+#pragma unroll
+            for (int i = 0; i < 3 * kC; ++i) w4[i] = a.w4[i];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) b4[d] = a.b4[d];
+        }
+        int64_t q = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+            const Unit t = unit_of(a, u);
+            const int64_t sample = t.m0 + r;
+            const bool valid = sample < a.n_samples;
+            for (int zo = 0; zo < L; ++zo, ++q) {
+                const int s = (int)(q & 3);
+                // one lane waits; the warp stays converged for the .sync.aligned TMEM loads
+                int got = 1;
+                if (lane == 0) got = wait_bar(accf_bar(s), (uint32_t)(q >> 2) & 1u, abort_flag) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int ox = 0; ox < t.fx; ++ox) {
+                    const int64_t site = ((int64_t)zo * L + t.y) * L + (t.x0 + ox);
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kN + (kLine - 1 - ox) * kC), v);
+                    if (!kHead) {
+                        uint32_t p[8];
+#pragma unroll
+                        for (int c = 0; c < kC; c += 2)
+                            p[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
+                        uint8_t* dst = a.out + (site * a.Sp + t.m0) * 32 + (r >> 3) * 256 + (r & 7) * 16;
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
+                        *reinterpret_cast<uint4*>(dst + 128) = make_uint4(p[4], p[5], p[6], p[7]);
+                    } else {
+                        float z[3] = {b4[0], b4[1], b4[2]};
+#pragma unroll
+                        for (int c = 0; c < kC; ++c) {
+                            const float y = fmaxf(v[c] + bias[c], 0.0f);
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) z[d] = fmaf(y, w4[d * kC + c], z[d]);
+                        }
+                        const int64_t wd = (t.m0 + warp * 32) / 64;
+                        const int hw = warp & 1;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            if (a.logits && valid)
+                                a.logits[((int64_t)d * a.L3 + site) * a.n_samples + sample] = z[d];
+                            const uint32_t bits = __ballot_sync(0xffffffffu, valid && z[d] > 0.0f);
+                            if (lane == 0 && wd < a.words) {
+                                if (bits) a.e32[2 * (((int64_t)d * a.L3 + site) * a.W + wd) + hw] ^= bits;
+                                a.dec32[(wd * a.L3 + site) * 8 + 2 * d + hw] = bits;
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce_bar(s));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kIssuerWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// First layer's input: [site][sample][8] BF16, channels s_{t-1}(n) then s_t(n)
+// for n = 0..2, then two zeros.  Rows past n_samples are zero.
+__global__ void k_expand_bits(int L3, int64_t Sp, int64_t W, int64_t words, const uint64_t* __restrict__ s_prev,
+                              const uint64_t* __restrict__ s_cur, uint4* __restrict__ out)
+{
+    const int64_t site = blockIdx.x;
+    const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+    if (m >= Sp) return;
+    const int64_t w = m >> 6;
+    const int sh = (int)(m & 63);
+    float c[6] = {0, 0, 0, 0, 0, 0};
+    if (w < words) {
+#pragma unroll
+        for (int n = 0; n < 3; ++n) {
+            c[n] = (float)((s_prev[((int64_t)n * L3 + site) * W + w] >> sh) & 1ULL);
+            c[3 + n] = (float)((s_cur[((int64_t)n * L3 + site) * W + w] >> sh) & 1ULL);
+        }
+    }
+    out[site * Sp + m] = make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), 0u);
+}
+
+int64_t tc_padded(int64_t n) { return (n + kTileM - 1) / kTileM * kTileM; }
+size_t r256(size_t x) { return (x + 255) / 256 * 256; }
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+template <bool kHead, bool kBitsIn>
+t3d_status launch_conv(const TcArgs& a, cudaStream_t st)
+{
+    static bool configured[64] = {};
+    int dev = 0;
+    T3D_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !configured[dev]) {
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<kHead, kBitsIn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kSmemBytes));
+        configured[dev] = true;
+    }
+    const int grid = (int)std::min<int64_t>(a.n_units, sm_count());
+    ProfScope prof(T3D_K_CNN, st);
+    k_conv_tc<kHead, kBitsIn><<<grid, kTcThreads, kSmemBytes, st>>>(a);
+    T3D_LAUNCH_CHECK("tensor-core convolution");
+    return T3D_OK;
+}
+
+}  // namespace
+
+size_t tc_workspace_bytes(int L, int64_t n_samples)
+{
+    const size_t sites = (size_t)L * L * L, Sp = (size_t)tc_padded(n_samples);
+    return r256(sites * Sp * 16) + 2 * r256(sites * Sp * 32);
+}
+
+t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t* s_prev, const uint64_t* s,
+                             uint64_t* e, uint64_t* dec, const Blob* blob, float* logits_out, void* work,
+                             cudaStream_t st)
+{
+    const int64_t Sp = tc_padded(n_samples), L3 = (int64_t)L * L * L;
+    uint8_t* base = static_cast<uint8_t*>(work);
+    uint8_t* in0 = base;
+    uint8_t* act0 = in0 + r256((size_t)L3 * Sp * 16);
+    uint8_t* act1 = act0 + r256((size_t)L3 * Sp * 32);
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.L = L;
+    a.L3 = (int)L3;
+    a.Sp = Sp;
+    a.n_samples = n_samples;
+    a.W = W;
+    a.words = words_for(n_samples);
+    a.nbx = (L + kLine - 1) / kLine;
+    a.n_units = (Sp / kTileM) * a.nbx * L;
+    {
+        ProfScope prof(T3D_K_CNN, st);
+        const dim3 grid((unsigned)L3, (unsigned)((Sp + 255) / 256));
+        k_expand_bits<<<grid, 256, 0, st>>>((int)L3, Sp, W, a.words, s_prev, s, reinterpret_cast<uint4*>(in0));
+        T3D_LAUNCH_CHECK("pre-decoder input expansion");
+    }
+    a.in = in0;
+    a.out = act0;
+    a.w = &blob->wf[0][0][0][0];
+    a.bias = blob->bias[0];
+    T3D_TRY((launch_conv<false, true>(a, st)));
+    a.in = act0;
+    a.out = act1;
+    a.w = &blob->wf[1][0][0][0];
+    a.bias = blob->bias[1];
+    T3D_TRY((launch_conv<false, false>(a, st)));
+    a.in = act1;
+    a.out = nullptr;
+    a.w = &blob->wf[2][0][0][0];
+    a.bias = blob->bias[2];
+    a.w4 = &blob->w4[0][0];
+    a.b4 = blob->b4;
+    a.e32 = reinterpret_cast<uint32_t*>(e);
+    a.dec32 = reinterpret_cast<uint32_t*>(dec);
+    a.logits = logits_out;
+    T3D_TRY((launch_conv<true, false>(a, st)));
+    return T3D_OK;
+}
+
+t3d_status tc_status()
+{
+    unsigned int flag = 0, zero = 0;
+    T3D_CUDA_CHECK(cudaDeviceSynchronize());
+    T3D_CUDA_CHECK(cudaMemcpyFromSymbol(&flag, g_tc_error, sizeof(flag)));
+    if (flag) {
+        T3D_CUDA_CHECK(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(zero)));
+        set_error("a tensor-core pre-decoder kernel gave up a bounded wait");
+        return T3D_ETIMEOUT;
+    }
+    return T3D_OK;
+}
+
+}  // namespace cnn
+}  // namespace t3d

@@ -9,6 +9,7 @@
 #include <cstdio>
 
 #include "../../include/toric3d.h"
+#include "t3d_device.cuh"
 
 namespace t3d {
 
@@ -100,6 +101,18 @@ t3d_status launch_syndrome(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t
 t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_apply,
                          uint32_t sweep0, uint64_t seed, uint32_t cycle, cudaStream_t st);
 t3d_status launch_logical(ItemTable& tab, cudaStream_t st);
+// gate[w] = 1 iff some sample of word w has more than max_weight unsatisfied
+// checks in s; *n_flagged (nullable) += flagged words.  scratch holds
+// gate_scratch_bytes(L, W) bytes.
+size_t gate_scratch_bytes(int L, int64_t W);
+t3d_status launch_gate(const Lattice& lat, int64_t W, const uint64_t* s, uint32_t max_weight, uint8_t* gate,
+                       unsigned long long* n_flagged, uint64_t* scratch, cudaStream_t st);
+
+// Learned pre-decoder pass (t3d_cnn.cu) on a batch or a chunk of one (rows of
+// stride W words).
+t3d_status launch_cnn_decode(int L, int64_t n_samples, int64_t W, const uint64_t* s_prev, uint64_t* s,
+                             uint64_t* e, const void* blob, float* logits_out, void* work, cudaStream_t st);
+size_t cnn_workspace_bytes(int L, int64_t n_samples);
 
 // Bytes of BP workspace per 64-sample word (two message buffers + syndrome copy).
 size_t bp_bytes_per_word(int L);

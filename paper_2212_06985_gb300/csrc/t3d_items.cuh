@@ -33,6 +33,7 @@ struct ItemDesc {
     unsigned long long* counts8;
     int64_t w0;           // BP: first 64-sample word of the current chunk
     int64_t words;        // BP: words in the current chunk
+    const uint8_t* gate;  // optional per-word flags (whole item): only flagged words are decoded
     int tx;               // bit-sliced kernels: words per thread-block row (power of 2)
     int64_t blocks;       // thread blocks this item needs in the current launch
 };

@@ -28,8 +28,22 @@ size_t state_bytes(int L, int64_t n_samples)
 struct Plan {
     ItemTable items;
     float* bp[kMaxItems];
-    int64_t chunk[kMaxItems];
+    int64_t chunk[kMaxItems];      // BP / pre-decoder chunk, words
+    // learned decoder
+    uint64_t* s_prev[kMaxItems];
+    uint64_t* s_raw[kMaxItems];
+    uint8_t* gate[kMaxItems];
+    uint64_t* gate_scratch[kMaxItems];
+    unsigned long long* n_fallback[kMaxItems];
+    void* cnn_work[kMaxItems];
+    int64_t cnn_chunk[kMaxItems];  // pre-decoder chunk, words
 };
+
+bool learned(const t3d_run_cfg& c) { return c.cnn_blob != nullptr; }
+bool needs_bp(const t3d_run_cfg& c)
+{
+    return c.bp_iters > 0 && (c.use_bp || (learned(c) && c.fallback_max_weight >= 0));
+}
 
 t3d_status validate_cfg(const t3d_run_cfg* c)
 {
@@ -42,7 +56,12 @@ t3d_status validate_cfg(const t3d_run_cfg* c)
     T3D_REQUIRE(c->n_apply == 0 || slen >= 1, "n_apply > 0 needs a schedule");
     for (size_t i = 0; i < slen; ++i)
         T3D_REQUIRE(c->schedule[i] == 'F' || c->schedule[i] == 'P', "schedule may hold only 'F' and 'P'");
-    if (c->use_bp) {
+    if (c->cnn_blob) {
+        T3D_REQUIRE(!c->use_bp, "the learned decoder replaces BP: use_bp must be 0");
+        T3D_REQUIRE(aligned(c->cnn_blob, 16), "cnn_blob must be 16-byte aligned");
+        T3D_REQUIRE(c->fallback_max_weight < 0 || c->bp_iters > 0, "the BP fallback needs bp_iters > 0");
+    }
+    if (c->use_bp || (c->cnn_blob && c->fallback_max_weight >= 0)) {
         T3D_REQUIRE(c->p > 0.0 && c->p < 1.0, "BP needs 0 < p < 1");
         T3D_REQUIRE(c->bp_iters >= 0, "bp_iters must be >= 0");
         T3D_REQUIRE(!c->bp_meas_nodes || c->q < 0.5, "measurement nodes need q < 0.5");
@@ -58,11 +77,17 @@ t3d_status validate_items(const t3d_run_cfg* c, const t3d_batch_item* items, int
     for (int i = 0; i < n_items; ++i) {
         const t3d_batch_item& it = items[i];
         T3D_TRY(check_lattice(it.L));
-        T3D_REQUIRE(!c->use_bp || it.L <= 128, "BP supports L <= 128 (item %d has L=%d)", i, it.L);
+        T3D_REQUIRE(!needs_bp(*c) || it.L <= 128, "BP supports L <= 128 (item %d has L=%d)", i, it.L);
         T3D_REQUIRE(it.n_samples >= 1 && words_for(it.n_samples) <= (1LL << 31), "item %d: n_samples out of range", i);
         T3D_REQUIRE(it.sample0 % 64 == 0, "item %d: sample0 must be a multiple of 64", i);
         T3D_TRY(check_words(it.e, "item e"));
         T3D_REQUIRE(it.counts8 == nullptr || aligned(it.counts8, 8), "item %d: counts8 must be 8-byte aligned", i);
+        if (c->cnn_blob) {
+            T3D_REQUIRE(it.L <= 128, "the pre-decoder supports L <= 128 (item %d has L=%d)", i, it.L);
+            T3D_TRY(check_words(it.s_prev, "item s_prev"));
+            T3D_REQUIRE(it.fallback_words == nullptr || aligned(it.fallback_words, 8),
+                        "item %d: fallback_words must be 8-byte aligned", i);
+        }
     }
     return T3D_OK;
 }
@@ -87,11 +112,28 @@ bool bp_chunks(const t3d_run_cfg& c, const t3d_batch_item* items, int n, size_t 
     return false;
 }
 
+int64_t chunk_words_of(const t3d_run_cfg& c, int64_t n_samples)
+{
+    const int64_t Wi = words_for(n_samples);
+    return c.bp_chunk_samples > 0 ? std::min(Wi, words_for(c.bp_chunk_samples)) : Wi;
+}
+
+size_t learned_bytes(const t3d_run_cfg& c, int L, int64_t n_samples)
+{
+    const int64_t cw = chunk_words_of(c, n_samples);
+    size_t b = round_up(state_bytes(L, n_samples)) + round_up(cnn_workspace_bytes(L, std::min(n_samples, cw * 64)));
+    if (c.fallback_max_weight >= 0)
+        b += round_up((size_t)words_for(n_samples)) + round_up(gate_scratch_bytes(L, words_for(n_samples)));
+    return b;
+}
+
 size_t batch_workspace_bytes(const t3d_run_cfg& c, const t3d_batch_item* items, int n)
 {
     size_t total = 0;
     for (int i = 0; i < n; ++i) total += 2 * round_up(state_bytes(items[i].L, items[i].n_samples));
-    if (c.use_bp && c.bp_iters > 0) {
+    if (learned(c))
+        for (int i = 0; i < n; ++i) total += learned_bytes(c, items[i].L, items[i].n_samples);
+    if (needs_bp(c)) {
         for (int i = 0; i < n; ++i) {
             const int64_t Wi = words_for(items[i].n_samples);
             const int64_t w = c.bp_chunk_samples > 0 ? std::min(Wi, words_for(c.bp_chunk_samples)) : Wi;
@@ -124,7 +166,29 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
         d.counts8 = reinterpret_cast<unsigned long long*>(items[i].counts8);
         used += 2 * sb;
     }
-    if (c.use_bp && c.bp_iters > 0) {
+    if (learned(c)) {
+        for (int i = 0; i < n; ++i) {
+            const size_t sb = round_up(state_bytes(items[i].L, items[i].n_samples));
+            T3D_REQUIRE(used + learned_bytes(c, items[i].L, items[i].n_samples) <= work_bytes,
+                        "workspace too small for the learned decoder");
+            pl.s_prev[i] = items[i].s_prev;
+            pl.s_raw[i] = reinterpret_cast<uint64_t*>(base + used);
+            used += sb;
+            pl.n_fallback[i] = reinterpret_cast<unsigned long long*>(items[i].fallback_words);
+            if (c.fallback_max_weight >= 0) {
+                const int64_t Wi = words_for(items[i].n_samples);
+                pl.gate[i] = reinterpret_cast<uint8_t*>(base + used);
+                used += round_up((size_t)Wi);
+                pl.gate_scratch[i] = reinterpret_cast<uint64_t*>(base + used);
+                used += round_up(gate_scratch_bytes(items[i].L, Wi));
+            }
+            pl.cnn_work[i] = base + used;
+            const int64_t cw = chunk_words_of(c, items[i].n_samples);
+            used += round_up(cnn_workspace_bytes(items[i].L, std::min(items[i].n_samples, cw * 64)));
+            pl.cnn_chunk[i] = cw;
+        }
+    }
+    if (needs_bp(c)) {
         T3D_REQUIRE(bp_chunks(c, items, n, work_bytes - used, pl.chunk), "workspace too small for BP chunks");
         for (int i = 0; i < n; ++i) {
             pl.bp[i] = reinterpret_cast<float*>(base + used);
@@ -133,6 +197,7 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
     } else if (c.use_bp) {
         for (int i = 0; i < n; ++i) pl.chunk[i] = std::max<int64_t>(1, words_for(items[i].n_samples));
     }
+
     return T3D_OK;
 }
 
@@ -147,12 +212,45 @@ t3d_status enqueue_run(const t3d_run_cfg& c, const Plan& pl, cudaStream_t st)
         T3D_TRY(launch_noise(tab, thr_p, c.seed, cycle, st));
         tab = pl.items;
         T3D_TRY(launch_syndrome(tab, thr_q, c.seed, cycle, st));
+        if (learned(c)) {
+            for (int i = 0; i < pl.items.n; ++i) {
+                const ItemDesc& d = pl.items.it[i];
+                T3D_CUDA_CHECK(cudaMemcpyAsync(pl.s_raw[i], d.s, (size_t)3 * d.lat.L3 * d.W * 8,
+                                               cudaMemcpyDeviceToDevice, st));
+                for (int64_t w0 = 0; w0 < d.W; w0 += pl.cnn_chunk[i]) {
+                    const int64_t n = std::min<int64_t>(pl.cnn_chunk[i] * 64, d.n_samples - w0 * 64);
+                    T3D_TRY(launch_cnn_decode(d.lat.L, n, d.W, pl.s_prev[i] + w0, d.s + w0, d.e + w0,
+                                              c.cnn_blob, nullptr, pl.cnn_work[i], st));
+                }
+            }
+        }
         if (c.use_bp)
             T3D_TRY(launch_bp(pl.items, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, pl.bp, pl.chunk,
                               nullptr, st));
         if (c.n_apply > 0) {
             tab = pl.items;
             T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
+        }
+        if (learned(c) && c.fallback_max_weight >= 0) {
+            ItemTable gated = pl.items;
+            for (int i = 0; i < gated.n; ++i) {
+                const ItemDesc& d = gated.it[i];
+                T3D_TRY(launch_gate(d.lat, d.W, d.s, (uint32_t)c.fallback_max_weight, pl.gate[i], pl.n_fallback[i],
+                                    pl.gate_scratch[i], st));
+                gated.it[i].gate = pl.gate[i];
+            }
+            T3D_TRY(launch_bp(gated, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, pl.bp, pl.chunk, nullptr, st));
+            if (c.n_apply > 0) {
+                tab = gated;
+                T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
+            }
+        }
+        if (learned(c)) {
+            for (int i = 0; i < pl.items.n; ++i) {
+                const ItemDesc& d = pl.items.it[i];
+                T3D_CUDA_CHECK(cudaMemcpyAsync(pl.s_prev[i], pl.s_raw[i], (size_t)3 * d.lat.L3 * d.W * 8,
+                                               cudaMemcpyDeviceToDevice, st));
+            }
         }
     }
     if (c.perfect_round) {
@@ -329,6 +427,7 @@ extern "C" t3d_status toric3d_run_cycles(const t3d_run_cfg* cfg, uint64_t* e, vo
 {
     clear_error();
     T3D_REQUIRE(cfg != nullptr, "cfg is NULL");
+    T3D_REQUIRE(cfg->cnn_blob == nullptr, "the learned decoder keeps s_prev state: use toric3d_run_batch");
     t3d_batch_item it = single(cfg, e, mask, counts8);
     return run_batch(cfg, &it, 1, work, work_bytes, stream);
 }

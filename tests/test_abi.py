@@ -122,3 +122,42 @@ def test_tuning_table_roundtrip():
     assert t3d.toric3d_get_blocks_per_sm("bp_step") == 3
     t3d.toric3d_set_blocks_per_sm("bp_step", 0)
     assert t3d.toric3d_get_blocks_per_sm("bp_step") == 0
+
+
+def test_learned_run_validation():
+    lib = t3d.lib()
+    items = (t3d.BatchItem * 1)()
+    items[0].L, items[0].n_samples, items[0].e, items[0].s_prev = 4, 64, 0x10000, 0x20000
+    blob = ctypes.c_void_p(0x30000)
+    cfg = t3d.make_run_cfg(4, 2, 0.04, 0.04, 0, 64, use_bp=True, bp_iters=4, schedule="F", n_apply=1)
+    cfg.cnn_blob = blob
+    assert lib.toric3d_run_batch(ctypes.byref(cfg), items, 1, FAKE, 1 << 30, None) == EINVAL
+    assert "use_bp must be 0" in _err()
+    cfg = t3d.make_run_cfg(4, 2, 0.04, 0.04, 0, 64, schedule="F", n_apply=1, fallback_max_weight=5)
+    cfg.cnn_blob = blob
+    assert lib.toric3d_run_batch(ctypes.byref(cfg), items, 1, FAKE, 1 << 30, None) == EINVAL
+    assert "bp_iters > 0" in _err()
+    cfg.fallback_max_weight = -1
+    items[0].s_prev = None
+    assert lib.toric3d_run_batch(ctypes.byref(cfg), items, 1, FAKE, 1 << 30, None) == EINVAL
+    assert "s_prev" in _err()
+    assert lib.toric3d_run_cycles(ctypes.byref(cfg), FAKE, FAKE, 1 << 30, None, None, None) == EINVAL
+    assert "toric3d_run_batch" in _err()
+    items[0].s_prev = 0x20000
+    # the learned decoder's workspace adds s_raw and the pre-decoder's scratch to the two state copies
+    plain = t3d.make_run_cfg(4, 2, 0.04, 0.04, 0, 64, schedule="F", n_apply=1)
+    assert t3d.toric3d_run_batch_workspace_bytes(cfg, items) > t3d.toric3d_run_batch_workspace_bytes(plain, items)
+    fb = t3d.make_run_cfg(4, 2, 0.04, 0.04, 0, 64, schedule="F", n_apply=1, bp_iters=4, fallback_max_weight=9)
+    fb.cnn_blob = blob
+    assert t3d.toric3d_run_batch_workspace_bytes(fb, items) > t3d.toric3d_run_batch_workspace_bytes(cfg, items)
+
+
+def test_gate_validation():
+    lib = t3d.lib()
+    assert lib.toric3d_gate(1, 1, FAKE, 0, FAKE, None, FAKE, 1 << 20, None) == EINVAL
+    assert lib.toric3d_gate(4, 0, FAKE, 0, FAKE, None, FAKE, 1 << 20, None) == EINVAL
+    assert lib.toric3d_gate(4, 1, FAKE, 0, None, None, FAKE, 1 << 20, None) == EINVAL
+    need = t3d.toric3d_gate_workspace_bytes(4, 1)
+    assert need > 0
+    assert lib.toric3d_gate(4, 1, FAKE, 0, FAKE, None, FAKE, need - 8, None) == EINVAL
+    assert "workspace" in _err()

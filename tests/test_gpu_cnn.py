@@ -22,7 +22,7 @@ def _blob(params):
     return p, blob
 
 
-@pytest.mark.parametrize("L,S", [(4, 96), (5, 64), (3, 200)])
+@pytest.mark.parametrize("L,S", [(4, 96), (5, 64), (3, 200), (8, 300), (12, 130), (2, 70)])
 def test_cnn_logits_and_corrections_match_reference(L, S):
     n = 3 * L ** 3
     params = ref.random_params(L)
@@ -34,6 +34,7 @@ def test_cnn_logits_and_corrections_match_reference(L, S):
     logits = torch.zeros((3, L ** 3, S), dtype=torch.float32, device=dev())
     t3d.toric3d_cnn_decode(L, S, s_prev, s, e, blob, workspace(t3d.toric3d_cnn_workspace_bytes(L, S)), logits)
     torch.cuda.synchronize()
+    t3d.toric3d_cnn_status()
     g = logits.cpu().numpy().transpose(2, 0, 1).reshape(S, 3, -1)
     z = ref.logits(params, L, sp, sc).numpy()
     err = np.abs(g - z)
