@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned pre-decoder + p-flip leg of the same workload")
+    ap.add_argument("--learned-chunk", type=int, default=16384,
+                    help="samples per pre-decoder launch (bounds its activation workspace)")
     return ap.parse_args()
 
 
@@ -189,6 +193,95 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CUDA arm
+# Algorithmic FLOPs of the pre-decoder per site and sample: three 3x3x3
+# convolutions (6 -> 16, 16 -> 16, 16 -> 16 channels) and the 16 -> 3 head.
+CNN_FLOP_PER_SITE = 2 * 27 * 16 * (6 + 16 + 16) + 2 * 16 * 3
+# Tensor-core FLOPs the kernels execute per site and sample (N = 8 sites x 16
+# channels per MMA including the zero blocks of the weight strips; the first
+# layer pairs two sites per K = 16): 90 MMAs of 128 x 128 x 16 per 8 x 128
+# site-samples for the hidden layers, 45 for the first.
+CNN_MMA_FLOP_PER_SITE = (45 + 90 + 90) * 2 * 128 * 128 * 16 / (8 * 128)
+WEIGHTS = os.path.join(ROOT, "paper_2212_06985_gb300", "weights", "cnn_L12_p04.npz")
+
+
+def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
+    """The same workload decoded by the learned pre-decoder + the same flip /
+    p-flip schedule instead of BP (one cycle per step through toric3d_run_batch)."""
+    import numpy as np
+    import torch
+
+    with np.load(WEIGHTS) as z:
+        params = torch.from_numpy(np.array(z["params"], dtype=np.float32)).to(dev)
+    blob = torch.empty(t3d.toric3d_cnn_blob_bytes(), dtype=torch.uint8, device=dev)
+    t3d.toric3d_cnn_prepare(params, blob)
+    sizes = w.sizes
+    W = inp.words_for(S)
+    states = [torch.zeros((inp.n_bits(L), W), dtype=torch.int64, device=dev) for L in sizes]
+    prevs = [torch.zeros_like(e) for e in states]
+    counts = [torch.zeros(8, dtype=torch.int64, device=dev) for _ in sizes]
+    batch = t3d.make_batch([dict(L=L, n_samples=S, sample0=sample0, e=e, s_prev=sp, counts8=c)
+                            for L, e, sp, c in zip(sizes, states, prevs, counts)])
+    cfg = t3d.make_run_cfg(w.L, 1, w.p, w.q, w.seed, S, sample0=sample0, schedule=w.schedule, n_apply=w.n_apply,
+                           bp_chunk_samples=min(S, args.learned_chunk), cnn_blob=blob, fallback_max_weight=-1)
+    work = torch.empty(t3d.toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
+
+    def step(t):
+        cfg.cycle0 = t
+        t3d.toric3d_run_batch(cfg, batch, work, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for t in range(args.warmup):
+            step(t)
+    stream.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    t3d.toric3d_profile_reset()
+    t3d.toric3d_profile_enable(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for t in range(args.warmup, args.warmup + args.steps):
+            step(t)
+        ev1.record(stream)
+    ev1.synchronize()
+    t3d.toric3d_profile_enable(False)
+    t3d.toric3d_cnn_status()
+    prof = {k: t3d.toric3d_profile_read(k) for k in t3d.KERNEL_KINDS}
+    t3d.toric3d_profile_reset()
+    ms = ev0.elapsed_time(ev1)
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    qubits = sum(inp.n_bits(L) for L in sizes)
+    sites = sum(L ** 3 for L in sizes)
+    cnn_ms, cnn_launches = prof["cnn"]
+    flop = CNN_FLOP_PER_SITE * sites * S * args.steps
+    tf_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
+    achieved = flop / (cnn_ms / 1e3) / 1e12 if cnn_ms > 0 else 0.0
+    del work
+    return {
+        "decoder": "learned pre-decoder (3 x conv3d 3x3x3, 16 ch, BF16 tensor cores) + " + w.schedule + " x "
+                   + str(w.n_apply), "weights": os.path.relpath(WEIGHTS, ROOT),
+        "value": qubits * S * world * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+        "gpu_launches": sum(v[1] for v in prof.values()),
+        "kernels_ms": {k: v[0] for k, v in prof.items() if v[1]},
+        "roofline": {"kernel": "k_conv_tc (3 layers) + k_expand_bits + k_dec_apply", "bound": "tensor",
+                     "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s", "frac": achieved / tf_peak,
+                     "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)" if peaks
+                     else "fallback 1.7 PFLOP/s sustained",
+                     "algorithmic_flop_per_site_sample": CNN_FLOP_PER_SITE,
+                     "executed_mma_tflops": CNN_MMA_FLOP_PER_SITE * sites * S * args.steps / (cnn_ms / 1e3) / 1e12
+                     if cnn_ms > 0 else None,
+                     "share_of_step": cnn_ms / ms if ms else None},
+        "last_cycle_logical_counts": [c.cpu().tolist() for c in counts],
+        "chunk_samples": min(S, args.learned_chunk),
+    }
+
+
 def cuda_arm(args):
     import torch
     import torch.distributed as dist
@@ -325,6 +418,11 @@ def cuda_arm(args):
                "note": "error states uploaded from and downloaded to pinned host memory every step"}
 
     fail_counts = [c.cpu().tolist() for c in counts]
+    learned = None
+    if not args.no_learned and w.decoder == "bp_pflip" and os.path.exists(WEIGHTS):
+        del work
+        learned = learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks)
+        learned["vs_bp_pflip"] = learned["value"] / value
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(w, args.cpu_seconds)
@@ -340,7 +438,8 @@ def cuda_arm(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "kernels_ms": {k: v[0] for k, v in prof.items() if v[1]},
                 "kernels_launches": {k: v[1] for k, v in prof.items() if v[1]},
-                "clocks": clk, "autotune": tuned, "last_cycle_logical_counts": fail_counts}
+                "clocks": clk, "autotune": tuned, "last_cycle_logical_counts": fail_counts,
+                "learned_pflip": learned}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

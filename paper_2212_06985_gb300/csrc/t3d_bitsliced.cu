@@ -64,7 +64,7 @@ __device__ __forceinline__ bool tile_site_word(const ItemDesc& d, int64_t lb, in
     const int t = threadIdx.x;
     w = word_tile * tx + (t & (tx - 1));
     site = (int)(site_tile * ty + t / tx);
-    return w < d.W && site < n_sites;
+    return w < (d.nw ? d.nw : d.W) && site < n_sites;
 }
 
 
@@ -395,8 +395,9 @@ t3d_status launch_noise(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t cy
     if (thr == 0) return T3D_OK;
     for (int i = 0; i < tab.n; ++i) {
         ItemDesc& d = tab.it[i];
-        d.tx = row_words(d.W);
-        d.blocks = tile_blocks(3LL * d.lat.L3, d.W, d.tx);
+        const int64_t nw = d.nw ? d.nw : d.W;
+        d.tx = row_words(nw);
+        d.blocks = tile_blocks(3LL * d.lat.L3, nw, d.tx);
     }
     finish_table(tab);
     ProfScope prof(T3D_K_NOISE, st);
@@ -410,8 +411,9 @@ t3d_status launch_syndrome(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t
 {
     for (int i = 0; i < tab.n; ++i) {
         ItemDesc& d = tab.it[i];
-        d.tx = row_words(d.W);
-        d.blocks = tile_blocks(3LL * d.lat.L3, d.W, d.tx);
+        const int64_t nw = d.nw ? d.nw : d.W;
+        d.tx = row_words(nw);
+        d.blocks = tile_blocks(3LL * d.lat.L3, nw, d.tx);
     }
     finish_table(tab);
     ProfScope prof(T3D_K_SYNDROME, st);
@@ -427,8 +429,9 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
     if (n_apply <= 0) return T3D_OK;
     for (int i = 0; i < tab.n; ++i) {
         ItemDesc& d = tab.it[i];
-        d.tx = row_words(d.W);
-        d.blocks = tile_blocks(d.lat.L3, d.W, d.tx);
+        const int64_t nw = d.nw ? d.nw : d.W;
+        d.tx = row_words(nw);
+        d.blocks = tile_blocks(d.lat.L3, nw, d.tx);
     }
     finish_table(tab);
     ItemTable t = tab;  // s and tmp swap roles every application
@@ -449,8 +452,10 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
     if (n_apply & 1) {
         for (int i = 0; i < tab.n; ++i) {
             const ItemDesc& d = tab.it[i];
-            T3D_CUDA_CHECK(cudaMemcpyAsync(d.s, d.tmp, (size_t)3 * d.lat.L3 * d.W * sizeof(uint64_t),
-                                           cudaMemcpyDeviceToDevice, st));
+            const size_t pitch = (size_t)d.W * sizeof(uint64_t);
+            const size_t width = (size_t)(d.nw ? d.nw : d.W) * sizeof(uint64_t);
+            T3D_CUDA_CHECK(cudaMemcpy2DAsync(d.s, pitch, d.tmp, pitch, width, (size_t)3 * d.lat.L3,
+                                             cudaMemcpyDeviceToDevice, st));
         }
     }
     return T3D_OK;

@@ -464,10 +464,10 @@ __global__ void k_adam(int n, float* __restrict__ p, float* __restrict__ m, floa
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// s ^= H d from the decision words left by the head: dec[word][site] holds the
-// three edges' words (as 32-bit halves) at the site.
-__global__ void k_dec_syndrome(Lattice lat, int64_t W, int64_t words, const uint64_t* __restrict__ dec,
-                               uint64_t* __restrict__ s)
+// e ^= d and s ^= H d from the decision words left by the head: dec[word][site]
+// holds the three edges' words (as 32-bit halves) at the site.
+__global__ void k_dec_apply(Lattice lat, int64_t W, int64_t words, const uint64_t* __restrict__ dec,
+                            uint64_t* __restrict__ e, uint64_t* __restrict__ s)
 {
     const int64_t w = (int64_t)blockIdx.y * 32 + (threadIdx.x & 31);
     const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
@@ -479,6 +479,11 @@ __global__ void k_dec_syndrome(Lattice lat, int64_t W, int64_t words, const uint
     for (int a = 0; a < 3; ++a) nb[a] = r + ((rc.x[a] + 1 == lat.L) ? step[a] * (1 - lat.L) : step[a]);
     const uint64_t* D = dec + w * (int64_t)lat.L3 * 4;
     auto Dd = [&](int site, int d) { return D[(int64_t)site * 4 + d]; };
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const uint64_t own = Dd(r, d);
+        if (own) e[((int64_t)d * lat.L3 + r) * W + w] ^= own;
+    }
     const uint64_t par0 = Dd(r, 1) ^ Dd(nb[2], 1) ^ Dd(r, 2) ^ Dd(nb[1], 2);
     const uint64_t par1 = Dd(r, 0) ^ Dd(nb[2], 0) ^ Dd(r, 2) ^ Dd(nb[0], 2);
     const uint64_t par2 = Dd(r, 0) ^ Dd(nb[1], 0) ^ Dd(r, 1) ^ Dd(nb[0], 1);
@@ -544,13 +549,12 @@ t3d_status launch_cnn_decode(int L, int64_t n_samples, int64_t W, const uint64_t
     const int64_t words = words_for(n_samples);
     uint64_t* dec = reinterpret_cast<uint64_t*>(work);
     void* fwd = static_cast<char*>(work) + round256((size_t)words * L * L * L * 32);
-    T3D_TRY(launch_forward_tc(L, n_samples, W, s_prev, s, e, dec, static_cast<const Blob*>(blob), logits_out, fwd,
-                              st));
+    T3D_TRY(launch_forward_tc(L, n_samples, W, s_prev, s, dec, static_cast<const Blob*>(blob), logits_out, fwd, st));
     ProfScope prof(T3D_K_CNN, st);
     const Lattice lat = make_lattice_host(L);
     dim3 sg((unsigned)((L * L * L + 7) / 8), (unsigned)((words + 31) / 32));
-    k_dec_syndrome<<<sg, 256, 0, st>>>(lat, W, words, dec, s);
-    T3D_LAUNCH_CHECK("cnn syndrome update");
+    k_dec_apply<<<sg, 256, 0, st>>>(lat, W, words, dec, e, s);
+    T3D_LAUNCH_CHECK("cnn correction");
     return T3D_OK;
 }
 

@@ -36,13 +36,16 @@ struct Blob {
 };
 
 // The tensor-core inference forward pass (conv 1..3 + head) on n_samples
-// samples whose bit-sliced rows have stride W words: flips e where a logit is
-// positive and leaves the decision words in dec ([word][site][4] uint64, the
-// three edges' words at the site).  work: tc_workspace_bytes(L, n_samples).
+// samples whose bit-sliced rows have stride W words: leaves the decisions
+// (logit > 0) in dec ([word][site][4] uint64, the three edges' words at the
+// site; e and s are updated from them by the caller).  work:
+// tc_workspace_bytes(L, n_samples).
 size_t tc_workspace_bytes(int L, int64_t n_samples);
 t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t* s_prev, const uint64_t* s,
-                             uint64_t* e, uint64_t* dec, const Blob* blob, float* logits_out, void* work,
-                             cudaStream_t st);
+                             uint64_t* dec, const Blob* blob, float* logits_out, void* work, cudaStream_t st);
+// Per-device launch attributes of the tensor-core kernels (call before any
+// stream capture; idempotent).
+t3d_status tc_prepare();
 // T3D_OK, or T3D_ETIMEOUT if a tensor-core kernel gave up a bounded wait since
 // the last call (reads and clears the device flag; synchronises the device).
 t3d_status tc_status();

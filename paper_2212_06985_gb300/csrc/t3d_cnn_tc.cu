@@ -34,8 +34,9 @@
 //   warp 4     producer: one thread issues the bulk copies of input tiles into
 //              a ring of shared-memory slots;
 //   warp 5     MMA issuer: one thread issues the MMAs and commits their
-//              completion to the slot's "empty" barrier and to the plane's
-//              "accumulators full" barrier.
+//              completion to the row's "empty" barrier and to the plane's
+//              "accumulators full" barrier (the code takes kIssuers threads
+//              owning alternate planes; two were slower than one on GB300).
 // Every wait is bounded (one second); a wait that gives up sets the device
 // error flag and the CTA winds down (waiting, again bounded, for its copies and
 // MMAs in flight, and freeing its TMEM) so the context stays usable.
@@ -45,15 +46,16 @@
 // same layout, [site][sample/8][channel/8][8 samples][8 channels] BF16, so a
 // tile (site, 128 samples) is one contiguous 4 KiB block: K-direction core
 // matrix stride (LBO) 128 B, M-direction stride (SBO) 256 B.  The first
-// layer's input (6 of 16 channels used) is stored as [site][sample][8]
-// (2 KiB per tile, SBO 128 B); its channels 8..15 come from a zero block that
-// sits 2 KiB after the tile in every ring slot (LBO 2 KiB).  Weight blocks:
+// layer's input (6 of 8 channels used) is stored as [site][sample][8]
+// (2 KiB per tile, SBO 128 B); two x-adjacent sites fill one 4 KiB slot as the
+// two K chunks of one operand (LBO 2 KiB), see pair_start.  Weight blocks:
 // [co/8][ci/8][co%8][ci%8] (512 B, LBO 128 B, SBO 256 B).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "t3d_cnn.cuh"
 #include "t3d_device.cuh"
@@ -76,21 +78,32 @@ constexpr int kStripPad = 7;                        // zero blocks between strip
 constexpr int kStripBlocks = kStripPad + 9 * (3 + kStripPad);   // 97
 constexpr int kWBytes = kStripBlocks * 512;         // 49,664 B
 constexpr int kEpiWarps = 4;
+constexpr int kEpiBatch = 4;                        // TMEM loads in flight per epilogue thread
 constexpr int kProducerWarp = 4;
-constexpr int kIssuerWarp = 5;
-constexpr int kTcThreads = 192;
+constexpr int kIssuerWarp = 5;                      // .. kIssuerWarp + kIssuers - 1
+constexpr int kIssuers = 1;                         // two issuers measured slower on GB300
+constexpr int kTcThreads = 32 * (kIssuerWarp + kIssuers);
 constexpr uint64_t kWaitNs = 1000000000ull;         // bound of every wait
 
 // Dynamic shared memory: ring | weight strips | barriers | misc.
 constexpr int kOffW = kRing * kSlotBytes;
 constexpr int kOffBar = kOffW + kWBytes;
-constexpr int kNumBars = 2 * kGroups + 2 * kPlanes + 1;   // full, empty, acc_full, acc_empty, done
+constexpr int kNumBars = 2 * kGroups + 2 * kPlanes + kIssuers;   // full, empty, acc_full, acc_empty, done
 constexpr int kOffMisc = kOffBar + kNumBars * 8;
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;        // + alignment slack
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 // Block index of W(dx = -1, dy, dz) in the strips; s = (dz + 1) * 3 + (dy + 1).
 __host__ __device__ constexpr int strip_start(int s) { return kStripPad + s * (3 + kStripPad); }
+
+// First layer (8 input channels per site): two x-adjacent input sites share
+// one K = 16 tile (K chunk 0 = site x, chunk 1 = site x + 1), and the pair
+// strip of (dy, dz) holds blocks [W(t) | W(t + 1)] for first-site offsets
+// t = -2 .. 1 (W = 0 outside -1..1) between 6 zero blocks; the view for the
+// pair starting at input offset xa begins at pair_start(s) + xa - 5.
+constexpr int kPairPad = 6;
+__host__ __device__ constexpr int pair_start(int s) { return kPairPad + s * (4 + kPairPad); }
+static_assert(kPairPad + 9 * (4 + kPairPad) <= kStripBlocks, "pair strips fit the strip area");
 
 // Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
@@ -114,7 +127,6 @@ struct TcArgs {
     const float* bias;          // [16]
     const float* w4;            // head [3][16]
     const float* b4;            // [3]
-    uint32_t* e32;              // head: error words as 32-bit halves
     uint32_t* dec32;            // head: decision words [word][site][8] 32-bit halves
     float* logits;              // head: optional [3][L^3][n_samples]
 };
@@ -249,10 +261,10 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
                  : "memory");
 }
 
-// Warp: 32 TMEM lanes x 16 consecutive 32-bit columns, one lane per thread.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// Warp: 32 TMEM lanes x 16 consecutive 32-bit columns, one lane per thread
+// (asynchronous: the registers are valid after tmem_wait_ld).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
 {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
@@ -260,9 +272,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
@@ -310,40 +324,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     auto empty_bar = [&](int i) { return bars + 8u * (uint32_t)(kGroups + i); };
     auto accf_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kGroups + i); };
     auto acce_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kGroups + kPlanes + i); };
-    const uint32_t done_bar = bars + 8u * (uint32_t)(2 * kGroups + 2 * kPlanes);
+    auto done_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kGroups + 2 * kPlanes + i); };
     uint32_t* misc = reinterpret_cast<uint32_t*>(sm + kOffMisc);   // [0] TMEM base, [1] abort flag
     volatile uint32_t* abort_flag = misc + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // weight strips: zero everything, then W(dx, dy, dz) at block strip_start(s) + dx + 1 in the
-    // B-operand layout [co/8][ci/8][co%8][ci%8]
+    // B-operand layout [co/8][ci/8][co%8][ci%8]; first layer: the pair strips
     for (int i = threadIdx.x; i < kWBytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(sm + kOffW)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     for (int i = threadIdx.x; i < kOff * kC * kC; i += blockDim.x) {
         const int k = i >> 8, co = (i >> 4) & 15, ci = i & 15;
-        const int blk = strip_start(k / 3) + k % 3;   // k / 3 = (dz + 1) * 3 + (dy + 1), k % 3 = dx + 1
-        const int off = blk * 512 + (co >> 3) * 256 + (ci >> 3) * 128 + (co & 7) * 16 + (ci & 7) * 2;
-        *reinterpret_cast<__nv_bfloat16*>(sm + kOffW + off) = a.w[i];
-    }
-    if (kBitsIn) {   // zero block 2 KiB after the tile in every slot: channels 8..15 of layer 1
-        for (int i = threadIdx.x; i < kRing * 128; i += blockDim.x) {
-            const int slot = i >> 7, j = i & 127;
-            reinterpret_cast<uint4*>(sm + slot * kSlotBytes + 2048)[j] = make_uint4(0, 0, 0, 0);
+        const int st = k / 3, dx = k % 3 - 1;   // st = (dz + 1) * 3 + (dy + 1)
+        const __nv_bfloat16 w = a.w[i];
+        const int row = (co >> 3) * 256 + (co & 7) * 16;
+        if (kBitsIn) {
+            if (ci >= 8) continue;   // no such input channel
+            // chunk 0 of the block with t = dx, chunk 1 of the block with t = dx - 1
+            *reinterpret_cast<__nv_bfloat16*>(sm + kOffW + (pair_start(st) + dx + 2) * 512 + row + ci * 2) = w;
+            *reinterpret_cast<__nv_bfloat16*>(sm + kOffW + (pair_start(st) + dx + 1) * 512 + row + 128 + ci * 2) = w;
+        } else {
+            const int off = (strip_start(st) + dx + 1) * 512 + row + (ci >> 3) * 128 + (ci & 7) * 2;
+            *reinterpret_cast<__nv_bfloat16*>(sm + kOffW + off) = w;
         }
     }
     fence_proxy_async_smem();
     if (threadIdx.x == 0) {
         for (int i = 0; i < kGroups; ++i) {
             mbar_init(full_bar(i), 1);
-            mbar_init(empty_bar(i), 1);
+            mbar_init(empty_bar(i), kIssuers);   // one commit per issuer
         }
         for (int i = 0; i < kPlanes; ++i) {
             mbar_init(accf_bar(i), 1);
             mbar_init(acce_bar(i), kEpiWarps);
         }
-        mbar_init(done_bar, 1);
+        for (int i = 0; i < kIssuers; ++i) mbar_init(done_bar(i), 1);
         misc[1] = 0;
         fence_mbar_init();
     }
@@ -373,13 +390,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                             ok = false;
                             break;
                         }
+                        // tiles x = x0-1 .. : pointer steps of one site, wrapping at x = L
                         const int64_t row = ((int64_t)zw * L + wrap(yi, L)) * L;
-                        mbar_arrive_expect_tx(full_bar(g), (uint32_t)(t.fx + 2) * tile_bytes);
-                        const uint32_t dst = ring + (uint32_t)(g * kRowSlots) * kSlotBytes;
-                        for (int xa = -1; xa <= t.fx; ++xa) {
-                            const int64_t site = row + wrap(t.x0 + xa, L);
-                            bulk_load(dst + (uint32_t)(xa + 1) * kSlotBytes, a.in + (site * a.Sp + t.m0) * in_row,
-                                      tile_bytes, full_bar(g));
+                        const int64_t site_bytes = a.Sp * in_row;
+                        const uint8_t* row_ptr = a.in + (row * a.Sp + t.m0) * in_row;
+                        int x = wrap(t.x0 - 1, L);
+                        const uint8_t* src = row_ptr + x * site_bytes;
+                        const int n_tiles = kBitsIn ? 2 * ((t.fx + 3) / 2) : t.fx + 2;
+                        const uint32_t dst_step = kBitsIn ? tile_bytes : (uint32_t)kSlotBytes;
+                        uint32_t dst = ring + (uint32_t)(g * kRowSlots) * kSlotBytes;
+                        mbar_arrive_expect_tx(full_bar(g), (uint32_t)n_tiles * tile_bytes);
+                        for (int i = 0; i < n_tiles; ++i) {
+                            bulk_load(dst, src, tile_bytes, full_bar(g));
+                            dst += dst_step;
+                            if (++x == L) {
+                                x = 0;
+                                src = row_ptr;
+                            } else {
+                                src += site_bytes;
+                            }
                         }
                         ++gseq;
                     }
@@ -394,11 +423,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
             }
         }
         __syncwarp();
-    } else if (warp == kIssuerWarp) {
+    } else if (warp >= kIssuerWarp && warp < kIssuerWarp + kIssuers) {
+        // issuer iss owns the output planes with sequence number q = iss (mod kIssuers): every
+        // accumulator is written by one thread, in program order
+        const int iss = warp - kIssuerWarp;
         if (lane == 0) {
             uint32_t gseq = 0;
             int64_t qbase = 0;
             bool ok = true;
+            // first layer: K chunk 1 is the pair's second site, 2 KiB further
             const uint32_t a_lbo = kBitsIn ? 2048u : 128u, a_sbo = kBitsIn ? 128u : 256u;
             const uint64_t bdesc0 = smem_desc(wsm, 128u, 256u);   // + 32 per 512-byte block
             for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
@@ -406,7 +439,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                 const bool full = t.fx == kLine;
                 for (int zi = -1; zi <= L && ok; ++zi) {
                     // output plane zi + 1 is first written by this input plane
-                    if (zi + 1 <= L - 1) {
+                    if (zi + 1 <= L - 1 && (int)((qbase + zi + 1) % kIssuers) == iss) {
                         const int64_t q = qbase + zi + 1;
                         const uint32_t v = (uint32_t)(q >> 2);
                         if (v > 0 && !wait_bar(acce_bar((int)(q & 3)), (v - 1) & 1u, abort_flag)) {
@@ -420,7 +453,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
                         const int zo = zi - (i - 1);
-                        colb[i] = (zo >= 0 && zo < L) ? (int)((qbase + zo) & 3) * kN : -1;
+                        colb[i] = (zo >= 0 && zo < L && (int)((qbase + zo) % kIssuers) == iss)
+                                      ? (int)((qbase + zo) & 3) * kN
+                                      : -1;
                     }
                     // one tile: input offset xa = x_i - x0 in [-1, 8], dy; the MMA into plane
                     // zi + 1 from the plane's first tile (xa = -1, dy = -1) overwrites D.
@@ -436,12 +471,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                     // the three rows of the plane, each one slot group behind one barrier
                     auto row_mmas = [&](int dyi) {
                         const int g = (int)(gseq % kGroups);
+                        // the copies and the MMAs meet through the barrier (both in the async proxy)
                         if (ok && !wait_bar(full_bar(g), (gseq / kGroups) & 1u, abort_flag)) ok = false;
                         if (!ok) return;
-                        tc_fence_after();
                         const uint64_t adesc0 =
                             smem_desc(ring + (uint32_t)(g * kRowSlots) * kSlotBytes, a_lbo, a_sbo);
-                        if (full) {
+                        if (kBitsIn) {
+                            // pair p: sites x0-1+2p, x0+2p (4 KiB slot p); view pair_start + xa - 5
+                            auto pair_mmas = [&](int p) {
+                                const int xa = 2 * p - 1;
+#pragma unroll
+                                for (int i = 0; i < 3; ++i) {
+                                    if (colb[i] < 0) continue;
+                                    const int blk = pair_start(i * 3 + dyi) + xa - 5;
+                                    const uint32_t acc = (i == 0 && dyi == 0 && p == 0) ? 0u : 1u;
+                                    mma_bf16(tmem + (uint32_t)colb[i], adesc0 + (uint64_t)(p * (kSlotBytes >> 4)),
+                                             bdesc0 + (uint64_t)(32 * blk), acc);
+                                }
+                            };
+                            if (full) {
+#pragma unroll
+                                for (int p = 0; p < (kLine + 2) / 2; ++p) pair_mmas(p);
+                            } else {
+                                for (int p = 0; p < (t.fx + 3) / 2; ++p) pair_mmas(p);
+                            }
+                        } else if (full) {
 #pragma unroll
                             for (int xa = -1; xa <= kLine; ++xa)
                                 tile_mmas(xa, dyi, adesc0 + (uint64_t)((xa + 1) * (kSlotBytes >> 4)));
@@ -457,13 +511,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                     row_mmas(2);
                     if (!ok) break;
                     // output plane zi - 1 has received its last contribution
-                    if (zi - 1 >= 0 && zi - 1 <= L - 1) mma_commit(accf_bar((int)((qbase + zi - 1) & 3)));
+                    if (zi - 1 >= 0 && zi - 1 <= L - 1 && (int)((qbase + zi - 1) % kIssuers) == iss)
+                        mma_commit(accf_bar((int)((qbase + zi - 1) & 3)));
                 }
                 qbase += L;
             }
             // every MMA issued has completed before TMEM is released
-            mma_commit(done_bar);
-            wait_bar(done_bar, 0, abort_flag, true);
+            mma_commit(done_bar(iss));
+            wait_bar(done_bar(iss), 0, abort_flag, true);
         }
         __syncwarp();
     } else {
@@ -497,36 +552,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                     break;
                 }
                 tc_fence_after();
-                for (int ox = 0; ox < t.fx; ++ox) {
-                    const int64_t site = ((int64_t)zo * L + t.y) * L + (t.x0 + ox);
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kN + (kLine - 1 - ox) * kC), v);
-                    if (!kHead) {
-                        uint32_t p[8];
+                // four outputs per batch of TMEM loads, one wait per batch
+                for (int ob = 0; ob < t.fx; ob += kEpiBatch) {
+                    uint32_t raw[kEpiBatch][16];
 #pragma unroll
-                        for (int c = 0; c < kC; c += 2)
-                            p[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
-                        uint8_t* dst = a.out + (site * a.Sp + t.m0) * 32 + (r >> 3) * 256 + (r & 7) * 16;
-                        *reinterpret_cast<uint4*>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
-                        *reinterpret_cast<uint4*>(dst + 128) = make_uint4(p[4], p[5], p[6], p[7]);
-                    } else {
-                        float z[3] = {b4[0], b4[1], b4[2]};
+                    for (int j = 0; j < kEpiBatch; ++j)
+                        if (ob + j < t.fx)
+                            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) +
+                                          (uint32_t)(s * kN + (kLine - 1 - (ob + j)) * kC),
+                                      raw[j]);
+                    tmem_wait_ld();
 #pragma unroll
-                        for (int c = 0; c < kC; ++c) {
-                            const float y = fmaxf(v[c] + bias[c], 0.0f);
+                    for (int j = 0; j < kEpiBatch; ++j) {
+                        if (ob + j >= t.fx) continue;
+                        const int64_t site = ((int64_t)zo * L + t.y) * L + (t.x0 + ob + j);
+                        float v[16];
 #pragma unroll
-                            for (int d = 0; d < 3; ++d) z[d] = fmaf(y, w4[d * kC + c], z[d]);
-                        }
-                        const int64_t wd = (t.m0 + warp * 32) / 64;
-                        const int hw = warp & 1;
+                        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(raw[j][c]);
+                        if (!kHead) {
+                            uint32_t p[8];
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            if (a.logits && valid)
-                                a.logits[((int64_t)d * a.L3 + site) * a.n_samples + sample] = z[d];
-                            const uint32_t bits = __ballot_sync(0xffffffffu, valid && z[d] > 0.0f);
-                            if (lane == 0 && wd < a.words) {
-                                if (bits) a.e32[2 * (((int64_t)d * a.L3 + site) * a.W + wd) + hw] ^= bits;
-                                a.dec32[(wd * a.L3 + site) * 8 + 2 * d + hw] = bits;
+                            for (int c = 0; c < kC; c += 2)
+                                p[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
+                            uint8_t* dst = a.out + (site * a.Sp + t.m0) * 32 + (r >> 3) * 256 + (r & 7) * 16;
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
+                            *reinterpret_cast<uint4*>(dst + 128) = make_uint4(p[4], p[5], p[6], p[7]);
+                        } else {
+                            float z[3] = {b4[0], b4[1], b4[2]};
+#pragma unroll
+                            for (int c = 0; c < kC; ++c) {
+                                const float y = fmaxf(v[c] + bias[c], 0.0f);
+#pragma unroll
+                                for (int d = 0; d < 3; ++d) z[d] = fmaf(y, w4[d * kC + c], z[d]);
+                            }
+                            const int64_t wd = (t.m0 + warp * 32) / 64;
+                            const int hw = warp & 1;
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                if (a.logits && valid)
+                                    a.logits[((int64_t)d * a.L3 + site) * a.n_samples + sample] = z[d];
+                                const uint32_t bits = __ballot_sync(0xffffffffu, valid && z[d] > 0.0f);
+                                if (lane == 0 && wd < a.words) a.dec32[(wd * a.L3 + site) * 8 + 2 * d + hw] = bits;
                             }
                         }
                     }
@@ -546,24 +612,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
 }
 
 // First layer's input: [site][sample][8] BF16, channels s_{t-1}(n) then s_t(n)
-// for n = 0..2, then two zeros.  Rows past n_samples are zero.
+// for n = 0..2, then two zeros.  Rows past n_samples are zero.  One warp per
+// site and 256 samples (4 words): lanes 0..23 load the 6 channels x 4 words,
+// and store j of the warp writes samples 32j .. 32j + 31 (512 contiguous bytes).
 __global__ void k_expand_bits(int L3, int64_t Sp, int64_t W, int64_t words, const uint64_t* __restrict__ s_prev,
                               const uint64_t* __restrict__ s_cur, uint4* __restrict__ out)
 {
-    const int64_t site = blockIdx.x;
-    const int64_t m = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
-    if (m >= Sp) return;
-    const int64_t w = m >> 6;
-    const int sh = (int)(m & 63);
-    float c[6] = {0, 0, 0, 0, 0, 0};
-    if (w < words) {
-#pragma unroll
-        for (int n = 0; n < 3; ++n) {
-            c[n] = (float)((s_prev[((int64_t)n * L3 + site) * W + w] >> sh) & 1ULL);
-            c[3 + n] = (float)((s_cur[((int64_t)n * L3 + site) * W + w] >> sh) & 1ULL);
+    const int64_t site = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const int64_t m0 = (int64_t)blockIdx.y * 256;
+    if (site >= L3) return;
+    uint64_t v = 0;
+    if (lane < 24) {
+        const int c = lane >> 2;
+        const int64_t w = (m0 >> 6) + (lane & 3);
+        if (w < words) {
+            const uint64_t* src = c < 3 ? s_prev : s_cur;
+            v = __ldg(&src[((int64_t)(c % 3) * L3 + site) * W + w]);
         }
     }
-    out[site * Sp + m] = make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), 0u);
+    constexpr uint32_t one = 0x3F80u;   // BF16 1.0
+    uint4* dst = out + site * Sp + m0 + lane;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (m0 + 32 * j >= Sp) break;
+        const uint32_t half = (uint32_t)(v >> (32 * (j & 1)));
+        uint32_t h[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) h[c] = ((__shfl_sync(0xffffffffu, half, c * 4 + (j >> 1)) >> lane) & 1u) * one;
+        dst[32 * j] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), 0u);
+    }
 }
 
 int64_t tc_padded(int64_t n) { return (n + kTileM - 1) / kTileM * kTileM; }
@@ -580,14 +658,6 @@ int sm_count()
 template <bool kHead, bool kBitsIn>
 t3d_status launch_conv(const TcArgs& a, cudaStream_t st)
 {
-    static bool configured[64] = {};
-    int dev = 0;
-    T3D_CUDA_CHECK(cudaGetDevice(&dev));
-    if (dev >= 0 && dev < 64 && !configured[dev]) {
-        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<kHead, kBitsIn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kSmemBytes));
-        configured[dev] = true;
-    }
     const int grid = (int)std::min<int64_t>(a.n_units, sm_count());
     ProfScope prof(T3D_K_CNN, st);
     k_conv_tc<kHead, kBitsIn><<<grid, kTcThreads, kSmemBytes, st>>>(a);
@@ -597,6 +667,26 @@ t3d_status launch_conv(const TcArgs& a, cudaStream_t st)
 
 }  // namespace
 
+t3d_status tc_prepare()
+{
+    static std::mutex mu;
+    static bool configured[64] = {};
+    int dev = 0;
+    T3D_CUDA_CHECK(cudaGetDevice(&dev));
+    T3D_REQUIRE(dev >= 0 && dev < 64, "device %d outside the 64 supported", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!configured[dev]) {
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kSmemBytes));
+        configured[dev] = true;
+    }
+    return T3D_OK;
+}
+
 size_t tc_workspace_bytes(int L, int64_t n_samples)
 {
     const size_t sites = (size_t)L * L * L, Sp = (size_t)tc_padded(n_samples);
@@ -604,8 +694,7 @@ size_t tc_workspace_bytes(int L, int64_t n_samples)
 }
 
 t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t* s_prev, const uint64_t* s,
-                             uint64_t* e, uint64_t* dec, const Blob* blob, float* logits_out, void* work,
-                             cudaStream_t st)
+                             uint64_t* dec, const Blob* blob, float* logits_out, void* work, cudaStream_t st)
 {
     const int64_t Sp = tc_padded(n_samples), L3 = (int64_t)L * L * L;
     uint8_t* base = static_cast<uint8_t*>(work);
@@ -622,9 +711,10 @@ t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t
     a.words = words_for(n_samples);
     a.nbx = (L + kLine - 1) / kLine;
     a.n_units = (Sp / kTileM) * a.nbx * L;
+    T3D_TRY(tc_prepare());
     {
         ProfScope prof(T3D_K_CNN, st);
-        const dim3 grid((unsigned)L3, (unsigned)((Sp + 255) / 256));
+        const dim3 grid((unsigned)((L3 + 7) / 8), (unsigned)((Sp + 255) / 256));
         k_expand_bits<<<grid, 256, 0, st>>>((int)L3, Sp, W, a.words, s_prev, s, reinterpret_cast<uint4*>(in0));
         T3D_LAUNCH_CHECK("pre-decoder input expansion");
     }
@@ -644,7 +734,6 @@ t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t
     a.bias = blob->bias[2];
     a.w4 = &blob->w4[0][0];
     a.b4 = blob->b4;
-    a.e32 = reinterpret_cast<uint32_t*>(e);
     a.dec32 = reinterpret_cast<uint32_t*>(dec);
     a.logits = logits_out;
     T3D_TRY((launch_conv<true, false>(a, st)));

@@ -19,7 +19,8 @@ constexpr int kMaxItems = 8;
 
 struct ItemDesc {
     Lattice lat;
-    int64_t W;            // 64-bit words per bit-sliced row
+    int64_t W;            // 64-bit words per bit-sliced row (row stride)
+    int64_t nw;           // bit-sliced kernels: words to process from the row start (0 = W)
     int64_t n_samples;
     uint64_t group0;      // global index of the item's first 64-sample word
     uint64_t* e;          // bit-sliced error state [3L^3][W]

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "t3d_cnn.cuh"
 #include "t3d_host.hpp"
 #include "t3d_items.cuh"
 
@@ -24,6 +25,7 @@ size_t state_bytes(int L, int64_t n_samples)
 {
     return (size_t)3 * L * L * L * (size_t)words_for(n_samples) * sizeof(uint64_t);
 }
+
 
 struct Plan {
     ItemTable items;
@@ -40,6 +42,7 @@ struct Plan {
 };
 
 bool learned(const t3d_run_cfg& c) { return c.cnn_blob != nullptr; }
+
 bool needs_bp(const t3d_run_cfg& c)
 {
     return c.bp_iters > 0 && (c.use_bp || (learned(c) && c.fallback_max_weight >= 0));
@@ -112,15 +115,22 @@ bool bp_chunks(const t3d_run_cfg& c, const t3d_batch_item* items, int n, size_t 
     return false;
 }
 
-int64_t chunk_words_of(const t3d_run_cfg& c, int64_t n_samples)
+// Pre-decoder chunk (words): cfg.bp_chunk_samples, or by default as many
+// samples as keep the pre-decoder's activations within kCnnAutoBytes.
+constexpr size_t kCnnAutoBytes = 8ull << 30;
+
+int64_t cnn_chunk_words(const t3d_run_cfg& c, int L, int64_t n_samples)
 {
     const int64_t Wi = words_for(n_samples);
-    return c.bp_chunk_samples > 0 ? std::min(Wi, words_for(c.bp_chunk_samples)) : Wi;
+    if (c.bp_chunk_samples > 0) return std::min(Wi, words_for(c.bp_chunk_samples));
+    const size_t per_sample = cnn_workspace_bytes(L, 128) / 128 + 1;
+    const int64_t fit = (int64_t)(kCnnAutoBytes / per_sample) / 128 * 128;
+    return std::min(Wi, std::max<int64_t>(2, words_for(fit)));
 }
 
 size_t learned_bytes(const t3d_run_cfg& c, int L, int64_t n_samples)
 {
-    const int64_t cw = chunk_words_of(c, n_samples);
+    const int64_t cw = cnn_chunk_words(c, L, n_samples);
     size_t b = round_up(state_bytes(L, n_samples)) + round_up(cnn_workspace_bytes(L, std::min(n_samples, cw * 64)));
     if (c.fallback_max_weight >= 0)
         b += round_up((size_t)words_for(n_samples)) + round_up(gate_scratch_bytes(L, words_for(n_samples)));
@@ -182,12 +192,13 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
                 pl.gate_scratch[i] = reinterpret_cast<uint64_t*>(base + used);
                 used += round_up(gate_scratch_bytes(items[i].L, Wi));
             }
+            const int64_t cw = cnn_chunk_words(c, items[i].L, items[i].n_samples);
             pl.cnn_work[i] = base + used;
-            const int64_t cw = chunk_words_of(c, items[i].n_samples);
             used += round_up(cnn_workspace_bytes(items[i].L, std::min(items[i].n_samples, cw * 64)));
             pl.cnn_chunk[i] = cw;
         }
     }
+    if (learned(c)) T3D_TRY(cnn::tc_prepare());   // before any stream capture
     if (needs_bp(c)) {
         T3D_REQUIRE(bp_chunks(c, items, n, work_bytes - used, pl.chunk), "workspace too small for BP chunks");
         for (int i = 0; i < n; ++i) {
@@ -201,6 +212,60 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
     return T3D_OK;
 }
 
+// Copy a word range of a bit-sliced array (3 L^3 rows of stride W words).
+t3d_status copy_rows(uint64_t* dst, const uint64_t* src, const ItemDesc& d, int64_t w0, int64_t nw, cudaStream_t st)
+{
+    const size_t pitch = (size_t)d.W * sizeof(uint64_t);
+    T3D_CUDA_CHECK(cudaMemcpy2DAsync(dst + w0, pitch, src + w0, pitch, (size_t)nw * sizeof(uint64_t),
+                                     (size_t)3 * d.lat.L3, cudaMemcpyDeviceToDevice, st));
+    return T3D_OK;
+}
+
+// One cycle of the learned decoder: qubit noise and the noisy measurement of
+// every item, the pre-decoder chunk by chunk (each chunk decodes from its own
+// (s_prev, s) rows), the flip / p-flip schedule, the optional fallback (gate,
+// then BP and the schedule on the flagged words), and s_prev <- the measured s.
+// (Running chunks on two streams, so that one chunk's pre-decoder overlaps the
+// other's sweeps, measured slower on GB300: the sweeps' blocks delay the
+// persistent one-CTA-per-SM convolutions.)
+t3d_status enqueue_learned_cycle(const t3d_run_cfg& c, const Plan& pl, uint32_t cycle, uint64_t thr_p,
+                                 uint64_t thr_q, int slen, cudaStream_t st)
+{
+    ItemTable tab = pl.items;
+    T3D_TRY(launch_noise(tab, thr_p, c.seed, cycle, st));
+    tab = pl.items;
+    T3D_TRY(launch_syndrome(tab, thr_q, c.seed, cycle, st));
+    for (int i = 0; i < pl.items.n; ++i) {
+        const ItemDesc& d = pl.items.it[i];
+        T3D_TRY(copy_rows(pl.s_raw[i], d.s, d, 0, d.W, st));
+        for (int64_t w0 = 0; w0 < d.W; w0 += pl.cnn_chunk[i]) {
+            const int64_t n = std::min<int64_t>(pl.cnn_chunk[i] * 64, d.n_samples - w0 * 64);
+            T3D_TRY(launch_cnn_decode(d.lat.L, n, d.W, pl.s_prev[i] + w0, d.s + w0, d.e + w0, c.cnn_blob, nullptr,
+                                      pl.cnn_work[i], st));
+        }
+    }
+    if (c.n_apply > 0) {
+        tab = pl.items;
+        T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
+    }
+    if (c.fallback_max_weight >= 0) {
+        ItemTable gated = pl.items;
+        for (int i = 0; i < gated.n; ++i) {
+            const ItemDesc& d = gated.it[i];
+            T3D_TRY(launch_gate(d.lat, d.W, d.s, (uint32_t)c.fallback_max_weight, pl.gate[i], pl.n_fallback[i],
+                                pl.gate_scratch[i], st));
+            gated.it[i].gate = pl.gate[i];
+        }
+        T3D_TRY(launch_bp(gated, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, pl.bp, pl.chunk, nullptr, st));
+        if (c.n_apply > 0) {
+            tab = gated;
+            T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
+        }
+    }
+    for (int i = 0; i < pl.items.n; ++i) T3D_TRY(copy_rows(pl.s_prev[i], pl.s_raw[i], pl.items.it[i], 0, pl.items.it[i].W, st));
+    return T3D_OK;
+}
+
 t3d_status enqueue_run(const t3d_run_cfg& c, const Plan& pl, cudaStream_t st)
 {
     const uint64_t thr_p = prob_threshold(c.p), thr_q = prob_threshold(c.q);
@@ -208,49 +273,20 @@ t3d_status enqueue_run(const t3d_run_cfg& c, const Plan& pl, cudaStream_t st)
     ItemTable tab;
     for (int t = 1; t <= c.T; ++t) {
         const uint32_t cycle = c.cycle0 + (uint32_t)t;
+        if (learned(c)) {
+            T3D_TRY(enqueue_learned_cycle(c, pl, cycle, thr_p, thr_q, slen, st));
+            continue;
+        }
         tab = pl.items;
         T3D_TRY(launch_noise(tab, thr_p, c.seed, cycle, st));
         tab = pl.items;
         T3D_TRY(launch_syndrome(tab, thr_q, c.seed, cycle, st));
-        if (learned(c)) {
-            for (int i = 0; i < pl.items.n; ++i) {
-                const ItemDesc& d = pl.items.it[i];
-                T3D_CUDA_CHECK(cudaMemcpyAsync(pl.s_raw[i], d.s, (size_t)3 * d.lat.L3 * d.W * 8,
-                                               cudaMemcpyDeviceToDevice, st));
-                for (int64_t w0 = 0; w0 < d.W; w0 += pl.cnn_chunk[i]) {
-                    const int64_t n = std::min<int64_t>(pl.cnn_chunk[i] * 64, d.n_samples - w0 * 64);
-                    T3D_TRY(launch_cnn_decode(d.lat.L, n, d.W, pl.s_prev[i] + w0, d.s + w0, d.e + w0,
-                                              c.cnn_blob, nullptr, pl.cnn_work[i], st));
-                }
-            }
-        }
         if (c.use_bp)
             T3D_TRY(launch_bp(pl.items, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, pl.bp, pl.chunk,
                               nullptr, st));
         if (c.n_apply > 0) {
             tab = pl.items;
             T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
-        }
-        if (learned(c) && c.fallback_max_weight >= 0) {
-            ItemTable gated = pl.items;
-            for (int i = 0; i < gated.n; ++i) {
-                const ItemDesc& d = gated.it[i];
-                T3D_TRY(launch_gate(d.lat, d.W, d.s, (uint32_t)c.fallback_max_weight, pl.gate[i], pl.n_fallback[i],
-                                    pl.gate_scratch[i], st));
-                gated.it[i].gate = pl.gate[i];
-            }
-            T3D_TRY(launch_bp(gated, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, pl.bp, pl.chunk, nullptr, st));
-            if (c.n_apply > 0) {
-                tab = gated;
-                T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
-            }
-        }
-        if (learned(c)) {
-            for (int i = 0; i < pl.items.n; ++i) {
-                const ItemDesc& d = pl.items.it[i];
-                T3D_CUDA_CHECK(cudaMemcpyAsync(pl.s_prev[i], pl.s_raw[i], (size_t)3 * d.lat.L3 * d.W * 8,
-                                               cudaMemcpyDeviceToDevice, st));
-            }
         }
     }
     if (c.perfect_round) {

@@ -104,12 +104,13 @@ def _run(L, S, T, blob, max_w, chunk=0, use_graph=False, split=None):
     return download_bits(e, S), download_bits(s_prev, S), int(fb.item()), counts.cpu().numpy()
 
 
-@pytest.mark.parametrize("max_w", [-1, 0, 60, 10 ** 6])
-def test_learned_run_equals_stepwise(max_w):
+@pytest.mark.parametrize("max_w,chunk", [(-1, 0), (0, 0), (60, 0), (10 ** 6, 0), (-1, 64), (60, 128)])
+def test_learned_run_equals_stepwise(max_w, chunk):
+    """chunk > 0 splits the samples into chunks that alternate between two streams."""
     L, S, T = 5, 200, 3
     blob = _blob(3)
     e_ref, sp_ref, flagged = _stepwise(L, S, T, blob, max_w)
-    e, sp, fb, counts = _run(L, S, T, blob, max_w)
+    e, sp, fb, counts = _run(L, S, T, blob, max_w, chunk=chunk)
     print(f"max_weight {max_w}: {flagged} fallback words over {T} cycles")
     assert np.array_equal(e, e_ref)
     assert np.array_equal(sp, sp_ref)
