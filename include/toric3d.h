@@ -35,8 +35,8 @@
  * Bernoulli(p) for a sample in lane j compares the 32-bit U whose bit 31-i is
  * bit j of word i (word i = output i%4 of block i/4) with P = floor(p*2^32 +
  * 1/2): the event happens iff U < P.  Streams: 0 qubit flips (site = edge),
- * 1 measurement flips (site = face), 2 p-flip coins (site = edge, coin = bit j
- * of output 0 of block 0).  `sample0` (a multiple of 64) is the global index
+ * 1 measurement flips (site = face), 2 p-flip coins (site = lattice site r:
+ * the coin of r's d-edge is bit j of output d of block 0).  `sample0` (a multiple of 64) is the global index
  * of a batch's first sample, so disjoint sample ranges on different GPUs or
  * in resumed runs draw exactly the numbers one large batch would.
  */

@@ -88,7 +88,7 @@ def _declare(L):
         "t3o_prob_to_threshold": (u64, [dbl]),
         "t3o_uniform32": (u32, [u64, i32, u64, u64, u64, u64]),
         "t3o_bernoulli": (i32, [dbl, u64, i32, u64, u64, u64, u64]),
-        "t3o_coin": (i32, [u64, u64, u64, u64, u64]),
+        "t3o_coin": (i32, [u64, u64, i32, u64, u64, u64]),
         "t3o_face_edges": (None, [i32, i64, _P]),
         "t3o_incidence": (None, [i32, _P, _P]),
         "t3o_syndrome": (None, [i32, _P, _P]),
@@ -152,8 +152,10 @@ def bernoulli(p, seed, stream, site, cycle, sweep, sample) -> int:
     return int(lib().t3o_bernoulli(float(p), seed, stream, site, cycle, sweep, sample))
 
 
-def coin(seed, edge, cycle, sweep, sample) -> int:
-    return int(lib().t3o_coin(seed, edge, cycle, sweep, sample))
+def coin(seed, L, edge, cycle, sweep, sample) -> int:
+    """p-flip coin of edge index `edge` = d L^3 + site."""
+    L3 = L ** 3
+    return int(lib().t3o_coin(seed, edge % L3, edge // L3, cycle, sweep, sample))
 
 
 # ---------------------------------------------------------------- lattice

@@ -28,8 +28,9 @@
  * group = sample / 64.  Bernoulli(p) for a sample with lane = sample % 64:
  * U is the 32-bit integer whose bit (31-j) is bit `lane` of word j
  * (word j = output j%4 of block j/4, j = 0..31); the event happens iff
- * U < P with P = floor(p * 2^32 + 0.5).  The p-flip coin is bit `lane` of
- * output 0 of block 0 of stream 2.
+ * U < P with P = floor(p * 2^32 + 0.5).  The p-flip coin of the d-edge at
+ * site r is bit `lane` of output d of block 0 of stream 2 keyed by site r
+ * (one block serves the three edges of a site).
  *
  * Parity pins: Philox against numpy.random.Philox; syndrome against the
  * code parameters [[3L^3,3,L]] of Sec. 2 (GF(2) rank 2L^3-2, weight-4 rows
@@ -124,11 +125,11 @@ int t3o_bernoulli(double p, uint64_t seed, int stream, uint64_t site, uint64_t c
     return (uint64_t)u < thr;
 }
 
-int t3o_coin(uint64_t seed, uint64_t edge, uint64_t cycle, uint64_t sweep, uint64_t sample)
+int t3o_coin(uint64_t seed, uint64_t site, int dir, uint64_t cycle, uint64_t sweep, uint64_t sample)
 {
     uint64_t w[4];
-    stream_block(seed, STREAM_COIN, edge, cycle, sweep, 0, sample / 64, w);
-    return (int)((w[0] >> (sample % 64)) & 1ULL);
+    stream_block(seed, STREAM_COIN, site, cycle, sweep, 0, sample / 64, w);
+    return (int)((w[dir] >> (sample % 64)) & 1ULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -238,7 +239,8 @@ static void apply_rule(int L, uint8_t* e, uint8_t* s, int probabilistic, uint64_
         if (sat < unsat)
             flip[v] = 1;
         else if (probabilistic && sat == unsat)
-            flip[v] = (uint8_t)t3o_coin(seed, (uint64_t)v, cycle, sweep, sample);
+            flip[v] = (uint8_t)t3o_coin(seed, (uint64_t)(v % ((int64_t)L * L * L)), (int)(v / ((int64_t)L * L * L)),
+                                        cycle, sweep, sample);
     }
     for (int64_t v = 0; v < n; ++v) {
         if (!flip[v]) continue;

@@ -121,16 +121,16 @@ __device__ __forceinline__ Moves site_moves(const Lattice& lat, int site)
     return m;
 }
 
-// One synchronous flip (or p-flip) application for the three faces at a site,
-// reading the item's s and writing its tmp.  The thread of site r decides the nine edges its faces touch -- (x,r), (y,r),
+// One synchronous flip application for the three faces at a site, reading the
+// item's s and writing its tmp (64 registers: four blocks per SM).  The thread
+// of site r decides the nine edges its faces touch -- (x,r), (y,r),
 // (z,r), (x,r+e_y), (x,r+e_z), (y,r+e_x), (y,r+e_z), (z,r+e_x), (z,r+e_y) --
 // each from its four faces in the old snapshot s_in, writes s_out at its three
 // faces (old value XOR its four edges' flips) and applies the flips of the
 // three edges at r to e.  Edge (a, r') lies on the faces with normal 3-a-c at
 // r' and r' - e_c for the two axes c != a.
-template <bool kProbabilistic>
-__global__ void __launch_bounds__(kThreads, 3)
-k_sweep(const __grid_constant__ ItemTable tab, uint64_t seed, uint32_t cycle, uint32_t sweep)
+__global__ void __launch_bounds__(kThreads, 4)
+k_flip(const __grid_constant__ ItemTable tab)
 {
     for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
         const Lattice lat = d.lat;
@@ -147,35 +147,114 @@ k_sweep(const __grid_constant__ ItemTable tab, uint64_t seed, uint32_t cycle, ui
             for (int n = 0; n < 3; ++n) s_out[((int64_t)n * lat.L3 + r) * W + w] = s_in[((int64_t)n * lat.L3 + r) * W + w];
             return;
         }
+        // row pointers of the three faces at r and the element offsets of the six neighbour
+        // sites (periodic wrap folded in): every neighbour load is one add away
         const Moves mv = site_moves(lat, r);
+        const int64_t L3W = (int64_t)lat.L3 * W;
+        const uint64_t* __restrict__ p0 = s_in + (int64_t)r * W + w;
+        const uint64_t* __restrict__ p1 = p0 + L3W;
+        const uint64_t* __restrict__ p2 = p1 + L3W;
+        const int64_t mx = (int64_t)mv.minus[0] * W, my = (int64_t)mv.minus[1] * W, mz = (int64_t)mv.minus[2] * W;
+        const int64_t px = (int64_t)mv.plus[0] * W, py = (int64_t)mv.plus[1] * W, pz = (int64_t)mv.plus[2] * W;
         const int rx = r + mv.plus[0], ry = r + mv.plus[1], rz = r + mv.plus[2];
-        const int64_t L3 = lat.L3;
-        auto S = [&](int n, int site) { return s_in[((int64_t)n * L3 + site) * W + w]; };
-        const uint64_t s0 = S(0, r), s1 = S(1, r), s2 = S(2, r);
-        const uint64_t group = d.group0 + (uint64_t)w;
-        auto decide = [&](uint64_t a, uint64_t b, uint64_t c, uint64_t dd, int dir, int site) {
-            uint64_t fl = at_least_three(a, b, c, dd);
-            if (kProbabilistic) {
-                const uint64_t two = exactly_two(a, b, c, dd);
-                if (two) fl |= two & coin_word(seed, (uint64_t)dir * L3 + site, cycle, sweep, group);
-            }
-            return fl;
-        };
-        const uint64_t fx0 = decide(s2, S(2, r + mv.minus[1]), s1, S(1, r + mv.minus[2]), 0, r);
-        const uint64_t fy0 = decide(s2, S(2, r + mv.minus[0]), s0, S(0, r + mv.minus[2]), 1, r);
-        const uint64_t fz0 = decide(s1, S(1, r + mv.minus[0]), s0, S(0, r + mv.minus[1]), 2, r);
-        const uint64_t fxy = decide(S(2, ry), s2, S(1, ry), S(1, ry + mv.minus[2]), 0, ry);
-        const uint64_t fxz = decide(S(2, rz), S(2, rz + mv.minus[1]), S(1, rz), s1, 0, rz);
-        const uint64_t fyx = decide(S(2, rx), s2, S(0, rx), S(0, rx + mv.minus[2]), 1, rx);
-        const uint64_t fyz = decide(S(2, rz), S(2, rz + mv.minus[0]), S(0, rz), s0, 1, rz);
-        const uint64_t fzx = decide(S(1, rx), s1, S(0, rx), S(0, rx + mv.minus[1]), 2, rx);
-        const uint64_t fzy = decide(S(1, ry), S(1, ry + mv.minus[0]), S(0, ry), s0, 2, ry);
-        s_out[((int64_t)0 * L3 + r) * W + w] = s0 ^ fy0 ^ fyz ^ fz0 ^ fzy;
-        s_out[((int64_t)1 * L3 + r) * W + w] = s1 ^ fx0 ^ fxz ^ fz0 ^ fzx;
-        s_out[((int64_t)2 * L3 + r) * W + w] = s2 ^ fx0 ^ fxy ^ fy0 ^ fyx;
-        if (fx0) e[((int64_t)0 * L3 + r) * W + w] ^= fx0;
-        if (fy0) e[((int64_t)1 * L3 + r) * W + w] ^= fy0;
-        if (fz0) e[((int64_t)2 * L3 + r) * W + w] ^= fz0;
+        const uint64_t s0 = p0[0], s1 = p1[0], s2 = p2[0];
+        // the nine edges whose flips touch this site's faces: the three at r and two each at
+        // r + e_x, r + e_y, r + e_z; their four checks each
+        const uint64_t q[9][4] = {
+            {s2, p2[my], s1, p1[mz]},                 // x-edge at r
+            {s2, p2[mx], s0, p0[mz]},                 // y-edge at r
+            {s1, p1[mx], s0, p0[my]},                 // z-edge at r
+            {p2[py], s2, p1[py], p1[py + mz]},        // x-edge at r + e_y
+            {p2[pz], p2[pz + my], p1[pz], s1},        // x-edge at r + e_z
+            {p2[px], s2, p0[px], p0[px + mz]},        // y-edge at r + e_x
+            {p2[pz], p2[pz + mx], p0[pz], s0},        // y-edge at r + e_z
+            {p1[px], s1, p0[px], p0[px + my]},        // z-edge at r + e_x
+            {p1[py], p1[py + mx], p0[py], s0}};       // z-edge at r + e_y
+        uint64_t f[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) f[k] = at_least_three(q[k][0], q[k][1], q[k][2], q[k][3]);
+        const uint64_t fx0 = f[0], fy0 = f[1], fz0 = f[2], fxy = f[3], fxz = f[4], fyx = f[5], fyz = f[6],
+                       fzx = f[7], fzy = f[8];
+        uint64_t* __restrict__ q0 = s_out + (int64_t)r * W + w;
+        q0[0] = s0 ^ fy0 ^ fyz ^ fz0 ^ fzy;
+        q0[L3W] = s1 ^ fx0 ^ fxz ^ fz0 ^ fzx;
+        q0[2 * L3W] = s2 ^ fx0 ^ fxy ^ fy0 ^ fyx;
+        uint64_t* __restrict__ e0 = e + (int64_t)r * W + w;
+        if (fx0) e0[0] ^= fx0;
+        if (fy0) e0[L3W] ^= fy0;
+        if (fz0) e0[2 * L3W] ^= fz0;
+    });
+}
+
+// p-flip in two passes, so that each (site, word) draws one Philox block.
+// Pass 1: the thread of site r decides its own three edges from their checks
+// (s at r, r - e_x, r - e_y, r - e_z), with the coin of the site's block for
+// the lanes with exactly two unsatisfied checks, writes the flip words to
+// d.tmp [3L^3][W] and applies them to e.
+__global__ void __launch_bounds__(kThreads, 4)
+k_pflip_decide(const __grid_constant__ ItemTable tab, uint64_t seed, uint32_t cycle, uint32_t sweep)
+{
+    for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
+        const Lattice lat = d.lat;
+        int r;
+        int64_t w;
+        if (!tile_site_word(d, lb, lat.L3, r, w)) return;
+        if (d.gate && !d.gate[w]) return;
+        const int64_t W = d.W;
+        const Moves mv = site_moves(lat, r);
+        const int64_t L3W = (int64_t)lat.L3 * W;
+        const uint64_t* __restrict__ p0 = d.s + (int64_t)r * W + w;
+        const uint64_t* __restrict__ p1 = p0 + L3W;
+        const uint64_t* __restrict__ p2 = p1 + L3W;
+        const int64_t mx = (int64_t)mv.minus[0] * W, my = (int64_t)mv.minus[1] * W, mz = (int64_t)mv.minus[2] * W;
+        const uint64_t s0 = p0[0], s1 = p1[0], s2 = p2[0];
+        const uint64_t q[3][4] = {{s2, p2[my], s1, p1[mz]},    // x-edge at r
+                                  {s2, p2[mx], s0, p0[mz]},    // y-edge at r
+                                  {s1, p1[mx], s0, p0[my]}};   // z-edge at r
+        uint64_t f[3], two[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            f[k] = at_least_three(q[k][0], q[k][1], q[k][2], q[k][3]);
+            two[k] = exactly_two(q[k][0], q[k][1], q[k][2], q[k][3]);
+        }
+        if (two[0] | two[1] | two[2]) {
+            const U64x4 c = coin_block(seed, (uint64_t)r, cycle, sweep, d.group0 + (uint64_t)w);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) f[k] |= two[k] & c.v[k];
+        }
+        uint64_t* __restrict__ fo = d.tmp + (int64_t)r * W + w;
+        uint64_t* __restrict__ e0 = d.e + (int64_t)r * W + w;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            fo[k * L3W] = f[k];
+            if (f[k]) e0[k * L3W] ^= f[k];
+        }
+    });
+}
+
+// Pass 2: every face of site r XORs in the flips of its four edges (in place:
+// each thread writes only its own faces and reads only flip words).
+__global__ void __launch_bounds__(kThreads, 6)
+k_pflip_apply(const __grid_constant__ ItemTable tab)
+{
+    for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
+        const Lattice lat = d.lat;
+        int r;
+        int64_t w;
+        if (!tile_site_word(d, lb, lat.L3, r, w)) return;
+        if (d.gate && !d.gate[w]) return;
+        const int64_t W = d.W;
+        const Moves mv = site_moves(lat, r);
+        const int64_t L3W = (int64_t)lat.L3 * W;
+        const uint64_t* __restrict__ fx = d.tmp + (int64_t)r * W + w;   // x-edge flips
+        const uint64_t* __restrict__ fy = fx + L3W;
+        const uint64_t* __restrict__ fz = fy + L3W;
+        const int64_t px = (int64_t)mv.plus[0] * W, py = (int64_t)mv.plus[1] * W, pz = (int64_t)mv.plus[2] * W;
+        const uint64_t fx0 = fx[0], fy0 = fy[0], fz0 = fz[0];
+        uint64_t* __restrict__ q0 = d.s + (int64_t)r * W + w;
+        q0[0] ^= fy0 ^ fy[pz] ^ fz0 ^ fz[py];             // normal x: y-edges at r, r + e_z; z-edges at r, r + e_y
+        q0[L3W] ^= fx0 ^ fx[pz] ^ fz0 ^ fz[px];           // normal y
+        q0[2 * L3W] ^= fx0 ^ fx[py] ^ fy0 ^ fy[px];       // normal z
     });
 }
 
@@ -434,22 +513,27 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
         d.blocks = tile_blocks(d.lat.L3, nw, d.tx);
     }
     finish_table(tab);
-    ItemTable t = tab;  // s and tmp swap roles every application
+    ItemTable t = tab;  // flip: s and tmp swap roles; p-flip: tmp holds the flip words, s updated in place
+    int swaps = 0;
     for (int k = 0; k < n_apply; ++k) {
         const bool pk = schedule[k % slen] == 'P';
         ProfScope prof(pk ? T3D_K_PFLIP : T3D_K_FLIP, st);
-        if (pk)
-            k_sweep<true><<<persistent_grid((const void*)k_sweep<true>, kThreads, T3D_K_PFLIP,
-                                            t.prefix[t.n]),
-                            kThreads, 0, st>>>(t, seed, cycle, sweep0 + (uint32_t)k);
-        else
-            k_sweep<false><<<persistent_grid((const void*)k_sweep<false>, kThreads, T3D_K_FLIP,
-                                             t.prefix[t.n]),
+        if (pk) {
+            k_pflip_decide<<<persistent_grid((const void*)k_pflip_decide, kThreads, T3D_K_PFLIP, t.prefix[t.n]),
                              kThreads, 0, st>>>(t, seed, cycle, sweep0 + (uint32_t)k);
-        T3D_LAUNCH_CHECK("flip sweep");
-        for (int i = 0; i < t.n; ++i) std::swap(t.it[i].s, t.it[i].tmp);
+            T3D_LAUNCH_CHECK("p-flip decisions");
+            k_pflip_apply<<<persistent_grid((const void*)k_pflip_apply, kThreads, T3D_K_PFLIP, t.prefix[t.n]),
+                            kThreads, 0, st>>>(t);
+            T3D_LAUNCH_CHECK("p-flip syndrome update");
+        } else {
+            k_flip<<<persistent_grid((const void*)k_flip, kThreads, T3D_K_FLIP, t.prefix[t.n]), kThreads, 0,
+                     st>>>(t);
+            T3D_LAUNCH_CHECK("flip sweep");
+            for (int i = 0; i < t.n; ++i) std::swap(t.it[i].s, t.it[i].tmp);
+            ++swaps;
+        }
     }
-    if (n_apply & 1) {
+    if (swaps & 1) {
         for (int i = 0; i < tab.n; ++i) {
             const ItemDesc& d = tab.it[i];
             const size_t pitch = (size_t)d.W * sizeof(uint64_t);

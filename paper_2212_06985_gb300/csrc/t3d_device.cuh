@@ -175,11 +175,12 @@ __device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, 
     return lt;
 }
 
-// p-flip coin word for 64 samples: output 0 of block 0 of stream 2.
-__device__ __forceinline__ uint64_t coin_word(uint64_t seed, uint64_t edge, uint32_t cycle,
-                                              uint32_t sweep, uint64_t group)
+// p-flip coin words for 64 samples of the three edges at a site: output d of
+// block 0 of stream 2 keyed by the site is the coin word of its d-edge.
+__device__ __forceinline__ U64x4 coin_block(uint64_t seed, uint64_t site, uint32_t cycle, uint32_t sweep,
+                                            uint64_t group)
 {
-    return philox4x64_10(group, edge, cycle, stream_word3(kStreamCoin, sweep, 0), seed, 0).v[0];
+    return philox4x64_10(group, site, cycle, stream_word3(kStreamCoin, sweep, 0), seed, 0);
 }
 
 // ----------------------------------------------------------------- majority logic

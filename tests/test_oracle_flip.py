@@ -76,7 +76,7 @@ def test_pflip_on_half_cube_flips_coin_chosen_vertex_edges(spec):
     for sample in range(40):
         e2, _ = oracle.pflip_once(L, e, s, seed=5, sample=sample, cycle=1, sweep=2)
         flipped = set(np.nonzero(e2 ^ e)[0].tolist())
-        want = {v for v in six if oracle.coin(5, v, 1, 2, sample)}
+        want = {v for v in six if oracle.coin(5, L, v, 1, 2, sample)}
         assert flipped == want
         seen |= flipped
     assert seen == set(six)
@@ -95,7 +95,7 @@ def test_opposite_face_pair_under_pflip_only_touches_the_cube():
     cube = {vertex_edge(L, V, sp) for sp in ["+x", "-x", "+y", "-y"]}
     for sample in range(20):
         e2, _ = oracle.pflip_once(L, e, s, seed=1, sample=sample, cycle=1, sweep=0)
-        assert set(np.nonzero(e2)[0].tolist()) == {v for v in cube if oracle.coin(1, v, 1, 0, sample)}
+        assert set(np.nonzero(e2)[0].tolist()) == {v for v in cube if oracle.coin(1, L, v, 1, 0, sample)}
 
 
 def test_fig5_pair_oscillates_under_parallel_flip():

@@ -74,13 +74,15 @@ def test_bernoulli_is_u_less_than_threshold():
             assert oracle.bernoulli(p, seed, 0, 5, 2, 0, sample) == int(u < oracle.prob_to_threshold(p))
 
 
-def test_coin_is_bit_of_first_word_and_fair():
-    seed = 4
+def test_coin_is_bit_of_the_sites_block_and_fair():
+    """The coin of the d-edge at site r: output d of block 0 of stream 2 keyed by r."""
+    seed, L = 4, 3
     for sample in (0, 1, 63, 64, 200):
         w = _numpy_block([sample // 64, 11, 3, (2 << 48) | (5 << 8)], [seed, 0])
-        assert oracle.coin(seed, 11, 3, 5, sample) == (int(w[0]) >> (sample % 64)) & 1
+        for d in range(3):
+            assert oracle.coin(seed, L, d * L ** 3 + 11, 3, 5, sample) == (int(w[d]) >> (sample % 64)) & 1
     n = 20000
-    heads = sum(oracle.coin(1, i % 311, 1, i // 311, i) for i in range(n))
+    heads = sum(oracle.coin(1, 7, i % 1029, 1, i // 1029, i) for i in range(n))
     assert abs(heads - n / 2) < 5 * (n / 4) ** 0.5
 
 
