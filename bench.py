@@ -39,7 +39,7 @@ METRIC = "qubit-cycles decoded/s at L=32 p=4%: BP+p-flip"
 # proportion to the samples a launch covers, so it scales to full launches):
 # profiles/k_bp_step_bp_pflip_L32_1024samples.md.  Set to None when the kernel
 # changes until it is captured again.
-BP_STEP_TRAFFIC = {"first_iteration": 15.72, "full_iteration": 31.94}
+BP_STEP_TRAFFIC = {"first_iteration": 15.68, "full_iteration": 31.94}
 UNIT = "qubit-cycles/s"
 
 

@@ -117,7 +117,7 @@ bool bp_chunks(const t3d_run_cfg& c, const t3d_batch_item* items, int n, size_t 
 
 // Pre-decoder chunk (words): cfg.bp_chunk_samples, or by default as many
 // samples as keep the pre-decoder's activations within kCnnAutoBytes.
-constexpr size_t kCnnAutoBytes = 8ull << 30;
+constexpr size_t kCnnAutoBytes = 16ull << 30;
 
 int64_t cnn_chunk_words(const t3d_run_cfg& c, int L, int64_t n_samples)
 {

@@ -1,0 +1,111 @@
+"""Micro-benchmarks of single library calls on synthetic seeded inputs (for
+profiling one kernel at a time; the whole-cycle benchmark is bench.py).
+
+  python -m paper_2212_06985_gb300.kernel_bench cnn   --L 24 --samples 16384
+  python -m paper_2212_06985_gb300.kernel_bench sweep --L 32 --samples 8192 --rule F
+  python -m paper_2212_06985_gb300.kernel_bench bp    --L 32 --samples 1024
+
+Every line printed is one JSON object with the call's mean time over --reps
+timed calls (CUDA events) after --warmup untimed ones.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+
+import torch
+
+from . import (n_bits, toric3d_bp, toric3d_bp_workspace_bytes, toric3d_cnn_blob_bytes, toric3d_cnn_decode,
+               toric3d_cnn_prepare, toric3d_cnn_status, toric3d_cnn_workspace_bytes, toric3d_flip_workspace_bytes,
+               toric3d_noise, toric3d_pflip, toric3d_syndrome, words_for)
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "cnn_L12_p04.npz")
+CNN_FLOP_PER_SITE = 2 * 27 * 16 * (6 + 16 + 16) + 2 * 16 * 3
+
+
+def _timed(fn, warmup, reps):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(reps):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def _state(L, S, p, seed, dev):
+    """A code cycle's state: qubit noise and one noisy measurement at rate p."""
+    e = torch.zeros((n_bits(L), words_for(S)), dtype=torch.int64, device=dev)
+    s = torch.zeros_like(e)
+    toric3d_noise(L, e, p, seed, 0, 1)
+    toric3d_syndrome(L, e, s, p, seed, 0, 1)
+    return e, s
+
+
+def bench_cnn(a, dev):
+    import numpy as np
+    from .learned import load_params
+    params = torch.from_numpy(load_params(a.weights) if os.path.exists(a.weights) else
+                              np.zeros(16515, dtype=np.float32)).to(dev)
+    blob = torch.empty(toric3d_cnn_blob_bytes(), dtype=torch.uint8, device=dev)
+    toric3d_cnn_prepare(params, blob)
+    e, s_prev = _state(a.L, a.samples, a.p, a.seed, dev)
+    _, s = _state(a.L, a.samples, a.p, a.seed + 1, dev)
+    work = torch.empty(toric3d_cnn_workspace_bytes(a.L, a.samples), dtype=torch.uint8, device=dev)
+    ms = _timed(lambda: toric3d_cnn_decode(a.L, a.samples, s_prev, s, e, blob, work), a.warmup, a.reps)
+    toric3d_cnn_status()
+    sites = a.L ** 3 * a.samples
+    return {"call": "toric3d_cnn_decode", "L": a.L, "samples": a.samples, "ms": ms,
+            "qubit_cycles_per_s": 3 * sites / (ms / 1e3),
+            "algorithmic_tflops": CNN_FLOP_PER_SITE * sites / (ms / 1e3) / 1e12}
+
+
+def bench_sweep(a, dev):
+    e, s = _state(a.L, a.samples, a.p, a.seed, dev)
+    W = words_for(a.samples)
+    work = torch.empty(toric3d_flip_workspace_bytes(a.L, W), dtype=torch.uint8, device=dev)
+    sched = a.rule * 2   # two applications per call (an even count leaves no copy-back)
+    ms = _timed(lambda: toric3d_pflip(a.L, e, s, sched, 2, 0, a.seed, 0, 1, work), a.warmup, a.reps) / 2
+    return {"call": "toric3d_pflip", "rule": a.rule, "L": a.L, "samples": a.samples, "ms_per_application": ms,
+            "algorithmic_GBps": n_bits(a.L) * a.samples * 0.5 / (ms / 1e3) / 1e9}
+
+
+def bench_bp(a, dev):
+    e, s = _state(a.L, a.samples, a.p, a.seed, dev)
+    work = torch.empty(toric3d_bp_workspace_bytes(a.L, a.samples), dtype=torch.uint8, device=dev)
+    e0, s0 = e.clone(), s.clone()
+
+    def call():
+        e.copy_(e0)
+        s.copy_(s0)
+        toric3d_bp(a.L, a.samples, e, s, a.p, a.p, a.iters, work)
+
+    ms = _timed(call, a.warmup, a.reps)
+    return {"call": "toric3d_bp", "L": a.L, "samples": a.samples, "iters": a.iters, "ms": ms}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("what", choices=["cnn", "sweep", "bp"])
+    ap.add_argument("--L", type=int, default=24)
+    ap.add_argument("--samples", type=int, default=16384)
+    ap.add_argument("--p", type=float, default=0.04)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--rule", choices=["F", "P"], default="F")
+    ap.add_argument("--iters", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--weights", default=WEIGHTS)
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda:0")
+    out = {"cnn": bench_cnn, "sweep": bench_sweep, "bp": bench_bp}[a.what](a, dev)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -116,14 +116,16 @@ def lr_at(step: int, steps: int, lr: float, warmup: int = 100) -> float:
     return lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * x)))
 
 
-def train(L: int = 12, p: float = 0.04, steps: int = 400, batch: int = 2048, lr: float = 2e-3,
+def train(L: int = 12, p=0.04, steps: int = 400, batch: int = 2048, lr: float = 2e-3,
           cycles_per_episode: int = 12, seed: int = 1, device="cuda:0", log_every: int = 50,
           init: np.ndarray | None = None):
     """Online training on simulator pairs; returns (params, loss history).
 
     Every step draws one fresh cycle of `batch` codes (episodes of
     cycles_per_episode cycles decoded by the BP + p-flip teacher), so the
-    network sees steps * batch (syndrome pair, error) examples, each once."""
+    network sees steps * batch (syndrome pair, error) examples, each once.
+    p (= q) is one rate or a list of rates taken by successive episodes."""
+    rates = list(p) if isinstance(p, (list, tuple)) else [p]
     dev = torch.device(device)
     params = torch.from_numpy(init if init is not None else init_params(seed)).to(dev)
     m, v = torch.zeros_like(params), torch.zeros_like(params)
@@ -139,7 +141,8 @@ def train(L: int = 12, p: float = 0.04, steps: int = 400, batch: int = 2048, lr:
     for step in range(1, steps + 1):
         if ens is None or ens.t >= cycles_per_episode:
             episode += 1
-            ens = Ensemble(L, batch, Decoder(p, p, seed * 1000003 + episode), dev)
+            pe = rates[(episode - 1) % len(rates)]
+            ens = Ensemble(L, batch, Decoder(pe, pe, seed * 1000003 + episode), dev)
             ens.measure()
             ens.decode_bp_pflip()
             ens.end_cycle()
@@ -218,7 +221,7 @@ def _main(argv=None):
     sub = ap.add_subparsers(dest="cmd", required=True)
     t = sub.add_parser("train", help="online training at L, p = q (BP + p-flip teacher)")
     t.add_argument("--L", type=int, default=12)
-    t.add_argument("--p", type=float, default=0.04)
+    t.add_argument("--p", type=float, nargs="+", default=[0.04], help="noise rate(s), one per episode in turn")
     t.add_argument("--steps", type=int, default=5000)
     t.add_argument("--batch", type=int, default=2048)
     t.add_argument("--lr", type=float, default=2e-3)
@@ -232,18 +235,22 @@ def _main(argv=None):
     e.add_argument("--seed", type=int, default=1234)
     e.add_argument("--fallback-max-weight", type=int, default=-1)
     e.add_argument("--weights", default=os.path.join(os.path.dirname(__file__), "weights", "cnn_L12_p04.npz"))
+    e.add_argument("--no-bp", action="store_true", help="skip the BP + p-flip comparison run")
     a = ap.parse_args(argv)
     if a.cmd == "train":
         params, hist = train(L=a.L, p=a.p, steps=a.steps, batch=a.batch, lr=a.lr, seed=a.seed,
                              log_every=max(1, a.steps // 25))
-        save_params(a.out, params, steps=a.steps, batch=a.batch, L=a.L, p=a.p)
+        save_params(a.out, params, steps=a.steps, batch=a.batch, L=a.L, p=np.asarray(a.p))
         print(json.dumps({"out": a.out, "loss": hist}))
         return 0
     params = load_params(a.weights)
     T = a.T or a.L
     for p in a.p:
         row = {"L": a.L, "p": p, "T": T, "samples": a.samples}
-        for name, prm, fb in [("bp_pflip", None, -1), ("learned_pflip", params, a.fallback_max_weight)]:
+        legs = [("learned_pflip", params, a.fallback_max_weight)]
+        if not a.no_bp:
+            legs.insert(0, ("bp_pflip", None, -1))
+        for name, prm, fb in legs:
             counts, ms, words = evaluate(a.L, p, T, a.samples, prm, a.seed, fallback_max_weight=fb)
             row[name] = {"failure_rate": failure_rate(counts), "counts": counts.tolist(), "ms": ms,
                          "qubit_cycles_per_s": n_bits(a.L) * a.samples * T / (ms / 1e3), "fallback_words": words}

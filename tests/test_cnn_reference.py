@@ -41,3 +41,38 @@ def test_gradient_matches_finite_differences():
         lp, _ = ref.loss_and_grad(pp, L, sp, sc, y)
         lm, _ = ref.loss_and_grad(pm, L, sp, sc, y)
         assert abs((lp - lm) / (2 * h) / n - g[i]) < 1e-3 * max(1.0, abs(g[i]))
+
+
+def test_convolution_matches_direct_loop():
+    """The reference's periodic convolution is out(r) = sum_k W[co][ci][k] in(r + offset_k),
+    offset of k = (kz, ky, kx) = (dz + 1, dy + 1, dx + 1), written out as loops in binary64."""
+    L, CI, CO = 5, 3, 2
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(1, CI, L, L, L))
+    w = rng.normal(size=(CO, CI, 3, 3, 3))
+    got = ref._conv(torch.from_numpy(x).float(), torch.from_numpy(w).float()).numpy()[0]
+    for (z, y, xx) in [(0, 0, 0), (4, 4, 4), (2, 0, 3), (1, 4, 0)]:
+        for co in range(CO):
+            acc = 0.0
+            for ci in range(CI):
+                for kz in range(3):
+                    for ky in range(3):
+                        for kx in range(3):
+                            acc += w[co, ci, kz, ky, kx] * x[0, ci, (z + kz - 1) % L, (y + ky - 1) % L,
+                                                              (xx + kx - 1) % L]
+            assert abs(got[co, z, y, xx] - acc) < 1e-4 * (1 + abs(acc))
+
+
+def test_feature_channels_follow_the_documented_order():
+    """Channel c < 3 of site r is s_{t-1}(face c, r), channel 3 + c is s_t(face c, r)."""
+    L, S = 3, 2
+    n = 3 * L ** 3
+    sp = inp.random_bits(S, n, 0.3, 5)
+    sc = inp.random_bits(S, n, 0.3, 6)
+    f = ref.features(L, sp, sc).numpy()
+    for s in range(S):
+        for c in range(3):
+            for site in (0, 7, L ** 3 - 1):
+                z, y, x = site // (L * L), (site // L) % L, site % L
+                assert f[s, c, z, y, x] == sp[s, c * L ** 3 + site]
+                assert f[s, 3 + c, z, y, x] == sc[s, c * L ** 3 + site]

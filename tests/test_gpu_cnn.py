@@ -90,3 +90,55 @@ def test_cnn_adam_steps_reduce_the_loss():
         t3d.toric3d_cnn_train_step(L, S, *args, p, m, v, step, 3e-3, blob, work, loss)
         losses.append(float(loss.item()))
     assert losses[-1] < 0.7 * losses[0]
+
+
+def _patch_logits(params, L, sp_bits, sc_bits, site):
+    """Reference logits of one site from its 7x7x7 periodic neighbourhood (three valid
+    3x3x3 convolutions shrink 7 -> 5 -> 3 -> 1)."""
+    import torch.nn.functional as F
+    P = ref.unpack(params)
+    L3 = L ** 3
+    z0, y0, x0 = site // (L * L), (site // L) % L, site % L
+    idx = np.array([[[((z % L) * L + (y % L)) * L + (x % L) for x in range(x0 - 3, x0 + 4)]
+                     for y in range(y0 - 3, y0 + 4)] for z in range(z0 - 3, z0 + 4)])
+    feat = np.stack([sp_bits[c * L3 + idx] for c in range(3)] + [sc_bits[c * L3 + idx] for c in range(3)])
+    x = torch.from_numpy(feat[None].astype(np.float32))
+    h = ref.bf16(torch.relu(F.conv3d(x, ref.bf16(P["w1"])) + P["b1"].view(1, -1, 1, 1, 1)))
+    h = ref.bf16(torch.relu(F.conv3d(h, ref.bf16(P["w2"])) + P["b2"].view(1, -1, 1, 1, 1)))
+    h = torch.relu(F.conv3d(h, ref.bf16(P["w3"])) + P["b3"].view(1, -1, 1, 1, 1))
+    return (P["w4"] @ h[0, :, 0, 0, 0] + P["b4"]).numpy()
+
+
+def test_cnn_full_size_sampled_decisions():
+    """L = 32 with a 16,384-sample launch (the bench's pre-decoder chunk): the decisions the
+    kernels apply to e at 300 sampled (site, sample) pairs equal the reference's sign wherever
+    |logit| > 0.05."""
+    from paper_2212_06985_gb300 import learned
+    L, S = 32, 16384
+    n, W = 3 * L ** 3, inp.words_for(S)
+    params = learned.load_params(learned.__file__.replace("learned.py", "weights/cnn_L12_p04.npz"))
+    g = torch.Generator(device=dev())
+    g.manual_seed(3)
+    rnd = lambda: torch.randint(-2 ** 62, 2 ** 62, (n, W), dtype=torch.int64, device=dev(), generator=g)
+    sp = rnd() & rnd() & rnd()           # about 1/8 of the checks unsatisfied
+    sc = sp ^ (rnd() & rnd() & rnd() & rnd())
+    e = torch.zeros_like(sp)
+    _, blob = _blob(params)
+    t3d.toric3d_cnn_decode(L, S, sp, sc.clone(), e, blob, workspace(t3d.toric3d_cnn_workspace_bytes(L, S)))
+    torch.cuda.synchronize()
+    t3d.toric3d_cnn_status()
+    rng = np.random.default_rng(4)
+    samples = rng.integers(0, S, 30)
+    sites = rng.integers(0, L ** 3, 10)
+    ew, spw, scw = (t.cpu().numpy().view(np.uint64) for t in (e, sp, sc))
+    checked = 0
+    for j in samples:
+        bit = lambda words: ((words[:, j // 64] >> np.uint64(j % 64)) & np.uint64(1)).astype(np.uint8)
+        spb, scb, eb = bit(spw), bit(scw), bit(ew)
+        for r in sites:
+            z = _patch_logits(params, L, spb, scb, int(r))
+            for d in range(3):
+                if abs(z[d]) > 0.05:
+                    assert eb[d * L ** 3 + r] == int(z[d] > 0), (j, r, d, z[d])
+                    checked += 1
+    assert checked > 600
