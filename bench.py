@@ -204,6 +204,20 @@ CNN_MMA_FLOP_PER_SITE = (45 + 90 + 90) * 2 * 128 * 128 * 16 / (8 * 128)
 WEIGHTS = os.path.join(ROOT, "paper_2212_06985_gb300", "weights", "cnn_L12_p04.npz")
 
 
+def bp_chunk(L, S):
+    """BP chunk: 25,024 samples, fewer where the two message buffers (48 L^3 bytes per
+    sample each) would pass 96 GB."""
+    fit = int(48e9 // (48 * L ** 3)) // 64 * 64
+    return max(64, min(S, 25024, fit))
+
+
+def learned_chunk(L, S, cap):
+    """Pre-decoder chunk: `cap` samples, fewer where its activations (80 B per site-sample)
+    would pass 48 GB."""
+    fit = int(48e9 // (80 * L ** 3)) // 128 * 128
+    return max(128, min(S, cap, fit))
+
+
 def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
     """The same workload decoded by the learned pre-decoder + the same flip /
     p-flip schedule instead of BP (one cycle per step through toric3d_run_batch)."""
@@ -222,7 +236,8 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
     batch = t3d.make_batch([dict(L=L, n_samples=S, sample0=sample0, e=e, s_prev=sp, counts8=c)
                             for L, e, sp, c in zip(sizes, states, prevs, counts)])
     cfg = t3d.make_run_cfg(w.L, 1, w.p, w.q, w.seed, S, sample0=sample0, schedule=w.schedule, n_apply=w.n_apply,
-                           bp_chunk_samples=min(S, args.learned_chunk), cnn_blob=blob, fallback_max_weight=-1)
+                           bp_chunk_samples=learned_chunk(max(sizes), S, args.learned_chunk), cnn_blob=blob,
+                           fallback_max_weight=-1)
     work = torch.empty(t3d.toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
 
     def step(t):
@@ -278,7 +293,7 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
                      if cnn_ms > 0 else None,
                      "share_of_step": cnn_ms / ms if ms else None},
         "last_cycle_logical_counts": [c.cpu().tolist() for c in counts],
-        "chunk_samples": min(S, args.learned_chunk),
+        "chunk_samples": learned_chunk(max(sizes), S, args.learned_chunk),
     }
 
 
@@ -307,7 +322,7 @@ def cuda_arm(args):
     W = inp.words_for(S)
     kw = dict(use_bp=w.decoder.startswith("bp"), bp_iters=w.bp_iters, bp_meas_nodes=w.bp_meas_nodes,
               schedule=w.schedule, n_apply=w.n_apply)
-    chunk = min(S, 25024)
+    chunk = bp_chunk(max(sizes), S)
     cfg = t3d.make_run_cfg(w.L, 1, w.p, w.q, w.seed, S, sample0=sample0, bp_chunk_samples=chunk, **kw)
     stream = torch.cuda.Stream(device=dev)
     states = [torch.zeros((inp.n_bits(L), W), dtype=torch.int64, device=dev) for L in sizes]

@@ -1,0 +1,101 @@
+"""Threshold experiments of the paper, run with the library's whole-run call.
+
+Presets (phenomenological noise, p = q, readout by majority vote on the
+logical Z lines of the final error, no noiseless round):
+  flip : one parallel flip application per code cycle, 1000 cycles (Sec. 3.1, Fig. 2)
+  bp   : 30 BP iterations per cycle, 500 cycles (Sec. 4.1, Fig. 6)
+  pbp  : 20 BP iterations then P F F P F F, 500 cycles (Sec. 4.2, Fig. 7)
+
+  python -m paper_2212_06985_gb300.threshold pbp --L 14 18 24 32 --p 0.053 0.054 0.055 0.056 --samples 10000
+
+Each (L, p) point prints one JSON line with the failure counts of logical
+qubit 0 (the paper plots one of the three; the code is symmetric) and of
+any qubit.  With two or more L the points are fitted to the paper's ansatz
+p_fail = a0 + a1 x + a2 x^2, x = (p - p_th) L^(1/nu) (Sec. 3.2, after Table 1).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import make_batch, make_run_cfg, n_bits, toric3d_run_batch, toric3d_run_batch_workspace_bytes, words_for
+
+PRESETS = {
+    "flip": dict(T=1000, use_bp=False, bp_iters=0, schedule="F", n_apply=1),
+    "bp": dict(T=500, use_bp=True, bp_iters=30, schedule="", n_apply=0),
+    "pbp": dict(T=500, use_bp=True, bp_iters=20, schedule="PFFPFF", n_apply=6),
+}
+
+
+def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | None = None,
+              device="cuda:0") -> dict:
+    """One whole run of `samples` codes; returns failure counts and the run time."""
+    pr = dict(PRESETS[preset])
+    if T is not None:
+        pr["T"] = T
+    dev = torch.device(device)
+    e = torch.zeros((n_bits(L), words_for(samples)), dtype=torch.int64, device=dev)
+    counts = torch.zeros(8, dtype=torch.int64, device=dev)
+    batch = make_batch([dict(L=L, n_samples=samples, e=e, counts8=counts)])
+    cfg = make_run_cfg(L, pr["T"], p, p, seed, samples, use_bp=pr["use_bp"], bp_iters=pr["bp_iters"],
+                       schedule=pr["schedule"], n_apply=pr["n_apply"])
+    work = torch.empty(toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    toric3d_run_batch(cfg, batch, work)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    c = counts.cpu().numpy()
+    fail0 = int(c[1::2].sum())          # mask values with bit 0 set
+    return {"preset": preset, "L": L, "p": p, "T": pr["T"], "samples": samples, "seed": seed,
+            "fail_q0": fail0, "fail_any": int(c[1:].sum()), "counts8": c.tolist(), "seconds": dt}
+
+
+def fit_threshold(points: list[dict]) -> dict | None:
+    """Least-squares fit of p_fail(q0) = a0 + a1 x + a2 x^2, x = (p - p_th) L^(1/nu)."""
+    from scipy.optimize import curve_fit
+    L = np.array([q["L"] for q in points], dtype=float)
+    p = np.array([q["p"] for q in points], dtype=float)
+    f = np.array([q["fail_q0"] / q["samples"] for q in points])
+    n = np.array([q["samples"] for q in points], dtype=float)
+    sigma = np.sqrt(np.maximum(f * (1 - f), 1.0 / n) / n)
+    if len(set(L)) < 2 or len(points) < 5:
+        return None
+
+    def model(X, pth, nu, a0, a1, a2):
+        x = (X[1] - pth) * X[0] ** (1.0 / nu)
+        return a0 + a1 * x + a2 * x * x
+
+    p0 = [float(np.median(p)), 1.0, float(np.median(f)), 1.0, 0.0]
+    popt, pcov = curve_fit(model, np.vstack([L, p]), f, p0=p0, sigma=sigma, maxfev=20000)
+    err = np.sqrt(np.diag(pcov))
+    return {"p_th": popt[0], "p_th_err": err[0], "nu": popt[1], "nu_err": err[1], "a": popt[2:].tolist()}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("preset", choices=sorted(PRESETS))
+    ap.add_argument("--L", type=int, nargs="+", default=[14, 18, 24])
+    ap.add_argument("--p", type=float, nargs="+", required=True)
+    ap.add_argument("--samples", type=int, default=10000)
+    ap.add_argument("--T", type=int, default=None, help="code cycles (default: the preset's)")
+    ap.add_argument("--seed", type=int, default=2212)
+    a = ap.parse_args(argv)
+    points = []
+    for L in a.L:
+        for k, p in enumerate(a.p):
+            q = run_point(a.preset, L, p, a.samples, a.seed + 1000 * L + k, a.T)
+            points.append(q)
+            print(json.dumps(q), flush=True)
+    fit = fit_threshold(points)
+    if fit is not None:
+        print(json.dumps({"fit": fit}), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -109,4 +109,6 @@ WORKLOADS = {
     # throughput point: L=32, p=q=4%, T=L, 10^5 samples, BP16 + 32 x PFFPFF
     "bp_pflip_L32": Workload("bp_pflip_L32", 32, 0.04, 0.04, 32, 100_000, 11, "bp_pflip",
                              "PFFPFF", 32, bp_iters=16),
+    "bp_pflip_L48": Workload("bp_pflip_L48", 48, 0.04, 0.04, 48, 100_000, 13, "bp_pflip",
+                             "PFFPFF", 32, bp_iters=16),
 }
