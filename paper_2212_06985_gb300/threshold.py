@@ -32,7 +32,7 @@ PRESETS = {
 
 
 def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | None = None,
-              device="cuda:0") -> dict:
+              meas_nodes: bool = True, device="cuda:0") -> dict:
     """One whole run of `samples` codes; returns failure counts and the run time."""
     pr = dict(PRESETS[preset])
     if T is not None:
@@ -42,7 +42,7 @@ def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | N
     counts = torch.zeros(8, dtype=torch.int64, device=dev)
     batch = make_batch([dict(L=L, n_samples=samples, e=e, counts8=counts)])
     cfg = make_run_cfg(L, pr["T"], p, p, seed, samples, use_bp=pr["use_bp"], bp_iters=pr["bp_iters"],
-                       schedule=pr["schedule"], n_apply=pr["n_apply"])
+                       bp_meas_nodes=meas_nodes, schedule=pr["schedule"], n_apply=pr["n_apply"])
     work = torch.empty(toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -51,29 +51,37 @@ def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | N
     dt = time.perf_counter() - t0
     c = counts.cpu().numpy()
     fail0 = int(c[1::2].sum())          # mask values with bit 0 set
-    return {"preset": preset, "L": L, "p": p, "T": pr["T"], "samples": samples, "seed": seed,
+    return {"preset": preset, "L": L, "p": p, "T": pr["T"], "meas_nodes": meas_nodes, "samples": samples,
+            "seed": seed,
             "fail_q0": fail0, "fail_any": int(c[1:].sum()), "counts8": c.tolist(), "seconds": dt}
 
 
 def fit_threshold(points: list[dict]) -> dict | None:
-    """Least-squares fit of p_fail(q0) = a0 + a1 x + a2 x^2, x = (p - p_th) L^(1/nu)."""
+    """Least-squares fit of p_fail(q0) = a0 + a1 x + a2 x^2, x = (p - p_th) L^(1/nu), over the
+    points that are neither empty nor saturated (0 < p_fail < 0.45); None when fewer than five
+    such points or fewer than two sizes remain, {"error": ...} when the fit does not converge."""
     from scipy.optimize import curve_fit
-    L = np.array([q["L"] for q in points], dtype=float)
-    p = np.array([q["p"] for q in points], dtype=float)
-    f = np.array([q["fail_q0"] / q["samples"] for q in points])
-    n = np.array([q["samples"] for q in points], dtype=float)
-    sigma = np.sqrt(np.maximum(f * (1 - f), 1.0 / n) / n)
-    if len(set(L)) < 2 or len(points) < 5:
+    use = [q for q in points if 0 < q["fail_q0"] < 0.45 * q["samples"]]
+    if len({q["L"] for q in use}) < 2 or len(use) < 5:
         return None
+    L = np.array([q["L"] for q in use], dtype=float)
+    p = np.array([q["p"] for q in use], dtype=float)
+    f = np.array([q["fail_q0"] / q["samples"] for q in use])
+    n = np.array([q["samples"] for q in use], dtype=float)
+    sigma = np.sqrt(f * (1 - f) / n)
 
     def model(X, pth, nu, a0, a1, a2):
         x = (X[1] - pth) * X[0] ** (1.0 / nu)
         return a0 + a1 * x + a2 * x * x
 
     p0 = [float(np.median(p)), 1.0, float(np.median(f)), 1.0, 0.0]
-    popt, pcov = curve_fit(model, np.vstack([L, p]), f, p0=p0, sigma=sigma, maxfev=20000)
+    try:
+        popt, pcov = curve_fit(model, np.vstack([L, p]), f, p0=p0, sigma=sigma, maxfev=20000)
+    except (RuntimeError, ValueError) as exc:
+        return {"error": str(exc), "points": len(use)}
     err = np.sqrt(np.diag(pcov))
-    return {"p_th": popt[0], "p_th_err": err[0], "nu": popt[1], "nu_err": err[1], "a": popt[2:].tolist()}
+    return {"p_th": popt[0], "p_th_err": err[0], "nu": popt[1], "nu_err": err[1], "a": popt[2:].tolist(),
+            "points": len(use)}
 
 
 def main(argv=None):
@@ -84,11 +92,13 @@ def main(argv=None):
     ap.add_argument("--samples", type=int, default=10000)
     ap.add_argument("--T", type=int, default=None, help="code cycles (default: the preset's)")
     ap.add_argument("--seed", type=int, default=2212)
+    ap.add_argument("--no-meas-nodes", action="store_true",
+                    help="BP without the measurement-error variables (checks taken as exact)")
     a = ap.parse_args(argv)
     points = []
     for L in a.L:
         for k, p in enumerate(a.p):
-            q = run_point(a.preset, L, p, a.samples, a.seed + 1000 * L + k, a.T)
+            q = run_point(a.preset, L, p, a.samples, a.seed + 1000 * L + k, a.T, not a.no_meas_nodes)
             points.append(q)
             print(json.dumps(q), flush=True)
     fit = fit_threshold(points)
