@@ -5,12 +5,16 @@ logical Z lines of the final error, no noiseless round):
   flip : one parallel flip application per code cycle, 1000 cycles (Sec. 3.1, Fig. 2)
   bp   : 30 BP iterations per cycle, 500 cycles (Sec. 4.1, Fig. 6)
   pbp  : 20 BP iterations then P F F P F F, 500 cycles (Sec. 4.2, Fig. 7)
+  table1 --nA n --lp l : n rule applications per cycle, every l-th one p-flip,
+         1000 cycles (Sec. 3.2, Table 1)
 
   python -m paper_2212_06985_gb300.threshold pbp --L 14 18 24 32 --p 0.053 0.054 0.055 0.056 --samples 10000
 
 Each (L, p) point prints one JSON line with the failure counts of logical
 qubit 0 (the paper plots one of the three; the code is symmetric) and of
-any qubit.  With two or more L the points are fitted to the paper's ansatz
+any qubit.  The last line gives the crossing read from the data (between the
+last rate where the largest L fails less often than the smallest and the
+next) and, with enough unsaturated points, the fit of the paper's ansatz
 p_fail = a0 + a1 x + a2 x^2, x = (p - p_th) L^(1/nu) (Sec. 3.2, after Table 1).
 """
 from __future__ import annotations
@@ -22,21 +26,25 @@ import time
 import numpy as np
 import torch
 
-from . import make_batch, make_run_cfg, n_bits, toric3d_run_batch, toric3d_run_batch_workspace_bytes, words_for
+from . import (make_batch, make_run_cfg, n_bits, table1_schedule, toric3d_run_batch,
+               toric3d_run_batch_workspace_bytes, words_for)
 
 PRESETS = {
     "flip": dict(T=1000, use_bp=False, bp_iters=0, schedule="F", n_apply=1),
     "bp": dict(T=500, use_bp=True, bp_iters=30, schedule="", n_apply=0),
     "pbp": dict(T=500, use_bp=True, bp_iters=20, schedule="PFFPFF", n_apply=6),
+    "table1": dict(T=1000, use_bp=False, bp_iters=0, schedule="", n_apply=0),   # schedule from (n_A, lambda_p)
 }
 
 
 def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | None = None,
-              meas_nodes: bool = True, device="cuda:0") -> dict:
+              meas_nodes: bool = True, n_A: int = 5, lambda_p: int = 3, device="cuda:0") -> dict:
     """One whole run of `samples` codes; returns failure counts and the run time."""
     pr = dict(PRESETS[preset])
     if T is not None:
         pr["T"] = T
+    if preset == "table1":
+        pr["schedule"], pr["n_apply"] = table1_schedule(n_A, lambda_p), n_A
     dev = torch.device(device)
     e = torch.zeros((n_bits(L), words_for(samples)), dtype=torch.int64, device=dev)
     counts = torch.zeros(8, dtype=torch.int64, device=dev)
@@ -51,9 +59,22 @@ def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | N
     dt = time.perf_counter() - t0
     c = counts.cpu().numpy()
     fail0 = int(c[1::2].sum())          # mask values with bit 0 set
-    return {"preset": preset, "L": L, "p": p, "T": pr["T"], "meas_nodes": meas_nodes, "samples": samples,
+    return {"preset": preset, "schedule": pr["schedule"], "L": L, "p": p, "T": pr["T"], "meas_nodes": meas_nodes,
+            "samples": samples,
             "seed": seed,
             "fail_q0": fail0, "fail_any": int(c[1:].sum()), "counts8": c.tolist(), "seconds": dt}
+
+
+def crossing_guess(points: list[dict]) -> float | None:
+    """The rate where the largest lattice starts failing more often than the smallest:
+    midpoint between the last p with f(L_max) < f(L_min) and the next p."""
+    Ls = sorted({q["L"] for q in points})
+    rate = {(q["L"], q["p"]): q["fail_q0"] / q["samples"] for q in points}
+    ps = sorted({q["p"] for q in points if (Ls[0], q["p"]) in rate and (Ls[-1], q["p"]) in rate})
+    for a, b in zip(ps, ps[1:]):
+        if rate[(Ls[-1], a)] < rate[(Ls[0], a)] and rate[(Ls[-1], b)] >= rate[(Ls[0], b)]:
+            return 0.5 * (a + b)
+    return None
 
 
 def fit_threshold(points: list[dict]) -> dict | None:
@@ -74,12 +95,15 @@ def fit_threshold(points: list[dict]) -> dict | None:
         x = (X[1] - pth) * X[0] ** (1.0 / nu)
         return a0 + a1 * x + a2 * x * x
 
-    p0 = [float(np.median(p)), 1.0, float(np.median(f)), 1.0, 0.0]
+    p0 = [crossing_guess(use) or float(np.median(p)), 1.0, float(np.median(f)), 1.0, 0.0]
     try:
         popt, pcov = curve_fit(model, np.vstack([L, p]), f, p0=p0, sigma=sigma, maxfev=20000)
     except (RuntimeError, ValueError) as exc:
         return {"error": str(exc), "points": len(use)}
     err = np.sqrt(np.diag(pcov))
+    if not (np.isfinite(err[0]) and popt[1] > 0):
+        return {"error": "fit did not determine p_th (transition too steep for the sampled rates)",
+                "points": len(use)}
     return {"p_th": popt[0], "p_th_err": err[0], "nu": popt[1], "nu_err": err[1], "a": popt[2:].tolist(),
             "points": len(use)}
 
@@ -92,18 +116,22 @@ def main(argv=None):
     ap.add_argument("--samples", type=int, default=10000)
     ap.add_argument("--T", type=int, default=None, help="code cycles (default: the preset's)")
     ap.add_argument("--seed", type=int, default=2212)
+    ap.add_argument("--nA", type=int, default=5, help="table1: rule applications per cycle")
+    ap.add_argument("--lp", type=int, default=3, help="table1: every lp-th application is p-flip")
     ap.add_argument("--no-meas-nodes", action="store_true",
                     help="BP without the measurement-error variables (checks taken as exact)")
     a = ap.parse_args(argv)
     points = []
     for L in a.L:
         for k, p in enumerate(a.p):
-            q = run_point(a.preset, L, p, a.samples, a.seed + 1000 * L + k, a.T, not a.no_meas_nodes)
+            q = run_point(a.preset, L, p, a.samples, a.seed + 1000 * L + k, a.T, not a.no_meas_nodes, a.nA, a.lp)
             points.append(q)
             print(json.dumps(q), flush=True)
-    fit = fit_threshold(points)
-    if fit is not None:
-        print(json.dumps({"fit": fit}), flush=True)
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        fit = fit_threshold(points)
+    print(json.dumps({"crossing": crossing_guess(points), "fit": fit}), flush=True)
     return 0
 
 

@@ -27,3 +27,10 @@ def test_presets_follow_the_paper():
     assert threshold.PRESETS["flip"]["T"] == 1000 and threshold.PRESETS["flip"]["schedule"] == "F"
     assert threshold.PRESETS["bp"]["bp_iters"] == 30 and threshold.PRESETS["bp"]["T"] == 500
     assert threshold.PRESETS["pbp"]["bp_iters"] == 20 and threshold.PRESETS["pbp"]["schedule"] == "PFFPFF"
+    assert threshold.PRESETS["table1"]["T"] == 1000 and not threshold.PRESETS["table1"]["use_bp"]
+
+
+def test_crossing_guess_brackets_the_crossing():
+    pts = [{"L": L, "p": p, "samples": 1000, "fail_q0": f}
+           for L, row in ((14, (10, 300, 900)), (24, (1, 150, 950))) for p, f in zip((0.040, 0.041, 0.042), row)]
+    assert threshold.crossing_guess(pts) == 0.0415
