@@ -7,6 +7,8 @@ logical Z lines of the final error, no noiseless round):
   pbp  : 20 BP iterations then P F F P F F, 500 cycles (Sec. 4.2, Fig. 7)
   table1 --nA n --lp l : n rule applications per cycle, every l-th one p-flip,
          1000 cycles (Sec. 3.2, Table 1)
+  table1-sweep : every non-empty cell of Table 1 on a 0.1% grid around the
+         paper's value, L = 14 and 24; one line per cell with the crossing
 
   python -m paper_2212_06985_gb300.threshold pbp --L 14 18 24 32 --p 0.053 0.054 0.055 0.056 --samples 10000
 
@@ -65,6 +67,27 @@ def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | N
             "fail_q0": fail0, "fail_any": int(c[1:].sum()), "counts8": c.tolist(), "seconds": dt}
 
 
+# Table 1 of the paper: thresholds (%) of flip + p-flip after 1000 cycles, keyed by
+# (n_A, lambda_p); lambda_p > n_A means n_A flip applications and no p-flip.
+TABLE1_PAPER = {(9, 2): 4.343, (9, 3): 4.652, (9, 4): 4.753, (9, 5): 4.652, (9, 6): 4.654,
+                (7, 2): 4.212, (7, 3): 4.629, (7, 4): 4.615, (7, 5): 4.620, (7, 6): 4.558,
+                (5, 2): 3.998, (5, 3): 4.445, (5, 4): 4.475, (5, 5): 4.274, (5, 6): 4.082,
+                (3, 2): 3.604, (3, 3): 3.752, (3, 4): 3.943, (1, 2): 2.611}
+
+
+def table1_sweep(Ls=(14, 24), samples: int = 3000, seed: int = 7000):
+    """Yield, for every cell of Table 1, the failure rates on the 0.1% grid from 0.2%
+    below to 0.2% above the paper's value (rounded to 0.1%) and the crossing."""
+    for (nA, lp), th in sorted(TABLE1_PAPER.items()):
+        centre = round(th, 1)
+        grid = [round((centre + 0.1 * k) / 100, 4) for k in range(-2, 3)]
+        pts = [run_point("table1", L, p, samples, seed + 100 * nA + 10 * lp + k + L, n_A=nA, lambda_p=lp)
+               for L in Ls for k, p in enumerate(grid)]
+        c = crossing_guess(pts)
+        yield {"nA": nA, "lp": lp, "paper_pct": th, "crossing_pct": None if c is None else round(100 * c, 3),
+               "rates": {f"L{q['L']}@{q['p']}": q["fail_q0"] / q["samples"] for q in pts}}
+
+
 def crossing_guess(points: list[dict]) -> float | None:
     """The rate where the largest lattice starts failing more often than the smallest:
     midpoint between the last p with f(L_max) < f(L_min) and the next p."""
@@ -110,9 +133,9 @@ def fit_threshold(points: list[dict]) -> dict | None:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("preset", choices=sorted(PRESETS))
+    ap.add_argument("preset", choices=sorted(PRESETS) + ["table1-sweep"])
     ap.add_argument("--L", type=int, nargs="+", default=[14, 18, 24])
-    ap.add_argument("--p", type=float, nargs="+", required=True)
+    ap.add_argument("--p", type=float, nargs="+", default=None, help="error rates (required but for table1-sweep)")
     ap.add_argument("--samples", type=int, default=10000)
     ap.add_argument("--T", type=int, default=None, help="code cycles (default: the preset's)")
     ap.add_argument("--seed", type=int, default=2212)
@@ -121,6 +144,12 @@ def main(argv=None):
     ap.add_argument("--no-meas-nodes", action="store_true",
                     help="BP without the measurement-error variables (checks taken as exact)")
     a = ap.parse_args(argv)
+    if a.preset == "table1-sweep":
+        for row in table1_sweep(tuple(a.L) if a.L != [14, 18, 24] else (14, 24), a.samples, a.seed):
+            print(json.dumps(row), flush=True)
+        return 0
+    if not a.p:
+        ap.error("--p is required")
     points = []
     for L in a.L:
         for k, p in enumerate(a.p):
