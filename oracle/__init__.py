@@ -65,6 +65,7 @@ class Cfg(ctypes.Structure):
         ("perfect_round", ctypes.c_int32),
         ("perfect_max_sweeps", ctypes.c_int32),
         ("cycle0", ctypes.c_uint32),
+        ("bp_meta", ctypes.c_int32),
     ]
 
 
@@ -99,6 +100,11 @@ def _declare(L):
         "t3o_flip_sequential": (i32, [i32, _P, _P, i32]),
         "t3o_bp": (None, [i32, i32, _P, _P, _P, dbl, dbl, i32, _P, _P, _P]),
         "t3o_toric_tanner": (None, [i32, _P, _P]),
+        "t3o_bp_priors": (None, [i32, i32, _P, _P, _P, _P, i32, _P]),
+        "t3o_cube_faces": (None, [i32, i64, _P]),
+        "t3o_meta_syndrome": (None, [i32, _P, _P]),
+        "t3o_meta_tanner": (None, [i32, _P, _P]),
+        "t3o_bp_meta_decode_batch": (None, [i32, i64, _P, _P, dbl, dbl, i32, _P]),
         "t3o_bp_decode": (None, [i32, _P, _P, dbl, dbl, i32, i32, _P]),
         "t3o_logical": (i32, [i32, _P, _P]),
         "t3o_run_sample": (i32, [_P, u64, _P]),
@@ -181,6 +187,48 @@ def toric_tanner(L: int):
     return cptr, cvar
 
 
+def bp_priors(cptr, cvar, syn, prior, iters):
+    """BP with one prior per variable on a CSR factor graph; returns the posteriors."""
+    cptr = np.ascontiguousarray(cptr, dtype=np.int32)
+    cvar = np.ascontiguousarray(cvar, dtype=np.int32)
+    prior = np.ascontiguousarray(prior, dtype=np.float64)
+    syn = _u8(syn)
+    llr = np.zeros(len(prior), dtype=np.float64)
+    lib().t3o_bp_priors(len(prior), len(cptr) - 1, _ptr(cptr), _ptr(cvar), _ptr(syn), _ptr(prior), iters,
+                        _ptr(llr))
+    return llr
+
+
+def cube_faces(L: int, site: int) -> np.ndarray:
+    out = np.zeros(6, dtype=np.int64)
+    lib().t3o_cube_faces(L, site, _ptr(out))
+    return out
+
+
+def meta_syndrome(L: int, s) -> np.ndarray:
+    s = _u8(s)
+    m = np.zeros(L ** 3, dtype=np.uint8)
+    lib().t3o_meta_syndrome(L, _ptr(s), _ptr(m))
+    return m
+
+
+def meta_tanner(L: int):
+    n = n_bits(L)
+    cptr = np.zeros(n + L ** 3 + 1, dtype=np.int32)
+    cvar = np.zeros(5 * n + 6 * L ** 3, dtype=np.int32)
+    lib().t3o_meta_tanner(L, _ptr(cptr), _ptr(cvar))
+    return cptr, cvar
+
+
+def bp_meta_decode_batch(L, e, s, p, q, iters):
+    """BP with meta-checks on each sample; returns (e, s, llr [S][2 * 3L^3])."""
+    e = _u8(e).copy()
+    s = _u8(s).copy()
+    llr = np.zeros((e.shape[0], 2 * e.shape[1]), dtype=np.float64)
+    lib().t3o_bp_meta_decode_batch(L, e.shape[0], _ptr(e), _ptr(s), float(p), float(q), iters, _ptr(llr))
+    return e, s, llr
+
+
 # ---------------------------------------------------------------- single sample
 def syndrome(L: int, e) -> np.ndarray:
     e = _u8(e)
@@ -258,7 +306,7 @@ def logical(L, e):
 
 def make_cfg(L, T, p, q, seed, *, use_bp=False, bp_iters=0, bp_meas_nodes=True,
              schedule="", n_apply=None, perfect_round=False, perfect_max_sweeps=0,
-             cycle0=0) -> Cfg:
+             cycle0=0, bp_meta=False) -> Cfg:
     c = Cfg()
     c.L, c.T, c.p, c.q, c.seed = L, T, float(p), float(q), seed
     c.use_bp, c.bp_iters, c.bp_meas_nodes = int(use_bp), bp_iters, int(bp_meas_nodes)
@@ -266,6 +314,7 @@ def make_cfg(L, T, p, q, seed, *, use_bp=False, bp_iters=0, bp_meas_nodes=True,
     c.schedule = schedule.encode()
     c.perfect_round, c.perfect_max_sweeps = int(perfect_round), perfect_max_sweeps
     c.cycle0 = cycle0
+    c.bp_meta = int(bp_meta)
     return c
 
 

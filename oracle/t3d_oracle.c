@@ -420,6 +420,164 @@ void t3o_bp_decode(int L, uint8_t* e, uint8_t* s, double p, double q, int meas_n
 }
 
 /* ------------------------------------------------------------------ */
+/* BP on a factor graph with one prior LLR per variable (Sec. 4.1, Eqs. */
+/* 1-4), the same flooding schedule and numerical guards as t3o_bp but  */
+/* with every variable explicit: used for BP with meta-checks, where    */
+/* the measurement-error variables have degree 3 instead of 1.          */
+/* ------------------------------------------------------------------ */
+void t3o_bp_priors(int nv, int nc, const int32_t* cptr, const int32_t* cvar, const uint8_t* syn,
+                   const double* prior, int iters, double* llr)
+{
+    int ne = cptr[nc];
+    double* vc = (double*)malloc((size_t)(ne > 0 ? ne : 1) * sizeof(double));
+    double* cv = (double*)calloc((size_t)(ne > 0 ? ne : 1), sizeof(double));
+    double* tv = (double*)malloc((size_t)(ne > 0 ? ne : 1) * sizeof(double));
+    int* vdeg = (int*)calloc((size_t)nv + 1, sizeof(int));
+    int* vptr = (int*)calloc((size_t)nv + 1, sizeof(int));
+    int* vedge = (int*)malloc((size_t)(ne > 0 ? ne : 1) * sizeof(int));
+    const double cap = 1.0 - 1e-15;
+
+    for (int t = 0; t < ne; ++t) vdeg[cvar[t]]++;
+    for (int v = 0; v < nv; ++v) vptr[v + 1] = vptr[v] + vdeg[v];
+    memset(vdeg, 0, (size_t)nv * sizeof(int));
+    for (int t = 0; t < ne; ++t) {
+        int v = cvar[t];
+        vedge[vptr[v] + vdeg[v]++] = t;
+    }
+    for (int it = 0; it < iters; ++it) {
+        /* variable -> check (Eq. 3; the prior alone on the first pass, when cv = 0) */
+        for (int v = 0; v < nv; ++v)
+            for (int i = vptr[v]; i < vptr[v + 1]; ++i) {
+                double m = prior[v];
+                for (int i2 = vptr[v]; i2 < vptr[v + 1]; ++i2)
+                    if (i2 != i) m += cv[vedge[i2]];
+                vc[vedge[i]] = m;
+            }
+        /* check -> variable (Eq. 2) */
+        for (int t = 0; t < ne; ++t) tv[t] = tanh(vc[t] / 2.0);
+        for (int c = 0; c < nc; ++c)
+            for (int t = cptr[c]; t < cptr[c + 1]; ++t) {
+                double prod = 1.0;
+                for (int t2 = cptr[c]; t2 < cptr[c + 1]; ++t2)
+                    if (t2 != t) prod *= tv[t2];
+                if (prod > cap) prod = cap;
+                if (prod < -cap) prod = -cap;
+                double m = 2.0 * atanh(prod);
+                if (syn[c] & 1) m = -m;
+                if (m > 30.0) m = 30.0;
+                if (m < -30.0) m = -30.0;
+                cv[t] = m;
+            }
+    }
+    /* posterior (Eq. 4) */
+    if (llr)
+        for (int v = 0; v < nv; ++v) {
+            double l = prior[v];
+            for (int i = vptr[v]; i < vptr[v + 1]; ++i) l += cv[vedge[i]];
+            llr[v] = l;
+        }
+    free(vc); free(cv); free(tv); free(vdeg); free(vptr); free(vedge);
+}
+
+/* The six faces of the unit cube at site r (spanning r .. r + e_x + e_y +
+ * e_z): for each axis a the face with normal a at r and the one at
+ * r + e_a.  Every face bounds exactly two cubes. */
+void t3o_cube_faces(int L, int64_t site, int64_t out[6])
+{
+    int r[3] = { (int)(site % L), (int)((site / L) % L), (int)(site / ((int64_t)L * L)) };
+    int64_t L3 = (int64_t)L * L * L;
+    for (int a = 0; a < 3; ++a) {
+        int q[3] = { r[0], r[1], r[2] };
+        q[a] = (r[a] + 1) % L;
+        out[2 * a] = a * L3 + site;
+        out[2 * a + 1] = a * L3 + ((int64_t)q[2] * L + q[1]) * L + q[0];
+    }
+}
+
+/* Meta-syndrome (Sec. 4.1, last paragraph): every error-free syndrome is a
+ * union of closed loops, so the six faces of a cube have even parity; the
+ * measured parity of cube c is the parity of the measurement errors on its
+ * faces.  m: L^3 bytes. */
+void t3o_meta_syndrome(int L, const uint8_t* s, uint8_t* m)
+{
+    int64_t L3 = (int64_t)L * L * L;
+    for (int64_t c = 0; c < L3; ++c) {
+        int64_t fc[6];
+        t3o_cube_faces(L, c, fc);
+        int par = 0;
+        for (int j = 0; j < 6; ++j) par ^= s[fc[j]] & 1;
+        m[c] = (uint8_t)par;
+    }
+}
+
+/* Factor graph of BP with meta-checks in CSR form.  Variables 0..n-1 are
+ * the qubits (edges), n + f the measurement error of face f.  Checks
+ * 0..n-1 are the faces (their four edges in t3o_face_edges order, then
+ * their measurement variable); checks n + c are the meta-checks, one per
+ * cube, over the measurement variables of its six faces. */
+void t3o_meta_tanner(int L, int32_t* cptr, int32_t* cvar)
+{
+    int64_t n = 3LL * L * L * L, L3 = (int64_t)L * L * L;
+    int64_t t = 0;
+    for (int64_t f = 0; f < n; ++f) {
+        int64_t ed[4];
+        cptr[f] = (int32_t)t;
+        t3o_face_edges(L, f, ed);
+        for (int j = 0; j < 4; ++j) cvar[t++] = (int32_t)ed[j];
+        cvar[t++] = (int32_t)(n + f);
+    }
+    for (int64_t c = 0; c < L3; ++c) {
+        int64_t fc[6];
+        cptr[n + c] = (int32_t)t;
+        t3o_cube_faces(L, c, fc);
+        for (int j = 0; j < 6; ++j) cvar[t++] = (int32_t)(n + fc[j]);
+    }
+    cptr[n + L3] = (int32_t)t;
+}
+
+/* BP with meta-checks for one sample (qubit priors log((1-p)/p),
+ * measurement priors log((1-q)/q)), then the hard decision on the qubits
+ * as in t3o_bp_decode: e ^= d, s ^= H d.  llr_out (optional, 2 * 3L^3):
+ * posteriors of the qubits, then of the measurement variables. */
+void t3o_bp_meta_decode(int L, uint8_t* e, uint8_t* s, double p, double q, int iters, double* llr_out)
+{
+    int64_t n = 3LL * L * L * L, L3 = (int64_t)L * L * L;
+    int64_t nc = n + L3, ne = 5 * n + 6 * L3;
+    int32_t* cptr = (int32_t*)malloc((size_t)(nc + 1) * sizeof(int32_t));
+    int32_t* cvar = (int32_t*)malloc((size_t)ne * sizeof(int32_t));
+    uint8_t* syn = (uint8_t*)malloc((size_t)nc);
+    double* prior = (double*)malloc((size_t)(2 * n) * sizeof(double));
+    double* llr = (double*)malloc((size_t)(2 * n) * sizeof(double));
+    t3o_meta_tanner(L, cptr, cvar);
+    memcpy(syn, s, (size_t)n);
+    t3o_meta_syndrome(L, s, syn + n);
+    for (int64_t v = 0; v < n; ++v) {
+        prior[v] = prior_llr(p);
+        prior[n + v] = prior_llr(q);
+    }
+    t3o_bp_priors((int)(2 * n), (int)nc, cptr, cvar, syn, prior, iters, llr);
+    for (int64_t v = 0; v < n; ++v)
+        if (llr[v] < 0.0) e[v] ^= 1;
+    for (int64_t f = 0; f < n; ++f) {
+        int64_t ed[4];
+        t3o_face_edges(L, f, ed);
+        int par = 0;
+        for (int j = 0; j < 4; ++j) par ^= (llr[ed[j]] < 0.0);
+        s[f] ^= (uint8_t)par;
+    }
+    if (llr_out) memcpy(llr_out, llr, (size_t)(2 * n) * sizeof(double));
+    free(cptr); free(cvar); free(syn); free(prior); free(llr);
+}
+
+void t3o_bp_meta_decode_batch(int L, int64_t n_samples, uint8_t* e, uint8_t* s, double p, double q,
+                              int iters, double* llr)
+{
+    int64_t n = 3LL * L * L * L;
+    for (int64_t i = 0; i < n_samples; ++i)
+        t3o_bp_meta_decode(L, e + i * n, s + i * n, p, q, iters, llr ? llr + i * 2 * n : NULL);
+}
+
+/* ------------------------------------------------------------------ */
 /* Logical readout (Fig. 2 caption, Sec. 3.1 and its footnote, App. A.2):*/
 /* for axis d the L^2 straight lines of d-edges (one per value of the   */
 /* two other coordinates) are a complete disjoint set of logical Z      */
@@ -477,6 +635,7 @@ typedef struct {
     int32_t perfect_round;
     int32_t perfect_max_sweeps;
     uint32_t cycle0;
+    int32_t bp_meta;     /* 1: BP with meta-checks (needs q > 0) in place of plain BP */
 } t3o_cfg;
 
 static int syndrome_clear(int64_t n, const uint8_t* s)
@@ -497,7 +656,9 @@ int t3o_run_sample(const t3o_cfg* cfg, uint64_t sample, uint8_t* e)
         uint32_t cycle = cfg->cycle0 + (uint32_t)t;
         t3o_noise(L, e, cfg->p, cfg->seed, sample, cycle);
         t3o_measure(L, e, s, cfg->q, cfg->seed, sample, cycle);
-        if (cfg->use_bp)
+        if (cfg->use_bp && cfg->bp_meta)
+            t3o_bp_meta_decode(L, e, s, cfg->p, cfg->q, cfg->bp_iters, NULL);
+        else if (cfg->use_bp)
             t3o_bp_decode(L, e, s, cfg->p, cfg->q, cfg->bp_meas_nodes, cfg->bp_iters, NULL);
         for (int k = 0; slen > 0 && k < cfg->n_apply; ++k) {
             if (cfg->schedule[(size_t)k % slen] == 'P')
