@@ -184,6 +184,51 @@ t3d_status toric3d_bp(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double
                       t3d_stream stream);
 
 /*
+ * BP with meta-checks (Sec. 4.1, last paragraph, where the paper proposes
+ * them without simulating them): every error-free syndrome is a set of closed
+ * loops, so the six faces of every unit cube have even parity.  The factor
+ * graph has the 3L^3 qubit variables (prior log((1-p)/p)), one measurement-
+ * error variable per face (prior log((1-q)/q)) joined to its face check and
+ * to the meta-checks of the two cubes the face bounds, the 3L^3 face checks
+ * (syndrome s) and the L^3 cube meta-checks (syndrome: parity of s over the
+ * cube's six faces).  `iters` flooding iterations of Eqs. 2-3 over that
+ * graph from the priors, FP32 messages clamped to |M| <= 30; then every qubit
+ * with posterior (Eq. 4) below zero is corrected, e ^= d and s ^= H d.
+ *   e, s      uint64_t[3L^3][ceil(n_samples/64)], device, updated in place
+ *   0 < p < 1, 0 < q < 1 (q = 0 has no measurement variables: toric3d_bp)
+ *   work      >= toric3d_bp_meta_workspace_bytes(L, 64) bytes of 256-byte
+ *             aligned device scratch; samples are processed in chunks of
+ *             whole 64-sample words as large as it allows
+ *   llr_out   nullable: float[2][3L^3][n_samples], the qubits' posteriors
+ *             then the measurement variables' (face order); needs a
+ *             workspace for all samples at once
+ * Returns T3D_EINVAL (message in toric3d_last_error) on a bad argument or a
+ * workspace too small for one word; nothing is launched then.
+ */
+size_t toric3d_bp_meta_workspace_bytes(int L, int64_t chunk_samples);
+t3d_status toric3d_bp_meta(int L, int64_t n_samples, uint64_t* e, uint64_t* s, double p, double q,
+                           int iters, void* work, size_t work_bytes, float* llr_out, t3d_stream stream);
+
+/*
+ * One flooding iteration of the meta-check BP above, for checking it message
+ * by message.  Message buffers are float[7][3L^3][S'], S' = 64 ceil(n_samples
+ * / 64) samples innermost: rows 4f + j (j = 0..3) face f -> its j-th edge
+ * (the a-edges at r and r + e_b, then the b-edges at r and r + e_a, a < b the
+ * face's in-plane axes), row 3L^3 * 4 + f face f -> its measurement
+ * variable, row 3L^3 * 5 + f the cube at the face's own site (the face is
+ * its lower face) -> that variable, row 3L^3 * 6 + f the cube one step down
+ * along the face's normal (upper face) -> that variable.  msg_out gets every
+ * check -> variable message computed from msg_in (all zero: the first
+ * iteration); the buffers must not overlap; toric3d_bp_meta_message_bytes
+ * gives their size and work (16-byte aligned device scratch for the edge
+ * totals) needs a seventh of it.
+ */
+size_t toric3d_bp_meta_message_bytes(int L, int64_t n_samples);
+t3d_status toric3d_bp_meta_step(int L, int64_t n_samples, const uint64_t* s, double p, double q,
+                                const float* msg_in, float* msg_out, void* work, size_t work_bytes,
+                                t3d_stream stream);
+
+/*
  * Fallback gate of the learned pre-decoder (no counterpart in the paper,
  * whose decoders have no fallback): gate[w] = 1 iff some sample of word w has
  * more than max_weight unsatisfied checks in s (s: uint64_t[3L^3][words],
@@ -219,8 +264,9 @@ t3d_status toric3d_unpack(int64_t n_bits, int64_t n_samples, const uint64_t* wor
 /*
  * A whole Monte Carlo run (Sec. 3.1 Fig. 2, Sec. 3.2, Sec. 4.2).  For cycles
  * t = cycle0+1 .. cycle0+T: qubit noise (p), one noisy measurement (q),
- * optional BP (bp_iters iterations, measurement-error variables iff
- * bp_meas_nodes) with its hard decision, then n_apply flip/p-flip
+ * optional BP (bp_iters iterations; bp_meas_nodes 0: checks taken as exact,
+ * 1: a measurement-error variable per check, 2: those variables joined by the
+ * cube meta-checks as in toric3d_bp_meta) with its hard decision, then n_apply flip/p-flip
  * applications cycling through `schedule` (application k keys the coins with
  * sweep index k).  Optionally a final noiseless measurement (cycle0+T+1)
  * decoded by up to perfect_max_sweeps flip applications.  Finally the

@@ -101,6 +101,7 @@ def _declare(L):
         "t3o_bp": (None, [i32, i32, _P, _P, _P, dbl, dbl, i32, _P, _P, _P]),
         "t3o_toric_tanner": (None, [i32, _P, _P]),
         "t3o_bp_priors": (None, [i32, i32, _P, _P, _P, _P, i32, _P]),
+        "t3o_bp_priors_from": (None, [i32, i32, _P, _P, _P, _P, i32, _P, _P, _P]),
         "t3o_cube_faces": (None, [i32, i64, _P]),
         "t3o_meta_syndrome": (None, [i32, _P, _P]),
         "t3o_meta_tanner": (None, [i32, _P, _P]),
@@ -197,6 +198,22 @@ def bp_priors(cptr, cvar, syn, prior, iters):
     lib().t3o_bp_priors(len(prior), len(cptr) - 1, _ptr(cptr), _ptr(cvar), _ptr(syn), _ptr(prior), iters,
                         _ptr(llr))
     return llr
+
+
+def bp_priors_from(cptr, cvar, syn, prior, iters, cv_in=None):
+    """bp_priors started from the check->variable messages cv_in (one per Tanner edge,
+    CSR order; None = zero); returns (posteriors, the last check->variable messages)."""
+    cptr = np.ascontiguousarray(cptr, dtype=np.int32)
+    cvar = np.ascontiguousarray(cvar, dtype=np.int32)
+    prior = np.ascontiguousarray(prior, dtype=np.float64)
+    syn = _u8(syn)
+    cv = None if cv_in is None else np.ascontiguousarray(cv_in, dtype=np.float64)
+    assert cv is None or cv.shape == (cptr[-1],)
+    cv_out = np.zeros(int(cptr[-1]), dtype=np.float64)
+    llr = np.zeros(len(prior), dtype=np.float64)
+    lib().t3o_bp_priors_from(len(prior), len(cptr) - 1, _ptr(cptr), _ptr(cvar), _ptr(syn), _ptr(prior), iters,
+                             _ptr(cv), _ptr(cv_out), _ptr(llr))
+    return llr, cv_out
 
 
 def cube_faces(L: int, site: int) -> np.ndarray:

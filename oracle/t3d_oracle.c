@@ -425,8 +425,20 @@ void t3o_bp_decode(int L, uint8_t* e, uint8_t* s, double p, double q, int meas_n
 /* with every variable explicit: used for BP with meta-checks, where    */
 /* the measurement-error variables have degree 3 instead of 1.          */
 /* ------------------------------------------------------------------ */
+void t3o_bp_priors_from(int nv, int nc, const int32_t* cptr, const int32_t* cvar, const uint8_t* syn,
+                        const double* prior, int iters, const double* cv_in, double* cv_out, double* llr);
+
 void t3o_bp_priors(int nv, int nc, const int32_t* cptr, const int32_t* cvar, const uint8_t* syn,
                    const double* prior, int iters, double* llr)
+{
+    t3o_bp_priors_from(nv, nc, cptr, cvar, syn, prior, iters, NULL, NULL, llr);
+}
+
+/* The same iterations started from given check->variable messages cv_in (one
+ * per Tanner edge t = cptr[c] + k; NULL: all zero, the start above), leaving
+ * the last ones in cv_out (nullable). */
+void t3o_bp_priors_from(int nv, int nc, const int32_t* cptr, const int32_t* cvar, const uint8_t* syn,
+                        const double* prior, int iters, const double* cv_in, double* cv_out, double* llr)
 {
     int ne = cptr[nc];
     double* vc = (double*)malloc((size_t)(ne > 0 ? ne : 1) * sizeof(double));
@@ -437,6 +449,7 @@ void t3o_bp_priors(int nv, int nc, const int32_t* cptr, const int32_t* cvar, con
     int* vedge = (int*)malloc((size_t)(ne > 0 ? ne : 1) * sizeof(int));
     const double cap = 1.0 - 1e-15;
 
+    if (cv_in) memcpy(cv, cv_in, (size_t)ne * sizeof(double));
     for (int t = 0; t < ne; ++t) vdeg[cvar[t]]++;
     for (int v = 0; v < nv; ++v) vptr[v + 1] = vptr[v] + vdeg[v];
     memset(vdeg, 0, (size_t)nv * sizeof(int));
@@ -476,6 +489,7 @@ void t3o_bp_priors(int nv, int nc, const int32_t* cptr, const int32_t* cvar, con
             for (int i = vptr[v]; i < vptr[v + 1]; ++i) l += cv[vedge[i]];
             llr[v] = l;
         }
+    if (cv_out) memcpy(cv_out, cv, (size_t)ne * sizeof(double));
     free(vc); free(cv); free(tv); free(vdeg); free(vptr); free(vedge);
 }
 

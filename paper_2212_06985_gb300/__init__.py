@@ -31,6 +31,7 @@ __all__ = [
     "EXPORTED_SYMBOLS", "replica_sample0", "BatchItem", "make_batch", "toric3d_run_batch",
     "toric3d_run_batch_workspace_bytes", "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm",
     "toric3d_autotune_batch", "toric3d_flip_noalloc", "toric3d_gate_workspace_bytes", "toric3d_gate",
+    "toric3d_bp_meta_workspace_bytes", "toric3d_bp_meta", "toric3d_bp_meta_message_bytes", "toric3d_bp_meta_step",
 ]
 
 EXPORTED_SYMBOLS = [
@@ -45,6 +46,7 @@ EXPORTED_SYMBOLS = [
     "toric3d_cnn_param_count", "toric3d_cnn_blob_bytes", "toric3d_cnn_prepare", "toric3d_cnn_workspace_bytes",
     "toric3d_cnn_decode", "toric3d_cnn_train_workspace_bytes", "toric3d_cnn_train_step",
     "toric3d_gate_workspace_bytes", "toric3d_gate", "toric3d_cnn_status",
+    "toric3d_bp_meta_workspace_bytes", "toric3d_bp_meta", "toric3d_bp_meta_message_bytes", "toric3d_bp_meta_step",
 ]
 
 KERNEL_KINDS = {"noise": 0, "syndrome": 1, "flip": 2, "pflip": 3, "bp_step": 4, "bp_decide": 5,
@@ -135,6 +137,10 @@ def _declare(h):
         "toric3d_bp_decide": (i32, [i32, i64, _P, dbl, _P, _P, _P, _P, sz, _P]),
         "toric3d_bp_workspace_bytes": (sz, [i32, i64]),
         "toric3d_bp": (i32, [i32, i64, _P, _P, dbl, dbl, i32, _P, sz, _P, _P]),
+        "toric3d_bp_meta_workspace_bytes": (sz, [i32, i64]),
+        "toric3d_bp_meta": (i32, [i32, i64, _P, _P, dbl, dbl, i32, _P, sz, _P, _P]),
+        "toric3d_bp_meta_message_bytes": (sz, [i32, i64]),
+        "toric3d_bp_meta_step": (i32, [i32, i64, _P, dbl, dbl, _P, _P, _P, sz, _P]),
         "toric3d_logical": (i32, [i32, i64, _P, _P, _P, _P]),
         "toric3d_gate_workspace_bytes": (ctypes.c_size_t, [i32, i64]),
         "toric3d_cnn_status": (i32, []),
@@ -273,6 +279,26 @@ def toric3d_bp(L, n_samples, e, s, p, q_meas, iters, work, llr_out=None, stream=
                             _stream(stream)))
 
 
+def toric3d_bp_meta_workspace_bytes(L: int, chunk_samples: int) -> int:
+    return int(lib().toric3d_bp_meta_workspace_bytes(L, chunk_samples))
+
+
+def toric3d_bp_meta_message_bytes(L: int, n_samples: int) -> int:
+    return int(lib().toric3d_bp_meta_message_bytes(L, n_samples))
+
+
+def toric3d_bp_meta_step(L, n_samples, s, p, q, msg_in, msg_out, work, stream=None):
+    _check(lib().toric3d_bp_meta_step(L, n_samples, _ptr(s), float(p), float(q), _ptr(msg_in), _ptr(msg_out),
+                                      _ptr(work), work.numel() * work.element_size(), _stream(stream)))
+
+
+def toric3d_bp_meta(L, n_samples, e, s, p, q, iters, work, llr_out=None, stream=None):
+    """BP with meta-checks (one per unit cube over its faces' measurement variables)."""
+    _check(lib().toric3d_bp_meta(L, n_samples, _ptr(e), _ptr(s), float(p), float(q), iters,
+                                 _ptr(work), work.numel() * work.element_size(), _ptr(llr_out),
+                                 _stream(stream)))
+
+
 def toric3d_logical(L, n_samples, e, mask=None, counts8=None, stream=None):
     _check(lib().toric3d_logical(L, n_samples, _ptr(e), _ptr(mask), _ptr(counts8), _stream(stream)))
 
@@ -297,11 +323,14 @@ def toric3d_gate(L, s, max_weight, gate, work, n_flagged=None, stream=None):
 def make_run_cfg(L, T, p, q, seed, n_samples, *, sample0=0, use_bp=False, bp_iters=0,
                  bp_meas_nodes=True, schedule="", n_apply=None, perfect_round=False,
                  perfect_max_sweeps=0, cycle0=0, use_graph=False, bp_chunk_samples=0, cnn_blob=None,
-                 fallback_max_weight=-1) -> RunCfg:
+                 fallback_max_weight=-1, bp_meta_checks=False) -> RunCfg:
+    """bp_meta_checks: BP over the measurement variables joined by the cube meta-checks
+    (bp_meas_nodes = 2 in the C struct; implies measurement variables)."""
     c = RunCfg()
     c.L, c.T, c.p, c.q, c.seed = L, T, float(p), float(q), seed
     c.sample0, c.n_samples = sample0, n_samples
-    c.use_bp, c.bp_iters, c.bp_meas_nodes = int(use_bp), bp_iters, int(bp_meas_nodes)
+    c.use_bp, c.bp_iters = int(use_bp), bp_iters
+    c.bp_meas_nodes = 2 if bp_meta_checks else int(bp_meas_nodes)
     c.n_apply = len(schedule) if n_apply is None else n_apply
     c.schedule = schedule.encode()
     c.perfect_round, c.perfect_max_sweeps = int(perfect_round), perfect_max_sweeps

@@ -564,6 +564,17 @@ size_t cnn_workspace_bytes(int L, int64_t n_samples)
     return round256((size_t)words_for(n_samples) * L * L * L * 32) + tc_workspace_bytes(L, n_samples);
 }
 
+// e ^= d, s ^= H d from decision words dec[word][site][4] (the three edges'
+// words at the site as 32-bit halves; slot 3 unused).
+t3d_status launch_dec_apply(const Lattice& lat, int64_t W, int64_t words, const uint64_t* dec, uint64_t* e,
+                            uint64_t* s, cudaStream_t st)
+{
+    dim3 sg((unsigned)((lat.L3 + 7) / 8), (unsigned)((words + 31) / 32));
+    cnn::k_dec_apply<<<sg, 256, 0, st>>>(lat, W, words, dec, e, s);
+    T3D_LAUNCH_CHECK("decision apply");
+    return T3D_OK;
+}
+
 }  // namespace t3d
 
 extern "C" t3d_status toric3d_cnn_decode(int L, int64_t n_samples, const uint64_t* s_prev, uint64_t* s,

@@ -101,6 +101,9 @@ t3d_status launch_syndrome(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t
 t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_apply,
                          uint32_t sweep0, uint64_t seed, uint32_t cycle, cudaStream_t st);
 t3d_status launch_logical(ItemTable& tab, cudaStream_t st);
+// e ^= d, s ^= H d from decision words dec[word][site][4] (32-bit halves).
+t3d_status launch_dec_apply(const Lattice& lat, int64_t W, int64_t words, const uint64_t* dec, uint64_t* e,
+                            uint64_t* s, cudaStream_t st);
 // gate[w] = 1 iff some sample of word w has more than max_weight unsatisfied
 // checks in s; *n_flagged (nullable) += flagged words.  scratch holds
 // gate_scratch_bytes(L, W) bytes.
@@ -124,5 +127,13 @@ t3d_status launch_bp(const ItemTable& items, double p, double q_meas, int iters,
 // cap and keeps the fastest in the tuning table (synchronises the stream).
 t3d_status autotune_bp(const ItemTable& items, double p, double q_meas, float* const* bufs,
                        const int64_t* chunk_words, cudaStream_t st, int* best_cap, float* best_ms);
+
+// BP with meta-checks (t3d_bp_meta.cu): workspace bytes per 64-sample word and
+// the decoder on n_samples samples in rows of stride W words, chunked to fit.
+namespace meta {
+size_t bytes_per_word(int L);
+t3d_status launch_bp_meta(const Lattice& lat, int64_t n_samples, int64_t W, uint64_t* e, uint64_t* s, double p,
+                          double q, int iters, void* work, size_t work_bytes, float* llr_out, cudaStream_t st);
+}  // namespace meta
 
 }  // namespace t3d

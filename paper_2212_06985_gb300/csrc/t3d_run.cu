@@ -48,6 +48,14 @@ bool needs_bp(const t3d_run_cfg& c)
     return c.bp_iters > 0 && (c.use_bp || (learned(c) && c.fallback_max_weight >= 0));
 }
 
+// bp_meas_nodes == 2: BP with the cube meta-checks over the measurement variables
+bool meta_checks(const t3d_run_cfg& c) { return c.use_bp && c.bp_meas_nodes == 2; }
+
+size_t bp_word_bytes(const t3d_run_cfg& c, int L)
+{
+    return meta_checks(c) ? meta::bytes_per_word(L) : bp_bytes_per_word(L);
+}
+
 t3d_status validate_cfg(const t3d_run_cfg* c)
 {
     T3D_REQUIRE(c != nullptr, "cfg is NULL");
@@ -67,7 +75,10 @@ t3d_status validate_cfg(const t3d_run_cfg* c)
     if (c->use_bp || (c->cnn_blob && c->fallback_max_weight >= 0)) {
         T3D_REQUIRE(c->p > 0.0 && c->p < 1.0, "BP needs 0 < p < 1");
         T3D_REQUIRE(c->bp_iters >= 0, "bp_iters must be >= 0");
+        T3D_REQUIRE(c->bp_meas_nodes >= 0 && c->bp_meas_nodes <= 2, "bp_meas_nodes must be 0, 1 or 2");
         T3D_REQUIRE(!c->bp_meas_nodes || c->q < 0.5, "measurement nodes need q < 0.5");
+        T3D_REQUIRE(c->bp_meas_nodes != 2 || (c->use_bp && c->q > 0.0),
+                    "meta-checks (bp_meas_nodes = 2) need use_bp and q > 0");
         T3D_REQUIRE(c->bp_chunk_samples >= 0, "bp_chunk_samples must be >= 0");
     }
     T3D_REQUIRE(!c->perfect_round || c->perfect_max_sweeps >= 0, "perfect_max_sweeps must be >= 0");
@@ -108,7 +119,7 @@ bool bp_chunks(const t3d_run_cfg& c, const t3d_batch_item* items, int n, size_t 
             int64_t w = (Wi + rounds - 1) / rounds;
             if (c.bp_chunk_samples > 0) w = std::min(w, words_for(c.bp_chunk_samples));
             chunk[i] = w;
-            need += round_up((size_t)w * bp_bytes_per_word(items[i].L));
+            need += round_up((size_t)w * bp_word_bytes(c, items[i].L));
         }
         if (need <= avail) return true;
     }
@@ -147,7 +158,7 @@ size_t batch_workspace_bytes(const t3d_run_cfg& c, const t3d_batch_item* items, 
         for (int i = 0; i < n; ++i) {
             const int64_t Wi = words_for(items[i].n_samples);
             const int64_t w = c.bp_chunk_samples > 0 ? std::min(Wi, words_for(c.bp_chunk_samples)) : Wi;
-            total += round_up((size_t)w * bp_bytes_per_word(items[i].L));
+            total += round_up((size_t)w * bp_word_bytes(c, items[i].L));
         }
     }
     return total;
@@ -203,7 +214,7 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
         T3D_REQUIRE(bp_chunks(c, items, n, work_bytes - used, pl.chunk), "workspace too small for BP chunks");
         for (int i = 0; i < n; ++i) {
             pl.bp[i] = reinterpret_cast<float*>(base + used);
-            used += round_up((size_t)pl.chunk[i] * bp_bytes_per_word(items[i].L));
+            used += round_up((size_t)pl.chunk[i] * bp_word_bytes(c, items[i].L));
         }
     } else if (c.use_bp) {
         for (int i = 0; i < n; ++i) pl.chunk[i] = std::max<int64_t>(1, words_for(items[i].n_samples));
@@ -281,9 +292,16 @@ t3d_status enqueue_run(const t3d_run_cfg& c, const Plan& pl, cudaStream_t st)
         T3D_TRY(launch_noise(tab, thr_p, c.seed, cycle, st));
         tab = pl.items;
         T3D_TRY(launch_syndrome(tab, thr_q, c.seed, cycle, st));
-        if (c.use_bp)
+        if (meta_checks(c)) {
+            for (int i = 0; i < pl.items.n; ++i) {
+                const ItemDesc& d = pl.items.it[i];
+                T3D_TRY(meta::launch_bp_meta(d.lat, d.n_samples, d.W, d.e, d.s, c.p, c.q, c.bp_iters, pl.bp[i],
+                                             (size_t)pl.chunk[i] * meta::bytes_per_word(d.lat.L), nullptr, st));
+            }
+        } else if (c.use_bp) {
             T3D_TRY(launch_bp(pl.items, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, pl.bp, pl.chunk,
                               nullptr, st));
+        }
         if (c.n_apply > 0) {
             tab = pl.items;
             T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
@@ -436,6 +454,7 @@ extern "C" t3d_status toric3d_autotune_batch(const t3d_run_cfg* cfg, const t3d_b
     T3D_TRY(validate_cfg(cfg));
     T3D_TRY(validate_items(cfg, items, n_items));
     T3D_REQUIRE(cfg->use_bp && cfg->bp_iters > 0, "autotuning needs a BP decoder");
+    T3D_REQUIRE(!meta_checks(*cfg), "autotuning covers the plain BP kernels only");
     Plan pl;
     T3D_TRY(plan_workspace(*cfg, items, n_items, work, work_bytes, pl));
     cudaStream_t st = as_stream(stream);

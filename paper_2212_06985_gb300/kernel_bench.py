@@ -4,6 +4,7 @@ profiling one kernel at a time; the whole-cycle benchmark is bench.py).
   python -m paper_2212_06985_gb300.kernel_bench cnn   --L 24 --samples 16384
   python -m paper_2212_06985_gb300.kernel_bench sweep --L 32 --samples 8192 --rule F
   python -m paper_2212_06985_gb300.kernel_bench bp    --L 32 --samples 1024
+  python -m paper_2212_06985_gb300.kernel_bench bpmeta --L 24 --samples 1024
 
 Every line printed is one JSON object with the call's mean time over --reps
 timed calls (CUDA events) after --warmup untimed ones.
@@ -16,12 +17,16 @@ import os
 
 import torch
 
-from . import (n_bits, toric3d_bp, toric3d_bp_workspace_bytes, toric3d_cnn_blob_bytes, toric3d_cnn_decode,
+from . import (n_bits, toric3d_bp, toric3d_bp_meta, toric3d_bp_meta_workspace_bytes, toric3d_bp_workspace_bytes, toric3d_cnn_blob_bytes, toric3d_cnn_decode,
                toric3d_cnn_prepare, toric3d_cnn_status, toric3d_cnn_workspace_bytes, toric3d_flip_workspace_bytes,
                toric3d_noise, toric3d_pflip, toric3d_syndrome, words_for)
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "cnn_L12_p04.npz")
 CNN_FLOP_PER_SITE = 2 * 27 * 16 * (6 + 16 + 16) + 2 * 16 * 3
+# BP with meta-checks, FP32 messages, per qubit-sample and iteration: edge totals
+# (read 4 face messages, write 1), faces (read 4 totals + 4 own messages + 2 cube
+# messages, write 5), cubes (12 reads + 6 writes per cube, i.e. per 3 faces)
+BP_META_BYTES = 4 * ((4 + 1) + (10 + 5) + (12 + 6) / 3)
 
 
 def _timed(fn, warmup, reps):
@@ -88,9 +93,25 @@ def bench_bp(a, dev):
     return {"call": "toric3d_bp", "L": a.L, "samples": a.samples, "iters": a.iters, "ms": ms}
 
 
+def bench_bp_meta(a, dev):
+    e, s = _state(a.L, a.samples, a.p, a.seed, dev)
+    work = torch.empty(toric3d_bp_meta_workspace_bytes(a.L, a.samples), dtype=torch.uint8, device=dev)
+    e0, s0 = e.clone(), s.clone()
+
+    def call():
+        e.copy_(e0)
+        s.copy_(s0)
+        toric3d_bp_meta(a.L, a.samples, e, s, a.p, a.p, a.iters, work)
+
+    ms = _timed(call, a.warmup, a.reps)
+    qs = n_bits(a.L) * 64 * words_for(a.samples)
+    return {"call": "toric3d_bp_meta", "L": a.L, "samples": a.samples, "iters": a.iters, "ms": ms,
+            "algorithmic_GBps_iterations": BP_META_BYTES * qs * a.iters / (ms / 1e3) / 1e9}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("what", choices=["cnn", "sweep", "bp"])
+    ap.add_argument("what", choices=["cnn", "sweep", "bp", "bpmeta"])
     ap.add_argument("--L", type=int, default=24)
     ap.add_argument("--samples", type=int, default=16384)
     ap.add_argument("--p", type=float, default=0.04)
@@ -102,7 +123,7 @@ def main(argv=None):
     ap.add_argument("--weights", default=WEIGHTS)
     a = ap.parse_args(argv)
     dev = torch.device("cuda:0")
-    out = {"cnn": bench_cnn, "sweep": bench_sweep, "bp": bench_bp}[a.what](a, dev)
+    out = {"cnn": bench_cnn, "sweep": bench_sweep, "bp": bench_bp, "bpmeta": bench_bp_meta}[a.what](a, dev)
     print(json.dumps(out), flush=True)
     return 0
 

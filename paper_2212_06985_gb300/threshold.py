@@ -7,6 +7,8 @@ logical Z lines of the final error, no noiseless round):
   pbp  : 20 BP iterations then P F F P F F, 500 cycles (Sec. 4.2, Fig. 7)
   table1 --nA n --lp l : n rule applications per cycle, every l-th one p-flip,
          1000 cycles (Sec. 3.2, Table 1)
+  --meta-checks : the BP presets with the cube meta-checks (Sec. 4.1, last
+         paragraph; the paper proposes them without simulating them)
   table1-sweep : every non-empty cell of Table 1 on a 0.1% grid around the
          paper's value, L = 14 and 24; one line per cell with the crossing
 
@@ -40,7 +42,8 @@ PRESETS = {
 
 
 def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | None = None,
-              meas_nodes: bool = True, n_A: int = 5, lambda_p: int = 3, device="cuda:0") -> dict:
+              meas_nodes: bool = True, n_A: int = 5, lambda_p: int = 3, meta_checks: bool = False,
+              device="cuda:0") -> dict:
     """One whole run of `samples` codes; returns failure counts and the run time."""
     pr = dict(PRESETS[preset])
     if T is not None:
@@ -52,7 +55,8 @@ def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | N
     counts = torch.zeros(8, dtype=torch.int64, device=dev)
     batch = make_batch([dict(L=L, n_samples=samples, e=e, counts8=counts)])
     cfg = make_run_cfg(L, pr["T"], p, p, seed, samples, use_bp=pr["use_bp"], bp_iters=pr["bp_iters"],
-                       bp_meas_nodes=meas_nodes, schedule=pr["schedule"], n_apply=pr["n_apply"])
+                       bp_meas_nodes=meas_nodes, bp_meta_checks=meta_checks, schedule=pr["schedule"],
+                       n_apply=pr["n_apply"])
     work = torch.empty(toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -62,6 +66,7 @@ def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | N
     c = counts.cpu().numpy()
     fail0 = int(c[1::2].sum())          # mask values with bit 0 set
     return {"preset": preset, "schedule": pr["schedule"], "L": L, "p": p, "T": pr["T"], "meas_nodes": meas_nodes,
+            "meta_checks": meta_checks,
             "samples": samples,
             "seed": seed,
             "fail_q0": fail0, "fail_any": int(c[1:].sum()), "counts8": c.tolist(), "seconds": dt}
@@ -141,6 +146,8 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=2212)
     ap.add_argument("--nA", type=int, default=5, help="table1: rule applications per cycle")
     ap.add_argument("--lp", type=int, default=3, help="table1: every lp-th application is p-flip")
+    ap.add_argument("--meta-checks", action="store_true",
+                    help="BP with the cube meta-checks over the measurement variables (Sec. 4.1, last paragraph)")
     ap.add_argument("--no-meas-nodes", action="store_true",
                     help="BP without the measurement-error variables (checks taken as exact)")
     a = ap.parse_args(argv)
@@ -153,7 +160,8 @@ def main(argv=None):
     points = []
     for L in a.L:
         for k, p in enumerate(a.p):
-            q = run_point(a.preset, L, p, a.samples, a.seed + 1000 * L + k, a.T, not a.no_meas_nodes, a.nA, a.lp)
+            q = run_point(a.preset, L, p, a.samples, a.seed + 1000 * L + k, a.T, not a.no_meas_nodes, a.nA, a.lp,
+                          a.meta_checks)
             points.append(q)
             print(json.dumps(q), flush=True)
     import warnings

@@ -95,6 +95,22 @@ def test_meta_bp_flags_an_isolated_measurement_error():
     assert (llr[0, :n] > 0).all()
 
 
+def test_bp_priors_from_resumes_exactly():
+    """k iterations, then m more from the returned messages, equal k + m iterations."""
+    L, p, q = 3, 0.05, 0.04
+    n = 3 * L ** 3
+    cptr, cvar = oracle.meta_tanner(L)
+    s = inp.random_bits(1, n, 0.15, 12)[0]
+    syn = np.r_[s, oracle.meta_syndrome(L, s)]
+    prior = np.r_[np.full(n, np.log((1 - p) / p)), np.full(n, np.log((1 - q) / q))]
+    llr7, cv7 = oracle.bp_priors_from(cptr, cvar, syn, prior, 7)
+    assert np.array_equal(llr7, oracle.bp_priors(cptr, cvar, syn, prior, 7))
+    _, cv3 = oracle.bp_priors_from(cptr, cvar, syn, prior, 3)
+    llr34, cv34 = oracle.bp_priors_from(cptr, cvar, syn, prior, 4, cv3)
+    assert np.array_equal(llr34, llr7) and np.array_equal(cv34, cv7)
+    assert np.array_equal(oracle.bp_priors_from(cptr, cvar, syn, prior, 0, cv7)[1], cv7)
+
+
 def test_meta_tanner_shape():
     L = 3
     n = 3 * L ** 3
