@@ -36,7 +36,7 @@ namespace t3d {
 namespace meta {
 namespace {
 
-constexpr int kThreads = 256;   // consecutive samples of one index
+constexpr int kThreads = 256;   // threads per block, each on consecutive samples of one index
 constexpr float kClamp = 30.0f;
 
 struct Bufs {
@@ -84,9 +84,10 @@ __device__ __forceinline__ void check_node(const float (&x)[K], bool syn, float 
     }
 }
 
-__device__ __forceinline__ int syn_bit(const Args& a, int64_t row, int64_t sample)
+// Syndrome bits of samples smp .. smp + 3 (smp a multiple of 4) in bits 0..3.
+__device__ __forceinline__ uint32_t syn_bits4(const Args& a, int64_t row, int64_t smp)
 {
-    return (int)((a.s[row * a.W + (sample >> 6)] >> (sample & 63)) & 1ULL);
+    return (uint32_t)(a.s[row * a.W + (smp >> 6)] >> (smp & 63)) & 0xFu;
 }
 
 __device__ __forceinline__ int64_t step_site(const Lattice& lat, const Coord& c, int ax, int delta)
@@ -111,24 +112,48 @@ __device__ __forceinline__ void edge_slots(const Lattice& lat, int d, int r, int
     }
 }
 
+// The iteration kernels give each thread four consecutive samples of one index
+// (16-byte loads and stores; the index arithmetic is shared by the four):
+// blockIdx.x is the index, blockIdx.y * blockDim.x + threadIdx.x the sample quad.
+__device__ __forceinline__ float4 ld4(const float* base, int64_t row, int64_t S, int64_t smp)
+{
+    return __ldg(reinterpret_cast<const float4*>(base + row * S + smp));
+}
+
+__device__ __forceinline__ void st4(float* base, int64_t row, int64_t S, int64_t smp, float4 v)
+{
+    *reinterpret_cast<float4*>(base + row * S + smp) = v;
+}
+
+__device__ __forceinline__ float comp(const float4& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
+
+__device__ __forceinline__ int64_t quad_sample(const Args& a)
+{
+    return ((int64_t)blockIdx.y * blockDim.x + threadIdx.x) * 4;
+}
+
 __global__ void __launch_bounds__(kThreads) k_edge_totals(const Args a, float* __restrict__ T)
 {
-    const int64_t smp = (int64_t)blockIdx.y * kThreads + threadIdx.x;
+    const int64_t smp = quad_sample(a);
     const int64_t v = blockIdx.x;
     if (smp >= a.S) return;
     const int d = (int)(v / a.lat.L3), r = (int)(v % a.lat.L3);
     int64_t f[4];
     int slot[4];
     edge_slots(a.lat, d, r, f, slot);
-    float t = a.l0;
+    float4 t = make_float4(a.l0, a.l0, a.l0, a.l0);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) t += a.in.F[(f[k] * 4 + slot[k]) * a.S + smp];
-    T[v * a.S + smp] = t;
+    for (int k = 0; k < 4; ++k) t = add4(t, ld4(a.in.F, f[k] * 4 + slot[k], a.S, smp));
+    st4(T, v, a.S, smp, t);
 }
 
 __global__ void __launch_bounds__(kThreads) k_faces(const Args a)
 {
-    const int64_t smp = (int64_t)blockIdx.y * kThreads + threadIdx.x;
+    const int64_t smp = quad_sample(a);
     const int64_t fc = blockIdx.x;
     if (smp >= a.S) return;
     const int n = (int)(fc / a.lat.L3), r = (int)(fc % a.lat.L3);
@@ -137,40 +162,62 @@ __global__ void __launch_bounds__(kThreads) k_faces(const Args a)
     const int64_t L3 = a.lat.L3;
     const int64_t ed[4] = {ax * L3 + r, ax * L3 + step_site(a.lat, c, bx, 1), bx * L3 + r,
                            bx * L3 + step_site(a.lat, c, ax, 1)};
-    float x[5], o[5];
+    float4 x4[5];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) x[j] = a.T[ed[j] * a.S + smp] - a.in.F[(fc * 4 + j) * a.S + smp];
-    x[4] = a.lq + a.in.Cl[fc * a.S + smp] + a.in.Ch[fc * a.S + smp];
-    check_node<5>(x, syn_bit(a, fc, smp), o);
+    for (int j = 0; j < 4; ++j) x4[j] = sub4(ld4(a.T, ed[j], a.S, smp), ld4(a.in.F, fc * 4 + j, a.S, smp));
+    const float4 lq = make_float4(a.lq, a.lq, a.lq, a.lq);
+    x4[4] = add4(add4(lq, ld4(a.in.Cl, fc, a.S, smp)), ld4(a.in.Ch, fc, a.S, smp));
+    const uint32_t syn = syn_bits4(a, fc, smp);
+    float o4[5][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a.out.F[(fc * 4 + j) * a.S + smp] = o[j];
-    a.out.Fm[fc * a.S + smp] = o[4];
+    for (int cpt = 0; cpt < 4; ++cpt) {
+        float x[5], o[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) x[j] = comp(x4[j], cpt);
+        check_node<5>(x, (syn >> cpt) & 1u, o);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) o4[j][cpt] = o[j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) st4(a.out.F, fc * 4 + j, a.S, smp, make_float4(o4[j][0], o4[j][1], o4[j][2], o4[j][3]));
+    st4(a.out.Fm, fc, a.S, smp, make_float4(o4[4][0], o4[4][1], o4[4][2], o4[4][3]));
 }
 
 __global__ void __launch_bounds__(kThreads) k_cubes(const Args a)
 {
-    const int64_t smp = (int64_t)blockIdx.y * kThreads + threadIdx.x;
+    const int64_t smp = quad_sample(a);
     const int r = blockIdx.x;
     if (smp >= a.S) return;
     const Coord c = site_coord(a.lat, r);
     const int64_t L3 = a.lat.L3;
     int64_t fl[3], fu[3];   // lower faces (n, r), upper faces (n, r + e_n)
-    int par = 0;
-    float x[6], o[6];
+    uint32_t par = 0;
+    float4 x4[6];
+    const float4 lq = make_float4(a.lq, a.lq, a.lq, a.lq);
 #pragma unroll
     for (int nn = 0; nn < 3; ++nn) {
         fl[nn] = nn * L3 + r;
         fu[nn] = nn * L3 + step_site(a.lat, c, nn, 1);
-        par ^= syn_bit(a, fl[nn], smp) ^ syn_bit(a, fu[nn], smp);
+        par ^= syn_bits4(a, fl[nn], smp) ^ syn_bits4(a, fu[nn], smp);
         // this cube is the lower-face cube of fl (its message is Cl) and the upper-face cube of fu (Ch)
-        x[2 * nn] = a.lq + a.in.Fm[fl[nn] * a.S + smp] + a.in.Ch[fl[nn] * a.S + smp];
-        x[2 * nn + 1] = a.lq + a.in.Fm[fu[nn] * a.S + smp] + a.in.Cl[fu[nn] * a.S + smp];
+        x4[2 * nn] = add4(add4(lq, ld4(a.in.Fm, fl[nn], a.S, smp)), ld4(a.in.Ch, fl[nn], a.S, smp));
+        x4[2 * nn + 1] = add4(add4(lq, ld4(a.in.Fm, fu[nn], a.S, smp)), ld4(a.in.Cl, fu[nn], a.S, smp));
     }
-    check_node<6>(x, par != 0, o);
+    float o4[6][4];
+#pragma unroll
+    for (int cpt = 0; cpt < 4; ++cpt) {
+        float x[6], o[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) x[j] = comp(x4[j], cpt);
+        check_node<6>(x, (par >> cpt) & 1u, o);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) o4[j][cpt] = o[j];
+    }
 #pragma unroll
     for (int nn = 0; nn < 3; ++nn) {
-        a.out.Cl[fl[nn] * a.S + smp] = o[2 * nn];
-        a.out.Ch[fu[nn] * a.S + smp] = o[2 * nn + 1];
+        st4(a.out.Cl, fl[nn], a.S, smp, make_float4(o4[2 * nn][0], o4[2 * nn][1], o4[2 * nn][2], o4[2 * nn][3]));
+        st4(a.out.Ch, fu[nn], a.S, smp,
+            make_float4(o4[2 * nn + 1][0], o4[2 * nn + 1][1], o4[2 * nn + 1][2], o4[2 * nn + 1][3]));
     }
 }
 
@@ -201,19 +248,24 @@ Bufs split_messages(float* m, int64_t n, int64_t S)
     return Bufs{m, m + 4 * n * S, m + 5 * n * S, m + 6 * n * S};
 }
 
+// Quad-kernel block: S / 4 sample quads, at most kThreads a block, whole warps.
+unsigned quad_threads(int64_t S) { return (unsigned)std::min<int64_t>(kThreads, (S / 4 + 31) / 32 * 32); }
+
+unsigned quad_blocks(int64_t S) { return (unsigned)((S / 4 + quad_threads(S) - 1) / quad_threads(S)); }
+
 // One flooding iteration: every check -> variable message of `out` from those of `in`.
 t3d_status launch_iteration(Args& a, float* T, const Bufs& in, const Bufs& out, cudaStream_t st)
 {
     const int64_t n = 3LL * a.lat.L3;
-    const unsigned gy = (unsigned)((a.S + kThreads - 1) / kThreads);
+    const unsigned tx = quad_threads(a.S), gy = quad_blocks(a.S);
     a.in = in;
     a.out = out;
     ProfScope prof(T3D_K_BP_STEP, st);
-    k_edge_totals<<<dim3((unsigned)n, gy), kThreads, 0, st>>>(a, T);
+    k_edge_totals<<<dim3((unsigned)n, gy), tx, 0, st>>>(a, T);
     T3D_LAUNCH_CHECK("meta-check BP edge totals");
-    k_faces<<<dim3((unsigned)n, gy), kThreads, 0, st>>>(a);
+    k_faces<<<dim3((unsigned)n, gy), tx, 0, st>>>(a);
     T3D_LAUNCH_CHECK("meta-check BP faces");
-    k_cubes<<<dim3((unsigned)a.lat.L3, gy), kThreads, 0, st>>>(a);
+    k_cubes<<<dim3((unsigned)a.lat.L3, gy), tx, 0, st>>>(a);
     T3D_LAUNCH_CHECK("meta-check BP cubes");
     return T3D_OK;
 }
@@ -273,13 +325,12 @@ t3d_status launch_bp_meta(const Lattice& lat, int64_t n_samples, int64_t W, uint
         // every message starts at zero: the first iteration sees the priors alone
         T3D_CUDA_CHECK(cudaMemsetAsync(b[0].F, 0, 7 * n * S * sizeof(float), st));
         Args a = make_args(lat, S, W, s + w0, p, q, T);
-        const unsigned gy = (unsigned)((S + kThreads - 1) / kThreads);
         for (int it = 0; it < iters; ++it) T3D_TRY(launch_iteration(a, T, b[it & 1], b[(it + 1) & 1], st));
         a.in = b[iters & 1];
         ProfScope prof(T3D_K_BP_DECIDE, st);
-        k_edge_totals<<<dim3((unsigned)n, gy), kThreads, 0, st>>>(a, T);
+        k_edge_totals<<<dim3((unsigned)n, quad_blocks(S)), quad_threads(S), 0, st>>>(a, T);
         T3D_LAUNCH_CHECK("meta-check BP posteriors");
-        k_decide<<<dim3((unsigned)n, gy), kThreads, 0, st>>>(a, ns, reinterpret_cast<uint32_t*>(dec), llr_out,
+        k_decide<<<dim3((unsigned)n, (unsigned)((S + kThreads - 1) / kThreads)), kThreads, 0, st>>>(a, ns, reinterpret_cast<uint32_t*>(dec), llr_out,
                                                              n_samples);
         T3D_LAUNCH_CHECK("meta-check BP decisions");
         T3D_TRY(launch_dec_apply(lat, W, cw, dec, e + w0, s + w0, st));
