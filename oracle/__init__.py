@@ -118,6 +118,12 @@ def _declare(L):
         "t3o_bp_batch": (None, [i32, i64, _P, dbl, dbl, i32, i32, _P, _P, _P]),
         "t3o_bp_decode_batch": (None, [i32, i64, _P, _P, dbl, dbl, i32, i32, _P]),
         "t3o_abi_version": (i32, []),
+        "t3o_tanner_syndrome_batch": (None, [i64, i64, _P, _P, i64, _P, _P]),
+        "t3o_tanner_noise_batch": (None, [i64, i64, _P, dbl, u64, u64, u32]),
+        "t3o_tanner_measure_batch": (None, [i64, i64, _P, _P, i64, _P, _P, dbl, u64, u64, u32]),
+        "t3o_tanner_coin": (i32, [u64, i64, u32, u32, u64]),
+        "t3o_tanner_rule_batch": (None, [i64, i64, _P, _P, i64, _P, _P, i32, u64, u64, u32, u32]),
+        "t3o_tanner_bp_batch": (None, [i64, i64, _P, _P, i64, _P, _P, _P, i32, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -405,4 +411,59 @@ def bp_decode_batch(L, e, s, p, q, meas_nodes, iters):
     llr = np.zeros(e.shape, dtype=np.float64)
     lib().t3o_bp_decode_batch(L, e.shape[0], _ptr(e), _ptr(s), float(p), float(q),
                               int(meas_nodes), iters, _ptr(llr))
+    return e, s, llr
+
+
+# ---------------------------------------------------------------- generic Tanner graphs
+def _csr(cptr, cvar):
+    return np.ascontiguousarray(cptr, dtype=np.int32), np.ascontiguousarray(cvar, dtype=np.int32)
+
+
+def tanner_syndrome_batch(cptr, cvar, e):
+    """s = H e per sample; e [S][n] -> s [S][m] (checks in CSR form)."""
+    cptr, cvar = _csr(cptr, cvar)
+    e = _u8(e)
+    s = np.zeros((e.shape[0], len(cptr) - 1), dtype=np.uint8)
+    lib().t3o_tanner_syndrome_batch(e.shape[1], len(cptr) - 1, _ptr(cptr), _ptr(cvar), e.shape[0], _ptr(e), _ptr(s))
+    return s
+
+
+def tanner_noise_batch(e, p, seed, sample0, cycle):
+    e = _u8(e).copy()
+    lib().t3o_tanner_noise_batch(e.shape[1], e.shape[0], _ptr(e), float(p), seed, sample0, cycle)
+    return e
+
+
+def tanner_measure_batch(cptr, cvar, e, q, seed, sample0, cycle):
+    cptr, cvar = _csr(cptr, cvar)
+    e = _u8(e)
+    s = np.zeros((e.shape[0], len(cptr) - 1), dtype=np.uint8)
+    lib().t3o_tanner_measure_batch(e.shape[1], len(cptr) - 1, _ptr(cptr), _ptr(cvar), e.shape[0], _ptr(e), _ptr(s),
+                                   float(q), seed, sample0, cycle)
+    return s
+
+
+def tanner_coin(seed, v, cycle, sweep, sample):
+    return int(lib().t3o_tanner_coin(seed, v, cycle, sweep, sample))
+
+
+def tanner_rule_batch(cptr, cvar, e, s, probabilistic=False, seed=0, sample0=0, cycle=0, sweep=0):
+    """One parallel flip (or p-flip) application per sample; returns (e, s)."""
+    cptr, cvar = _csr(cptr, cvar)
+    e = _u8(e).copy()
+    s = _u8(s).copy()
+    lib().t3o_tanner_rule_batch(e.shape[1], len(cptr) - 1, _ptr(cptr), _ptr(cvar), e.shape[0], _ptr(e), _ptr(s),
+                                int(probabilistic), seed, sample0, cycle, sweep)
+    return e, s
+
+
+def tanner_bp_batch(cptr, cvar, e, s, prior, iters):
+    """BP with per-variable priors and the hard decision; returns (e, s, llr [S][n])."""
+    cptr, cvar = _csr(cptr, cvar)
+    e = _u8(e).copy()
+    s = _u8(s).copy()
+    prior = np.ascontiguousarray(prior, dtype=np.float64)
+    llr = np.zeros(e.shape, dtype=np.float64)
+    lib().t3o_tanner_bp_batch(e.shape[1], len(cptr) - 1, _ptr(cptr), _ptr(cvar), e.shape[0], _ptr(e), _ptr(s),
+                              _ptr(prior), iters, _ptr(llr))
     return e, s, llr

@@ -38,7 +38,10 @@
  * p-flip against the worked examples of Sec. 3 (Fig. 3(a), 3(b), Fig. 5,
  * the opposite-face pair); BP against exact marginals on acyclic Tanner
  * graphs and the closed form of its first iteration; the logical readout
- * against membranes and stabilisers.  See tests/test_oracle_*.py.
+ * against membranes and stabilisers; the generic Tanner-graph decoders
+ * against the toric ones on the toric code's own graph, the stated coin
+ * key, and single errors of the 2D toric code (hypergraph product of two
+ * cycles).  See tests/test_oracle_*.py.
  */
 #include <math.h>
 #include <stdint.h>
@@ -765,3 +768,118 @@ void t3o_bp_decode_batch(int L, int64_t n_samples, uint8_t* e, uint8_t* s, doubl
 }
 
 int t3o_abi_version(void) { return 1; }
+
+/* ------------------------------------------------------------------ */
+/* Generic Tanner graphs (Sec. 5 asks whether these decoders carry over */
+/* to other LDPC codes).  A code is given by its checks in CSR form:    */
+/* check c acts on variables cvar[cptr[c]] .. cvar[cptr[c+1]-1].  The   */
+/* rules are the toric code's, stated per variable: flip a variable     */
+/* when more of its checks are unsatisfied than satisfied (Sec. 3.1);   */
+/* p-flip also flips, with probability 1/2, a variable with exactly as  */
+/* many unsatisfied as satisfied checks (Sec. 3.2).  Noise keys the     */
+/* generator with the variable index as site (stream 0), measurement    */
+/* errors with the check index (stream 1), as on the toric code.  The   */
+/* p-flip coin of variable v is bit `lane` of output v mod 4 of block 0 */
+/* of stream 2 keyed by site v / 4 (one block serves four variables).   */
+/* ------------------------------------------------------------------ */
+void t3o_tanner_syndrome(int64_t m, const int32_t* cptr, const int32_t* cvar, const uint8_t* e, uint8_t* s)
+{
+    for (int64_t c = 0; c < m; ++c) {
+        uint8_t par = 0;
+        for (int32_t t = cptr[c]; t < cptr[c + 1]; ++t) par ^= e[cvar[t]];
+        s[c] = par;
+    }
+}
+
+void t3o_tanner_noise(int64_t n, uint8_t* e, double p, uint64_t seed, uint64_t sample, uint32_t cycle)
+{
+    for (int64_t v = 0; v < n; ++v)
+        if (t3o_bernoulli(p, seed, STREAM_QUBIT, (uint64_t)v, cycle, 0, sample)) e[v] ^= 1;
+}
+
+void t3o_tanner_measure(int64_t m, const int32_t* cptr, const int32_t* cvar, const uint8_t* e, uint8_t* s,
+                        double q, uint64_t seed, uint64_t sample, uint32_t cycle)
+{
+    t3o_tanner_syndrome(m, cptr, cvar, e, s);
+    for (int64_t c = 0; c < m; ++c)
+        if (t3o_bernoulli(q, seed, STREAM_MEAS, (uint64_t)c, cycle, 0, sample)) s[c] ^= 1;
+}
+
+int t3o_tanner_coin(uint64_t seed, int64_t v, uint32_t cycle, uint32_t sweep, uint64_t sample)
+{
+    return t3o_coin(seed, (uint64_t)(v / 4), (int)(v % 4), cycle, sweep, sample);
+}
+
+/* One parallel application: every variable decides from the same syndrome, then e ^= f, s ^= H f. */
+void t3o_tanner_rule(int64_t n, int64_t m, const int32_t* cptr, const int32_t* cvar, uint8_t* e, uint8_t* s,
+                     int probabilistic, uint64_t seed, uint64_t sample, uint32_t cycle, uint32_t sweep)
+{
+    int32_t* deg = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    int32_t* unsat = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    uint8_t* flip = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+    for (int64_t c = 0; c < m; ++c)
+        for (int32_t t = cptr[c]; t < cptr[c + 1]; ++t) {
+            deg[cvar[t]]++;
+            unsat[cvar[t]] += s[c];
+        }
+    for (int64_t v = 0; v < n; ++v) {
+        int sat = deg[v] - unsat[v];
+        if (unsat[v] > sat)
+            flip[v] = 1;
+        else if (probabilistic && unsat[v] == sat && deg[v] > 0)
+            flip[v] = (uint8_t)t3o_tanner_coin(seed, v, cycle, sweep, sample);
+    }
+    for (int64_t v = 0; v < n; ++v) e[v] ^= flip[v];
+    for (int64_t c = 0; c < m; ++c)
+        for (int32_t t = cptr[c]; t < cptr[c + 1]; ++t) s[c] ^= flip[cvar[t]];
+    free(deg); free(unsat); free(flip);
+}
+
+void t3o_tanner_syndrome_batch(int64_t n, int64_t m, const int32_t* cptr, const int32_t* cvar, int64_t n_samples,
+                               const uint8_t* e, uint8_t* s)
+{
+    for (int64_t i = 0; i < n_samples; ++i) t3o_tanner_syndrome(m, cptr, cvar, e + i * n, s + i * m);
+}
+
+void t3o_tanner_noise_batch(int64_t n, int64_t n_samples, uint8_t* e, double p, uint64_t seed, uint64_t sample0,
+                            uint32_t cycle)
+{
+    for (int64_t i = 0; i < n_samples; ++i) t3o_tanner_noise(n, e + i * n, p, seed, sample0 + (uint64_t)i, cycle);
+}
+
+void t3o_tanner_measure_batch(int64_t n, int64_t m, const int32_t* cptr, const int32_t* cvar, int64_t n_samples,
+                              const uint8_t* e, uint8_t* s, double q, uint64_t seed, uint64_t sample0,
+                              uint32_t cycle)
+{
+    for (int64_t i = 0; i < n_samples; ++i)
+        t3o_tanner_measure(m, cptr, cvar, e + i * n, s + i * m, q, seed, sample0 + (uint64_t)i, cycle);
+}
+
+void t3o_tanner_rule_batch(int64_t n, int64_t m, const int32_t* cptr, const int32_t* cvar, int64_t n_samples,
+                           uint8_t* e, uint8_t* s, int probabilistic, uint64_t seed, uint64_t sample0,
+                           uint32_t cycle, uint32_t sweep)
+{
+    for (int64_t i = 0; i < n_samples; ++i)
+        t3o_tanner_rule(n, m, cptr, cvar, e + i * n, s + i * m, probabilistic, seed, sample0 + (uint64_t)i,
+                        cycle, sweep);
+}
+
+/* BP with one prior per variable on a batch: syndromes s (n_samples x m), posteriors
+ * llr (n_samples x n), hard decision applied: e ^= d, s ^= H d. */
+void t3o_tanner_bp_batch(int64_t n, int64_t m, const int32_t* cptr, const int32_t* cvar, int64_t n_samples,
+                         uint8_t* e, uint8_t* s, const double* prior, int iters, double* llr)
+{
+    double* l = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    uint8_t* d = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n_samples; ++i) {
+        t3o_bp_priors((int)n, (int)m, cptr, cvar, s + i * m, prior, iters, l);
+        for (int64_t v = 0; v < n; ++v) {
+            d[v] = l[v] < 0.0;
+            e[i * n + v] ^= d[v];
+        }
+        for (int64_t c = 0; c < m; ++c)
+            for (int32_t t = cptr[c]; t < cptr[c + 1]; ++t) s[i * m + c] ^= d[cvar[t]];
+        if (llr) memcpy(llr + i * n, l, (size_t)n * sizeof(double));
+    }
+    free(l); free(d);
+}

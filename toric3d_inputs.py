@@ -112,3 +112,81 @@ WORKLOADS = {
     "bp_pflip_L48": Workload("bp_pflip_L48", 48, 0.04, 0.04, 48, 100_000, 13, "bp_pflip",
                              "PFFPFF", 32, bp_iters=16),
 }
+
+
+# ---------------------------------------------------------------- other LDPC codes
+# Code structure only (parity-check matrices as CSR lists), for the generic
+# Tanner-graph decoders: seeded random biregular classical codes and their
+# hypergraph product (Tillich-Zemor), whose Z checks are a quantum LDPC code
+# with the same kind of local, low-degree Tanner graph as the toric code.
+
+def random_biregular(n: int, m: int, dv: int, dc: int, seed: int) -> np.ndarray:
+    """A classical parity-check matrix as the [m][dc] bit indices of its rows: column
+    weight dv, row weight dc (n dv = m dc), from the configuration model; a row that
+    repeats a bit swaps that entry with a random entry of another row until every row
+    is simple."""
+    assert n * dv == m * dc, "n dv must equal m dc"
+    rng = np.random.default_rng(seed)
+    rows = np.repeat(np.arange(n), dv)
+    rng.shuffle(rows)
+    rows = rows.reshape(m, dc)
+    for _ in range(100 * m * dc):
+        bad = [r for r in range(m) if len(set(rows[r].tolist())) < dc]
+        if not bad:
+            return rows
+        r = bad[0]
+        vals, counts = np.unique(rows[r], return_counts=True)
+        k = int(np.nonzero(rows[r] == vals[counts > 1][0])[0][0])
+        r2, k2 = int(rng.integers(m)), int(rng.integers(dc))
+        rows[r, k], rows[r2, k2] = rows[r2, k2], rows[r, k]
+    raise RuntimeError("no simple biregular graph found")
+
+
+def cyclic_repetition(L: int) -> np.ndarray:
+    """Rows {i, i+1 mod L} of the length-L cyclic repetition code, [L][2]."""
+    return np.stack([np.arange(L), (np.arange(L) + 1) % L], axis=1)
+
+
+def hypergraph_product(rows1: np.ndarray, n1: int, rows2: np.ndarray, n2: int):
+    """Check lists (one list of qubit indices per check) of the hypergraph product of
+    the classical codes with rows rows1 (m1 checks on n1 bits) and rows2 (m2 on n2):
+    qubits (a, b) -> a n2 + b for the n1 n2 bit pairs, then n1 n2 + i m2 + j for the
+    m1 m2 check pairs;  X check (i, b) = {(a, b) : a in row i of code 1} +
+    {(i, j) : b in row j of code 2};  Z check (a, j) = {(a, b) : b in row j of code 2}
+    + {(i, j) : a in row i of code 1}, i.e. HX = [H1 x I | I x H2^T],
+    HZ = [I x H2 | H1^T x I]."""
+    m1, m2 = len(rows1), len(rows2)
+    rows_of_bit1 = [[] for _ in range(n1)]
+    for i, r in enumerate(rows1):
+        for a in r:
+            rows_of_bit1[int(a)].append(i)
+    rows_of_bit2 = [[] for _ in range(n2)]
+    for j, r in enumerate(rows2):
+        for b in r:
+            rows_of_bit2[int(b)].append(j)
+    base = n1 * n2
+    X = [[int(a) * n2 + b for a in rows1[i]] + [base + i * m2 + j for j in rows_of_bit2[b]]
+         for i in range(m1) for b in range(n2)]
+    Z = [[a * n2 + int(b) for b in rows2[j]] + [base + i * m2 + j for i in rows_of_bit1[a]]
+         for a in range(n1) for j in range(m2)]
+    return X, Z, n1 * n2 + m1 * m2
+
+
+def csr(check_lists):
+    """Check lists as CSR (cptr int32 [m+1], cvar int32 [nnz], each row sorted)."""
+    cptr = np.zeros(len(check_lists) + 1, dtype=np.int64)
+    cptr[1:] = np.cumsum([len(c) for c in check_lists])
+    cvar = np.concatenate([np.sort(np.asarray(c, dtype=np.int64)) for c in check_lists])
+    return cptr.astype(np.int32), cvar.astype(np.int32)
+
+
+def hgp_workload(n_classical: int, seed: int):
+    """Z checks of the hypergraph product of two seeded (3, 4)-biregular classical codes
+    with n_classical bits and 3 n_classical / 4 checks each: n^2 + (3n/4)^2 qubits,
+    3n^2/4 checks of weight 7, qubit degree 3 or 4.  Returns (cptr, cvar, n_qubits)."""
+    m = 3 * n_classical // 4
+    r1 = random_biregular(n_classical, m, 3, 4, seed)
+    r2 = random_biregular(n_classical, m, 3, 4, seed + 1)
+    _, Z, n = hypergraph_product(r1, n_classical, r2, n_classical)
+    cptr, cvar = csr(Z)
+    return cptr, cvar, n
