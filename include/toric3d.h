@@ -229,6 +229,92 @@ t3d_status toric3d_bp_meta_step(int L, int64_t n_samples, const uint64_t* s, dou
                                 t3d_stream stream);
 
 /*
+ * Decoders on a generic Tanner graph.  Sec. 5 asks whether these local
+ * decoders carry over to other LDPC codes; these calls run the same rules on
+ * any code given by its checks: noise, noisy measurement, flip / p-flip and
+ * BP.  A graph is prepared once into a device blob:
+ *   cptr int32[n_checks + 1], cvar int32[cptr[n_checks]]  (HOST arrays, CSR:
+ *        check c acts on variables cvar[cptr[c]] .. cvar[cptr[c+1]-1]; no
+ *        variable twice in a check; every degree <= 32)
+ *   blob >= toric3d_tanner_bytes(n_vars, n_checks, cptr[n_checks]) bytes of
+ *        256-byte aligned device memory, owned by the caller, which must
+ *        outlive every call that uses the graph
+ * toric3d_tanner_prepare validates the lists, builds the variable-side lists
+ * on the host and copies everything into the blob synchronously; `out` then
+ * describes the graph (device pointers into the blob) and is passed by
+ * address to the calls below.  Errors: T3D_EINVAL (message in
+ * toric3d_last_error) on bad lists or sizes; nothing is written then.
+ */
+typedef struct {
+    int64_t n_vars;
+    int64_t n_checks;
+    int64_t n_edges;
+    int32_t max_var_degree;
+    int32_t max_check_degree;
+    const int32_t* cptr;    /* device: check -> first Tanner edge (CSR) */
+    const int32_t* cvar;    /* device: Tanner edge -> variable */
+    const int32_t* vptr;    /* device: variable -> first entry of vedge / vcheck */
+    const int32_t* vedge;   /* device: the Tanner edges of each variable, checks ascending */
+    const int32_t* vcheck;  /* device: the check of each of those edges */
+} t3d_tanner;
+
+size_t toric3d_tanner_bytes(int64_t n_vars, int64_t n_checks, int64_t n_edges);
+t3d_status toric3d_tanner_prepare(int64_t n_vars, int64_t n_checks, const int32_t* cptr, const int32_t* cvar,
+                                  void* blob, size_t blob_bytes, t3d_tanner* out);
+
+/*
+ * Bit-sliced state as on the toric code: e uint64_t[n_vars][W], s
+ * uint64_t[n_checks][W], W = ceil(n_samples / 64), sample 64 w + j in bit j
+ * of word w; sample0 (a multiple of 64) is the index of the first sample.
+ * Noise (Sec. 3.1): e ^= Bernoulli(p) keyed by the variable index (stream 0).
+ * Syndrome: s = H e ^ Bernoulli(q) keyed by the check index (stream 1).
+ * Generator and keys as in toric3d_noise / toric3d_syndrome, so on the toric
+ * code's own graph these equal those calls.
+ */
+t3d_status toric3d_tanner_noise(const t3d_tanner* g, int64_t n_samples, uint64_t* e, double p, uint64_t seed,
+                                uint64_t sample0, uint32_t cycle, t3d_stream stream);
+t3d_status toric3d_tanner_syndrome(const t3d_tanner* g, int64_t n_samples, const uint64_t* e, uint64_t* s,
+                                   double q, uint64_t seed, uint64_t sample0, uint32_t cycle, t3d_stream stream);
+
+/*
+ * n_apply parallel applications cycling through `schedule` ('F' flip, 'P'
+ * p-flip): every variable counts its unsatisfied checks u in the current
+ * syndrome; it flips when u > deg - u (Sec. 3.1) and, in p-flip, when
+ * u == deg - u and its coin is 1 (Sec. 3.2); then e ^= f and s ^= H f.
+ * Application k keys the coins with sweep sweep0 + k; the coin of variable v
+ * is bit (sample mod 64) of output v mod 4 of Philox block 0 of stream 2
+ * keyed by site v / 4.  work: toric3d_tanner_flip_workspace_bytes of 8-byte
+ * aligned device scratch (the flip words).
+ */
+size_t toric3d_tanner_flip_workspace_bytes(const t3d_tanner* g, int64_t n_samples);
+t3d_status toric3d_tanner_pflip(const t3d_tanner* g, int64_t n_samples, uint64_t* e, uint64_t* s,
+                                const char* schedule, int n_apply, uint32_t sweep0, uint64_t seed, uint64_t sample0,
+                                uint32_t cycle, void* work, size_t work_bytes, t3d_stream stream);
+
+/*
+ * Product-sum BP (Sec. 4.1, Eqs. 1-4) with one prior LLR per variable
+ * (prior: device float[n_vars]; measurement errors are modelled by adding
+ * variables to the graph): `iters` flooding iterations from the priors, FP32
+ * messages clamped to |M| <= 30, then every variable with posterior < 0 is
+ * corrected, e ^= d and s ^= H d.  work >= toric3d_tanner_bp_workspace_bytes
+ * (g, 64) bytes of 256-byte aligned device scratch; samples run in chunks of
+ * whole words as large as it allows.  llr_out (nullable): float[n_vars]
+ * [n_samples] posteriors; it needs a workspace for all samples at once.
+ * toric3d_tanner_bp_step runs one iteration for message-by-message checks:
+ * messages float[n_edges][S'] (S' = 64 W, samples innermost, Tanner edges in
+ * the CSR order of cptr / cvar), msg_in all zero for the first iteration,
+ * msg_in and msg_out of toric3d_tanner_bp_message_bytes each and not
+ * overlapping, work >= n_vars * S' floats (16-byte aligned).
+ */
+size_t toric3d_tanner_bp_workspace_bytes(const t3d_tanner* g, int64_t chunk_samples);
+t3d_status toric3d_tanner_bp(const t3d_tanner* g, int64_t n_samples, uint64_t* e, uint64_t* s, const float* prior,
+                             int iters, void* work, size_t work_bytes, float* llr_out, t3d_stream stream);
+size_t toric3d_tanner_bp_message_bytes(const t3d_tanner* g, int64_t n_samples);
+t3d_status toric3d_tanner_bp_step(const t3d_tanner* g, int64_t n_samples, const uint64_t* s, const float* prior,
+                                  const float* msg_in, float* msg_out, void* work, size_t work_bytes,
+                                  t3d_stream stream);
+
+/*
  * Fallback gate of the learned pre-decoder (no counterpart in the paper,
  * whose decoders have no fallback): gate[w] = 1 iff some sample of word w has
  * more than max_weight unsatisfied checks in s (s: uint64_t[3L^3][words],

@@ -21,6 +21,7 @@ import torch
 from . import build as _build
 
 __all__ = [
+    "TannerGraph", "tanner_prepare",
     "T3DError", "RunCfg", "lib", "n_bits", "words_for", "table1_schedule",
     "toric3d_noise", "toric3d_syndrome", "toric3d_flip", "toric3d_pflip",
     "toric3d_bp_step", "toric3d_bp_decide", "toric3d_bp_decide_workspace_bytes", "toric3d_bp", "toric3d_logical",
@@ -32,6 +33,9 @@ __all__ = [
     "toric3d_run_batch_workspace_bytes", "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm",
     "toric3d_autotune_batch", "toric3d_flip_noalloc", "toric3d_gate_workspace_bytes", "toric3d_gate",
     "toric3d_bp_meta_workspace_bytes", "toric3d_bp_meta", "toric3d_bp_meta_message_bytes", "toric3d_bp_meta_step",
+    "toric3d_tanner_bytes", "toric3d_tanner_prepare", "toric3d_tanner_noise", "toric3d_tanner_syndrome",
+    "toric3d_tanner_flip_workspace_bytes", "toric3d_tanner_pflip", "toric3d_tanner_bp_workspace_bytes",
+    "toric3d_tanner_bp", "toric3d_tanner_bp_message_bytes", "toric3d_tanner_bp_step",
 ]
 
 EXPORTED_SYMBOLS = [
@@ -47,6 +51,9 @@ EXPORTED_SYMBOLS = [
     "toric3d_cnn_decode", "toric3d_cnn_train_workspace_bytes", "toric3d_cnn_train_step",
     "toric3d_gate_workspace_bytes", "toric3d_gate", "toric3d_cnn_status",
     "toric3d_bp_meta_workspace_bytes", "toric3d_bp_meta", "toric3d_bp_meta_message_bytes", "toric3d_bp_meta_step",
+    "toric3d_tanner_bytes", "toric3d_tanner_prepare", "toric3d_tanner_noise", "toric3d_tanner_syndrome",
+    "toric3d_tanner_flip_workspace_bytes", "toric3d_tanner_pflip", "toric3d_tanner_bp_workspace_bytes",
+    "toric3d_tanner_bp", "toric3d_tanner_bp_message_bytes", "toric3d_tanner_bp_step",
 ]
 
 KERNEL_KINDS = {"noise": 0, "syndrome": 1, "flip": 2, "pflip": 3, "bp_step": 4, "bp_decide": 5,
@@ -59,6 +66,23 @@ class T3DError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"toric3d error {status}: {message}")
         self.status = status
+
+
+class Tanner(ctypes.Structure):
+    """Mirror of ``t3d_tanner`` in include/toric3d.h."""
+
+    _fields_ = [
+        ("n_vars", ctypes.c_int64),
+        ("n_checks", ctypes.c_int64),
+        ("n_edges", ctypes.c_int64),
+        ("max_var_degree", ctypes.c_int32),
+        ("max_check_degree", ctypes.c_int32),
+        ("cptr", ctypes.c_void_p),
+        ("cvar", ctypes.c_void_p),
+        ("vptr", ctypes.c_void_p),
+        ("vedge", ctypes.c_void_p),
+        ("vcheck", ctypes.c_void_p),
+    ]
 
 
 class RunCfg(ctypes.Structure):
@@ -140,6 +164,17 @@ def _declare(h):
         "toric3d_bp_meta_workspace_bytes": (sz, [i32, i64]),
         "toric3d_bp_meta": (i32, [i32, i64, _P, _P, dbl, dbl, i32, _P, sz, _P, _P]),
         "toric3d_bp_meta_message_bytes": (sz, [i32, i64]),
+        "toric3d_tanner_bytes": (sz, [i64, i64, i64]),
+        "toric3d_tanner_prepare": (i32, [i64, i64, _P, _P, _P, sz, ctypes.POINTER(Tanner)]),
+        "toric3d_tanner_noise": (i32, [ctypes.POINTER(Tanner), i64, _P, dbl, u64, u64, u32, _P]),
+        "toric3d_tanner_syndrome": (i32, [ctypes.POINTER(Tanner), i64, _P, _P, dbl, u64, u64, u32, _P]),
+        "toric3d_tanner_flip_workspace_bytes": (sz, [ctypes.POINTER(Tanner), i64]),
+        "toric3d_tanner_pflip": (i32, [ctypes.POINTER(Tanner), i64, _P, _P, ctypes.c_char_p, i32, u32, u64, u64, u32,
+                                       _P, sz, _P]),
+        "toric3d_tanner_bp_workspace_bytes": (sz, [ctypes.POINTER(Tanner), i64]),
+        "toric3d_tanner_bp": (i32, [ctypes.POINTER(Tanner), i64, _P, _P, _P, i32, _P, sz, _P, _P]),
+        "toric3d_tanner_bp_message_bytes": (sz, [ctypes.POINTER(Tanner), i64]),
+        "toric3d_tanner_bp_step": (i32, [ctypes.POINTER(Tanner), i64, _P, _P, _P, _P, _P, sz, _P]),
         "toric3d_bp_meta_step": (i32, [i32, i64, _P, dbl, dbl, _P, _P, _P, sz, _P]),
         "toric3d_logical": (i32, [i32, i64, _P, _P, _P, _P]),
         "toric3d_gate_workspace_bytes": (ctypes.c_size_t, [i32, i64]),
@@ -465,3 +500,83 @@ def toric3d_cnn_train_step(L, n_samples, s_prev, s, e_label, params, adam_m, ada
                                         _ptr(adam_m), _ptr(adam_v), int(step), float(lr), _ptr(blob),
                                         _ptr(grads_out), _ptr(loss_out), _ptr(work),
                                         work.numel() * work.element_size(), _stream(stream)))
+
+
+# ------------------------------------------------------------------ generic Tanner graphs
+class TannerGraph:
+    """A code prepared for the toric3d_tanner_* calls: the C descriptor plus the
+    device blob it points into (kept alive with this object)."""
+
+    def __init__(self, desc: Tanner, blob):
+        self.desc = desc
+        self.blob = blob
+
+    @property
+    def n_vars(self):
+        return int(self.desc.n_vars)
+
+    @property
+    def n_checks(self):
+        return int(self.desc.n_checks)
+
+    @property
+    def n_edges(self):
+        return int(self.desc.n_edges)
+
+    def ref(self):
+        return ctypes.byref(self.desc)
+
+
+def tanner_prepare(cptr, cvar, n_vars: int, device="cuda:0") -> TannerGraph:
+    """Checks in CSR form (host int32 arrays) -> a prepared graph on `device`."""
+    import numpy as np
+    cptr = np.ascontiguousarray(cptr, dtype=np.int32)
+    cvar = np.ascontiguousarray(cvar, dtype=np.int32)
+    m = len(cptr) - 1
+    nbytes = int(lib().toric3d_tanner_bytes(n_vars, m, int(cptr[-1])))
+    if nbytes == 0:
+        raise T3DError(1, "invalid graph sizes")
+    blob = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    desc = Tanner()
+    _check(lib().toric3d_tanner_prepare(n_vars, m, cptr.ctypes.data_as(ctypes.c_void_p),
+                                        cvar.ctypes.data_as(ctypes.c_void_p), _ptr(blob), nbytes,
+                                        ctypes.byref(desc)))
+    return TannerGraph(desc, blob)
+
+
+def toric3d_tanner_noise(g: TannerGraph, n_samples, e, p, seed, sample0, cycle, stream=None):
+    _check(lib().toric3d_tanner_noise(g.ref(), n_samples, _ptr(e), float(p), seed, sample0, cycle, _stream(stream)))
+
+
+def toric3d_tanner_syndrome(g: TannerGraph, n_samples, e, s, q, seed, sample0, cycle, stream=None):
+    _check(lib().toric3d_tanner_syndrome(g.ref(), n_samples, _ptr(e), _ptr(s), float(q), seed, sample0, cycle,
+                                         _stream(stream)))
+
+
+def toric3d_tanner_flip_workspace_bytes(g: TannerGraph, n_samples) -> int:
+    return int(lib().toric3d_tanner_flip_workspace_bytes(g.ref(), n_samples))
+
+
+def toric3d_tanner_pflip(g: TannerGraph, n_samples, e, s, schedule, n_apply, sweep0, seed, sample0, cycle, work,
+                         stream=None):
+    _check(lib().toric3d_tanner_pflip(g.ref(), n_samples, _ptr(e), _ptr(s), schedule.encode(), n_apply, sweep0, seed,
+                                      sample0, cycle, _ptr(work), work.numel() * work.element_size(),
+                                      _stream(stream)))
+
+
+def toric3d_tanner_bp_workspace_bytes(g: TannerGraph, chunk_samples) -> int:
+    return int(lib().toric3d_tanner_bp_workspace_bytes(g.ref(), chunk_samples))
+
+
+def toric3d_tanner_bp(g: TannerGraph, n_samples, e, s, prior, iters, work, llr_out=None, stream=None):
+    _check(lib().toric3d_tanner_bp(g.ref(), n_samples, _ptr(e), _ptr(s), _ptr(prior), iters, _ptr(work),
+                                   work.numel() * work.element_size(), _ptr(llr_out), _stream(stream)))
+
+
+def toric3d_tanner_bp_message_bytes(g: TannerGraph, n_samples) -> int:
+    return int(lib().toric3d_tanner_bp_message_bytes(g.ref(), n_samples))
+
+
+def toric3d_tanner_bp_step(g: TannerGraph, n_samples, s, prior, msg_in, msg_out, work, stream=None):
+    _check(lib().toric3d_tanner_bp_step(g.ref(), n_samples, _ptr(s), _ptr(prior), _ptr(msg_in), _ptr(msg_out),
+                                        _ptr(work), work.numel() * work.element_size(), _stream(stream)))

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtoric3d.so")
 SOURCES = ["t3d_api.cu", "t3d_bitsliced.cu", "t3d_bp.cu", "t3d_run.cu", "t3d_noalloc.cu", "t3d_cnn.cu",
-           "t3d_cnn_tc.cu", "t3d_bp_meta.cu"]
+           "t3d_cnn_tc.cu", "t3d_bp_meta.cu",
+           "t3d_tanner.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

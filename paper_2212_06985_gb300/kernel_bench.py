@@ -5,6 +5,11 @@ profiling one kernel at a time; the whole-cycle benchmark is bench.py).
   python -m paper_2212_06985_gb300.kernel_bench sweep --L 32 --samples 8192 --rule F
   python -m paper_2212_06985_gb300.kernel_bench bp    --L 32 --samples 1024
   python -m paper_2212_06985_gb300.kernel_bench bpmeta --L 24 --samples 1024
+  python -m paper_2212_06985_gb300.kernel_bench tanner --n-classical 400 --samples 1024
+
+The tanner case decodes the Z checks of the hypergraph product of two seeded
+(3,4)-biregular classical codes (toric3d_inputs.hgp_workload; run from the
+repository root): one p-flip application (PF, mean of the two) and BP.
 
 Every line printed is one JSON object with the call's mean time over --reps
 timed calls (CUDA events) after --warmup untimed ones.
@@ -109,9 +114,40 @@ def bench_bp_meta(a, dev):
             "algorithmic_GBps_iterations": BP_META_BYTES * qs * a.iters / (ms / 1e3) / 1e9}
 
 
+def bench_tanner(a, dev):
+    import toric3d_inputs
+    from . import (tanner_prepare, toric3d_tanner_bp, toric3d_tanner_bp_workspace_bytes,
+                   toric3d_tanner_flip_workspace_bytes, toric3d_tanner_noise, toric3d_tanner_pflip,
+                   toric3d_tanner_syndrome)
+    cptr, cvar, n = toric3d_inputs.hgp_workload(a.n_classical, a.seed)
+    g = tanner_prepare(cptr, cvar, n, dev)
+    S, W = a.samples, words_for(a.samples)
+    e = torch.zeros((n, W), dtype=torch.int64, device=dev)
+    s = torch.zeros((g.n_checks, W), dtype=torch.int64, device=dev)
+    toric3d_tanner_noise(g, S, e, a.p, a.seed, 0, 1)
+    toric3d_tanner_syndrome(g, S, e, s, a.p, a.seed, 0, 1)
+    fwork = torch.empty(toric3d_tanner_flip_workspace_bytes(g, S), dtype=torch.uint8, device=dev)
+    ms_rule = _timed(lambda: toric3d_tanner_pflip(g, S, e, s, "PF", 2, 0, a.seed, 0, 1, fwork), a.warmup, a.reps) / 2
+    prior = torch.full((n,), float(__import__("math").log((1 - a.p) / a.p)), dtype=torch.float32, device=dev)
+    work = torch.empty(toric3d_tanner_bp_workspace_bytes(g, S), dtype=torch.uint8, device=dev)
+    e0, s0 = e.clone(), s.clone()
+
+    def bp():
+        e.copy_(e0)
+        s.copy_(s0)
+        toric3d_tanner_bp(g, S, e, s, prior, a.iters, work)
+
+    ms_bp = _timed(bp, a.warmup, a.reps)
+    bp_bytes = (16 * g.n_edges + 4 * n) * 64 * W * a.iters   # FP32 messages, totals and gathers per iteration
+    return {"call": "toric3d_tanner", "code": f"hgp({a.n_classical})", "n_vars": n, "n_checks": g.n_checks,
+            "n_edges": g.n_edges, "samples": S, "ms_per_rule_application": ms_rule,
+            "rule_variable_samples_per_s": n * 64 * W / (ms_rule / 1e3), "bp_iters": a.iters, "bp_ms": ms_bp,
+            "bp_algorithmic_GBps": bp_bytes / (ms_bp / 1e3) / 1e9}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("what", choices=["cnn", "sweep", "bp", "bpmeta"])
+    ap.add_argument("what", choices=["cnn", "sweep", "bp", "bpmeta", "tanner"])
     ap.add_argument("--L", type=int, default=24)
     ap.add_argument("--samples", type=int, default=16384)
     ap.add_argument("--p", type=float, default=0.04)
@@ -121,9 +157,10 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--weights", default=WEIGHTS)
+    ap.add_argument("--n-classical", type=int, default=400, help="tanner: bits of each classical code")
     a = ap.parse_args(argv)
     dev = torch.device("cuda:0")
-    out = {"cnn": bench_cnn, "sweep": bench_sweep, "bp": bench_bp, "bpmeta": bench_bp_meta}[a.what](a, dev)
+    out = {"cnn": bench_cnn, "sweep": bench_sweep, "bp": bench_bp, "bpmeta": bench_bp_meta, "tanner": bench_tanner}[a.what](a, dev)
     print(json.dumps(out), flush=True)
     return 0
 
