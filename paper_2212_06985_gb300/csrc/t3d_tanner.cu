@@ -47,17 +47,27 @@ struct G {
 
 G view(const t3d_tanner& g) { return G{g.n_vars, g.n_checks, g.cptr, g.cvar, g.vptr, g.vedge, g.vcheck}; }
 
-// (index, word) of a bit-sliced thread: blocks of 32 words x 8 indices.
+// (index, word) of a bit-sliced thread: blocks of tx words x ty indices, 256 threads,
+// tx = min(32, W rounded up to a power of two) so that few word lanes idle.
 __device__ __forceinline__ bool index_word(int64_t count, int64_t W, int64_t& i, int64_t& w)
 {
-    i = (int64_t)blockIdx.x * 8 + threadIdx.y;
-    w = (int64_t)blockIdx.y * 32 + threadIdx.x;
+    i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    w = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
     return i < count && w < W;
 }
 
-dim3 bs_grid(int64_t count, int64_t W) { return dim3((unsigned)((count + 7) / 8), (unsigned)((W + 31) / 32)); }
+dim3 bs_block(int64_t W)
+{
+    unsigned tx = 1;
+    while (tx < 32 && tx < W) tx *= 2;
+    return dim3(tx, kThreads / tx);
+}
 
-const dim3 kBsBlock(32, 8);
+dim3 bs_grid(int64_t count, int64_t W)
+{
+    const dim3 b = bs_block(W);
+    return dim3((unsigned)((count + b.y - 1) / b.y), (unsigned)((W + b.x - 1) / b.x));
+}
 
 __global__ void k_tg_noise(const G g, int64_t W, uint64_t* __restrict__ e, uint64_t thr, uint64_t seed,
                            uint64_t group0, uint32_t cycle)
@@ -264,7 +274,7 @@ __device__ void check_loop(const BpArgs& a, int64_t c, int32_t t0, int deg, int6
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_tg_checks(const BpArgs a)
+__global__ void __launch_bounds__(kThreads, 3) k_tg_checks(const BpArgs a)
 {
     const int64_t smp = quad_sample(), c = blockIdx.x;
     if (smp >= a.S) return;
@@ -437,7 +447,7 @@ extern "C" t3d_status toric3d_tanner_noise(const t3d_tanner* g, int64_t n_sample
     const int64_t W = words_for(n_samples);
     cudaStream_t st = as_stream(stream);
     ProfScope prof(T3D_K_NOISE, st);
-    k_tg_noise<<<bs_grid(g->n_vars, W), kBsBlock, 0, st>>>(view(*g), W, e, prob_threshold(p), seed, sample0 / 64,
+    k_tg_noise<<<bs_grid(g->n_vars, W), bs_block(W), 0, st>>>(view(*g), W, e, prob_threshold(p), seed, sample0 / 64,
                                                             cycle);
     T3D_LAUNCH_CHECK("Tanner noise");
     return T3D_OK;
@@ -457,7 +467,7 @@ extern "C" t3d_status toric3d_tanner_syndrome(const t3d_tanner* g, int64_t n_sam
     const int64_t W = words_for(n_samples);
     cudaStream_t st = as_stream(stream);
     ProfScope prof(T3D_K_SYNDROME, st);
-    k_tg_syndrome<<<bs_grid(g->n_checks, W), kBsBlock, 0, st>>>(view(*g), W, e, s, prob_threshold(q), seed,
+    k_tg_syndrome<<<bs_grid(g->n_checks, W), bs_block(W), 0, st>>>(view(*g), W, e, s, prob_threshold(q), seed,
                                                                  sample0 / 64, cycle);
     T3D_LAUNCH_CHECK("Tanner syndrome");
     return T3D_OK;
@@ -494,10 +504,10 @@ extern "C" t3d_status toric3d_tanner_pflip(const t3d_tanner* g, int64_t n_sample
     for (int k = 0; k < n_apply; ++k) {
         const bool prob = schedule[k % slen] == 'P';
         ProfScope prof(prob ? T3D_K_PFLIP : T3D_K_FLIP, st);
-        k_tg_decide<<<bs_grid((g->n_vars + 3) / 4, W), kBsBlock, 0, st>>>(gv, W, e, s, f, prob ? 1 : 0, seed,
+        k_tg_decide<<<bs_grid((g->n_vars + 3) / 4, W), bs_block(W), 0, st>>>(gv, W, e, s, f, prob ? 1 : 0, seed,
                                                                            sample0 / 64, cycle, sweep0 + k);
         T3D_LAUNCH_CHECK("Tanner rule decisions");
-        k_tg_apply<<<bs_grid(g->n_checks, W), kBsBlock, 0, st>>>(gv, W, s, W, f, W);
+        k_tg_apply<<<bs_grid(g->n_checks, W), bs_block(W), 0, st>>>(gv, W, s, W, f, W);
         T3D_LAUNCH_CHECK("Tanner rule syndrome update");
     }
     return T3D_OK;
@@ -592,7 +602,7 @@ extern "C" t3d_status toric3d_tanner_bp(const t3d_tanner* g, int64_t n_samples, 
         k_tg_decide_bp<<<dim3((unsigned)g->n_vars, (unsigned)((S + kThreads - 1) / kThreads)), kThreads, 0, st>>>(
             a, std::min<int64_t>(S, n_samples - 64 * w0), e + w0, d, cw, llr_out, n_samples);
         T3D_LAUNCH_CHECK("Tanner BP decisions");
-        k_tg_apply<<<bs_grid(g->n_checks, cw), kBsBlock, 0, st>>>(gv, cw, s + w0, W, d, cw);
+        k_tg_apply<<<bs_grid(g->n_checks, cw), bs_block(cw), 0, st>>>(gv, cw, s + w0, W, d, cw);
         T3D_LAUNCH_CHECK("Tanner BP syndrome update");
     }
     return T3D_OK;
