@@ -39,6 +39,7 @@ def _batch(kw, specs, ws_bytes=None, use_graph=False, tune=False):
     assert need > 0
     work = workspace(ws_bytes or need)
     stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())   # inputs were written on the current stream
     with torch.cuda.stream(stream):
         if tune:
             cap, ms = t3d.toric3d_autotune_batch(cfg, batch, work)

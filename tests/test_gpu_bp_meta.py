@@ -248,6 +248,7 @@ def test_run_with_meta_checks_equals_stepwise(use_graph, chunk):
     e2 = torch.zeros_like(e)
     mask = torch.zeros(S, dtype=torch.uint8, device=dev())
     stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())   # inputs were written on the current stream
     with torch.cuda.stream(stream):
         t3d.toric3d_run_cycles(cfg, e2, workspace(t3d.toric3d_run_workspace_bytes(cfg)), mask, None)
     stream.synchronize()

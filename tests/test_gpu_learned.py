@@ -90,6 +90,7 @@ def _run(L, S, T, blob, max_w, chunk=0, use_graph=False, split=None):
     counts = torch.zeros(8, dtype=torch.int64, device=dev())
     batch = t3d.make_batch([dict(L=L, n_samples=S, e=e, s_prev=s_prev, fallback_words=fb, counts8=counts)])
     stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())   # inputs were written on the current stream
     parts = [(0, T)] if split is None else [(0, split), (split, T - split)]
     with torch.cuda.stream(stream):
         for cycle0, t in parts:

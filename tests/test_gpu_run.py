@@ -24,6 +24,7 @@ def _gpu_run(cfg, e_bits=None):
     counts = torch.zeros(8, dtype=torch.int64, device=dev())
     stream = torch.cuda.Stream() if cfg.use_graph else None
     if stream is not None:
+        stream.wait_stream(torch.cuda.current_stream())   # inputs were written on the current stream
         with torch.cuda.stream(stream):
             t3d.toric3d_run_cycles(cfg, e, work, mask, counts)
         stream.synchronize()
