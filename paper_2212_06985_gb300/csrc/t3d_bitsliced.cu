@@ -156,7 +156,6 @@ k_flip(const __grid_constant__ ItemTable tab)
         const uint64_t* __restrict__ p2 = p1 + L3W;
         const int64_t mx = (int64_t)mv.minus[0] * W, my = (int64_t)mv.minus[1] * W, mz = (int64_t)mv.minus[2] * W;
         const int64_t px = (int64_t)mv.plus[0] * W, py = (int64_t)mv.plus[1] * W, pz = (int64_t)mv.plus[2] * W;
-        const int rx = r + mv.plus[0], ry = r + mv.plus[1], rz = r + mv.plus[2];
         const uint64_t s0 = p0[0], s1 = p1[0], s2 = p2[0];
         // the nine edges whose flips touch this site's faces: the three at r and two each at
         // r + e_x, r + e_y, r + e_z; their four checks each
@@ -184,6 +183,138 @@ k_flip(const __grid_constant__ ItemTable tab)
         if (fy0) e0[L3W] ^= fy0;
         if (fz0) e0[2 * L3W] ^= fz0;
     });
+}
+
+// The same flip application with the syndrome staged through shared memory.
+// A block owns one z-plane of one tile of Wt words (d.tx) and sweeps y from 0
+// to L-1; thread (x, wl) handles site (x, y, z), word wl of the tile.  The
+// lines its nine edges' checks come from -- plane z at y-1, y, y+1, plane z-1
+// at y and y+1 (faces 0, 1), plane z+1 at y-1 and y -- sit in rings of
+// shared-memory face-lines (L x Wt words each, the periodic x-halo being the
+// line itself), so each step loads three new lines of plane z, z-1 and z+1
+// (8 face-lines) instead of 24 scattered words per thread.  The loads of the
+// next step's lines and of the step's error words are issued before the
+// current step computes (software pipelining across the y sweep); 85
+// registers, three blocks per SM.
+constexpr int kTileWords = 256;                 // L x Wt <= 256 words per face-line
+constexpr int kTileSlots = 9 + 4 + 6;           // plane z: 3 lines x 3 faces; z-1: 2 x 2; z+1: 2 x 3
+
+__device__ __forceinline__ int ring3(int y) { return (y + 3) % 3; }
+__device__ __forceinline__ int ring2(int y) { return (y + 2) & 1; }
+
+__global__ void __launch_bounds__(kThreads, 3)
+k_flip_tiled(const __grid_constant__ ItemTable tab)
+{
+    __shared__ uint64_t sm[kTileSlots * kTileWords];
+    for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
+        __syncthreads();   // the previous block's last step may still read the rings
+        const Lattice lat = d.lat;
+        const int L = lat.L, Wt = d.tx;
+        const int64_t W = d.W, nw = d.nw ? d.nw : d.W, L3W = (int64_t)lat.L3 * W;
+        const int z = (int)(lb % L);
+        const int64_t w = (lb / L) * Wt + (threadIdx.x & (Wt - 1));
+        const int x = threadIdx.x / Wt, wl = threadIdx.x & (Wt - 1);
+        const bool act = x < L && w < nw;
+        const bool dec = act && !(d.gate && !d.gate[w]);
+        const int zm = z == 0 ? L - 1 : z - 1, zp = z + 1 == L ? 0 : z + 1;
+        const int xm = x == 0 ? L - 1 : x - 1, xp = x + 1 == L ? 0 : x + 1;
+        const int me = x * Wt + wl;
+        // this thread's word of face n at (x, yy, zz)
+        auto gword = [&](const uint64_t* base, int n, int yy, int zz) {
+            const int yw = (yy + L) % L;
+            return base[(int64_t)n * L3W + ((int64_t)(zz * L + yw) * L + x) * W + w];
+        };
+        auto put = [&](int slot, uint64_t v) { sm[slot * kTileWords + me] = v; };
+        auto P0 = [&](int yy, int n, int xx) { return sm[(ring3(yy) * 3 + n) * kTileWords + xx * Wt + wl]; };
+        auto Pm = [&](int yy, int n, int xx) { return sm[(9 + ring2(yy) * 2 + n) * kTileWords + xx * Wt + wl]; };
+        auto Pp = [&](int yy, int n, int xx) { return sm[(13 + ring2(yy) * 3 + n) * kTileWords + xx * Wt + wl]; };
+        // the eight face-line words entering at step yy (plane z at yy+1, plane z+1 at yy,
+        // plane z-1 at yy+1 faces 0, 1) and the three error words of the site at yy
+        uint64_t nx[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ex[3] = {0, 0, 0};
+        auto fetch = [&](int yy) {
+            if (!act) return;
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                nx[n] = gword(d.s, n, yy + 1, z);
+                nx[3 + n] = gword(d.s, n, yy, zp);
+            }
+            nx[6] = gword(d.s, 0, yy + 1, zm);
+            nx[7] = gword(d.s, 1, yy + 1, zm);
+            if (dec) {
+#pragma unroll
+                for (int n = 0; n < 3; ++n) ex[n] = gword(d.e, n, yy, z);
+            }
+        };
+        auto stash = [&](int yy) {
+            if (!act) return;
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                put(ring3(yy + 1) * 3 + n, nx[n]);
+                put(13 + ring2(yy) * 3 + n, nx[3 + n]);
+            }
+            put(9 + ring2(yy + 1) * 2 + 0, nx[6]);
+            put(9 + ring2(yy + 1) * 2 + 1, nx[7]);
+        };
+        // fill: plane z lines -1 and 0, plane z-1 line 0, plane z+1 line -1
+        if (act) {
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                put(ring3(-1) * 3 + n, gword(d.s, n, -1, z));
+                put(ring3(0) * 3 + n, gword(d.s, n, 0, z));
+                put(13 + ring2(-1) * 3 + n, gword(d.s, n, -1, zp));
+            }
+            put(9 + ring2(0) * 2 + 0, gword(d.s, 0, 0, zm));
+            put(9 + ring2(0) * 2 + 1, gword(d.s, 1, 0, zm));
+        }
+        fetch(0);
+        for (int y = 0; y < L; ++y) {
+            stash(y);
+            const uint64_t e0v = ex[0], e1v = ex[1], e2v = ex[2];
+            __syncthreads();
+            if (y + 1 < L) fetch(y + 1);   // in flight while this step computes
+            if (act) {
+                const uint64_t s0 = P0(y, 0, x), s1 = P0(y, 1, x), s2 = P0(y, 2, x);
+                const int64_t own = ((int64_t)(z * L + y) * L + x) * W + w;
+                uint64_t* __restrict__ q0 = d.tmp + own;
+                if (!dec) {
+                    q0[0] = s0;
+                    q0[L3W] = s1;
+                    q0[2 * L3W] = s2;
+                } else {
+                    const uint64_t q[9][4] = {
+                        {s2, P0(y - 1, 2, x), s1, Pm(y, 1, x)},                       // x-edge at r
+                        {s2, P0(y, 2, xm), s0, Pm(y, 0, x)},                          // y-edge at r
+                        {s1, P0(y, 1, xm), s0, P0(y - 1, 0, x)},                      // z-edge at r
+                        {P0(y + 1, 2, x), s2, P0(y + 1, 1, x), Pm(y + 1, 1, x)},      // x-edge at r + e_y
+                        {Pp(y, 2, x), Pp(y - 1, 2, x), Pp(y, 1, x), s1},              // x-edge at r + e_z
+                        {P0(y, 2, xp), s2, P0(y, 0, xp), Pm(y, 0, xp)},               // y-edge at r + e_x
+                        {Pp(y, 2, x), Pp(y, 2, xm), Pp(y, 0, x), s0},                 // y-edge at r + e_z
+                        {P0(y, 1, xp), s1, P0(y, 0, xp), P0(y - 1, 0, xp)},           // z-edge at r + e_x
+                        {P0(y + 1, 1, x), P0(y + 1, 1, xm), P0(y + 1, 0, x), s0}};    // z-edge at r + e_y
+                    uint64_t f[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) f[k] = at_least_three(q[k][0], q[k][1], q[k][2], q[k][3]);
+                    q0[0] = s0 ^ f[1] ^ f[6] ^ f[2] ^ f[8];
+                    q0[L3W] = s1 ^ f[0] ^ f[4] ^ f[2] ^ f[7];
+                    q0[2 * L3W] = s2 ^ f[0] ^ f[3] ^ f[1] ^ f[5];
+                    uint64_t* __restrict__ e0 = d.e + own;   // this thread alone writes its site's edges
+                    if (f[0]) e0[0] = e0v ^ f[0];
+                    if (f[1]) e0[L3W] = e1v ^ f[1];
+                    if (f[2]) e0[2 * L3W] = e2v ^ f[2];
+                }
+            }
+            __syncthreads();
+        }
+    });
+}
+
+// Words per tile row of k_flip_tiled: L x Wt <= 256, Wt a power of two <= 32 and
+// no wider than the batch.
+int tiled_words(int L, int64_t nw)
+{
+    int wt = 32;
+    while (wt > 1 && (L * wt > kTileWords || wt / 2 >= nw)) wt /= 2;
+    return wt;
 }
 
 // p-flip in two passes, so that each (site, word) draws one Philox block.
@@ -513,6 +644,17 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
         d.blocks = tile_blocks(d.lat.L3, nw, d.tx);
     }
     finish_table(tab);
+    // the shared-memory flip handles lattices whose face-line fits a tile row
+    bool tiled = true;
+    ItemTable tt = tab;
+    for (int i = 0; i < tt.n; ++i) {
+        ItemDesc& d = tt.it[i];
+        const int64_t nw = d.nw ? d.nw : d.W;
+        tiled = tiled && d.lat.L <= kTileWords / 4;
+        d.tx = tiled_words(d.lat.L, nw);
+        d.blocks = (int64_t)d.lat.L * ((nw + d.tx - 1) / d.tx);
+    }
+    finish_table(tt);
     ItemTable t = tab;  // flip: s and tmp swap roles; p-flip: tmp holds the flip words, s updated in place
     int swaps = 0;
     for (int k = 0; k < n_apply; ++k) {
@@ -526,10 +668,16 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
                             kThreads, 0, st>>>(t);
             T3D_LAUNCH_CHECK("p-flip syndrome update");
         } else {
-            k_flip<<<persistent_grid((const void*)k_flip, kThreads, T3D_K_FLIP, t.prefix[t.n]), kThreads, 0,
-                     st>>>(t);
+            if (tiled) {
+                k_flip_tiled<<<persistent_grid((const void*)k_flip_tiled, kThreads, T3D_K_FLIP, tt.prefix[tt.n]),
+                               kThreads, 0, st>>>(tt);
+            } else {
+                k_flip<<<persistent_grid((const void*)k_flip, kThreads, T3D_K_FLIP, t.prefix[t.n]), kThreads, 0,
+                         st>>>(t);
+            }
             T3D_LAUNCH_CHECK("flip sweep");
             for (int i = 0; i < t.n; ++i) std::swap(t.it[i].s, t.it[i].tmp);
+            for (int i = 0; i < tt.n; ++i) std::swap(tt.it[i].s, tt.it[i].tmp);
             ++swaps;
         }
     }
