@@ -647,13 +647,15 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
         d.blocks = tile_blocks(d.lat.L3, nw, d.tx);
     }
     finish_table(tab);
-    // the shared-memory flip handles lattices whose face-line fits a tile row
+    // the shared-memory flip when every face-line of the batch fits a tile row of at
+    // least 8 words (L <= 32); with 4-word rows (L = 40 .. 64) it measured slower than
+    // k_flip (L = 48: 3.18 vs 2.67 ms, L = 64: 3.49 vs 1.57 ms; L = 32: 1.12 vs 1.32 ms)
     bool tiled = true;
     ItemTable tt = tab;
     for (int i = 0; i < tt.n; ++i) {
         ItemDesc& d = tt.it[i];
         const int64_t nw = d.nw ? d.nw : d.W;
-        tiled = tiled && d.lat.L <= kTileWords / 4;
+        tiled = tiled && d.lat.L <= kTileWords / 8;
         d.tx = tiled_words(d.lat.L, nw);
         d.blocks = (int64_t)d.lat.L * ((nw + d.tx - 1) / d.tx);
     }
