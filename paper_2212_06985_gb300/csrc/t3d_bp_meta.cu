@@ -388,6 +388,8 @@ extern "C" t3d_status toric3d_bp_meta(int L, int64_t n_samples, uint64_t* e, uin
     T3D_REQUIRE(n_samples >= 1 && words_for(n_samples) <= 65535LL * 32, "n_samples out of range");
     T3D_TRY(check_words(e, "e"));
     T3D_TRY(check_words(s, "s"));
+    const size_t state = (size_t)3 * L * L * L * (size_t)words_for(n_samples) * 8;
+    T3D_REQUIRE(disjoint(e, state, s, state), "e and s must not overlap");
     T3D_REQUIRE(p > 0.0 && p < 1.0, "BP needs 0 < p < 1");
     T3D_REQUIRE(q > 0.0 && q < 1.0, "meta-checks need measurement errors: 0 < q < 1");
     T3D_REQUIRE(iters >= 0, "negative iteration count");

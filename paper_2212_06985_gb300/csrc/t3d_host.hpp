@@ -21,6 +21,13 @@ constexpr int kMaxL = 256;
 
 inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// Byte ranges [a, a + na) and [b, b + nb) share no byte.
+inline bool disjoint(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x + na <= y || y + nb <= x;
+}
+
 inline uint64_t prob_threshold(double p)
 {
     if (!(p > 0.0)) return 0;

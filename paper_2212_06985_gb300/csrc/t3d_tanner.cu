@@ -462,6 +462,8 @@ extern "C" t3d_status toric3d_tanner_syndrome(const t3d_tanner* g, int64_t n_sam
     T3D_TRY(check_samples(n_samples, 65535LL * 32));
     T3D_TRY(check_words(e, "e"));
     T3D_TRY(check_words(s, "s"));
+    T3D_REQUIRE(disjoint(e, (size_t)g->n_vars * words_for(n_samples) * 8, s, (size_t)g->n_checks * words_for(n_samples) * 8),
+                "e and s must not overlap");
     T3D_REQUIRE(q >= 0.0 && q <= 1.0, "q must lie in [0, 1]");
     T3D_REQUIRE(sample0 % 64 == 0, "sample0 must be a multiple of 64");
     const int64_t W = words_for(n_samples);
@@ -489,6 +491,8 @@ extern "C" t3d_status toric3d_tanner_pflip(const t3d_tanner* g, int64_t n_sample
     T3D_TRY(check_samples(n_samples, 65535LL * 32));
     T3D_TRY(check_words(e, "e"));
     T3D_TRY(check_words(s, "s"));
+    T3D_REQUIRE(disjoint(e, (size_t)g->n_vars * words_for(n_samples) * 8, s, (size_t)g->n_checks * words_for(n_samples) * 8),
+                "e and s must not overlap");
     T3D_REQUIRE(n_apply >= 0, "n_apply must be >= 0");
     const size_t slen = schedule ? strnlen(schedule, 64) : 0;
     T3D_REQUIRE(n_apply == 0 || (slen >= 1 && slen < 64), "n_apply > 0 needs a schedule of 1..63 letters");
@@ -562,6 +566,8 @@ extern "C" t3d_status toric3d_tanner_bp(const t3d_tanner* g, int64_t n_samples, 
     T3D_TRY(check_samples(n_samples, 65535LL * 32));
     T3D_TRY(check_words(e, "e"));
     T3D_TRY(check_words(s, "s"));
+    T3D_REQUIRE(disjoint(e, (size_t)g->n_vars * words_for(n_samples) * 8, s, (size_t)g->n_checks * words_for(n_samples) * 8),
+                "e and s must not overlap");
     T3D_REQUIRE(prior != nullptr && aligned(prior, 4), "prior must be a device float array");
     T3D_REQUIRE(iters >= 0, "negative iteration count");
     T3D_REQUIRE(work != nullptr && aligned(work, 256), "work must be a 256-byte aligned device pointer");

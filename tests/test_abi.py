@@ -161,3 +161,83 @@ def test_gate_validation():
     assert need > 0
     assert lib.toric3d_gate(4, 1, FAKE, 0, FAKE, None, FAKE, need - 8, None) == EINVAL
     assert "workspace" in _err()
+
+
+def test_meta_check_bp_sizes_and_validation():
+    lib = t3d.lib()
+    L, S = 4, 100
+    n, W = 3 * L ** 3, 2
+    assert t3d.toric3d_bp_meta_message_bytes(L, S) == 7 * n * 64 * W * 4
+    per_word = t3d.toric3d_bp_meta_workspace_bytes(L, 64)
+    assert per_word >= 64 * 15 * n * 4 + L ** 3 * 32
+    assert t3d.toric3d_bp_meta_workspace_bytes(L, S) == 2 * per_word
+    assert t3d.toric3d_bp_meta_workspace_bytes(1, S) == 0
+    other = ctypes.c_void_p(0x10000 + n * W * 8)
+    assert lib.toric3d_bp_meta(L, S, FAKE, other, 0.04, 0.0, 5, FAKE, 1 << 30, None, None) == EINVAL
+    assert "0 < q < 1" in _err()
+    assert lib.toric3d_bp_meta(L, S, FAKE, other, 1.0, 0.04, 5, FAKE, 1 << 30, None, None) == EINVAL
+    assert "0 < p < 1" in _err()
+    assert lib.toric3d_bp_meta(L, S, FAKE, other, 0.04, 0.04, 5, FAKE, per_word - 1, None, None) == EINVAL
+    assert "workspace too small" in _err()
+    assert lib.toric3d_bp_meta(L, S, FAKE, other, 0.04, 0.04, 5, FAKE, per_word, FAKE, None) == EINVAL
+    assert "llr_out" in _err()
+    assert lib.toric3d_bp_meta(L, S, FAKE, ctypes.c_void_p(0x10008), 0.04, 0.04, 5, FAKE, 1 << 30, None,
+                               None) == EINVAL
+    assert "overlap" in _err()
+    mb = t3d.toric3d_bp_meta_message_bytes(L, S)
+    assert lib.toric3d_bp_meta_step(L, S, FAKE, 0.04, 0.04, FAKE, ctypes.c_void_p(0x10000 + mb - 16), FAKE,
+                                    1 << 30, None) == EINVAL
+    assert "overlap" in _err()
+    # whole runs: meta-checks need BP and measurement errors
+    cfg = t3d.make_run_cfg(L, 2, 0.04, 0.0, 0, S, use_bp=True, bp_iters=4, bp_meta_checks=True, schedule="F")
+    assert cfg.bp_meas_nodes == 2
+    assert lib.toric3d_run_cycles(ctypes.byref(cfg), FAKE, FAKE, 1 << 30, None, None, None) == EINVAL
+    assert "meta-checks" in _err()
+    cfg = t3d.make_run_cfg(L, 2, 0.04, 0.04, 0, S, use_bp=True, bp_iters=4, bp_meta_checks=True, schedule="F")
+    plain = t3d.make_run_cfg(L, 2, 0.04, 0.04, 0, S, use_bp=True, bp_iters=4, schedule="F")
+    assert t3d.toric3d_run_workspace_bytes(cfg) > t3d.toric3d_run_workspace_bytes(plain)
+
+
+def _prep(cptr, cvar, n, blob=FAKE, nbytes=1 << 20):
+    import numpy as np
+    cptr = np.asarray(cptr, np.int32)
+    cvar = np.asarray(cvar, np.int32)
+    desc = t3d.Tanner()
+    st = t3d.lib().toric3d_tanner_prepare(n, len(cptr) - 1, cptr.ctypes.data_as(ctypes.c_void_p),
+                                          cvar.ctypes.data_as(ctypes.c_void_p), blob, nbytes, ctypes.byref(desc))
+    return st, desc
+
+
+@pytest.mark.parametrize("cptr,cvar,n,needle", [
+    ([0, 2, 4], [0, 0, 1, 2], 3, "twice"),
+    ([0, 2, 4], [0, 3, 1, 2], 3, "out of range"),
+    ([0, 33], list(range(33)), 40, "degree 33"),
+    ([1, 2], [0, 1], 3, "cptr[0]"),
+    ([0, 2, 1], [0, 1], 3, "non-decreasing"),
+    ([0, 0], [], 3, "edges"),
+])
+def test_tanner_prepare_rejects_bad_lists(cptr, cvar, n, needle):
+    st, _ = _prep(cptr, cvar, n)
+    assert st == EINVAL and needle in _err()
+
+
+def test_tanner_prepare_rejects_variable_degree_above_32_and_small_blobs():
+    cptr = list(range(0, 34))
+    cvar = [0] * 33                  # variable 0 in 33 checks of degree 1
+    st, _ = _prep(cptr, cvar, 1)
+    assert st == EINVAL and "variable 0 has degree 33" in _err()
+    need = t3d.lib().toric3d_tanner_bytes(3, 2, 4)
+    assert need > 0
+    st, _ = _prep([0, 2, 4], [0, 1, 1, 2], 3, nbytes=need - 1)
+    assert st == EINVAL and "blob too small" in _err()
+    st, _ = _prep([0, 2, 4], [0, 1, 1, 2], 3, blob=MIS)
+    assert st == EINVAL and "aligned" in _err()
+
+
+def test_tanner_calls_reject_unprepared_graphs():
+    lib = t3d.lib()
+    g = t3d.Tanner()   # all zero: not prepared
+    assert lib.toric3d_tanner_noise(ctypes.byref(g), 64, FAKE, 0.1, 0, 0, 1, None) == EINVAL
+    assert "not prepared" in _err()
+    assert lib.toric3d_tanner_flip_workspace_bytes(None, 64) == 0
+    assert lib.toric3d_tanner_bp_workspace_bytes(None, 64) == 0
