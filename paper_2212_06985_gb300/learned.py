@@ -160,6 +160,9 @@ def train(L: int = 12, p=0.04, steps: int = 400, batch: int = 2048, lr: float = 
     return params.cpu().numpy(), history
 
 
+BP_CHUNK_BYTES = 48 << 30
+
+
 def evaluate(L: int, p: float, T: int, n_samples: int, params: np.ndarray | None, seed: int,
              fallback_max_weight: int = -1, dec: Decoder | None = None, use_graph: bool = True,
              device="cuda:0"):
@@ -180,9 +183,14 @@ def evaluate(L: int, p: float, T: int, n_samples: int, params: np.ndarray | None
         blob = torch.empty(toric3d_cnn_blob_bytes(), dtype=torch.uint8, device=dev)
         toric3d_cnn_prepare(torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).to(dev), blob)
     batch = make_batch([dict(L=L, n_samples=n_samples, e=e, counts8=counts, s_prev=s_prev, fallback_words=fb)])
+    # BP messages of at most BP_CHUNK_BYTES at a time (all samples in one chunk would need
+    # about 3 GB per 1000 samples at L = 32)
+    per_word = toric3d_bp_workspace_bytes(L, 64)
+    chunk = n_samples if W * per_word <= BP_CHUNK_BYTES else max(1, BP_CHUNK_BYTES // per_word) * 64
     cfg = make_run_cfg(L, T, p, dec.q, dec.seed, n_samples, use_bp=params is None, bp_iters=dec.bp_iters,
                        schedule=dec.schedule, n_apply=dec.n_apply, use_graph=use_graph, cnn_blob=blob,
-                       fallback_max_weight=fallback_max_weight if params is not None else -1)
+                       fallback_max_weight=fallback_max_weight if params is not None else -1,
+                       bp_chunk_samples=chunk if params is None else 0)
     work = torch.empty(toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
