@@ -269,7 +269,10 @@ t3d_status toric3d_tanner_prepare(int64_t n_vars, int64_t n_checks, const int32_
  * Noise (Sec. 3.1): e ^= Bernoulli(p) keyed by the variable index (stream 0).
  * Syndrome: s = H e ^ Bernoulli(q) keyed by the check index (stream 1).
  * Generator and keys as in toric3d_noise / toric3d_syndrome, so on the toric
- * code's own graph these equal those calls.
+ * code's own graph these equal those calls.  Logical readout of a generic
+ * code is the same parity computation: prepare a second graph whose rows are
+ * the code's logical Z operators and call toric3d_tanner_syndrome on it with
+ * q = 0; bit l of sample i is then the parity of e over logical l.
  */
 t3d_status toric3d_tanner_noise(const t3d_tanner* g, int64_t n_samples, uint64_t* e, double p, uint64_t seed,
                                 uint64_t sample0, uint32_t cycle, t3d_stream stream);

@@ -123,6 +123,28 @@ def test_noise_measure_schedule_bit_exact(name, S, sample0):
         assert np.array_equal(download_bits(e, S), ora_e) and np.array_equal(download_bits(s, S), ora_s)
 
 
+def test_logical_parities_through_a_logical_graph():
+    """Logical readout of a generic code: the syndrome of e with respect to a graph whose
+    rows are qubit sets (here straight lines of the hypergraph product of two cycles, the
+    2D toric code) is the parity of e on each set, bit-exact; with logical operators as
+    the rows this is the readout."""
+    L, S = 6, 150
+    X, Z, n = inp.hypergraph_product(inp.cyclic_repetition(L), L, inp.cyclic_repetition(L), L)
+    # qubits (a, b) -> a L + b: the line a = 0 and the line b = 0 of the first block, and the
+    # same two lines of the second block (n1 n2 + i L + j)
+    logicals = [[b for b in range(L)], [a * L for a in range(L)],
+                [L * L + j for j in range(L)], [L * L + i * L for i in range(L)]]
+    lptr, lvar = inp.csr(logicals)
+    g = t3d.tanner_prepare(lptr, lvar, n)
+    ebits = inp.random_bits(S, n, 0.2, 3)
+    e = upload_bits(ebits)
+    out = torch.zeros((len(logicals), inp.words_for(S)), dtype=torch.int64, device=dev())
+    t3d.toric3d_tanner_syndrome(g, S, e, out, 0.0, 1, 0, 1)
+    torch.cuda.synchronize()
+    want = np.stack([ebits[:, l].sum(axis=1) % 2 for l in logicals], axis=1).astype(np.uint8)
+    assert np.array_equal(download_bits(out, S), want)
+
+
 def _rows_bound(cptr, cvar, prior, cv_in, n):
     """Per Tanner edge: the FP32 rounding of the other inputs of its check (each input
     T_v - M is a sum of deg_v + 2 terms: (deg_v + 2) u times the magnitudes)."""
