@@ -36,8 +36,14 @@ namespace t3d {
 namespace meta {
 namespace {
 
+using bpm::add4;
+using bpm::check_node;
+using bpm::comp;
+using bpm::ld4;
+using bpm::st4;
+using bpm::sub4;
+
 constexpr int kThreads = 256;   // threads per block, each on consecutive samples of one index
-constexpr float kClamp = 30.0f;
 
 struct Bufs {
     float* F;     // [3L^3][4][S]
@@ -56,33 +62,6 @@ struct Args {
     Bufs in, out;
 };
 
-// Check node over K inputs (Eq. 2): out[i] = (-1)^{syn} times the product of
-// the other inputs' signs times 2 atanh(prod_{j != i} tanh(|x_j|/2)), from
-// prefix and suffix products of the (t, d) pairs; clamped to kClamp.
-template <int K>
-__device__ __forceinline__ void check_node(const float (&x)[K], bool syn, float (&out)[K])
-{
-    bpm::TD v[K], pre[K], suf[K];
-    uint32_t sgn_all = syn ? 0x80000000u : 0u;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        v[i] = bpm::td_of(x[i]);
-        sgn_all ^= __float_as_uint(x[i]);
-    }
-    pre[0] = bpm::TD{1.0f, 0.0f};
-#pragma unroll
-    for (int i = 1; i < K; ++i) pre[i] = bpm::td_mul(pre[i - 1], v[i - 1]);
-    suf[K - 1] = bpm::TD{1.0f, 0.0f};
-#pragma unroll
-    for (int i = K - 2; i >= 0; --i) suf[i] = bpm::td_mul(v[i + 1], suf[i + 1]);
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        const bpm::TD o = bpm::td_mul(pre[i], suf[i]);
-        const float mag = fminf(bpm::two_atanh(o.t, o.d), kClamp);
-        const uint32_t sgn = (sgn_all ^ __float_as_uint(x[i])) & 0x80000000u;
-        out[i] = __uint_as_float(__float_as_uint(mag) | sgn);
-    }
-}
 
 // Syndrome bits of samples smp .. smp + 3 (smp a multiple of 4) in bits 0..3.
 __device__ __forceinline__ uint32_t syn_bits4(const Args& a, int64_t row, int64_t smp)
@@ -112,25 +91,8 @@ __device__ __forceinline__ void edge_slots(const Lattice& lat, int d, int r, int
     }
 }
 
-// The iteration kernels give each thread four consecutive samples of one index
-// (16-byte loads and stores; the index arithmetic is shared by the four):
+// The iteration kernels give each thread four consecutive samples of one index:
 // blockIdx.x is the index, blockIdx.y * blockDim.x + threadIdx.x the sample quad.
-__device__ __forceinline__ float4 ld4(const float* base, int64_t row, int64_t S, int64_t smp)
-{
-    return __ldg(reinterpret_cast<const float4*>(base + row * S + smp));
-}
-
-__device__ __forceinline__ void st4(float* base, int64_t row, int64_t S, int64_t smp, float4 v)
-{
-    *reinterpret_cast<float4*>(base + row * S + smp) = v;
-}
-
-__device__ __forceinline__ float comp(const float4& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
-
-__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-
-__device__ __forceinline__ float4 sub4(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
-
 __device__ __forceinline__ int64_t quad_sample(const Args& a)
 {
     return ((int64_t)blockIdx.y * blockDim.x + threadIdx.x) * 4;

@@ -31,10 +31,14 @@ namespace t3d {
 namespace tg {
 namespace {
 
+using bpm::check_node;
+using bpm::comp;
+using bpm::ld4;
+using bpm::st4;
+
 constexpr int kMaxDeg = 32;          // largest variable and check degree accepted
 constexpr int kCounterBits = 6;      // counts 0..32
 constexpr int kThreads = 256;
-constexpr float kClamp = 30.0f;
 
 struct G {
     int64_t n, m;
@@ -166,17 +170,6 @@ struct BpArgs {
 
 __device__ __forceinline__ int64_t quad_sample() { return ((int64_t)blockIdx.y * blockDim.x + threadIdx.x) * 4; }
 
-__device__ __forceinline__ float4 ld4(const float* base, int64_t row, int64_t S, int64_t smp)
-{
-    return __ldg(reinterpret_cast<const float4*>(base + row * S + smp));
-}
-
-__device__ __forceinline__ void st4(float* base, int64_t row, int64_t S, int64_t smp, float4 v)
-{
-    *reinterpret_cast<float4*>(base + row * S + smp) = v;
-}
-
-__device__ __forceinline__ float comp(const float4& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
 
 // T_v = prior_v + sum of the messages into v (Eq. 3 / Eq. 4 without the leave-one-out).
 __global__ void __launch_bounds__(kThreads) k_tg_totals(const BpArgs a)
@@ -197,31 +190,6 @@ __device__ __forceinline__ uint32_t syn_bits4(const BpArgs& a, int64_t c, int64_
     return (uint32_t)(a.s[c * a.W + (smp >> 6)] >> (smp & 63)) & 0xFu;
 }
 
-// Eq. 2 for one sample over K inputs, prefix / suffix (t, d) products.
-template <int K>
-__device__ __forceinline__ void check_node(const float (&x)[K], bool syn, float (&out)[K])
-{
-    bpm::TD v[K], pre[K], suf[K];
-    uint32_t sgn_all = syn ? 0x80000000u : 0u;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        v[i] = bpm::td_of(x[i]);
-        sgn_all ^= __float_as_uint(x[i]);
-    }
-    pre[0] = bpm::TD{1.0f, 0.0f};
-#pragma unroll
-    for (int i = 1; i < K; ++i) pre[i] = bpm::td_mul(pre[i - 1], v[i - 1]);
-    suf[K - 1] = bpm::TD{1.0f, 0.0f};
-#pragma unroll
-    for (int i = K - 2; i >= 0; --i) suf[i] = bpm::td_mul(v[i + 1], suf[i + 1]);
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        const bpm::TD o = bpm::td_mul(pre[i], suf[i]);
-        const float mag = fminf(bpm::two_atanh(o.t, o.d), kClamp);
-        const uint32_t sgn = (sgn_all ^ __float_as_uint(x[i])) & 0x80000000u;
-        out[i] = __uint_as_float(__float_as_uint(mag) | sgn);
-    }
-}
 
 template <int K>
 __device__ __forceinline__ void check_quad(const BpArgs& a, int64_t c, int32_t t0, int64_t smp)
@@ -266,7 +234,7 @@ __device__ void check_loop(const BpArgs& a, int64_t c, int32_t t0, int deg, int6
         for (int k = deg - 1; k >= 0; --k) {
             const float x = a.T[(int64_t)a.g.cvar[t0 + k] * a.S + sm] - a.in[(int64_t)(t0 + k) * a.S + sm];
             const bpm::TD o = bpm::td_mul(pre[k], suf);
-            const float mag = fminf(bpm::two_atanh(o.t, o.d), kClamp);
+            const float mag = fminf(bpm::two_atanh(o.t, o.d), bpm::kCheckClamp);
             const uint32_t sgn = (sgn_all ^ __float_as_uint(x)) & 0x80000000u;
             a.out[(int64_t)(t0 + k) * a.S + sm] = __uint_as_float(__float_as_uint(mag) | sgn);
             suf = bpm::td_mul(bpm::td_of(x), suf);
