@@ -1,4 +1,4 @@
-"""Training and evaluation drivers for the learned local pre-decoder.
+"""Training and evaluation of the learned local pre-decoder.
 
 Host-side orchestration only: every step (noise, measurement, BP, flip and
 p-flip, the network's forward and backward passes, Adam) runs in the library's

@@ -1,4 +1,4 @@
-"""Host-side pieces of the learned pre-decoder's training driver (no GPU):
+"""Host-side pieces of the learned pre-decoder's training loop (no GPU):
 parameter initialisation, the learning-rate schedule, weight files, and the
 committed trained weights."""
 import os
