@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--workload", default="bp_pflip_L32", choices=sorted(inp.WORKLOADS))
     ap.add_argument("--samples", type=int, default=0, help="samples per GPU (default: the workload's)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
+    ap.add_argument("--reference-seconds", type=float, default=60.0,
+                    help="--impl reference: oracle time over all steps (default 60 s)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -120,7 +122,7 @@ def reference_arm(args):
         return 0
     w = inp.WORKLOADS[args.workload]
     S = args.samples or w.n_samples
-    budget = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    budget = max(0.5, args.reference_seconds / max(1, args.steps + args.warmup))
     for i in range(args.warmup):
         time_oracle(w, budget / 4, cycle0=i)
     vals, secs, last = [], [], None
