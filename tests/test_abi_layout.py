@@ -13,6 +13,7 @@ import paper_2212_06985_gb300 as t3d
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 MIRRORS = {"t3d_run_cfg": t3d.RunCfg, "t3d_batch_item": t3d.BatchItem, "t3d_tanner": t3d.Tanner}
+KINDS = sorted(t3d.KERNEL_KINDS)
 
 
 @pytest.fixture(scope="module")
@@ -26,6 +27,9 @@ def c_layout(tmp_path_factory):
         lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
         for fname, _ in py._fields_:
             lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    for name in KINDS:
+        lines.append(f'    printf("kind {name} %d\\n", (int)T3D_K_{name.upper()});')
+    lines.append('    printf("kind count %d\\n", (int)T3D_K_COUNT);')
     lines += ['    return 0;', '}']
     src = d / "layout.c"
     src.write_text("\n".join(lines) + "\n")
@@ -46,3 +50,9 @@ def test_python_mirror_matches_c_layout(c_layout, cname):
     assert ctypes.sizeof(py) == c_layout[(cname, "size")]
     for fname, _ in py._fields_:
         assert getattr(py, fname).offset == c_layout[(cname, fname)], fname
+
+
+def test_kernel_kinds_match_c_enum(c_layout):
+    for name, value in t3d.KERNEL_KINDS.items():
+        assert c_layout[("kind", name)] == value, name
+    assert c_layout[("kind", "count")] == len(t3d.KERNEL_KINDS)
