@@ -32,7 +32,10 @@ sys.path.insert(0, ROOT)
 
 import toric3d_inputs as inp  # noqa: E402
 
-METRIC = "qubit-cycles decoded/s at L=32 p=4%: BP+p-flip"
+METRIC = "qubit-cycles decoded/s at L=32 p=4%: BP+p-flip vs learned+p-flip, equal logical err"
+# `value` is the BP + p-flip decoder (the decoder the reference arm times); the line's
+# learned_pflip object holds learned + p-flip on the same workload and its ratio.
+VALUE_IS = "BP+p-flip; learned_pflip.value = learned+p-flip, learned_pflip.vs_bp_pflip = their ratio"
 
 # DRAM bytes (read + write) per edge-sample of the dominant kernel from one
 # ncu capture of the current k_bp_step (L = 32, 1024 samples; traffic grows in
@@ -131,7 +134,8 @@ def reference_arm(args):
         vals.append(last["value"])
         secs.append(last["seconds"])
     value = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "value_is": "BP+p-flip (the oracle)",
+            "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded Philox noise)", "config": workload_config(w, S),
@@ -446,7 +450,8 @@ def cuda_arm(args):
         cpu.pop("seconds", None)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC, "value": value, "value_is": VALUE_IS, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+u64",
                 "data": "synthetic (seeded Philox phenomenological noise)",
