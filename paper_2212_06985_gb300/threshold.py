@@ -11,6 +11,14 @@ logical Z lines of the final error, no noiseless round):
          paragraph; the paper proposes them without simulating them)
   table1-sweep : every non-empty cell of Table 1 on a 0.1% grid around the
          paper's value, L = 14 and 24; one line per cell with the crossing
+  table2 : p-BP at L = 14, 500 cycles (App. A.2, Table 2), the histogram of
+         the eight logical error patterns set against the paper's by a
+         chi-square test of homogeneity (patterns pooled by weight, the code
+         being symmetric under axis permutations), over all runs and over
+         the failed runs alone
+  --reading r : bp / pbp / table2 under another reading of BP inside a run
+         (readings.py: restart, warm, halfiter, measdecide), composed from the
+         library's single-step calls
 
   python -m paper_2212_06985_gb300.threshold pbp --L 14 18 24 32 --p 0.053 0.054 0.055 0.056 --samples 10000
 
@@ -32,6 +40,7 @@ import torch
 
 from . import (make_batch, make_run_cfg, n_bits, table1_schedule, toric3d_run_batch,
                toric3d_run_batch_workspace_bytes, words_for)
+from .readings import READINGS, run_stepwise
 
 PRESETS = {
     "flip": dict(T=1000, use_bp=False, bp_iters=0, schedule="F", n_apply=1),
@@ -43,11 +52,20 @@ PRESETS = {
 
 def run_point(preset: str, L: int, p: float, samples: int, seed: int, T: int | None = None,
               meas_nodes: bool = True, n_A: int = 5, lambda_p: int = 3, meta_checks: bool = False,
-              device="cuda:0") -> dict:
-    """One whole run of `samples` codes; returns failure counts and the run time."""
+              reading: str | None = None, device="cuda:0") -> dict:
+    """One whole run of `samples` codes; returns failure counts and the run time.
+    reading (bp / pbp only): compose the run step by step under that reading of
+    BP inside a run (readings.py) instead of the whole-run call."""
     pr = dict(PRESETS[preset])
     if T is not None:
         pr["T"] = T
+    if reading is not None:
+        if not pr["use_bp"] or meta_checks or not meas_nodes:
+            raise ValueError("--reading applies to the bp / pbp presets with measurement variables")
+        r = run_stepwise(L, p, p, samples, seed, pr["T"], pr["bp_iters"], pr["schedule"], pr["n_apply"],
+                         reading, device=device)
+        r.update(preset=preset, meas_nodes=True, meta_checks=False)
+        return r
     if preset == "table1":
         pr["schedule"], pr["n_apply"] = table1_schedule(n_A, lambda_p), n_A
     dev = torch.device(device)
@@ -91,6 +109,44 @@ def table1_sweep(Ls=(14, 24), samples: int = 3000, seed: int = 7000):
         c = crossing_guess(pts)
         yield {"nA": nA, "lp": lp, "paper_pct": th, "crossing_pct": None if c is None else round(100 * c, 3),
                "rates": {f"L{q['L']}@{q['p']}": q["fail_q0"] / q["samples"] for q in pts}}
+
+
+# Table 2 of the paper (App. A.2): logical X error patterns over the three encoded
+# qubits after 500 cycles of p-BP at L = 14, p = q = 5.44% (printed "0.544"), 1000 runs.
+TABLE2_PAPER = {"000": 731, "100": 52, "010": 53, "001": 62, "110": 21, "101": 30, "011": 26, "111": 25}
+TABLE2_SETUP = dict(L=14, p=0.0544, T=500, runs=1000)
+
+
+def pattern_counts(counts8) -> dict:
+    """Mask histogram (bit d = logical qubit d) -> {"abc": count}, a = qubit 0."""
+    return {f"{m & 1}{(m >> 1) & 1}{(m >> 2) & 1}": int(counts8[m]) for m in range(8)}
+
+
+def by_weight(patterns: dict) -> list[int]:
+    """Pattern counts pooled by the number of failed logical qubits (0..3)."""
+    w = [0, 0, 0, 0]
+    for k, v in patterns.items():
+        w[k.count("1")] += v
+    return w
+
+
+def table2_compare(counts8) -> dict:
+    """Chi-square tests of homogeneity between a measured pattern histogram and
+    Table 2, on the weight classes 0..3 (all runs) and 1..3 (failed runs only,
+    the correlation structure whatever the overall failure rate)."""
+    from scipy.stats import chi2_contingency
+    ours = by_weight(pattern_counts(counts8))
+    paper = by_weight(TABLE2_PAPER)
+    out = {"weights": ours, "paper_weights": paper}
+    for name, sl in (("all", slice(0, 4)), ("failed", slice(1, 4))):
+        a, b = ours[sl], paper[sl]
+        keep = [i for i in range(len(a)) if a[i] + b[i] > 0]
+        if len(keep) < 2 or sum(a) == 0:
+            out[name] = None
+            continue
+        chi2, pv, dof, _ = chi2_contingency([[a[i] for i in keep], [b[i] for i in keep]])
+        out[name] = {"chi2": float(chi2), "dof": int(dof), "p_value": float(pv)}
+    return out
 
 
 def crossing_guess(points: list[dict]) -> float | None:
@@ -138,7 +194,7 @@ def fit_threshold(points: list[dict]) -> dict | None:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("preset", choices=sorted(PRESETS) + ["table1-sweep"])
+    ap.add_argument("preset", choices=sorted(PRESETS) + ["table1-sweep", "table2"])
     ap.add_argument("--L", type=int, nargs="+", default=[14, 18, 24])
     ap.add_argument("--p", type=float, nargs="+", default=None, help="error rates (required but for table1-sweep)")
     ap.add_argument("--samples", type=int, default=10000)
@@ -150,7 +206,19 @@ def main(argv=None):
                     help="BP with the cube meta-checks over the measurement variables (Sec. 4.1, last paragraph)")
     ap.add_argument("--no-meas-nodes", action="store_true",
                     help="BP without the measurement-error variables (checks taken as exact)")
+    ap.add_argument("--reading", choices=READINGS, default=None,
+                    help="bp / pbp / table2: compose the runs step by step under this reading of BP in a run")
     a = ap.parse_args(argv)
+    if a.preset == "table2":
+        ps = a.p or [TABLE2_SETUP["p"]]
+        samples = a.samples if a.samples != 10000 else TABLE2_SETUP["runs"]
+        for k, p in enumerate(ps):
+            q = run_point("pbp", TABLE2_SETUP["L"] if a.L == [14, 18, 24] else a.L[0], p, samples,
+                          a.seed + k, a.T, reading=a.reading)
+            q["patterns"] = pattern_counts(q["counts8"])
+            q["table2"] = table2_compare(q["counts8"])
+            print(json.dumps(q), flush=True)
+        return 0
     if a.preset == "table1-sweep":
         for row in table1_sweep(tuple(a.L) if a.L != [14, 18, 24] else (14, 24), a.samples, a.seed):
             print(json.dumps(row), flush=True)
@@ -161,7 +229,7 @@ def main(argv=None):
     for L in a.L:
         for k, p in enumerate(a.p):
             q = run_point(a.preset, L, p, a.samples, a.seed + 1000 * L + k, a.T, not a.no_meas_nodes, a.nA, a.lp,
-                          a.meta_checks)
+                          a.meta_checks, a.reading)
             points.append(q)
             print(json.dumps(q), flush=True)
     import warnings
