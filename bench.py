@@ -39,9 +39,8 @@ VALUE_IS = "BP+p-flip; learned_pflip.value = learned+p-flip, learned_pflip.vs_bp
 
 # DRAM bytes (read + write) per edge-sample of the dominant kernel from one
 # ncu capture of the current k_bp_step (L = 32, 1024 samples; traffic grows in
-# proportion to the samples a launch covers, so it scales to full launches):
-# profiles/k_bp_step_bp_pflip_L32_1024samples.md.  Set to None when the kernel
-# changes until it is captured again.
+# proportion to the samples a launch covers, so it scales to full launches).
+# Set to None when the kernel changes until it is captured again.
 BP_STEP_TRAFFIC = {"first_iteration": 15.68, "full_iteration": 31.94}
 UNIT = "qubit-cycles/s"
 
@@ -65,6 +64,8 @@ def parse():
                     help="skip the learned pre-decoder + p-flip leg of the same workload")
     ap.add_argument("--learned-chunk", type=int, default=16384,
                     help="samples per pre-decoder launch (bounds its activation workspace)")
+    ap.add_argument("--fallback-sigmas", type=float, default=4.0,
+                    help="learned leg: BP + p-flip fallback above q 3L^3 + this many sigma unsatisfied checks")
     return ap.parse_args()
 
 
@@ -138,7 +139,8 @@ def reference_arm(args):
             "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded Philox noise)", "config": workload_config(w, S),
+            "data": "synthetic (seeded Philox noise)",
+            "config": dict(workload_config(w, S), parallelism=f"replicas{args.gpus}"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -239,11 +241,15 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
     states = [torch.zeros((inp.n_bits(L), W), dtype=torch.int64, device=dev) for L in sizes]
     prevs = [torch.zeros_like(e) for e in states]
     counts = [torch.zeros(8, dtype=torch.int64, device=dev) for _ in sizes]
-    batch = t3d.make_batch([dict(L=L, n_samples=S, sample0=sample0, e=e, s_prev=sp, counts8=c)
-                            for L, e, sp, c in zip(sizes, states, prevs, counts)])
+    fallback = [torch.zeros(1, dtype=torch.int64, device=dev) for _ in sizes]
+    batch = t3d.make_batch([dict(L=L, n_samples=S, sample0=sample0, e=e, s_prev=sp, counts8=c, fallback_words=f)
+                            for L, e, sp, c, f in zip(sizes, states, prevs, counts, fallback)])
+    # BP + p-flip fallback for every 64-sample word in which a sample's decoded syndrome keeps
+    # more unsatisfied checks than the noisy measurement alone leaves (q 3L^3 + k sigma)
     cfg = t3d.make_run_cfg(w.L, 1, w.p, w.q, w.seed, S, sample0=sample0, schedule=w.schedule, n_apply=w.n_apply,
+                           bp_iters=w.bp_iters, bp_meas_nodes=w.bp_meas_nodes,
                            bp_chunk_samples=learned_chunk(max(sizes), S, args.learned_chunk), cnn_blob=blob,
-                           fallback_max_weight=-1)
+                           fallback_max_weight=0, fallback_sigmas=args.fallback_sigmas)
     work = torch.empty(t3d.toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
 
     def step(t):
@@ -256,6 +262,7 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
     stream.synchronize()
     barrier()
     torch.cuda.synchronize()
+    fb0 = sum(int(f.item()) for f in fallback)
     t3d.toric3d_profile_reset()
     t3d.toric3d_profile_enable(True)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -268,6 +275,7 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
     ev1.synchronize()
     t3d.toric3d_profile_enable(False)
     t3d.toric3d_cnn_status()
+    fb_timed = sum(int(f.item()) for f in fallback) - fb0
     prof = {k: t3d.toric3d_profile_read(k) for k in t3d.KERNEL_KINDS}
     t3d.toric3d_profile_reset()
     ms = ev0.elapsed_time(ev1)
@@ -298,7 +306,16 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
                      "executed_mma_tflops": CNN_MMA_FLOP_PER_SITE * sites * S * args.steps / (cnn_ms / 1e3) / 1e12
                      if cnn_ms > 0 else None,
                      "share_of_step": cnn_ms / ms if ms else None},
-        "last_cycle_logical_counts": [c.cpu().tolist() for c in counts],
+        "fallback": {"gate": f"fallback_max_weight 0 + fallback_sigmas {args.fallback_sigmas}: a word goes back to "
+                             f"BP{w.bp_iters} + the schedule when a sample keeps more than q 3L^3 + "
+                             f"{args.fallback_sigmas} sigma unsatisfied checks",
+                     "thresholds": {str(L): int(math.floor(w.q * inp.n_bits(L) + args.fallback_sigmas *
+                                                           math.sqrt(w.q * (1 - w.q) * inp.n_bits(L))))
+                                    for L in sizes},
+                     "words_per_step": fb_timed / args.steps,
+                     "word_fraction": fb_timed / (args.steps * W * len(sizes))},
+        "logical_counts": [c.cpu().tolist() for c in counts],
+        "logical_counts_after_cycles": args.warmup + args.steps,
         "chunk_samples": learned_chunk(max(sizes), S, args.learned_chunk),
     }
 
@@ -460,7 +477,8 @@ def cuda_arm(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "kernels_ms": {k: v[0] for k, v in prof.items() if v[1]},
                 "kernels_launches": {k: v[1] for k, v in prof.items() if v[1]},
-                "clocks": clk, "autotune": tuned, "last_cycle_logical_counts": fail_counts,
+                "clocks": clk, "autotune": tuned, "logical_counts": fail_counts,
+                "logical_counts_after_cycles": args.warmup + args.steps,
                 "learned_pflip": learned}
         print(json.dumps(line), flush=True)
     if world > 1:

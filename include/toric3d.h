@@ -110,9 +110,10 @@ t3d_status toric3d_flip(int L, int64_t words, uint64_t* e, uint64_t* s, int swee
  * that loads the library until the process exits), so this call allocates
  * nothing.  It rejects (T3D_EINVAL) any L, words with 3 L^3 * words * 8 bytes
  * above 32 MiB.  The first call on a device looks up the array's address with
- * that device current; make it before any stream capture.  All calls share
- * the array: calls that overlap on the GPU race, so order them.  Nothing in
- * the array needs clearing between calls.
+ * that device current, and so does the first call after the device's CUDA
+ * context changed (cudaDeviceReset); make those calls before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race, so
+ * order them.  Nothing in the array needs clearing between calls.
  */
 t3d_status toric3d_flip_noalloc(int L, int64_t words, uint64_t* e, uint64_t* s, int sweeps,
                                 t3d_stream stream);
@@ -382,8 +383,13 @@ typedef struct {
     const void* cnn_blob;      /* learned pre-decoder (toric3d_cnn_prepare) decoding in place of BP
                                   (use_bp must be 0; toric3d_run_batch only, items carry s_prev); NULL = none */
     int32_t fallback_max_weight; /* with cnn_blob: after the schedule, every 64-sample word in which a sample
-                                    keeps more than this many unsatisfied checks is decoded again by BP
-                                    (bp_iters) + the schedule; -1 = no fallback */
+                                    keeps more than this many unsatisfied checks (plus the allowance of
+                                    fallback_sigmas) is decoded again by BP (bp_iters) + the schedule;
+                                    -1 = no fallback */
+    double fallback_sigmas;      /* > 0: the threshold of each lattice also allows the unsatisfied checks the
+                                    noisy measurement alone leaves, floor(q n + fallback_sigmas sqrt(q (1-q) n))
+                                    with n = 3L^3 (isolated measurement errors stay unsatisfied after any
+                                    decoder); 0 = none */
 } t3d_run_cfg;
 
 /* Workspace toric3d_run_cycles needs for `cfg` (uses cfg->bp_chunk_samples, 0 = all). */
@@ -436,6 +442,13 @@ t3d_status toric3d_cnn_decode(int L, int64_t n_samples, const uint64_t* s_prev, 
  * its bounded waits (its results are then invalid) since the last call.
  * Reads and clears the device flag; synchronises the device. */
 t3d_status toric3d_cnn_status(void);
+/* Test hook: bound (ns) of the pre-decoder's bounded waits that may give up
+ * (default and maximum 1 s; 0 restores the default).  A short bound makes
+ * those waits run out, so the give-up path (error flag, wind-down that still
+ * waits up to 1 s for the kernel's own copies and MMAs in flight, TMEM freed)
+ * can be exercised without a fault.  Synchronises the device; process-wide
+ * state of the calling device. */
+t3d_status toric3d_cnn_debug_wait_limit(uint64_t ns);
 size_t toric3d_cnn_train_workspace_bytes(int L, int64_t n_samples);
 t3d_status toric3d_cnn_train_step(int L, int64_t n_samples, const uint64_t* s_prev,
                                   const uint64_t* s, const uint64_t* e_label, float* params,

@@ -49,7 +49,7 @@ EXPORTED_SYMBOLS = [
     "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "toric3d_flip_noalloc",
     "toric3d_cnn_param_count", "toric3d_cnn_blob_bytes", "toric3d_cnn_prepare", "toric3d_cnn_workspace_bytes",
     "toric3d_cnn_decode", "toric3d_cnn_train_workspace_bytes", "toric3d_cnn_train_step",
-    "toric3d_gate_workspace_bytes", "toric3d_gate", "toric3d_cnn_status",
+    "toric3d_gate_workspace_bytes", "toric3d_gate", "toric3d_cnn_status", "toric3d_cnn_debug_wait_limit",
     "toric3d_bp_meta_workspace_bytes", "toric3d_bp_meta", "toric3d_bp_meta_message_bytes", "toric3d_bp_meta_step",
     "toric3d_tanner_bytes", "toric3d_tanner_prepare", "toric3d_tanner_noise", "toric3d_tanner_syndrome",
     "toric3d_tanner_flip_workspace_bytes", "toric3d_tanner_pflip", "toric3d_tanner_bp_workspace_bytes",
@@ -108,6 +108,7 @@ class RunCfg(ctypes.Structure):
         ("bp_chunk_samples", ctypes.c_int64),
         ("cnn_blob", ctypes.c_void_p),
         ("fallback_max_weight", ctypes.c_int32),
+        ("fallback_sigmas", ctypes.c_double),
     ]
 
 
@@ -179,6 +180,7 @@ def _declare(h):
         "toric3d_logical": (i32, [i32, i64, _P, _P, _P, _P]),
         "toric3d_gate_workspace_bytes": (ctypes.c_size_t, [i32, i64]),
         "toric3d_cnn_status": (i32, []),
+        "toric3d_cnn_debug_wait_limit": (i32, [u64]),
         "toric3d_gate": (i32, [i32, i64, _P, ctypes.c_uint32, _P, _P, _P, ctypes.c_size_t, _P]),
         "toric3d_pack": (i32, [i64, i64, _P, _P, _P]),
         "toric3d_unpack": (i32, [i64, i64, _P, _P, _P]),
@@ -358,9 +360,11 @@ def toric3d_gate(L, s, max_weight, gate, work, n_flagged=None, stream=None):
 def make_run_cfg(L, T, p, q, seed, n_samples, *, sample0=0, use_bp=False, bp_iters=0,
                  bp_meas_nodes=True, schedule="", n_apply=None, perfect_round=False,
                  perfect_max_sweeps=0, cycle0=0, use_graph=False, bp_chunk_samples=0, cnn_blob=None,
-                 fallback_max_weight=-1, bp_meta_checks=False) -> RunCfg:
+                 fallback_max_weight=-1, bp_meta_checks=False, fallback_sigmas=0.0) -> RunCfg:
     """bp_meta_checks: BP over the measurement variables joined by the cube meta-checks
-    (bp_meas_nodes = 2 in the C struct; implies measurement variables)."""
+    (bp_meas_nodes = 2 in the C struct; implies measurement variables).  fallback_sigmas:
+    the learned decoder's fallback threshold also allows q 3L^3 + fallback_sigmas standard
+    deviations of unsatisfied checks (the measurement errors any decoder leaves)."""
     c = RunCfg()
     c.L, c.T, c.p, c.q, c.seed = L, T, float(p), float(q), seed
     c.sample0, c.n_samples = sample0, n_samples
@@ -371,6 +375,7 @@ def make_run_cfg(L, T, p, q, seed, n_samples, *, sample0=0, use_bp=False, bp_ite
     c.perfect_round, c.perfect_max_sweeps = int(perfect_round), perfect_max_sweeps
     c.cycle0, c.use_graph, c.bp_chunk_samples = cycle0, int(use_graph), bp_chunk_samples
     c.cnn_blob, c.fallback_max_weight = _ptr(cnn_blob), fallback_max_weight
+    c.fallback_sigmas = float(fallback_sigmas)
     return c
 
 
@@ -488,6 +493,12 @@ def toric3d_cnn_decode(L, n_samples, s_prev, s, e, blob, work, logits_out=None, 
 def toric3d_cnn_status():
     """Raise T3DError if a tensor-core pre-decoder kernel gave up a bounded wait."""
     _check(lib().toric3d_cnn_status())
+
+
+def toric3d_cnn_debug_wait_limit(ns: int):
+    """Test hook: shorten (ns > 0) or restore (0) the bound of the pre-decoder's
+    waits that may give up."""
+    _check(lib().toric3d_cnn_debug_wait_limit(int(ns)))
 
 
 def toric3d_cnn_train_workspace_bytes(L: int, n_samples: int) -> int:

@@ -141,12 +141,7 @@ k_flip(const __grid_constant__ ItemTable tab)
         uint64_t* __restrict__ s_out = d.tmp;
         uint64_t* __restrict__ e = d.e;
         const int64_t W = d.W;
-        if (d.gate && !d.gate[w]) {
-            // word not decoded: carry its syndrome into the other buffer unchanged
-#pragma unroll
-            for (int n = 0; n < 3; ++n) s_out[((int64_t)n * lat.L3 + r) * W + w] = s_in[((int64_t)n * lat.L3 + r) * W + w];
-            return;
-        }
+        if (!word_live(d, w)) return;
         // row pointers of the three faces at r and the element offsets of the six neighbour
         // sites (periodic wrap folded in): every neighbour load is one add away
         const Moves mv = site_moves(lat, r);
@@ -214,8 +209,7 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
         const int z = (int)(lb % L);
         const int64_t w = (lb / L) * Wt + (threadIdx.x & (Wt - 1));
         const int x = threadIdx.x / Wt, wl = threadIdx.x & (Wt - 1);
-        const bool act = x < L && w < nw;
-        const bool dec = act && !(d.gate && !d.gate[w]);
+        const bool act = x < L && w < nw && word_live(d, w);
         const int zm = z == 0 ? L - 1 : z - 1, zp = z + 1 == L ? 0 : z + 1;
         const int xm = x == 0 ? L - 1 : x - 1, xp = x + 1 == L ? 0 : x + 1;
         const int me = x * Wt + wl;
@@ -240,10 +234,8 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
             }
             nx[6] = gword(d.s, 0, yy + 1, zm);
             nx[7] = gword(d.s, 1, yy + 1, zm);
-            if (dec) {
 #pragma unroll
-                for (int n = 0; n < 3; ++n) ex[n] = gword(d.e, n, yy, z);
-            }
+            for (int n = 0; n < 3; ++n) ex[n] = gword(d.e, n, yy, z);
         };
         auto stash = [&](int yy) {
             if (!act) return;
@@ -276,11 +268,7 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
                 const uint64_t s0 = P0(y, 0, x), s1 = P0(y, 1, x), s2 = P0(y, 2, x);
                 const int64_t own = ((int64_t)(z * L + y) * L + x) * W + w;
                 uint64_t* __restrict__ q0 = d.tmp + own;
-                if (!dec) {
-                    q0[0] = s0;
-                    q0[L3W] = s1;
-                    q0[2 * L3W] = s2;
-                } else {
+                {
                     const uint64_t q[9][4] = {
                         {s2, P0(y - 1, 2, x), s1, Pm(y, 1, x)},                       // x-edge at r
                         {s2, P0(y, 2, xm), s0, Pm(y, 0, x)},                          // y-edge at r
@@ -334,7 +322,7 @@ k_pflip_decide(const __grid_constant__ ItemTable tab, uint64_t seed, uint32_t cy
         int r;
         int64_t w;
         if (!tile_site_word(d, lb, lat.L3, r, w)) return;
-        if (d.gate && !d.gate[w]) return;
+        if (!word_live(d, w)) return;
         const int64_t W = d.W;
         const Moves mv = site_moves(lat, r);
         const int64_t L3W = (int64_t)lat.L3 * W;
@@ -351,7 +339,7 @@ k_pflip_decide(const __grid_constant__ ItemTable tab, uint64_t seed, uint32_t cy
                                   {s1, p1[mx], s0, p0[my]}};   // z-edge at r
         uint64_t* __restrict__ e0 = d.e + (int64_t)r * W + w;
         const uint64_t ex[3] = {e0[0], e0[L3W], e0[2 * L3W]};
-        const U64x4 c = coin_block(seed, (uint64_t)r, cycle, sweep, d.group0 + (uint64_t)w);
+        const U64x4 c = coin_block(seed, (uint64_t)r, cycle, sweep, word_group(d, w));
         uint64_t f[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
@@ -376,7 +364,7 @@ k_pflip_apply(const __grid_constant__ ItemTable tab)
         int r;
         int64_t w;
         if (!tile_site_word(d, lb, lat.L3, r, w)) return;
-        if (d.gate && !d.gate[w]) return;
+        if (!word_live(d, w)) return;
         const int64_t W = d.W;
         const Moves mv = site_moves(lat, r);
         const int64_t L3W = (int64_t)lat.L3 * W;
@@ -645,6 +633,8 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
         const int64_t nw = d.nw ? d.nw : d.W;
         d.tx = row_words(nw);
         d.blocks = tile_blocks(d.lat.L3, nw, d.tx);
+        d.live_wpu = d.tx;
+        d.live_bpu = tile_blocks(d.lat.L3, d.tx, d.tx);   // site tiles of one word row
     }
     finish_table(tab);
     // the shared-memory flip when every face-line of the batch fits a tile row of at
@@ -658,6 +648,8 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
         tiled = tiled && d.lat.L <= kTileWords / 8;
         d.tx = tiled_words(d.lat.L, nw);
         d.blocks = (int64_t)d.lat.L * ((nw + d.tx - 1) / d.tx);
+        d.live_wpu = d.tx;
+        d.live_bpu = d.lat.L;   // one z-plane per block, word tiles outermost
     }
     finish_table(tt);
     ItemTable t = tab;  // flip: s and tmp swap roles; p-flip: tmp holds the flip words, s updated in place
@@ -738,6 +730,91 @@ t3d_status launch_gate(const Lattice& lat, int64_t W, const uint64_t* s, uint32_
     T3D_LAUNCH_CHECK("fallback gate count");
     k_gate_decide<<<(unsigned)((W + 255) / 256), 256, 0, st>>>(W, Y, scratch, max_weight, gate, n_flagged);
     T3D_LAUNCH_CHECK("fallback gate decide");
+    return T3D_OK;
+}
+
+namespace {
+
+// Fallback compaction.  k_compact_words: one block lists the flagged words of
+// gate[0..W) in increasing order (wsrc) and their count (*live), by a block
+// prefix sum over 1024 flags at a time.
+constexpr int kCompactThreads = 1024;
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact_words(const uint8_t* __restrict__ gate, int64_t W, uint32_t* __restrict__ wsrc, int64_t* __restrict__ live)
+{
+    __shared__ int warp_base[kCompactThreads / 32];
+    __shared__ int total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t base = 0;
+    for (int64_t c0 = 0; c0 < W; c0 += kCompactThreads) {
+        const int64_t w = c0 + threadIdx.x;
+        const bool f = w < W && gate[w] != 0;
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) warp_base[warp] = __popc(b);
+        __syncthreads();
+        if (warp == 0) {
+            const int v = warp_base[lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            warp_base[lane] = incl - v;
+            if (lane == 31) total = incl;
+        }
+        __syncthreads();
+        if (f) wsrc[base + warp_base[warp] + __popc(b & ((1u << lane) - 1u))] = (uint32_t)w;
+        base += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *live = base;
+}
+
+// Copy the live word columns between the batch arrays (row stride W) and their
+// compacted copies: gather a[r][wsrc[k]] -> c[r][k], or scatter back.  A warp
+// takes one row and strides over the live columns.
+__global__ void __launch_bounds__(kThreads)
+k_move_words(int64_t rows, int64_t W, const int64_t* __restrict__ live, const uint32_t* __restrict__ wsrc,
+             uint64_t* a0, uint64_t* c0, uint64_t* a1, uint64_t* c1, bool gather)
+{
+    const int64_t n = *live;
+    if (n == 0) return;
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); r < rows;
+         r += (int64_t)gridDim.x * (kThreads / 32)) {
+        for (int64_t k = lane; k < n; k += 32) {
+            const int64_t ia = r * W + wsrc[k], ic = r * W + k;
+            if (gather) {
+                c0[ic] = a0[ia];
+                c1[ic] = a1[ia];
+            } else {
+                a0[ia] = c0[ic];
+                a1[ia] = c1[ic];
+            }
+        }
+    }
+}
+
+}  // namespace
+
+t3d_status launch_compact_words(const uint8_t* gate, int64_t W, uint32_t* wsrc, int64_t* live, cudaStream_t st)
+{
+    ProfScope prof(T3D_K_LOGICAL, st);
+    k_compact_words<<<1, kCompactThreads, 0, st>>>(gate, W, wsrc, live);
+    T3D_LAUNCH_CHECK("fallback word compaction");
+    return T3D_OK;
+}
+
+t3d_status launch_move_words(const Lattice& lat, int64_t W, const int64_t* live, const uint32_t* wsrc, uint64_t* e,
+                             uint64_t* e_c, uint64_t* s, uint64_t* s_c, bool gather, cudaStream_t st)
+{
+    const int64_t rows = 3LL * lat.L3;
+    const int64_t blocks = std::min<int64_t>((rows + kThreads / 32 - 1) / (kThreads / 32), 152LL * 8);
+    ProfScope prof(T3D_K_LOGICAL, st);
+    k_move_words<<<(unsigned)blocks, kThreads, 0, st>>>(rows, W, live, wsrc, e, e_c, s, s_c, gather);
+    T3D_LAUNCH_CHECK("fallback word gather / scatter");
     return T3D_OK;
 }
 

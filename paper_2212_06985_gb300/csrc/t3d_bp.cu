@@ -130,7 +130,7 @@ k_bp_step(const __grid_constant__ ItemTable tab, float l0, TD q, float m1)
     const int64_t W = d.W;
     SiteWarp sw;
     if (!site_warp(lat, lb, sw)) return;
-    if (d.gate && !d.gate[d.w0 + sw.w]) return;
+    if (!word_live(d, sw.w)) return;
     const int lane = threadIdx.x & 31;
     Syn3* __restrict__ syn = reinterpret_cast<Syn3*>(d.syn);
     uint64_t s0, s1, s2;
@@ -267,7 +267,7 @@ k_bp_decide(const __grid_constant__ ItemTable tab, float l0)
     const int64_t W = d.W;
     SiteWarp sw;
     if (!site_warp(lat, lb, sw)) return;
-    if (d.gate && !d.gate[d.w0 + sw.w]) return;
+    if (!word_live(d, sw.w)) return;
     const int lane = threadIdx.x & 31;
     const int64_t sample0 = sw.w * kWord + 2 * lane;
     const bool valid0 = sample0 < d.n_samples, valid1 = sample0 + 1 < d.n_samples;
@@ -339,7 +339,7 @@ k_bp_syndrome(const __grid_constant__ ItemTable tab)
     const int r = (int)((lb - word_tile * site_tiles) * kSynSitesPerBlock + (threadIdx.x / kSynWordsPerRow));
     const int64_t w = word_tile * kSynWordsPerRow + (threadIdx.x % kSynWordsPerRow);
     if (r >= lat.L3 || w >= d.words) return;
-    if (d.gate && !d.gate[d.w0 + w]) return;
+    if (!word_live(d, w)) return;
     const Coord rc = site_coord(lat, r);
     const int step[3] = {1, lat.L, lat.L2};
     int nb[3];
@@ -385,7 +385,12 @@ int64_t word_syn_bytes(int L) { return (int64_t)L * L * L * (int64_t)sizeof(Syn3
 
 void set_blocks(ItemTable& tab)
 {
-    for (int i = 0; i < tab.n; ++i) tab.it[i].blocks = site_blocks(tab.it[i].lat.L3) * tab.it[i].words;
+    for (int i = 0; i < tab.n; ++i) {
+        ItemDesc& d = tab.it[i];
+        d.blocks = site_blocks(d.lat.L3) * d.words;
+        d.live_wpu = 1;
+        d.live_bpu = site_blocks(d.lat.L3);
+    }
     finish_table(tab);
 }
 
@@ -419,7 +424,12 @@ t3d_status launch_decide(ItemTable& tab, double p, cudaStream_t st)
                       kBpThreads, 0, st>>>(tab, prior(p));
         T3D_LAUNCH_CHECK("bp decide");
     }
-    for (int i = 0; i < tab.n; ++i) tab.it[i].blocks = syn_blocks(tab.it[i].lat.L3, tab.it[i].words);
+    for (int i = 0; i < tab.n; ++i) {
+        ItemDesc& d = tab.it[i];
+        d.blocks = syn_blocks(d.lat.L3, d.words);
+        d.live_wpu = kSynWordsPerRow;
+        d.live_bpu = (d.lat.L3 + kSynSitesPerBlock - 1) / kSynSitesPerBlock;
+    }
     finish_table(tab);
     ProfScope prof(T3D_K_BP_DECIDE, st);
     k_bp_syndrome<<<persistent_grid((const void*)k_bp_syndrome, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n]),

@@ -524,6 +524,12 @@ extern "C" t3d_status toric3d_cnn_status(void)
     return tc_status();
 }
 
+extern "C" t3d_status toric3d_cnn_debug_wait_limit(uint64_t ns)
+{
+    clear_error();
+    return tc_set_wait_limit(ns);
+}
+
 extern "C" size_t toric3d_cnn_workspace_bytes(int L, int64_t n_samples)
 {
     if (L < 2 || L > 128 || n_samples < 1) return 0;

@@ -49,6 +49,7 @@ t3d_status tc_prepare();
 // T3D_OK, or T3D_ETIMEOUT if a tensor-core kernel gave up a bounded wait since
 // the last call (reads and clears the device flag; synchronises the device).
 t3d_status tc_status();
+t3d_status tc_set_wait_limit(uint64_t ns);
 
 }  // namespace cnn
 }  // namespace t3d

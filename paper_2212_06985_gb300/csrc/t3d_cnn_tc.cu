@@ -37,9 +37,11 @@
 //              completion to the row's "empty" barrier and to the plane's
 //              "accumulators full" barrier (the code takes kIssuers threads
 //              owning alternate planes; two were slower than one on GB300).
-// Every wait is bounded (one second); a wait that gives up sets the device
-// error flag and the CTA winds down (waiting, again bounded, for its copies and
-// MMAs in flight, and freeing its TMEM) so the context stays usable.
+// Every wait is bounded (one second; toric3d_cnn_debug_wait_limit shortens the
+// waits that may give up, so a test can make them run out); a wait that gives
+// up sets the device error flag and the CTA winds down (waiting, again bounded
+// but always by the full second, for its copies and MMAs in flight, and
+// freeing its TMEM) so the context stays usable.
 //
 // Shared-memory operand layout ("no swizzle", K-major): core matrices of 8 rows
 // x 16 bytes stored contiguously.  Hidden activations in global memory use the
@@ -112,6 +114,8 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN 
                             ((uint32_t)(kTileM >> 4) << 24);
 
 __device__ unsigned int g_tc_error;   // bit 0: a bounded wait gave up
+// bound of the waits that may give up (the wind-down drains always use kWaitNs)
+__device__ unsigned long long g_tc_wait_ns = kWaitNs;
 
 struct TcArgs {
     int L, L3;
@@ -174,18 +178,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity.  Gives up after kWaitNs, or
-// early once another role of the CTA has given up (abort flag), unless
-// ignore_abort (the final drain of work in flight).
+// Bounded wait for the phase of the given parity.  Gives up after
+// g_tc_wait_ns, or early once another role of the CTA has given up (abort
+// flag), unless ignore_abort (the final drain of work in flight, bounded by
+// kWaitNs whatever the debug limit).
 __device__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag, bool ignore_abort = false)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
+    const uint64_t limit = ignore_abort ? kWaitNs : *(volatile unsigned long long*)&g_tc_wait_ns;
     for (;;) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
         if (!ignore_abort && *abort_flag) return false;
-        if (global_ns() - t0 > kWaitNs) {
+        if (global_ns() - t0 > limit) {
             *abort_flag = 1;
             atomicOr(&g_tc_error, 1u);
             return false;
@@ -737,6 +743,15 @@ t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t
     a.dec32 = reinterpret_cast<uint32_t*>(dec);
     a.logits = logits_out;
     T3D_TRY((launch_conv<true, false>(a, st)));
+    return T3D_OK;
+}
+
+t3d_status tc_set_wait_limit(uint64_t ns)
+{
+    const unsigned long long v = ns ? (unsigned long long)ns : (unsigned long long)kWaitNs;
+    T3D_REQUIRE(v <= kWaitNs, "the wait limit cannot exceed %llu ns", (unsigned long long)kWaitNs);
+    T3D_CUDA_CHECK(cudaDeviceSynchronize());
+    T3D_CUDA_CHECK(cudaMemcpyToSymbol(g_tc_wait_ns, &v, sizeof(v)));
     return T3D_OK;
 }
 

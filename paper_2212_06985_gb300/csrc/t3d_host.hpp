@@ -115,6 +115,12 @@ t3d_status launch_dec_apply(const Lattice& lat, int64_t W, int64_t words, const 
 // checks in s; *n_flagged (nullable) += flagged words.  scratch holds
 // gate_scratch_bytes(L, W) bytes.
 size_t gate_scratch_bytes(int L, int64_t W);
+// Fallback compaction: wsrc[0..*live) = the flagged words of gate[0..W), in
+// order; then gather (or scatter back) those word columns of e and s into (from)
+// the first *live columns of e_c and s_c (same row stride W).
+t3d_status launch_compact_words(const uint8_t* gate, int64_t W, uint32_t* wsrc, int64_t* live, cudaStream_t st);
+t3d_status launch_move_words(const Lattice& lat, int64_t W, const int64_t* live, const uint32_t* wsrc, uint64_t* e,
+                             uint64_t* e_c, uint64_t* s, uint64_t* s_c, bool gather, cudaStream_t st);
 t3d_status launch_gate(const Lattice& lat, int64_t W, const uint64_t* s, uint32_t max_weight, uint8_t* gate,
                        unsigned long long* n_flagged, uint64_t* scratch, cudaStream_t st);
 

@@ -34,7 +34,15 @@ struct ItemDesc {
     unsigned long long* counts8;
     int64_t w0;           // BP: first 64-sample word of the current chunk
     int64_t words;        // BP: words in the current chunk
-    const uint8_t* gate;  // optional per-word flags (whole item): only flagged words are decoded
+    // Compacted word columns (the learned decoder's fallback): when live is set, only the
+    // words w0 + w < *live hold data and the others are skipped; word w of the arrays is
+    // word wsrc[w] of the batch (its random numbers are keyed by group0 + wsrc[w]).  A
+    // launch over a single such item walks only the blocks that hold live words: local
+    // block lb covers words [(lb / live_bpu) * live_wpu, + live_wpu) of the launch.
+    const int64_t* live;  // device, nullable
+    const uint32_t* wsrc; // device, nullable
+    int64_t live_bpu;     // blocks per unit of live_wpu words (set by each launcher)
+    int live_wpu;
     int tx;               // bit-sliced kernels: words per thread-block row (power of 2)
     int64_t blocks;       // thread blocks this item needs in the current launch
 };
@@ -53,11 +61,35 @@ __device__ __forceinline__ int item_of(const ItemTable& tab, int64_t b)
     return i;
 }
 
+// Whether word w (of the launch's word range) holds data.
+__device__ __forceinline__ bool word_live(const ItemDesc& d, int64_t w)
+{
+    return d.live == nullptr || d.w0 + w < *d.live;
+}
+
+// Group (64-sample word of the whole batch) that keys word w's random numbers.
+__device__ __forceinline__ uint64_t word_group(const ItemDesc& d, int64_t w)
+{
+    return d.group0 + (d.wsrc ? (uint64_t)d.wsrc[w] : (uint64_t)w);
+}
+
+// Blocks of a compacted single-item launch that hold live words.
+__device__ __forceinline__ int64_t live_blocks(const ItemDesc& d)
+{
+    if (d.live_wpu <= 0) return d.blocks;   // launcher without a live layout: per-word checks only
+    const int64_t lw = *d.live - d.w0;
+    if (lw <= 0) return 0;
+    const int64_t b = (lw + d.live_wpu - 1) / d.live_wpu * d.live_bpu;
+    return b < d.blocks ? b : d.blocks;
+}
+
 // Persistent grid-stride walk over every item's blocks: f(item, local block).
+// The bound is uniform across a thread block, so f may synchronise the block.
 template <class F>
 __device__ __forceinline__ void for_each_item_block(const ItemTable& tab, F&& f)
 {
-    const int64_t total = tab.prefix[tab.n];
+    int64_t total = tab.prefix[tab.n];
+    if (tab.n == 1 && tab.it[0].live) total = live_blocks(tab.it[0]);
     for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
         const int i = item_of(tab, b);
         f(tab.it[i], b - tab.prefix[i]);

@@ -15,15 +15,17 @@
 // Costs and rules of the built-in scratch:
 // * every GPU that loads this library holds the array (kScratchBytes) until
 //   the process exits;
-// * the array's device address is looked up once per device, on that
-//   device's first call (with the device current); make that first call
-//   before any stream capture on the device;
+// * the array's device address is looked up on a device's first call (with
+//   the device current) and again whenever the device's CUDA context has
+//   changed since (after cudaDeviceReset the module is loaded anew and the
+//   array moves); make those calls outside any stream capture;
 // * all calls share the one array, so calls whose work overlaps on the GPU
 //   (for example on two streams without ordering) race and corrupt each
 //   other's results; order them;
 // * the array keeps the last call's contents; nothing in it needs to start at
 //   zero, because every application overwrites the whole syndrome copy
 //   before reading it.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -43,25 +45,68 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) uint64_t g_flip_scratch[kScratchBytes / sizeof(uint64_t)];
 
 std::mutex g_scratch_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id;   // unique id of the CUDA context the address belongs to
+    void* addr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
+// Driver calls reached through the runtime (the library does not link libcuda).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+t3d_status resolve_driver_calls()
+{
+    if (g_ctx_get_current && g_ctx_get_id) return T3D_OK;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    T3D_CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+    T3D_CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+    T3D_REQUIRE(q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2,
+                "the driver lacks cuCtxGetCurrent / cuCtxGetId");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    return T3D_OK;
+}
+
+// Id of the calling thread's current context, 0 if there is none yet.
+t3d_status current_context_id(unsigned long long* id)
+{
+    CUcontext ctx = nullptr;
+    *id = 0;
+    T3D_REQUIRE(g_ctx_get_current(&ctx) == CUDA_SUCCESS, "cuCtxGetCurrent failed");
+    if (ctx) T3D_REQUIRE(g_ctx_get_id(ctx, id) == CUDA_SUCCESS, "cuCtxGetId failed");
+    return T3D_OK;
+}
+
+// Device address of the scratch array in the current device's current context:
+// looked up on the first call and again whenever that context has changed.
 t3d_status scratch_address(void** out)
 {
     int dev = 0;
     T3D_CUDA_CHECK(cudaGetDevice(&dev));
     T3D_REQUIRE(dev >= 0 && dev < kMaxDevices, "device %d outside the %d supported", dev, kMaxDevices);
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
+    T3D_TRY(resolve_driver_calls());
+    unsigned long long id = 0;
+    T3D_TRY(current_context_id(&id));
+    ScratchAddr& c = g_scratch_addr[dev];
+    if (id == 0 || c.addr == nullptr || c.ctx_id != id) {
         void* p = nullptr;
-        cudaError_t err = cudaGetSymbolAddress(&p, g_flip_scratch);
+        cudaError_t err = cudaGetSymbolAddress(&p, g_flip_scratch);   // creates the context if needed
         if (err != cudaSuccess || p == nullptr) {
             set_error("cudaGetSymbolAddress of the flip scratch failed: %s", cudaGetErrorString(err));
             return T3D_ECUDA;
         }
-        g_scratch_addr[dev] = p;
+        T3D_TRY(current_context_id(&id));
+        T3D_REQUIRE(id != 0, "no current CUDA context after the symbol lookup");
+        c.ctx_id = id;
+        c.addr = p;
     }
-    *out = g_scratch_addr[dev];
+    *out = c.addr;
     return T3D_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -36,6 +37,11 @@ struct Plan {
     uint64_t* s_raw[kMaxItems];
     uint8_t* gate[kMaxItems];
     uint64_t* gate_scratch[kMaxItems];
+    uint32_t gate_weight[kMaxItems];   // fallback threshold of each item
+    uint32_t* wsrc[kMaxItems];         // flagged words, compacted
+    int64_t* live[kMaxItems];          // their number (device)
+    uint64_t* e_c[kMaxItems];          // the flagged words' e and s columns, compacted
+    uint64_t* s_c[kMaxItems];
     unsigned long long* n_fallback[kMaxItems];
     void* cnn_work[kMaxItems];
     int64_t cnn_chunk[kMaxItems];  // pre-decoder chunk, words
@@ -71,6 +77,7 @@ t3d_status validate_cfg(const t3d_run_cfg* c)
         T3D_REQUIRE(!c->use_bp, "the learned decoder replaces BP: use_bp must be 0");
         T3D_REQUIRE(aligned(c->cnn_blob, 16), "cnn_blob must be 16-byte aligned");
         T3D_REQUIRE(c->fallback_max_weight < 0 || c->bp_iters > 0, "the BP fallback needs bp_iters > 0");
+        T3D_REQUIRE(c->fallback_sigmas >= 0.0 && c->fallback_sigmas <= 1000.0, "fallback_sigmas must lie in [0, 1000]");
     }
     if (c->use_bp || (c->cnn_blob && c->fallback_max_weight >= 0)) {
         T3D_REQUIRE(c->p > 0.0 && c->p < 1.0, "BP needs 0 < p < 1");
@@ -139,12 +146,30 @@ int64_t cnn_chunk_words(const t3d_run_cfg& c, int L, int64_t n_samples)
     return std::min(Wi, std::max<int64_t>(2, words_for(fit)));
 }
 
+// Fallback threshold of a lattice: fallback_max_weight, plus with
+// fallback_sigmas > 0 the expected number of measurement errors among the 3L^3
+// checks and that many standard deviations (binomial): a sample is sent back to
+// BP when its decoded syndrome keeps more unsatisfied checks than the noisy
+// measurement alone explains.
+uint32_t fallback_weight(const t3d_run_cfg& c, int L)
+{
+    double w = (double)c.fallback_max_weight;
+    if (c.fallback_sigmas > 0.0) {
+        const double n = 3.0 * L * L * L;
+        w += std::floor(c.q * n + c.fallback_sigmas * std::sqrt(c.q * (1.0 - c.q) * n));
+    }
+    return (uint32_t)std::min(w, 4294967295.0);
+}
+
 size_t learned_bytes(const t3d_run_cfg& c, int L, int64_t n_samples)
 {
     const int64_t cw = cnn_chunk_words(c, L, n_samples);
     size_t b = round_up(state_bytes(L, n_samples)) + round_up(cnn_workspace_bytes(L, std::min(n_samples, cw * 64)));
-    if (c.fallback_max_weight >= 0)
-        b += round_up((size_t)words_for(n_samples)) + round_up(gate_scratch_bytes(L, words_for(n_samples)));
+    if (c.fallback_max_weight >= 0) {
+        const int64_t Wi = words_for(n_samples);
+        b += round_up((size_t)Wi) + round_up(gate_scratch_bytes(L, Wi)) + round_up((size_t)Wi * sizeof(uint32_t)) +
+             round_up(sizeof(int64_t)) + 2 * round_up(state_bytes(L, n_samples));
+    }
     return b;
 }
 
@@ -202,6 +227,15 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
                 used += round_up((size_t)Wi);
                 pl.gate_scratch[i] = reinterpret_cast<uint64_t*>(base + used);
                 used += round_up(gate_scratch_bytes(items[i].L, Wi));
+                pl.wsrc[i] = reinterpret_cast<uint32_t*>(base + used);
+                used += round_up((size_t)Wi * sizeof(uint32_t));
+                pl.live[i] = reinterpret_cast<int64_t*>(base + used);
+                used += round_up(sizeof(int64_t));
+                pl.e_c[i] = reinterpret_cast<uint64_t*>(base + used);
+                used += sb;
+                pl.s_c[i] = reinterpret_cast<uint64_t*>(base + used);
+                used += sb;
+                pl.gate_weight[i] = fallback_weight(c, items[i].L);
             }
             const int64_t cw = cnn_chunk_words(c, items[i].L, items[i].n_samples);
             pl.cnn_work[i] = base + used;
@@ -260,17 +294,26 @@ t3d_status enqueue_learned_cycle(const t3d_run_cfg& c, const Plan& pl, uint32_t 
         T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
     }
     if (c.fallback_max_weight >= 0) {
-        ItemTable gated = pl.items;
-        for (int i = 0; i < gated.n; ++i) {
-            const ItemDesc& d = gated.it[i];
-            T3D_TRY(launch_gate(d.lat, d.W, d.s, (uint32_t)c.fallback_max_weight, pl.gate[i], pl.n_fallback[i],
+        // the flagged words' columns are compacted to the front of two scratch arrays, decoded
+        // there (BP + the schedule, every launch walking only the live words) and copied back
+        for (int i = 0; i < pl.items.n; ++i) {
+            const ItemDesc& d = pl.items.it[i];
+            T3D_TRY(launch_gate(d.lat, d.W, d.s, pl.gate_weight[i], pl.gate[i], pl.n_fallback[i],
                                 pl.gate_scratch[i], st));
-            gated.it[i].gate = pl.gate[i];
-        }
-        T3D_TRY(launch_bp(gated, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, pl.bp, pl.chunk, nullptr, st));
-        if (c.n_apply > 0) {
-            tab = gated;
-            T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
+            T3D_TRY(launch_compact_words(pl.gate[i], d.W, pl.wsrc[i], pl.live[i], st));
+            T3D_TRY(launch_move_words(d.lat, d.W, pl.live[i], pl.wsrc[i], d.e, pl.e_c[i], d.s, pl.s_c[i], true, st));
+            ItemTable one;
+            std::memset(&one, 0, sizeof(one));
+            one.n = 1;
+            one.it[0] = d;
+            one.it[0].e = pl.e_c[i];
+            one.it[0].s = pl.s_c[i];
+            one.it[0].live = pl.live[i];
+            one.it[0].wsrc = pl.wsrc[i];
+            T3D_TRY(launch_bp(one, c.p, c.bp_meas_nodes ? c.q : 0.0, c.bp_iters, &pl.bp[i], &pl.chunk[i], nullptr,
+                              st));
+            if (c.n_apply > 0) T3D_TRY(launch_sweeps(one, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
+            T3D_TRY(launch_move_words(d.lat, d.W, pl.live[i], pl.wsrc[i], d.e, pl.e_c[i], d.s, pl.s_c[i], false, st));
         }
     }
     for (int i = 0; i < pl.items.n; ++i) T3D_TRY(copy_rows(pl.s_prev[i], pl.s_raw[i], pl.items.it[i], 0, pl.items.it[i].W, st));
@@ -339,6 +382,7 @@ struct GraphKey {
 struct GraphEntry {
     GraphKey key;
     cudaGraphExec_t exec;
+    cudaEvent_t done;    // recorded after every launch of exec
     bool used;
 };
 
@@ -364,6 +408,7 @@ t3d_status run_with_graph(const t3d_run_cfg& c, const t3d_batch_item* items, int
     for (auto& g : g_graphs) {
         if (g.used && std::memcmp(&g.key, &key, sizeof(GraphKey)) == 0) {
             T3D_CUDA_CHECK(cudaGraphLaunch(g.exec, st));
+            T3D_CUDA_CHECK(cudaEventRecord(g.done, st));
             return T3D_OK;
         }
     }
@@ -387,16 +432,31 @@ t3d_status run_with_graph(const t3d_run_cfg& c, const t3d_batch_item* items, int
         return T3D_ECUDA;
     }
     GraphEntry& slot = g_graphs[g_graph_next];
-    g_graph_next = (g_graph_next + 1) % kGraphCache;
     if (slot.used) {
-        // the evicted graph may still be running on its stream: wait before freeing it
-        cudaStreamSynchronize(slot.key.stream);
+        // the evicted graph's last launch may still be running: wait for it (its event,
+        // not its stream, which the caller may have destroyed since) before freeing it
+        cudaError_t w = cudaEventSynchronize(slot.done);
+        if (w != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            set_error("waiting for an evicted run graph failed: %s", cudaGetErrorString(w));
+            return T3D_ECUDA;
+        }
         cudaGraphExecDestroy(slot.exec);
+        slot.used = false;
+    } else {
+        cudaError_t ce = cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming);
+        if (ce != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            set_error("cudaEventCreate failed: %s", cudaGetErrorString(ce));
+            return T3D_ECUDA;
+        }
     }
+    g_graph_next = (g_graph_next + 1) % kGraphCache;
     slot.key = key;
     slot.exec = exec;
     slot.used = true;
     T3D_CUDA_CHECK(cudaGraphLaunch(exec, st));
+    T3D_CUDA_CHECK(cudaEventRecord(slot.done, st));
     return T3D_OK;
 }
 

@@ -165,7 +165,7 @@ BP_CHUNK_BYTES = 48 << 30
 
 def evaluate(L: int, p: float, T: int, n_samples: int, params: np.ndarray | None, seed: int,
              fallback_max_weight: int = -1, dec: Decoder | None = None, use_graph: bool = True,
-             device="cuda:0"):
+             device="cuda:0", fallback_sigmas: float = 0.0):
     """One whole run of T noisy cycles through toric3d_run_batch, decoded by
     BP + p-flip (params is None) or by the learned pre-decoder + p-flip (with
     the BP + p-flip fallback when fallback_max_weight >= 0).  Returns the
@@ -190,6 +190,7 @@ def evaluate(L: int, p: float, T: int, n_samples: int, params: np.ndarray | None
     cfg = make_run_cfg(L, T, p, dec.q, dec.seed, n_samples, use_bp=params is None, bp_iters=dec.bp_iters,
                        schedule=dec.schedule, n_apply=dec.n_apply, use_graph=use_graph, cnn_blob=blob,
                        fallback_max_weight=fallback_max_weight if params is not None else -1,
+                       fallback_sigmas=fallback_sigmas if params is not None else 0.0,
                        bp_chunk_samples=chunk if params is None else 0)
     work = torch.empty(toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -207,6 +208,34 @@ def failure_rate(counts) -> float:
     """Fraction of samples with a logical error on any of the three logical qubits."""
     counts = np.asarray(counts)
     return float(counts[1:].sum() / max(1, counts.sum()))
+
+
+def wilson_interval(k: int, n: int, z: float = 1.959964) -> tuple[float, float]:
+    """95% Wilson score interval of a binomial proportion k / n."""
+    if n == 0:
+        return 0.0, 1.0
+    ph = k / n
+    den = 1 + z * z / n
+    mid = (ph + z * z / (2 * n)) / den
+    half = z * np.sqrt(ph * (1 - ph) / n + z * z / (4 * n * n)) / den
+    return max(0.0, mid - half), min(1.0, mid + half)
+
+
+def two_proportion_test(k1: int, n1: int, k2: int, n2: int) -> dict:
+    """Is the second failure rate higher than the first?  One-sided pooled z-test and
+    Fisher's exact test (the latter also where the counts are small or zero)."""
+    from math import erf, sqrt
+    p1, p2 = k1 / n1, k2 / n2
+    pool = (k1 + k2) / (n1 + n2)
+    se = sqrt(pool * (1 - pool) * (1 / n1 + 1 / n2))
+    z = (p2 - p1) / se if se > 0 else 0.0
+    out = {"z": z, "p_one_sided_z": 0.5 * (1 - erf(z / sqrt(2))) if se > 0 else 1.0}
+    try:
+        from scipy.stats import fisher_exact
+        out["p_one_sided_fisher"] = float(fisher_exact([[k2, n2 - k2], [k1, n1 - k1]], alternative="greater")[1])
+    except ImportError:
+        pass
+    return out
 
 
 def save_params(path: str, params: np.ndarray, **meta):
@@ -242,6 +271,8 @@ def _main(argv=None):
     e.add_argument("--T", type=int, default=0, help="cycles (default L)")
     e.add_argument("--seed", type=int, default=1234)
     e.add_argument("--fallback-max-weight", type=int, default=-1)
+    e.add_argument("--fallback-sigmas", type=float, default=0.0,
+                   help="add q 3L^3 + this many binomial standard deviations to the fallback threshold")
     e.add_argument("--weights", default=os.path.join(os.path.dirname(__file__), "weights", "cnn_L12_p04.npz"))
     e.add_argument("--no-bp", action="store_true", help="skip the BP + p-flip comparison run")
     a = ap.parse_args(argv)
@@ -259,9 +290,17 @@ def _main(argv=None):
         if not a.no_bp:
             legs.insert(0, ("bp_pflip", None, -1))
         for name, prm, fb in legs:
-            counts, ms, words = evaluate(a.L, p, T, a.samples, prm, a.seed, fallback_max_weight=fb)
-            row[name] = {"failure_rate": failure_rate(counts), "counts": counts.tolist(), "ms": ms,
-                         "qubit_cycles_per_s": n_bits(a.L) * a.samples * T / (ms / 1e3), "fallback_words": words}
+            counts, ms, words = evaluate(a.L, p, T, a.samples, prm, a.seed, fallback_max_weight=fb,
+                                         fallback_sigmas=a.fallback_sigmas)
+            k = int(np.asarray(counts)[1:].sum())
+            row[name] = {"failure_rate": failure_rate(counts), "failures": k,
+                         "ci95": wilson_interval(k, a.samples), "counts": counts.tolist(), "ms": ms,
+                         "qubit_cycles_per_s": n_bits(a.L) * a.samples * T / (ms / 1e3), "fallback_words": words,
+                         "fallback_word_fraction": words / (T * words_for(a.samples))}
+        if "bp_pflip" in row:
+            row["learned_worse_than_bp"] = two_proportion_test(row["bp_pflip"]["failures"], a.samples,
+                                                               row["learned_pflip"]["failures"], a.samples)
+            row["speedup"] = row["learned_pflip"]["qubit_cycles_per_s"] / row["bp_pflip"]["qubit_cycles_per_s"]
         print(json.dumps(row), flush=True)
     return 0
 

@@ -142,3 +142,38 @@ def test_cnn_full_size_sampled_decisions():
                     assert eb[d * L ** 3 + r] == int(z[d] > 0), (j, r, d, z[d])
                     checked += 1
     assert checked > 600
+
+
+def test_cnn_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A 1 ns bound makes the tensor-core kernels' waits run out (nothing faults:
+    the wind-down still drains the kernel's own copies and MMAs for up to 1 s and
+    frees its TMEM).  The status call reports T3D_ETIMEOUT once; with the bound
+    restored the same decode on the same context matches the reference."""
+    L, S = 4, 96
+    n = 3 * L ** 3
+    params = ref.random_params(L)
+    sp = inp.random_bits(S, n, 0.15, 10 + L)
+    sc = inp.random_bits(S, n, 0.15, 20 + L)
+    _, blob = _blob(params)
+    work = workspace(t3d.toric3d_cnn_workspace_bytes(L, S))
+    logits = torch.zeros((3, L ** 3, S), dtype=torch.float32, device=dev())
+    t3d.toric3d_cnn_status()                                   # start from a clear flag
+    t3d.toric3d_cnn_debug_wait_limit(1)
+    try:
+        t3d.toric3d_cnn_decode(L, S, upload_bits(sp), upload_bits(sc), upload_bits(np.zeros_like(sc)), blob, work,
+                               logits)
+        with pytest.raises(t3d.T3DError) as exc:
+            t3d.toric3d_cnn_status()
+        assert exc.value.status == 3                           # T3D_ETIMEOUT
+        t3d.toric3d_cnn_status()                               # the flag was cleared by the read
+    finally:
+        t3d.toric3d_cnn_debug_wait_limit(0)
+    with pytest.raises(t3d.T3DError):
+        t3d.toric3d_cnn_debug_wait_limit(2_000_000_000)        # above the 1 s maximum
+    e = upload_bits(np.zeros_like(sc))
+    t3d.toric3d_cnn_decode(L, S, upload_bits(sp), upload_bits(sc), e, blob, work, logits)
+    torch.cuda.synchronize()
+    t3d.toric3d_cnn_status()
+    g = logits.cpu().numpy().transpose(2, 0, 1).reshape(S, 3, -1)
+    z = ref.logits(params, L, sp, sc).numpy()
+    assert np.abs(g - z).max() < 0.02 + 0.01 * np.abs(z).max()

@@ -82,7 +82,7 @@ def _stepwise(L, S, T, blob, max_w, sample0=0):
     return download_bits(e, S), download_bits(s_prev, S), flagged
 
 
-def _run(L, S, T, blob, max_w, chunk=0, use_graph=False, split=None):
+def _run(L, S, T, blob, max_w, chunk=0, use_graph=False, split=None, sigmas=0.0):
     n, W = 3 * L ** 3, inp.words_for(S)
     e = torch.zeros((n, W), dtype=torch.int64, device=dev())
     s_prev = torch.zeros_like(e)
@@ -97,7 +97,7 @@ def _run(L, S, T, blob, max_w, chunk=0, use_graph=False, split=None):
             cfg = t3d.make_run_cfg(L, t, DEC["p"], DEC["p"], DEC["seed"], S, schedule=DEC["schedule"],
                                    n_apply=DEC["n_apply"], bp_iters=DEC["bp_iters"], cnn_blob=blob,
                                    fallback_max_weight=max_w, bp_chunk_samples=chunk, cycle0=cycle0,
-                                   use_graph=use_graph)
+                                   use_graph=use_graph, fallback_sigmas=sigmas)
             work = workspace(t3d.toric3d_run_batch_workspace_bytes(cfg, batch))
             t3d.toric3d_run_batch(cfg, batch, work)
     stream.synchronize()
@@ -129,3 +129,19 @@ def test_learned_run_chunks_graphs_and_splits_are_invisible():
         assert np.array_equal(got[1], base[1]), kw
         assert got[2] == base[2], kw
         assert np.array_equal(got[3], base[3]), kw
+
+
+@pytest.mark.parametrize("L,S,sigmas", [(5, 200, 1.0), (4, 64 * 7 + 3, 0.5)])
+def test_fallback_threshold_from_measurement_noise(L, S, sigmas):
+    """fallback_sigmas adds floor(q n + k sqrt(q (1 - q) n)), n = 3L^3, to the threshold:
+    the run equals the stepwise cycle gated at that weight, words past the first flagged
+    ones included (the flagged words are compacted before BP and the schedule)."""
+    n = 3 * L ** 3
+    q = DEC["p"]
+    thr = int(np.floor(q * n + sigmas * np.sqrt(q * (1 - q) * n)))
+    blob = _blob(11)
+    e_ref, sp_ref, flagged = _stepwise(L, S, 3, blob, thr)
+    e, sp, fb, _ = _run(L, S, 3, blob, 0, sigmas=sigmas)
+    print(f"threshold {thr}: {flagged} fallback words")
+    assert flagged > 0
+    assert np.array_equal(e, e_ref) and np.array_equal(sp, sp_ref) and fb == flagged
