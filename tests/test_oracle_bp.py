@@ -135,6 +135,43 @@ def test_half_cube_correction_is_all_or_nothing(p, meas):
         assert positive_seen
 
 
+@pytest.mark.parametrize("L", [4, 6])
+@pytest.mark.parametrize("p", [0.03, 0.04, 0.051, 0.0546, 0.06])
+def test_half_cube_keeps_every_llr_positive_with_30_iterations(L, p):
+    """Sec. 4.1 on the half-cube error: BP cannot choose between the two halves of the
+    stabiliser, every qubit of its support keeps l > 0 and nothing is corrected.  At the
+    paper's BP setting (30 iterations per cycle, measurement variables, p = q) that holds
+    exactly: all six posteriors of the vertex are positive and the error is unchanged."""
+    V = (1, 1, 2)
+    six = [vertex_edge(L, V, sp) for sp in ["+x", "-x", "+y", "-y", "+z", "-z"]]
+    for spec in (["+x", "+y", "+z"], ["-x", "+y", "-z"]):
+        e = edges_at_vertex(L, V, spec)
+        s = oracle.syndrome(L, e)
+        e2, s2, llr = oracle.bp_decode(L, e, s, p, p, True, 30)
+        assert (llr[six] > 0).all() and (llr > 0).all()
+        assert np.array_equal(e2, e) and np.array_equal(s2, s)
+
+
+@pytest.mark.parametrize("p", [0.04, 0.0544, 0.06])
+def test_half_cube_at_20_iterations_applies_the_whole_stabiliser(p):
+    """Known departure from the Sec. 4.1 statement at p-BP's 20 iterations (Sec. 4.2): the
+    flooding schedule oscillates on this syndrome with period 4 (the six posteriors are
+    negative at iterations 2-3, 6-7, 10-11, 14-15, 18-19 and 20), so BP applies the whole
+    stabiliser -- which leaves the other half of it, an equivalent error, so the paper's
+    point that BP does no harm holds, but not its l > 0.  The readings of BP inside a run
+    in readings.py (warm start, half-iteration counting, measurement decisions) do not
+    change this: the qubits' posteriors of one decode are the same in all of them but the
+    half-iteration count, which moves the decision to 10 iterations (negative too)."""
+    L, V = 4, (1, 1, 2)
+    six = [vertex_edge(L, V, sp) for sp in ["+x", "-x", "+y", "-y", "+z", "-z"]]
+    e = edges_at_vertex(L, V, ["+x", "+y", "+z"])
+    s = oracle.syndrome(L, e)
+    e2, s2, llr = oracle.bp_decode(L, e, s, p, p, True, 20)
+    assert (llr[six] < 0).all()
+    assert np.array_equal(e2 ^ e, stabiliser(L, V)) and np.array_equal(s2, s)
+    assert oracle.logical(L, e2)[0] == oracle.logical(L, e)[0]
+
+
 def test_bp_posterior_commutes_with_lattice_symmetries():
     L, p = 4, 0.04
     n = 3 * L ** 3
