@@ -204,11 +204,12 @@ class ClockSampler:
 # Algorithmic FLOPs of the pre-decoder per site and sample: three 3x3x3
 # convolutions (6 -> 16, 16 -> 16, 16 -> 16 channels) and the 16 -> 3 head.
 CNN_FLOP_PER_SITE = 2 * 27 * 16 * (6 + 16 + 16) + 2 * 16 * 3
-# Tensor-core FLOPs the kernels execute per site and sample (N = 8 sites x 16
-# channels per MMA including the zero blocks of the weight strips; the first
-# layer pairs two sites per K = 16): 90 MMAs of 128 x 128 x 16 per 8 x 128
-# site-samples for the hidden layers, 45 for the first.
-CNN_MMA_FLOP_PER_SITE = (45 + 90 + 90) * 2 * 128 * 128 * 16 / (8 * 128)
+# Tensor-core FLOPs the kernels execute per site and sample (2 x 2 columns of
+# output sites; each MMA spans the TMEM columns an input tile reaches, zero
+# blocks included): 168 weight blocks of 16 x 16 per input plane of a column
+# (4 sites) and 128 samples in a hidden layer, 88 in the first (two sites per
+# K = 16), each block 128 x 16 x 16 multiply-adds.
+CNN_MMA_FLOP_PER_SITE = (88 + 168 + 168) * 2 * 128 * 16 * 16 / (4 * 128)
 WEIGHTS = os.path.join(ROOT, "paper_2212_06985_gb300", "weights", "cnn_L12_p04.npz")
 
 
@@ -297,7 +298,7 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
         "value": qubits * S * world * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
         "gpu_launches": sum(v[1] for v in prof.values()),
         "kernels_ms": {k: v[0] for k, v in prof.items() if v[1]},
-        "roofline": {"kernel": "k_conv_tc (3 layers) + k_expand_bits + k_dec_apply", "bound": "tensor",
+        "roofline": {"kernel": "k_conv_col (3 layers) + k_expand_bits + k_dec_apply", "bound": "tensor",
                      "achieved": achieved, "peak": tf_peak, "unit": "TFLOP/s", "frac": achieved / tf_peak,
                      "traffic": None,
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)" if peaks
@@ -318,6 +319,55 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
         "logical_counts_after_cycles": args.warmup + args.steps,
         "chunk_samples": learned_chunk(max(sizes), S, args.learned_chunk),
     }
+
+
+# Flip / p-flip cycles.  Algorithmic bytes per qubit-sample of one launch of each
+# kernel kind: noise reads and writes e (0.25 B); the measurement reads e and
+# writes s (0.25 B); a flip application reads s and e and writes both (0.5 B);
+# a p-flip application (decision pass + syndrome pass) also writes and reads
+# the flip words (0.875 B).
+SWEEP_BYTES = {"noise": 0.25, "syndrome": 0.25, "flip": 0.5, "pflip": 0.875}
+# Warp instructions per 64-sample word of each qubit (noise), check (syndrome)
+# or site (one p-flip application) at p = q = 4%, from one ncu capture of the
+# current kernels (smsp__inst_executed.sum over the launch's words); None until
+# captured.  The Philox arithmetic binds these kernels on the issue rate.
+SWEEP_INST = {"noise": None, "syndrome": None, "pflip": None}
+
+
+def sweep_roofline(prof, w, qubits, S, steps, ms, hbm_peak, peak_source, clk):
+    """Roofline of the dominant kernel of a flip / p-flip cycle: HBM for the flip
+    application, the instruction-issue rate (152 SMs x 4 schedulers x 1 warp
+    instruction per clock at the sampled SM clock) for the Philox-bound kernels
+    once their instruction counts are known; the whole cycle's HBM fraction beside."""
+    n_p = sum(1 for k in range(w.n_apply) if w.schedule[k % len(w.schedule)] == "P")
+    per_step = {"noise": 1, "syndrome": 1, "flip": w.n_apply - n_p, "pflip": n_p}
+    kinds = {k: prof[k] for k in SWEEP_BYTES if prof[k][1]}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    d_ms, d_launches = kinds[dom]
+    apps = per_step[dom] * steps                      # applications (a p-flip one is two launches)
+    t_app = d_ms / apps / 1e3
+    words = (S + 63) // 64
+    cycle_bytes = sum(SWEEP_BYTES[k] * per_step[k] for k in SWEEP_BYTES) * qubits * S * steps
+    out = {"kernel": {"noise": "k_noise", "syndrome": "k_syndrome", "flip": "k_flip_tiled",
+                      "pflip": "k_pflip_decide + k_pflip_apply"}[dom],
+           "launches": d_launches, "avg_launch_ms": d_ms / d_launches, "ms_per_application": 1e3 * t_app,
+           "share_of_step": d_ms / ms, "cycle_hbm_frac": cycle_bytes / (ms / 1e3) / 1e9 / hbm_peak,
+           "kernels_hbm_frac": {k: SWEEP_BYTES[k] * qubits * S * steps * per_step[k] / (v[0] / 1e3) / 1e9 / hbm_peak
+                                for k, v in kinds.items()},
+           "traffic": None, "peak_source": peak_source}
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    units = {"noise": qubits, "syndrome": qubits, "pflip": qubits // 3}   # edges, faces, sites
+    if SWEEP_INST.get(dom):
+        peak = 152 * 4 * sm_mhz * 1e6 / 1e9
+        achieved = SWEEP_INST[dom] * units[dom] * words / t_app / 1e9
+        out.update(bound="alu", achieved=achieved, peak=peak, unit="Ginst/s", frac=achieved / peak,
+                   peak_derivation=f"152 SMs x 4 schedulers x 1 warp instruction/clock x {sm_mhz:.0f} MHz")
+    else:
+        alg = SWEEP_BYTES[dom] * qubits * S
+        achieved = alg / t_app / 1e9
+        out.update(bound="hbm", achieved=achieved, peak=hbm_peak, unit="GB/s", frac=achieved / hbm_peak,
+                   algorithmic_bytes_per_application=alg)
+    return out
 
 
 def cuda_arm(args):
@@ -400,26 +450,29 @@ def cuda_arm(args):
     total_qc = qubits * S * world * args.steps
     value = total_qc / (ms / 1e3)
 
-    # dominant kernel: BP iteration (algorithmic bytes per edge-sample: 16 B read + 16 B written;
-    # the first iteration of each chunk reads nothing)
-    bp_ms, bp_launches = prof["bp_step"]
-    rounds = math.ceil(S / chunk)
-    alg_bytes = qubits * S * args.steps * (32.0 * (w.bp_iters - 1) + 16.0)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = alg_bytes / (bp_ms / 1e3) / 1e9 if bp_ms > 0 else 0.0
-    traffic = None
-    if BP_STEP_TRAFFIC and bp_launches:
-        traffic = qubits * S * args.steps * (BP_STEP_TRAFFIC["first_iteration"] +
-                                             BP_STEP_TRAFFIC["full_iteration"] * (w.bp_iters - 1)) / bp_launches
-    roofline = {"kernel": "k_bp_step", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s",
-                "launches": bp_launches, "avg_launch_ms": bp_ms / max(bp_launches, 1),
-                "share_of_step": bp_ms / ms if ms else None,
-                "expected_launches": w.bp_iters * rounds * args.steps,
-                "algorithmic_bytes_per_launch": alg_bytes / max(bp_launches, 1)}
+    peak_source = "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6.8 TB/s"
+    if kw["use_bp"]:
+        # dominant kernel: BP iteration (algorithmic bytes per edge-sample: 16 B read + 16 B
+        # written; the first iteration of each chunk reads nothing)
+        bp_ms, bp_launches = prof["bp_step"]
+        rounds = math.ceil(S / chunk)
+        alg_bytes = qubits * S * args.steps * (32.0 * (w.bp_iters - 1) + 16.0)
+        achieved = alg_bytes / (bp_ms / 1e3) / 1e9 if bp_ms > 0 else 0.0
+        traffic = None
+        if BP_STEP_TRAFFIC and bp_launches:
+            traffic = qubits * S * args.steps * (BP_STEP_TRAFFIC["first_iteration"] +
+                                                 BP_STEP_TRAFFIC["full_iteration"] * (w.bp_iters - 1)) / bp_launches
+        roofline = {"kernel": "k_bp_step", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_source,
+                    "launches": bp_launches, "avg_launch_ms": bp_ms / max(bp_launches, 1),
+                    "share_of_step": bp_ms / ms if ms else None,
+                    "expected_launches": w.bp_iters * rounds * args.steps,
+                    "algorithmic_bytes_per_launch": alg_bytes / max(bp_launches, 1)}
+    else:
+        roofline = sweep_roofline(prof, w, qubits, S, args.steps, ms, hbm_peak, peak_source, clk)
 
     # end-to-end: the error states round-trip through pinned host memory every step
     e2e = None

@@ -56,6 +56,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -123,7 +124,8 @@ struct TcArgs {
     int64_t n_samples;
     int64_t W;                  // row stride of the bit-sliced arrays (words)
     int64_t words;              // words of this pass
-    int nbx;                    // lines of 8 sites along x
+    int nbx;                    // line kernel: lines of 8 sites along x
+    int ncx;                    // column kernel: 2 x 2 columns per axis (ceil(L / 2))
     int64_t n_units;
     const uint8_t* in;          // input activations
     uint8_t* out;               // hidden layers: output activations
@@ -258,6 +260,35 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         "}\n" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(kIdesc), "r"(accumulate)
         : "memory");
+}
+
+// The same with an instruction descriptor chosen per MMA (N varies).
+__device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc)
+{
+    asm volatile(
+        "{\n"
+        ".reg .pred pa;\n"
+        "setp.ne.b32 pa, 1, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc)
+        : "memory");
+}
+
+// Warp: zero 32 TMEM lanes x 16 consecutive 32-bit columns (one lane per thread).
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr)
+{
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};\n" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Arrive on the barrier once every MMA this thread issued so far has completed.
@@ -617,6 +648,364 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     }
 }
 
+// ------------------------------------------------------------------ column kernel
+// The convolution with dense operands: a work unit is one 128-sample tile x one
+// 2 x 2 column of output sites (x0, x0 + 1) x (y0, y0 + 1) run through all L
+// planes in z.  Every input site (xi, yi) of an input plane zi with
+// xi = x0 - 1 .. x0 + 2, yi = y0 - 1 .. y0 + 2 feeds the column sites within
+// one step of it in x and y, in the three output planes zi - 1, zi, zi + 1;
+// TMEM keeps eight output planes of 64 columns (4 sites x 16 channels, site
+// j = jx + 2 jy) in a ring, so one MMA covers the input tile's whole reach:
+// the columns from (plane zi - 1, its lowest site lo) to (plane zi + 1, its
+// highest site hi), N = 16 (4 (P2 - P1) + hi - lo + 1) for the planes P1..P2
+// that exist (N = 192 for the four inner sites).  Its B operand is a window of
+// one per-position sequence of weight blocks [plane zi - 1: sites lo..3 |
+// plane zi: 0..3 | plane zi + 1: 0..hi], W(xi - xo, yi - yo, zi - zo) or zero
+// where the site is out of reach; of the blocks multiplied 64% are non-zero
+// (108 of 168 per plane; the line kernel: 30%).  A window that would cross
+// the ring's end is split in two MMAs.  TMEM columns are zeroed by the
+// epilogue after it drains a plane (and once at the start), so every MMA
+// accumulates.  The first layer pairs x-adjacent input sites in one K = 16
+// operand (chunk c = site 2p - 1 + c of the row) as the line kernel does.
+constexpr int kColRows = 8;                               // input rows (4 tiles, one y and z) in flight
+constexpr int kColRowBytes = 4 * kSlotBytes;              // 16 KiB (first layer: 8 KiB used)
+constexpr int kColSlots = 8;                              // output planes resident in TMEM
+constexpr int kColPlaneCols = 4 * kC;                     // 64
+constexpr int kColWBlocks = 168;                          // windows of the 16 positions (hidden layers)
+constexpr int kColOffW = kColRows * kColRowBytes;
+constexpr int kColOffBar = kColOffW + kColWBlocks * 512;
+constexpr int kColNumBars = 2 * kColRows + 2 * kColSlots + 1;   // full, empty, acc_full, acc_empty, done
+constexpr int kColOffMisc = kColOffBar + kColNumBars * 8;
+constexpr int kColOffPos = kColOffMisc + 16;              // ColPos[16]
+constexpr int kColSmemBytes = kColOffPos + 16 * 12 + 1024;
+static_assert(kColSmemBytes <= 227 * 1024, "shared memory budget");
+static_assert(kColSlots * kColPlaneCols == 512, "TMEM ring");
+
+// Operand position p of a row (hidden: the site x0 - 1 + p; first layer: the
+// pair x0 - 1 + 2p, x0 + 2p) at row b (yi = y0 - 1 + b): the column sites in
+// reach span lo..hi, and its weight sequence starts at block base.
+struct ColPos {
+    int base, lo, hi;
+};
+
+__host__ __device__ inline int col_chunk_dx(bool bits_in, int p, int c) { return bits_in ? 2 * p - 1 + c : p - 1; }
+
+__host__ __device__ inline bool col_reach(bool bits_in, int p, int jx)
+{
+    for (int c = 0; c < 2; ++c) {
+        const int dx = col_chunk_dx(bits_in, p, c) - jx;
+        if (dx >= -1 && dx <= 1) return true;
+    }
+    return false;
+}
+
+__host__ __device__ inline ColPos col_pos(bool bits_in, int p, int b)
+{
+    const int P = bits_in ? 2 : 4;
+    int base = 0;
+    ColPos r = {0, 0, 0};
+    for (int bb = 0; bb < 4; ++bb)
+        for (int pp = 0; pp < P; ++pp) {
+            int jx_lo = 2, jx_hi = -1;
+            for (int jx = 0; jx < 2; ++jx)
+                if (col_reach(bits_in, pp, jx)) {
+                    jx_lo = jx < jx_lo ? jx : jx_lo;
+                    jx_hi = jx;
+                }
+            const int jy_lo = bb == 3 ? 1 : 0, jy_hi = bb == 0 ? 0 : 1;   // yi - yo in -1..1
+            const int lo = jx_lo + 2 * jy_lo, hi = jx_hi + 2 * jy_hi;
+            if (bb == b && pp == p) {
+                r.base = base;
+                r.lo = lo;
+                r.hi = hi;
+            }
+            base += (4 - lo) + 4 + (hi + 1);
+        }
+    return r;
+}
+
+__device__ __forceinline__ Unit col_unit_of(const TcArgs& a, int64_t u)
+{
+    const int64_t cols = (int64_t)a.ncx * a.ncx;
+    const int64_t tile = u / cols;
+    const int rem = (int)(u - tile * cols);
+    Unit t;
+    t.m0 = tile * kTileM;
+    t.y = (rem / a.ncx) * 2;
+    t.x0 = (rem % a.ncx) * 2;
+    t.fx = 0;
+    return t;
+}
+
+template <bool kHead, bool kBitsIn>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constant__ TcArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t ring = smem_u32(sm);
+    const uint32_t wsm = ring + kColOffW;
+    const uint32_t bars = ring + kColOffBar;
+    auto full_bar = [&](int i) { return bars + 8u * (uint32_t)i; };
+    auto empty_bar = [&](int i) { return bars + 8u * (uint32_t)(kColRows + i); };
+    auto accf_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColRows + i); };
+    auto acce_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColRows + kColSlots + i); };
+    const uint32_t done_bar = bars + 8u * (uint32_t)(2 * kColRows + 2 * kColSlots);
+    uint32_t* misc = reinterpret_cast<uint32_t*>(sm + kColOffMisc);   // [0] TMEM base, [1] abort flag
+    volatile uint32_t* abort_flag = misc + 1;
+    ColPos* s_pos = reinterpret_cast<ColPos*>(sm + kColOffPos);   // [b * P + p]
+    constexpr int P = kBitsIn ? 2 : 4;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x < 4 * P) s_pos[threadIdx.x] = col_pos(kBitsIn, threadIdx.x % P, threadIdx.x / P);
+    __syncthreads();
+    // weight windows: for every position (p, b) and element e of its sequence, block
+    // W(dx, dy, dz) in the B-operand layout [co/8][chunk][co%8][ci%8], zero out of reach
+    {
+        const ColPos last = s_pos[4 * P - 1];
+        const int n_blocks = last.base + (4 - last.lo) + 4 + (last.hi + 1);
+        for (int i = threadIdx.x; i < n_blocks * 256; i += blockDim.x) {
+            const int blk = i >> 8, co = (i >> 4) & 15, kk = i & 15;   // kk = chunk * 8 + ci
+            // the position owning block blk
+            int pb = 0;
+            while (pb + 1 < 4 * P && s_pos[pb + 1].base <= blk) ++pb;
+            const ColPos pos = s_pos[pb];
+            const int p = pb % P, b = pb / P;
+            const int e = blk - pos.base;
+            const int part = (e + pos.lo) >> 2, j = (e + pos.lo) & 3;   // block index = 4 part + j - lo
+            const int jx = j & 1, jy = j >> 1;
+            const int c = kk >> 3, ci = kk & 7;
+            const int dx = col_chunk_dx(kBitsIn, p, c) - jx;
+            const int dy = (b - 1) - jy;
+            const int dz = 1 - part;
+            __nv_bfloat16 w = __float2bfloat16_rn(0.0f);
+            const int ch = kBitsIn ? ci : c * 8 + ci;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) {
+                const int k = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                w = a.w[(k * kC + co) * kC + ch];
+            }
+            *reinterpret_cast<__nv_bfloat16*>(sm + kColOffW + blk * 512 + (co >> 3) * 256 + c * 128 + (co & 7) * 16 +
+                                              ci * 2) = w;
+        }
+    }
+    fence_proxy_async_smem();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kColRows; ++i) {
+            mbar_init(full_bar(i), 1);
+            mbar_init(empty_bar(i), 1);
+        }
+        for (int i = 0; i < kColSlots; ++i) {
+            mbar_init(accf_bar(i), 1);
+            mbar_init(acce_bar(i), kEpiWarps);
+        }
+        mbar_init(done_bar, 1);
+        misc[1] = 0;
+        fence_mbar_init();
+    }
+    if (warp == kIssuerWarp) tmem_alloc(smem_u32(misc), kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = misc[0];
+    // every accumulator starts at zero (the epilogue re-zeroes a plane after draining it)
+    if (warp < kEpiWarps) {
+#pragma unroll 4
+        for (int c = 0; c < kColSlots * kColPlaneCols; c += 16) tmem_zero16(tmem + ((uint32_t)(warp * 32) << 16) + c);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const int L = a.L;
+    const uint32_t in_row = kBitsIn ? 16u : 32u;
+    const uint32_t tile_bytes = kTileM * in_row;
+
+    if (warp == kProducerWarp) {
+        if (lane == 0) {
+            uint32_t rseq = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+                const Unit t = col_unit_of(a, u);
+                for (int zi = -1; zi <= L && ok; ++zi) {
+                    const int zw = wrap(zi, L);
+                    for (int yi = t.y - 1; yi <= t.y + 2; ++yi) {
+                        const int g = (int)(rseq % kColRows);
+                        const uint32_t use = rseq / kColRows;
+                        if (use > 0 && !wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        const int64_t row = ((int64_t)zw * L + wrap(wrap(yi, L), L)) * L;
+                        uint32_t dst = ring + (uint32_t)g * kColRowBytes;
+                        mbar_arrive_expect_tx(full_bar(g), 4u * tile_bytes);
+                        for (int i = 0; i < 4; ++i) {
+                            const int xi = wrap(wrap(t.x0 - 1 + i, L), L);
+                            bulk_load(dst, a.in + ((row + xi) * a.Sp + t.m0) * in_row, tile_bytes, full_bar(g));
+                            dst += tile_bytes;
+                        }
+                        ++rseq;
+                    }
+                }
+            }
+            // copies still in flight land before the CTA exits
+            const uint32_t last = rseq < (uint32_t)kColRows ? rseq : (uint32_t)kColRows;
+            for (uint32_t g = 0; g < last; ++g) {
+                const uint32_t q = rseq - 1 - ((rseq - 1 - g) % kColRows);
+                wait_bar(full_bar((int)g), (q / kColRows) & 1u, abort_flag, true);
+            }
+        }
+        __syncwarp();
+    } else if (warp == kIssuerWarp) {
+        if (lane == 0) {
+            uint32_t rseq = 0;
+            int64_t qbase = 0;
+            bool ok = true;
+            const uint32_t a_lbo = kBitsIn ? 2048u : 128u, a_sbo = kBitsIn ? 128u : 256u;
+            const uint64_t bdesc0 = smem_desc(wsm, 128u, 256u);   // + 32 per 512-byte block
+            constexpr uint32_t kIdescBase = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileM >> 4) << 24);
+            for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+                for (int zi = -1; zi <= L && ok; ++zi) {
+                    // output plane zi + 1 is first written by this input plane: its slot must be drained
+                    if (zi + 1 <= L - 1) {
+                        const int64_t q = qbase + zi + 1;
+                        const uint32_t v = (uint32_t)(q >> 3);
+                        if (v > 0 && !wait_bar(acce_bar((int)(q & 7)), (v - 1) & 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    const int t1 = zi - 1 < 0 ? 0 : zi - 1, t2 = zi + 1 > L - 1 ? L - 1 : zi + 1;
+                    const int P1 = t1 - (zi - 1), P2 = t2 - (zi - 1);           // parts 0..2
+                    const int s1 = (int)((qbase + t1) & 7);
+                    const int wrap_at = s1 + (t2 - t1) > 7 ? t1 + (8 - s1) : -1;   // first plane in slot 0
+                    for (int b = 0; b < 4; ++b) {
+                        const int g = (int)(rseq % kColRows);
+                        if (!wait_bar(full_bar(g), (rseq / kColRows) & 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint64_t adesc0 = smem_desc(ring + (uint32_t)g * kColRowBytes, a_lbo, a_sbo);
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            const ColPos pos = s_pos[b * P + p];
+                            const uint64_t adesc = adesc0 + (uint64_t)(p * (kSlotBytes >> 4));
+                            auto issue = [&](int pa, int ja, int pz, int jz, int col) {
+                                // blocks (pa, ja) .. (pz, jz) of the sequence into TMEM column col
+                                const int b0 = 4 * pa + ja - pos.lo, nb = 4 * (pz - pa) + jz - ja + 1;
+                                mma_bf16_n(tmem + (uint32_t)col, adesc, bdesc0 + (uint64_t)(32 * (pos.base + b0)),
+                                           kIdescBase | ((uint32_t)(nb * 16 / 8) << 17));
+                            };
+                            if (wrap_at < 0) {
+                                issue(P1, pos.lo, P2, pos.hi, s1 * kColPlaneCols + pos.lo * kC);
+                            } else {
+                                const int Pw = wrap_at - (zi - 1);
+                                issue(P1, pos.lo, Pw - 1, 3, s1 * kColPlaneCols + pos.lo * kC);
+                                issue(Pw, 0, P2, pos.hi, 0);
+                            }
+                        }
+                        mma_commit(empty_bar(g));
+                        ++rseq;
+                    }
+                    if (!ok) break;
+                    // output plane zi - 1 has received its last contribution
+                    if (zi - 1 >= 0) mma_commit(accf_bar((int)((qbase + zi - 1) & 7)));
+                }
+                qbase += L;
+            }
+            // every MMA issued has completed before TMEM is released
+            mma_commit(done_bar);
+            wait_bar(done_bar, 0, abort_flag, true);
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warp w owns TMEM lanes (= tile rows = samples) 32w .. 32w + 31
+        const int r = warp * 32 + lane;
+        float bias[kC];
+#pragma unroll
+        for (int c = 0; c < kC; ++c) bias[c] = a.bias[c];
+        float w4[kHead ? 3 * kC : 1];
+        float b4[3] = {0.0f, 0.0f, 0.0f};
+        if (kHead) {
+#pragma unroll
+            for (int i = 0; i < 3 * kC; ++i) w4[i] = a.w4[i];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) b4[d] = a.b4[d];
+        }
+        int64_t q = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+            const Unit t = col_unit_of(a, u);
+            const int64_t sample = t.m0 + r;
+            const bool valid = sample < a.n_samples;
+            for (int zo = 0; zo < L; ++zo, ++q) {
+                const int s = (int)(q & 7);
+                int got = 1;
+                if (lane == 0) got = wait_bar(accf_bar(s), (uint32_t)(q >> 3) & 1u, abort_flag) ? 1 : 0;
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kColPlaneCols);
+                uint32_t raw[4][16];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tmem_ld16(lane_base + (uint32_t)(j * kC), raw[j]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) tmem_zero16(lane_base + (uint32_t)(j * kC));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int xo = t.x0 + (j & 1), yo = t.y + (j >> 1);
+                    if (xo >= L || yo >= L) continue;   // the odd lattice's last column
+                    const int64_t site = ((int64_t)zo * L + yo) * L + xo;
+                    float v[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(raw[j][c]);
+                    if (!kHead) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int c = 0; c < kC; c += 2)
+                            pk[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
+                        uint8_t* dst = a.out + (site * a.Sp + t.m0) * 32 + (r >> 3) * 256 + (r & 7) * 16;
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    } else {
+                        float z[3] = {b4[0], b4[1], b4[2]};
+#pragma unroll
+                        for (int c = 0; c < kC; ++c) {
+                            const float y = fmaxf(v[c] + bias[c], 0.0f);
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) z[d] = fmaf(y, w4[d * kC + c], z[d]);
+                        }
+                        const int64_t wd = (t.m0 + warp * 32) / 64;
+                        const int hw = warp & 1;
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) {
+                            if (a.logits && valid)
+                                a.logits[((int64_t)d * a.L3 + site) * a.n_samples + sample] = z[d];
+                            const uint32_t bits = __ballot_sync(0xffffffffu, valid && z[d] > 0.0f);
+                            if (lane == 0 && wd < a.words) a.dec32[(wd * a.L3 + site) * 8 + 2 * d + hw] = bits;
+                        }
+                    }
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce_bar(s));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kIssuerWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
 // First layer's input: [site][sample][8] BF16, channels s_{t-1}(n) then s_t(n)
 // for n = 0..2, then two zeros.  Rows past n_samples are zero.  One warp per
 // site and 256 samples (4 words): lanes 0..23 load the 6 channels x 4 words,
@@ -671,6 +1060,26 @@ t3d_status launch_conv(const TcArgs& a, cudaStream_t st)
     return T3D_OK;
 }
 
+template <bool kHead, bool kBitsIn>
+t3d_status launch_conv_col(const TcArgs& a, cudaStream_t st)
+{
+    const int grid = (int)std::min<int64_t>(a.n_units, sm_count());
+    ProfScope prof(T3D_K_CNN, st);
+    k_conv_col<kHead, kBitsIn><<<grid, kTcThreads, kColSmemBytes, st>>>(a);
+    T3D_LAUNCH_CHECK("tensor-core convolution (2 x 2 columns)");
+    return T3D_OK;
+}
+
+// The line kernel stays selectable (T3D_CNN_LINES=1 in the environment) for comparisons.
+bool use_line_kernel()
+{
+    static const bool lines = [] {
+        const char* v = std::getenv("T3D_CNN_LINES");
+        return v && v[0] == '1';
+    }();
+    return lines;
+}
+
 }  // namespace
 
 t3d_status tc_prepare()
@@ -688,6 +1097,12 @@ t3d_status tc_prepare()
                                             kSmemBytes));
         T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             kSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kColSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kColSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kColSmemBytes));
         configured[dev] = true;
     }
     return T3D_OK;
@@ -716,7 +1131,9 @@ t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t
     a.W = W;
     a.words = words_for(n_samples);
     a.nbx = (L + kLine - 1) / kLine;
-    a.n_units = (Sp / kTileM) * a.nbx * L;
+    a.ncx = (L + 1) / 2;
+    const bool lines = use_line_kernel();
+    a.n_units = lines ? (Sp / kTileM) * a.nbx * L : (Sp / kTileM) * a.ncx * a.ncx;
     T3D_TRY(tc_prepare());
     {
         ProfScope prof(T3D_K_CNN, st);
@@ -728,12 +1145,12 @@ t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t
     a.out = act0;
     a.w = &blob->wf[0][0][0][0];
     a.bias = blob->bias[0];
-    T3D_TRY((launch_conv<false, true>(a, st)));
+    T3D_TRY((lines ? launch_conv<false, true>(a, st) : launch_conv_col<false, true>(a, st)));
     a.in = act0;
     a.out = act1;
     a.w = &blob->wf[1][0][0][0];
     a.bias = blob->bias[1];
-    T3D_TRY((launch_conv<false, false>(a, st)));
+    T3D_TRY((lines ? launch_conv<false, false>(a, st) : launch_conv_col<false, false>(a, st)));
     a.in = act1;
     a.out = nullptr;
     a.w = &blob->wf[2][0][0][0];
@@ -742,7 +1159,7 @@ t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t
     a.b4 = blob->b4;
     a.dec32 = reinterpret_cast<uint32_t*>(dec);
     a.logits = logits_out;
-    T3D_TRY((launch_conv<true, false>(a, st)));
+    T3D_TRY((lines ? launch_conv<true, false>(a, st) : launch_conv_col<true, false>(a, st)));
     return T3D_OK;
 }
 

@@ -3,6 +3,7 @@ profiling one kernel at a time; the whole-cycle benchmark is bench.py).
 
   python -m paper_2212_06985_gb300.kernel_bench cnn   --L 24 --samples 16384
   python -m paper_2212_06985_gb300.kernel_bench sweep --L 32 --samples 8192 --rule F
+  python -m paper_2212_06985_gb300.kernel_bench cycle --L 32 --samples 8192 --schedule FFPFF
   python -m paper_2212_06985_gb300.kernel_bench bp    --L 32 --samples 1024
   python -m paper_2212_06985_gb300.kernel_bench bpmeta --L 24 --samples 1024
   python -m paper_2212_06985_gb300.kernel_bench tanner --n-classical 400 --samples 1024
@@ -84,6 +85,26 @@ def bench_sweep(a, dev):
             "algorithmic_GBps": n_bits(a.L) * a.samples * 0.5 / (ms / 1e3) / 1e9}
 
 
+def bench_cycle(a, dev):
+    """One code cycle of the flip / p-flip decoders: qubit noise, the noisy
+    measurement and the schedule (each call a new cycle index)."""
+    W = words_for(a.samples)
+    e = torch.zeros((n_bits(a.L), W), dtype=torch.int64, device=dev)
+    s = torch.zeros_like(e)
+    work = torch.empty(toric3d_flip_workspace_bytes(a.L, W), dtype=torch.uint8, device=dev)
+    cyc = [0]
+
+    def call():
+        cyc[0] += 1
+        toric3d_noise(a.L, e, a.p, a.seed, 0, cyc[0])
+        toric3d_syndrome(a.L, e, s, a.p, a.seed, 0, cyc[0])
+        toric3d_pflip(a.L, e, s, a.schedule, len(a.schedule), 0, a.seed, 0, cyc[0], work)
+
+    ms = _timed(call, a.warmup, a.reps)
+    return {"call": "noise + syndrome + toric3d_pflip", "schedule": a.schedule, "L": a.L, "samples": a.samples,
+            "ms_per_cycle": ms, "qubit_cycles_per_s": n_bits(a.L) * a.samples / (ms / 1e3)}
+
+
 def bench_bp(a, dev):
     e, s = _state(a.L, a.samples, a.p, a.seed, dev)
     work = torch.empty(toric3d_bp_workspace_bytes(a.L, a.samples), dtype=torch.uint8, device=dev)
@@ -147,7 +168,8 @@ def bench_tanner(a, dev):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("what", choices=["cnn", "sweep", "bp", "bpmeta", "tanner"])
+    ap.add_argument("what", choices=["cnn", "sweep", "cycle", "bp", "bpmeta", "tanner"])
+    ap.add_argument("--schedule", default="FFPFF", help="cycle: the flip / p-flip schedule")
     ap.add_argument("--L", type=int, default=24)
     ap.add_argument("--samples", type=int, default=16384)
     ap.add_argument("--p", type=float, default=0.04)
@@ -160,7 +182,7 @@ def main(argv=None):
     ap.add_argument("--n-classical", type=int, default=400, help="tanner: bits of each classical code")
     a = ap.parse_args(argv)
     dev = torch.device("cuda:0")
-    out = {"cnn": bench_cnn, "sweep": bench_sweep, "bp": bench_bp, "bpmeta": bench_bp_meta, "tanner": bench_tanner}[a.what](a, dev)
+    out = {"cnn": bench_cnn, "sweep": bench_sweep, "cycle": bench_cycle, "bp": bench_bp, "bpmeta": bench_bp_meta, "tanner": bench_tanner}[a.what](a, dev)
     print(json.dumps(out), flush=True)
     return 0
 

@@ -25,3 +25,29 @@ def test_reference_arm_prints_one_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"] == "flip_L4"
     assert d["metric"] == json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
+
+
+def test_reference_config_has_the_cuda_arms_keys():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "flip_L4", "--steps", "1",
+                        "--warmup", "0", "--reference-seconds", "1"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["config"]["parallelism"] == "replicas1"
+
+
+def test_sweep_roofline_of_a_pflip_cycle():
+    """The flip / p-flip workload's roofline from per-kind kernel times (no GPU)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import toric3d_inputs as inp
+    w = inp.WORKLOADS["pflip_L32"]
+    q, S, steps = inp.n_bits(32), 100_000, 2
+    prof = {k: (0.0, 0) for k in ("noise", "syndrome", "flip", "pflip", "bp_step", "bp_decide", "logical", "layout",
+                                  "cnn")}
+    prof.update(noise=(12.6, 2), syndrome=(14.0, 2), flip=(9.0, 8), pflip=(4.0, 4))
+    r = bench.sweep_roofline(prof, w, q, S, steps, 40.0, 6780.0, "test", {"sm_mhz": 2070.0})
+    assert r["kernel"] == "k_syndrome" and abs(r["ms_per_application"] - 7.0) < 1e-9
+    assert r["bound"] in ("alu", "hbm") and 0 < r["frac"] < 1
+    flip = r["kernels_hbm_frac"]["flip"]             # 0.5 B x qubits x S per 1.125 ms application (4 F per cycle)
+    assert abs(flip - 0.5 * q * S / 1.125e-3 / 1e9 / 6780.0) < 1e-9
+    assert 0 < r["cycle_hbm_frac"] < 1

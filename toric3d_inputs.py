@@ -100,6 +100,7 @@ WORKLOADS = {
     # p-flip with the Sec. 3.2 example schedule FFPFF, T=L, 10^6 samples per point
     "pflip_L8": Workload("pflip_L8", 8, 0.03, 0.03, 8, 1_000_000, 1000, "pflip", "FFPFF", 5),
     "pflip_L16": Workload("pflip_L16", 16, 0.03, 0.03, 16, 1_000_000, 1000, "pflip", "FFPFF", 5),
+    "pflip_L32": Workload("pflip_L32", 32, 0.04, 0.04, 32, 100_000, 17, "pflip", "FFPFF", 5),
     # BP (16 FP32 iterations) + 32 applications cycling PFFPFF, T=L
     "bp_pflip_L16": Workload("bp_pflip_L16", 16, 0.04, 0.04, 16, 100_000, 7, "bp_pflip",
                              "PFFPFF", 32, bp_iters=16),
