@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
     ap.add_argument("--reference-seconds", type=float, default=60.0,
                     help="--impl reference: oracle time over all steps (default 60 s)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -474,39 +474,71 @@ def cuda_arm(args):
     else:
         roofline = sweep_roofline(prof, w, qubits, S, args.steps, ms, hbm_peak, peak_source, clk)
 
-    # end-to-end: the error states round-trip through pinned host memory every step
+    # end-to-end: every step uploads each error state from pinned host memory, decodes one
+    # cycle through the C ABI and downloads the state, the masks and the counts.  The batch
+    # runs as two halves (consecutive 64-sample-aligned sample ranges, the same samples as
+    # one batch) decoded one after the other on the compute stream, each half with its own
+    # copy stream, so one half's copies overlap the other half's decoding.
     e2e = None
     if not args.no_e2e:
-        hosts = [torch.empty_like(e, device="cpu").pin_memory() for e in states]
-        for h, e in zip(hosts, states):
-            h.copy_(e)
-        mask_host = [torch.empty(S, dtype=torch.uint8, pin_memory=True) for _ in sizes]
-        counts_host = [torch.empty(8, dtype=torch.int64, pin_memory=True) for _ in sizes]
+        S0 = min(S, (S // 2 + 63) // 64 * 64)
+        parts = [(0, S0), (S0, S - S0)] if S - S0 > 0 else [(0, S)]
+        halves = []
+        for off, n in parts:
+            hw = inp.words_for(n)
+            h_states = [torch.empty((inp.n_bits(L), hw), dtype=torch.int64, device=dev) for L in sizes]
+            h_masks = [torch.zeros(n, dtype=torch.uint8, device=dev) for _ in sizes]
+            h_counts = [torch.zeros(8, dtype=torch.int64, device=dev) for _ in sizes]
+            h_host = [torch.empty((inp.n_bits(L), hw), dtype=torch.int64, pin_memory=True) for L in sizes]
+            for hh, e in zip(h_host, states):
+                hh.copy_(e[:, off // 64:off // 64 + hw])
+            h_batch = t3d.make_batch([dict(L=L, n_samples=n, sample0=sample0 + off, e=e, mask=m, counts8=c)
+                                      for L, e, m, c in zip(sizes, h_states, h_masks, h_counts)])
+            h_cfg = t3d.make_run_cfg(w.L, 1, w.p, w.q, w.seed, n, sample0=sample0 + off,
+                                     bp_chunk_samples=chunk, **kw)
+            assert t3d.toric3d_run_batch_workspace_bytes(h_cfg, h_batch) <= work.numel()
+            halves.append(dict(n=n, states=h_states, masks=h_masks, counts=h_counts, host=h_host, batch=h_batch,
+                               cfg=h_cfg, mask_host=[torch.empty(n, dtype=torch.uint8, pin_memory=True) for _ in sizes],
+                               counts_host=[torch.empty(8, dtype=torch.int64, pin_memory=True) for _ in sizes],
+                               cs=torch.cuda.Stream(device=dev), up=torch.cuda.Event(), done=torch.cuda.Event()))
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            for i in range(args.e2e_steps):
-                for h, e in zip(hosts, states):
-                    e.copy_(h, non_blocking=True)
-                step(args.warmup + args.steps + i)
-                for h, e in zip(hosts, states):
-                    h.copy_(e, non_blocking=True)
-                for mh, m in zip(mask_host, masks):
-                    mh.copy_(m, non_blocking=True)
-                for ch, c in zip(counts_host, counts):
-                    ch.copy_(c, non_blocking=True)
+        for i in range(args.e2e_steps):
+            for h in halves:                         # uploads (after the half's previous download)
+                with torch.cuda.stream(h["cs"]):
+                    for d_e, h_e in zip(h["states"], h["host"]):
+                        d_e.copy_(h_e, non_blocking=True)
+                    h["up"].record(h["cs"])
+            for h in halves:                         # decoding, one half after the other
+                stream.wait_event(h["up"])
+                h["cfg"].cycle0 = args.warmup + args.steps + i
+                t3d.toric3d_run_batch(h["cfg"], h["batch"], work, stream=stream)
+                h["done"].record(stream)
+                with torch.cuda.stream(h["cs"]):     # downloads
+                    h["cs"].wait_event(h["done"])
+                    for d_e, h_e in zip(h["states"], h["host"]):
+                        h_e.copy_(d_e, non_blocking=True)
+                    for mh, m in zip(h["mask_host"], h["masks"]):
+                        mh.copy_(m, non_blocking=True)
+                    for ch, c in zip(h["counts_host"], h["counts"]):
+                        ch.copy_(c, non_blocking=True)
+        for h in halves:
+            h["cs"].synchronize()
         stream.synchronize()
         dt = time.perf_counter() - t0
         dt_t = torch.tensor([dt], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
         dt = float(dt_t.item())
-        state_bytes = sum(e.numel() * 8 for e in states)
+        state_bytes = sum(e.numel() * 8 for h in halves for e in h["states"])
         e2e = {"value": qubits * S * world * args.e2e_steps / dt, "unit": UNIT,
-               "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes + len(sizes) * (S + 64),
-               "steps": args.e2e_steps,
-               "note": "error states uploaded from and downloaded to pinned host memory every step"}
+               "h2d_bytes_per_step": state_bytes,
+               "d2h_bytes_per_step": state_bytes + sum(h["n"] + 64 for h in halves) * len(sizes),
+               "steps": args.e2e_steps, "ms_per_step": 1e3 * dt / args.e2e_steps,
+               "note": "error states uploaded from and downloaded to pinned host memory every step, "
+                       "two halves whose copies overlap the other half's decoding"}
+        del halves
 
     fail_counts = [c.cpu().tolist() for c in counts]
     learned = None

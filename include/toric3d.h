@@ -384,8 +384,9 @@ typedef struct {
                                   (use_bp must be 0; toric3d_run_batch only, items carry s_prev); NULL = none */
     int32_t fallback_max_weight; /* with cnn_blob: after the schedule, every 64-sample word in which a sample
                                     keeps more than this many unsatisfied checks (plus the allowance of
-                                    fallback_sigmas) is decoded again by BP (bp_iters) + the schedule;
-                                    -1 = no fallback */
+                                    fallback_sigmas) is decoded again from the cycle's start (the error
+                                    after the noise, the measured syndrome) by BP (bp_iters) + the
+                                    schedule, whose result replaces the learned one; -1 = no fallback */
     double fallback_sigmas;      /* > 0: the threshold of each lattice also allows the unsatisfied checks the
                                     noisy measurement alone leaves, floor(q n + fallback_sigmas sqrt(q (1-q) n))
                                     with n = 3L^3 (isolated measurement errors stay unsatisfied after any

@@ -77,11 +77,14 @@ void set_tuned_blocks_per_sm(int kind, int blocks_per_sm)
     if (kind >= 0 && kind < T3D_K_COUNT) g_tuned[kind] = blocks_per_sm > 0 ? blocks_per_sm : 0;
 }
 
-unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks)
+unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks, bool device_bound)
 {
     const int64_t max_grid = 0x7fffffffLL;
     if (blocks < 1) return 1;
-    const int cap = tuned_blocks_per_sm(kind);
+    int cap = tuned_blocks_per_sm(kind);
+    // a launch whose work is bounded on the device (compacted words) walks only a few of its
+    // blocks: resident blocks only, so the empty ones are not launched
+    if (cap <= 0 && device_bound) cap = 1 << 20;
     if (cap <= 0) return (unsigned)std::min(blocks, max_grid);  // one block per work unit
     int dev = 0;
     cudaGetDevice(&dev);

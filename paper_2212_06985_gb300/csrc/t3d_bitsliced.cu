@@ -602,7 +602,7 @@ t3d_status launch_noise(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t cy
     }
     finish_table(tab);
     ProfScope prof(T3D_K_NOISE, st);
-    k_noise<<<persistent_grid((const void*)k_noise, kThreads, T3D_K_NOISE, tab.prefix[tab.n]), kThreads,
+    k_noise<<<persistent_grid((const void*)k_noise, kThreads, T3D_K_NOISE, tab.prefix[tab.n], has_live(tab)), kThreads,
               0, st>>>(tab, thr, seed, cycle);
     T3D_LAUNCH_CHECK("noise");
     return T3D_OK;
@@ -618,7 +618,7 @@ t3d_status launch_syndrome(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t
     }
     finish_table(tab);
     ProfScope prof(T3D_K_SYNDROME, st);
-    k_syndrome<<<persistent_grid((const void*)k_syndrome, kThreads, T3D_K_SYNDROME, tab.prefix[tab.n]),
+    k_syndrome<<<persistent_grid((const void*)k_syndrome, kThreads, T3D_K_SYNDROME, tab.prefix[tab.n], has_live(tab)),
                  kThreads, 0, st>>>(tab, thr, seed, cycle);
     T3D_LAUNCH_CHECK("syndrome");
     return T3D_OK;
@@ -658,18 +658,18 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
         const bool pk = schedule[k % slen] == 'P';
         ProfScope prof(pk ? T3D_K_PFLIP : T3D_K_FLIP, st);
         if (pk) {
-            k_pflip_decide<<<persistent_grid((const void*)k_pflip_decide, kThreads, T3D_K_PFLIP, t.prefix[t.n]),
+            k_pflip_decide<<<persistent_grid((const void*)k_pflip_decide, kThreads, T3D_K_PFLIP, t.prefix[t.n], has_live(t)),
                              kThreads, 0, st>>>(t, seed, cycle, sweep0 + (uint32_t)k);
             T3D_LAUNCH_CHECK("p-flip decisions");
-            k_pflip_apply<<<persistent_grid((const void*)k_pflip_apply, kThreads, T3D_K_PFLIP, t.prefix[t.n]),
+            k_pflip_apply<<<persistent_grid((const void*)k_pflip_apply, kThreads, T3D_K_PFLIP, t.prefix[t.n], has_live(t)),
                             kThreads, 0, st>>>(t);
             T3D_LAUNCH_CHECK("p-flip syndrome update");
         } else {
             if (tiled) {
-                k_flip_tiled<<<persistent_grid((const void*)k_flip_tiled, kThreads, T3D_K_FLIP, tt.prefix[tt.n]),
+                k_flip_tiled<<<persistent_grid((const void*)k_flip_tiled, kThreads, T3D_K_FLIP, tt.prefix[tt.n], has_live(tt)),
                                kThreads, 0, st>>>(tt);
             } else {
-                k_flip<<<persistent_grid((const void*)k_flip, kThreads, T3D_K_FLIP, t.prefix[t.n]), kThreads, 0,
+                k_flip<<<persistent_grid((const void*)k_flip, kThreads, T3D_K_FLIP, t.prefix[t.n], has_live(t)), kThreads, 0,
                          st>>>(t);
             }
             T3D_LAUNCH_CHECK("flip sweep");
@@ -699,7 +699,7 @@ t3d_status launch_logical(ItemTable& tab, cudaStream_t st)
     }
     finish_table(tab);
     ProfScope prof(T3D_K_LOGICAL, st);
-    k_logical<<<persistent_grid((const void*)k_logical, 32 * kLineSplit, T3D_K_LOGICAL, tab.prefix[tab.n]),
+    k_logical<<<persistent_grid((const void*)k_logical, 32 * kLineSplit, T3D_K_LOGICAL, tab.prefix[tab.n], has_live(tab)),
                 32 * kLineSplit, 0, st>>>(tab);
     T3D_LAUNCH_CHECK("logical");
     return T3D_OK;

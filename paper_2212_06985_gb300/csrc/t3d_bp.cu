@@ -398,18 +398,19 @@ t3d_status launch_step(ItemTable& tab, int mode, double p, double q_meas, cudaSt
 {
     set_blocks(tab);
     const int64_t blocks = tab.prefix[tab.n];
+    const bool live = has_live(tab);
     ProfScope prof(T3D_K_BP_STEP, st);
     if (mode == kSynWordsSave)
         k_bp_step<kSynWordsSave><<<persistent_grid((const void*)k_bp_step<kSynWordsSave>, kBpThreads,
-                                                   T3D_K_BP_STEP, blocks),
+                                                   T3D_K_BP_STEP, blocks, live),
                                    kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas), first_message(p, q_meas));
     else if (mode == kSynSaved)
         k_bp_step<kSynSaved><<<persistent_grid((const void*)k_bp_step<kSynSaved>, kBpThreads, T3D_K_BP_STEP,
-                                               blocks),
+                                               blocks, live),
                                kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas), first_message(p, q_meas));
     else
         k_bp_step<kSynWords><<<persistent_grid((const void*)k_bp_step<kSynWords>, kBpThreads, T3D_K_BP_STEP,
-                                               blocks),
+                                               blocks, live),
                                kBpThreads, 0, st>>>(tab, prior(p), meas_pair(q_meas), first_message(p, q_meas));
     T3D_LAUNCH_CHECK("bp step");
     return T3D_OK;
@@ -420,7 +421,7 @@ t3d_status launch_decide(ItemTable& tab, double p, cudaStream_t st)
     set_blocks(tab);
     {
         ProfScope prof(T3D_K_BP_DECIDE, st);
-        k_bp_decide<<<persistent_grid((const void*)k_bp_decide, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n]),
+        k_bp_decide<<<persistent_grid((const void*)k_bp_decide, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n], has_live(tab)),
                       kBpThreads, 0, st>>>(tab, prior(p));
         T3D_LAUNCH_CHECK("bp decide");
     }
@@ -432,7 +433,7 @@ t3d_status launch_decide(ItemTable& tab, double p, cudaStream_t st)
     }
     finish_table(tab);
     ProfScope prof(T3D_K_BP_DECIDE, st);
-    k_bp_syndrome<<<persistent_grid((const void*)k_bp_syndrome, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n]),
+    k_bp_syndrome<<<persistent_grid((const void*)k_bp_syndrome, kBpThreads, T3D_K_BP_DECIDE, tab.prefix[tab.n], has_live(tab)),
                     kBpThreads, 0, st>>>(tab);
     T3D_LAUNCH_CHECK("bp syndrome update");
     return T3D_OK;

@@ -91,7 +91,9 @@ t3d_status check_words(const void* p, const char* name);
 // Grid size for a grid-stride kernel with `blocks` work units: one block per
 // unit by default; with a tuned cap of c blocks per SM, a persistent grid of
 // SMs x min(c, resident blocks) that walks the units.
-unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks);
+// device_bound: the launch's work is bounded by a device-side count (ItemDesc::live); the
+// grid is then at most the resident blocks even when untuned.
+unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks, bool device_bound = false);
 
 // Launch tuning chosen by the autotuner (0 = use the occupancy limit).
 int tuned_blocks_per_sm(int kind);

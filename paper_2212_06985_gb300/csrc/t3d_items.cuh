@@ -96,6 +96,13 @@ __device__ __forceinline__ void for_each_item_block(const ItemTable& tab, F&& f)
     }
 }
 
+inline bool has_live(const ItemTable& tab)
+{
+    for (int i = 0; i < tab.n; ++i)
+        if (tab.it[i].live) return true;
+    return false;
+}
+
 inline void finish_table(ItemTable& tab)
 {
     tab.prefix[0] = 0;

@@ -42,6 +42,7 @@ struct Plan {
     int64_t* live[kMaxItems];          // their number (device)
     uint64_t* e_c[kMaxItems];          // the flagged words' e and s columns, compacted
     uint64_t* s_c[kMaxItems];
+    uint64_t* e_pre[kMaxItems];        // the error state before the cycle's decoding
     unsigned long long* n_fallback[kMaxItems];
     void* cnn_work[kMaxItems];
     int64_t cnn_chunk[kMaxItems];  // pre-decoder chunk, words
@@ -168,7 +169,7 @@ size_t learned_bytes(const t3d_run_cfg& c, int L, int64_t n_samples)
     if (c.fallback_max_weight >= 0) {
         const int64_t Wi = words_for(n_samples);
         b += round_up((size_t)Wi) + round_up(gate_scratch_bytes(L, Wi)) + round_up((size_t)Wi * sizeof(uint32_t)) +
-             round_up(sizeof(int64_t)) + 2 * round_up(state_bytes(L, n_samples));
+             round_up(sizeof(int64_t)) + 3 * round_up(state_bytes(L, n_samples));
     }
     return b;
 }
@@ -235,6 +236,8 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
                 used += sb;
                 pl.s_c[i] = reinterpret_cast<uint64_t*>(base + used);
                 used += sb;
+                pl.e_pre[i] = reinterpret_cast<uint64_t*>(base + used);
+                used += sb;
                 pl.gate_weight[i] = fallback_weight(c, items[i].L);
             }
             const int64_t cw = cnn_chunk_words(c, items[i].L, items[i].n_samples);
@@ -268,8 +271,10 @@ t3d_status copy_rows(uint64_t* dst, const uint64_t* src, const ItemDesc& d, int6
 
 // One cycle of the learned decoder: qubit noise and the noisy measurement of
 // every item, the pre-decoder chunk by chunk (each chunk decodes from its own
-// (s_prev, s) rows), the flip / p-flip schedule, the optional fallback (gate,
-// then BP and the schedule on the flagged words), and s_prev <- the measured s.
+// (s_prev, s) rows), the flip / p-flip schedule, the optional fallback (gate;
+// the flagged words are decoded again from the cycle's start, the error after
+// the noise and the measured syndrome, by BP and the schedule, whose result
+// replaces the learned one), and s_prev <- the measured s.
 // (Running chunks on two streams, so that one chunk's pre-decoder overlaps the
 // other's sweeps, measured slower on GB300: the sweeps' blocks delay the
 // persistent one-CTA-per-SM convolutions.)
@@ -283,6 +288,7 @@ t3d_status enqueue_learned_cycle(const t3d_run_cfg& c, const Plan& pl, uint32_t 
     for (int i = 0; i < pl.items.n; ++i) {
         const ItemDesc& d = pl.items.it[i];
         T3D_TRY(copy_rows(pl.s_raw[i], d.s, d, 0, d.W, st));
+        if (c.fallback_max_weight >= 0) T3D_TRY(copy_rows(pl.e_pre[i], d.e, d, 0, d.W, st));
         for (int64_t w0 = 0; w0 < d.W; w0 += pl.cnn_chunk[i]) {
             const int64_t n = std::min<int64_t>(pl.cnn_chunk[i] * 64, d.n_samples - w0 * 64);
             T3D_TRY(launch_cnn_decode(d.lat.L, n, d.W, pl.s_prev[i] + w0, d.s + w0, d.e + w0, c.cnn_blob, nullptr,
@@ -294,14 +300,16 @@ t3d_status enqueue_learned_cycle(const t3d_run_cfg& c, const Plan& pl, uint32_t 
         T3D_TRY(launch_sweeps(tab, c.schedule, slen, c.n_apply, 0, c.seed, cycle, st));
     }
     if (c.fallback_max_weight >= 0) {
-        // the flagged words' columns are compacted to the front of two scratch arrays, decoded
-        // there (BP + the schedule, every launch walking only the live words) and copied back
+        // the flagged words' columns of the cycle's start (error after the noise, measured
+        // syndrome) are compacted to the front of two scratch arrays, decoded there by BP + the
+        // schedule (every launch walking only the live words), and replace the learned result
         for (int i = 0; i < pl.items.n; ++i) {
             const ItemDesc& d = pl.items.it[i];
             T3D_TRY(launch_gate(d.lat, d.W, d.s, pl.gate_weight[i], pl.gate[i], pl.n_fallback[i],
                                 pl.gate_scratch[i], st));
             T3D_TRY(launch_compact_words(pl.gate[i], d.W, pl.wsrc[i], pl.live[i], st));
-            T3D_TRY(launch_move_words(d.lat, d.W, pl.live[i], pl.wsrc[i], d.e, pl.e_c[i], d.s, pl.s_c[i], true, st));
+            T3D_TRY(launch_move_words(d.lat, d.W, pl.live[i], pl.wsrc[i], pl.e_pre[i], pl.e_c[i], pl.s_raw[i],
+                                      pl.s_c[i], true, st));
             ItemTable one;
             std::memset(&one, 0, sizeof(one));
             one.n = 1;

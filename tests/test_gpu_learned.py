@@ -2,8 +2,9 @@
 against the PyTorch reference in test_gpu_cnn.py): the fallback gate against
 syndrome weights counted on the CPU, and whole runs through
 toric3d_run_batch against the same cycle assembled from the single-step entry
-points (noise, measurement, pre-decoder, p-flip schedule, gate, BP + schedule
-on the flagged words only)."""
+points (noise, measurement, pre-decoder, p-flip schedule, gate, and for the
+flagged words only BP + schedule from the cycle's start, whose result replaces
+the learned one)."""
 import numpy as np
 import pytest
 import torch
@@ -62,6 +63,7 @@ def _stepwise(L, S, T, blob, max_w, sample0=0):
         t3d.toric3d_noise(L, e, p, seed, sample0, t)
         t3d.toric3d_syndrome(L, e, s, p, seed, sample0, t)
         s_raw = s.clone()
+        e_pre = e.clone()
         t3d.toric3d_cnn_decode(L, S, s_prev, s, e, blob, cnn_work)
         t3d.toric3d_pflip(L, e, s, DEC["schedule"], DEC["n_apply"], 0, seed, sample0, t, flip_work)
         if max_w >= 0:
@@ -69,8 +71,8 @@ def _stepwise(L, S, T, blob, max_w, sample0=0):
             lanes = np.unpackbits(weight.view(np.uint8).reshape(n, W, 8), axis=2, bitorder="little")
             per_lane = lanes.sum(axis=0)                       # [W][64]
             for w in np.nonzero((per_lane > max_w).any(axis=1))[0]:
-                flagged += 1
-                ew, sw = e[:, w:w + 1].contiguous(), s[:, w:w + 1].contiguous()
+                flagged += 1              # decoded again from the cycle's start by BP + the schedule
+                ew, sw = e_pre[:, w:w + 1].contiguous(), s_raw[:, w:w + 1].contiguous()
                 t3d.toric3d_bp(L, 64, ew, sw, p, p, DEC["bp_iters"], bp_work)
                 t3d.toric3d_pflip(L, ew, sw, DEC["schedule"], DEC["n_apply"], 0, seed, sample0 + 64 * int(w), t,
                                   w1_work)
