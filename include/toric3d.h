@@ -30,15 +30,17 @@
  * calling thread's last failure.  No exception crosses the ABI.
  *
  * Random numbers (the paper only says "random number in (0,1)", Sec. 3.2):
- * Philox4x64-10 (Salmon et al., SC'11) with key (seed, 0) and counter
- * (group, site, cycle, stream<<48 | sweep<<8 | block), group = sample / 64.
- * Bernoulli(p) for a sample in lane j compares the 32-bit U whose bit 31-i is
- * bit j of word i (word i = output i%4 of block i/4) with P = floor(p*2^32 +
- * 1/2): the event happens iff U < P.  Streams: 0 qubit flips (site = edge),
- * 1 measurement flips (site = face), 2 p-flip coins (site = lattice site r:
- * the coin of r's d-edge is bit j of output d of block 0).  `sample0` (a multiple of 64) is the global index
- * of a batch's first sample, so disjoint sample ranges on different GPUs or
- * in resumed runs draw exactly the numbers one large batch would.
+ * Philox4x32-10 (Salmon et al., SC'11) with key (seed mod 2^32, seed >> 32)
+ * and counter (group mod 2^32, site, cycle, stream<<30 | sweep<<8 | block),
+ * group = sample / 64; sweep indices stay below 2^22.  Word i (64 bits) of a
+ * stream position is outputs 0 | 1<<32 (i even) or 2 | 3<<32 (i odd) of block
+ * i/2.  Bernoulli(p) for a sample in lane j compares the 32-bit U whose bit
+ * 31-i is bit j of word i with P = floor(p*2^32 + 1/2): the event happens iff
+ * U < P.  Streams: 0 qubit flips (site = edge), 1 measurement flips (site =
+ * face), 2 p-flip coins (site = lattice site r: the coin of r's d-edge is bit
+ * j of word d).  `sample0` (a multiple of 64) is the global index of a
+ * batch's first sample, so disjoint sample ranges on different GPUs or in
+ * resumed runs draw exactly the numbers one large batch would.
  */
 #ifndef TORIC3D_H
 #define TORIC3D_H
@@ -123,8 +125,8 @@ t3d_status toric3d_flip_noalloc(int L, int64_t words, uint64_t* e, uint64_t* s, 
  * Table 1 footnote, Sec. 4.2): n_apply synchronous applications whose kinds
  * cycle through `schedule`, a host string over {'F','P'} of length 1..63.  A
  * 'P' application also flips each qubit with exactly 2 of 4 unsatisfied checks
- * whose coin is 1; application k uses coin sweep index sweep0 + k.  e and s in
- * place; work as for toric3d_flip.
+ * whose coin is 1; application k uses coin sweep index sweep0 + k (sweep0 +
+ * n_apply <= 2^22).  e and s in place; work as for toric3d_flip.
  */
 t3d_status toric3d_pflip(int L, int64_t words, uint64_t* e, uint64_t* s, const char* schedule,
                          int n_apply, uint32_t sweep0, uint64_t seed, uint64_t sample0,
@@ -285,10 +287,10 @@ t3d_status toric3d_tanner_syndrome(const t3d_tanner* g, int64_t n_samples, const
  * p-flip): every variable counts its unsatisfied checks u in the current
  * syndrome; it flips when u > deg - u (Sec. 3.1) and, in p-flip, when
  * u == deg - u and its coin is 1 (Sec. 3.2); then e ^= f and s ^= H f.
- * Application k keys the coins with sweep sweep0 + k; the coin of variable v
- * is bit (sample mod 64) of output v mod 4 of Philox block 0 of stream 2
- * keyed by site v / 4.  work: toric3d_tanner_flip_workspace_bytes of 8-byte
- * aligned device scratch (the flip words).
+ * Application k keys the coins with sweep sweep0 + k (sweep0 + n_apply <=
+ * 2^22); the coin of variable v is bit (sample mod 64) of word v mod 4 of
+ * stream 2 keyed by site v / 4.  work: toric3d_tanner_flip_workspace_bytes of
+ * 8-byte aligned device scratch (the flip words).
  */
 size_t toric3d_tanner_flip_workspace_bytes(const t3d_tanner* g, int64_t n_samples);
 t3d_status toric3d_tanner_pflip(const t3d_tanner* g, int64_t n_samples, uint64_t* e, uint64_t* s,

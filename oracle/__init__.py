@@ -7,8 +7,8 @@ C (``t3d_oracle.c``, one sample at a time, uint8 bits, binary64 belief
 propagation); this module only compiles it with gcc and marshals numpy arrays
 through ctypes.
 
-Parity pins (tests/test_oracle_*.py): Philox4x64-10 against numpy's
-independent implementation; the syndrome map against the code parameters
+Parity pins (tests/test_oracle_*.py): Philox4x32-10 against its published
+known-answer vectors and Triton's independent implementation; the syndrome map against the code parameters
 [[3L^3, 3, L]] of Sec. 2; flip and p-flip against the worked examples of
 Sec. 3 (Fig. 3(a) half cube, Fig. 3(b) planar error, Fig. 5 oscillating pair,
 the opposite-face pair); BP against exact marginals on acyclic graphs and the
@@ -85,7 +85,7 @@ def _declare(L):
     u64, i64, i32, u32, dbl = (ctypes.c_uint64, ctypes.c_int64, ctypes.c_int,
                                ctypes.c_uint32, ctypes.c_double)
     sig = {
-        "t3o_philox4x64": (None, [_P, _P, _P]),
+        "t3o_philox4x32": (None, [_P, _P, _P]),
         "t3o_prob_to_threshold": (u64, [dbl]),
         "t3o_uniform32": (u32, [u64, i32, u64, u64, u64, u64]),
         "t3o_bernoulli": (i32, [dbl, u64, i32, u64, u64, u64, u64]),
@@ -145,11 +145,12 @@ def n_bits(L: int) -> int:
 
 
 # ---------------------------------------------------------------- Philox / RNG
-def philox4x64(counter, key):
-    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint64))
-    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64))
-    out = np.zeros(4, dtype=np.uint64)
-    lib().t3o_philox4x64(_ptr(c), _ptr(k), _ptr(out))
+def philox4x32(counter, key):
+    """One Philox4x32-10 block: counter (4 x uint32), key (2 x uint32) -> 4 x uint32."""
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint64).astype(np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint64).astype(np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    lib().t3o_philox4x32(_ptr(c), _ptr(k), _ptr(out))
     return out
 
 

@@ -23,16 +23,18 @@
  * r+e_a.
  *
  * Random numbers (the paper only says "random number in (0,1)", Sec. 3.2):
- * Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed, 0),
- * counter = (group, site, cycle, stream<<48 | sweep<<8 | block), where
- * group = sample / 64.  Bernoulli(p) for a sample with lane = sample % 64:
- * U is the 32-bit integer whose bit (31-j) is bit `lane` of word j
- * (word j = output j%4 of block j/4, j = 0..31); the event happens iff
- * U < P with P = floor(p * 2^32 + 0.5).  The p-flip coin of the d-edge at
- * site r is bit `lane` of output d of block 0 of stream 2 keyed by site r
- * (one block serves the three edges of a site).
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed mod 2^32,
+ * seed >> 32), counter = (group mod 2^32, site, cycle, stream<<30 | sweep<<8
+ * | block), where group = sample / 64 (sweep < 2^22).  A block gives two
+ * 64-bit words: word i is outputs 2(i%2) (low half) and 2(i%2)+1 (high half)
+ * of block i/2.  Bernoulli(p) for a sample with lane = sample % 64: U is the
+ * 32-bit integer whose bit (31-j) is bit `lane` of word j (j = 0..31); the
+ * event happens iff U < P with P = floor(p * 2^32 + 0.5).  The p-flip coin of
+ * the d-edge at site r is bit `lane` of word d of stream 2 keyed by site r
+ * (blocks 0 and 1 serve the three edges of a site).
  *
- * Parity pins: Philox against numpy.random.Philox; syndrome against the
+ * Parity pins: Philox against its published known-answer vectors and
+ * Triton's independent implementation; syndrome against the
  * code parameters [[3L^3,3,L]] of Sec. 2 (GF(2) rank 2L^3-2, weight-4 rows
  * and columns, zero-syndrome membranes and vertex stabilisers); flip and
  * p-flip against the worked examples of Sec. 3 (Fig. 3(a), 3(b), Fig. 5,
@@ -49,35 +51,27 @@
 #include <string.h>
 
 /* ------------------------------------------------------------------ */
-/* Philox4x64-10 from its published definition (SC'11, Sec. 3 of that  */
-/* paper): ten rounds of two 64x64->128 multiplies, a fixed permutation */
-/* and a Weyl-sequence key schedule.                                   */
+/* Philox4x32-10 from its published definition (SC'11, Sec. 3 of that  */
+/* paper): ten rounds of two 32x32->64 multiplies, a fixed permutation  */
+/* and a Weyl-sequence key schedule.                                    */
 /* ------------------------------------------------------------------ */
-static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo)
+void t3o_philox4x32(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
 {
-    unsigned __int128 prod = (unsigned __int128)a * (unsigned __int128)b;
-    *lo = (uint64_t)prod;
-    *hi = (uint64_t)(prod >> 64);
-}
-
-void t3o_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4])
-{
-    const uint64_t mult0 = 0xD2E7470EE14C6C93ULL, mult1 = 0xCA5A826395121157ULL;
-    const uint64_t weyl0 = 0x9E3779B97F4A7C15ULL, weyl1 = 0xBB67AE8584CAA73BULL;
-    uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
-    uint64_t k0 = key_in[0], k1 = key_in[1];
+    const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
     for (int round = 0; round < 10; ++round) {
         if (round > 0) {
             k0 += weyl0;
             k1 += weyl1;
         }
-        uint64_t hi0, lo0, hi1, lo1;
-        mulhilo64(mult0, c0, &hi0, &lo0);
-        mulhilo64(mult1, c2, &hi1, &lo1);
-        uint64_t n0 = hi1 ^ c1 ^ k0;
-        uint64_t n1 = lo1;
-        uint64_t n2 = hi0 ^ c3 ^ k1;
-        uint64_t n3 = lo0;
+        uint64_t prod0 = (uint64_t)mult0 * c0;
+        uint64_t prod1 = (uint64_t)mult1 * c2;
+        uint32_t n0 = (uint32_t)(prod1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)prod1;
+        uint32_t n2 = (uint32_t)(prod0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)prod0;
         c0 = n0; c1 = n1; c2 = n2; c3 = n3;
     }
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
@@ -85,13 +79,20 @@ void t3o_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t
 
 enum { STREAM_QUBIT = 0, STREAM_MEAS = 1, STREAM_COIN = 2 };
 
-static void stream_block(uint64_t seed, int stream, uint64_t site, uint64_t cycle,
-                         uint64_t sweep, uint64_t block, uint64_t group, uint64_t out[4])
+/* Word i (64 bits) of the random stream at (seed, stream, site, cycle, sweep,
+ * group): outputs 2(i%2) (low half) and 2(i%2)+1 (high half) of block i/2,
+ * counter (group mod 2^32, site, cycle, stream<<30 | sweep<<8 | i/2), key
+ * (seed mod 2^32, seed >> 32). */
+static uint64_t stream_word(uint64_t seed, int stream, uint64_t site, uint64_t cycle, uint64_t sweep,
+                            uint64_t group, int i)
 {
-    uint64_t ctr[4] = { group, site, cycle,
-                        ((uint64_t)stream << 48) | (sweep << 8) | block };
-    uint64_t key[2] = { seed, 0 };
-    t3o_philox4x64(ctr, key, out);
+    uint32_t ctr[4] = { (uint32_t)group, (uint32_t)site, (uint32_t)cycle,
+                        ((uint32_t)stream << 30) | ((uint32_t)sweep << 8) | (uint32_t)(i / 2) };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t out[4];
+    t3o_philox4x32(ctr, key, out);
+    int j = 2 * (i % 2);
+    return (uint64_t)out[j] | ((uint64_t)out[j + 1] << 32);
 }
 
 uint64_t t3o_prob_to_threshold(double p)
@@ -107,14 +108,10 @@ uint32_t t3o_uniform32(uint64_t seed, int stream, uint64_t site, uint64_t cycle,
 {
     uint64_t group = sample / 64, lane = sample % 64;
     uint32_t u = 0;
-    for (int blk = 0; blk < 8; ++blk) {
-        uint64_t w[4];
-        stream_block(seed, stream, site, cycle, sweep, (uint64_t)blk, group, w);
-        for (int i = 0; i < 4; ++i) {
-            int j = 4 * blk + i;
-            uint32_t bit = (uint32_t)((w[i] >> lane) & 1ULL);
-            u |= bit << (31 - j);
-        }
+    for (int j = 0; j < 32; ++j) {
+        uint64_t w = stream_word(seed, stream, site, cycle, sweep, group, j);
+        uint32_t bit = (uint32_t)((w >> lane) & 1ULL);
+        u |= bit << (31 - j);
     }
     return u;
 }
@@ -130,9 +127,8 @@ int t3o_bernoulli(double p, uint64_t seed, int stream, uint64_t site, uint64_t c
 
 int t3o_coin(uint64_t seed, uint64_t site, int dir, uint64_t cycle, uint64_t sweep, uint64_t sample)
 {
-    uint64_t w[4];
-    stream_block(seed, STREAM_COIN, site, cycle, sweep, 0, sample / 64, w);
-    return (int)((w[dir] >> (sample % 64)) & 1ULL);
+    uint64_t w = stream_word(seed, STREAM_COIN, site, cycle, sweep, sample / 64, dir);
+    return (int)((w >> (sample % 64)) & 1ULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -779,8 +775,8 @@ int t3o_abi_version(void) { return 1; }
 /* many unsatisfied as satisfied checks (Sec. 3.2).  Noise keys the     */
 /* generator with the variable index as site (stream 0), measurement    */
 /* errors with the check index (stream 1), as on the toric code.  The   */
-/* p-flip coin of variable v is bit `lane` of output v mod 4 of block 0 */
-/* of stream 2 keyed by site v / 4 (one block serves four variables).   */
+/* p-flip coin of variable v is bit `lane` of word v mod 4 of stream 2 */
+/* keyed by site v / 4 (two blocks serve four variables).               */
 /* ------------------------------------------------------------------ */
 void t3o_tanner_syndrome(int64_t m, const int32_t* cptr, const int32_t* cvar, const uint8_t* e, uint8_t* s)
 {

@@ -339,7 +339,7 @@ k_pflip_decide(const __grid_constant__ ItemTable tab, uint64_t seed, uint32_t cy
                                   {s1, p1[mx], s0, p0[my]}};   // z-edge at r
         uint64_t* __restrict__ e0 = d.e + (int64_t)r * W + w;
         const uint64_t ex[3] = {e0[0], e0[L3W], e0[2 * L3W]};
-        const U64x4 c = coin_block(seed, (uint64_t)r, cycle, sweep, word_group(d, w));
+        const U64x4 c = coin_words(seed, (uint64_t)r, cycle, sweep, word_group(d, w));
         uint64_t f[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
@@ -911,6 +911,7 @@ static t3d_status sweeps_common(int L, int64_t words, uint64_t* e, uint64_t* s, 
     T3D_TRY(check_words(e, "e"));
     T3D_TRY(check_words(s, "s"));
     T3D_REQUIRE(n_apply >= 0, "negative number of applications");
+    T3D_REQUIRE((uint64_t)sweep0 + (uint64_t)n_apply <= kMaxSweep, "sweep indices must stay below 2^22");
     T3D_REQUIRE(sample0 % 64 == 0, "sample0 must be a multiple of 64");
     if (n_apply == 0) return T3D_OK;
     T3D_REQUIRE(schedule != nullptr, "schedule is NULL");

@@ -1,6 +1,6 @@
 // Device-side building blocks shared by the toric3d kernels: lattice index
 // arithmetic for the periodic L^3 cubic lattice (Sec. 2 of arXiv:2212.06985,
-// primal picture: qubits on edges, Z checks on faces), the Philox4x64-10
+// primal picture: qubits on edges, Z checks on faces), the Philox4x32-10
 // counter-based generator and the bit-sliced Bernoulli comparator.
 #pragma once
 
@@ -106,50 +106,62 @@ __device__ __forceinline__ FaceEdges face_edges(const Lattice& lat, int n, const
 // face_edges(): edge 0 = (a, r) when n != 1, edge 2 = (b, r) when n == 1.
 __device__ __forceinline__ int owned_edge_slot(int n) { return (n == 1) ? 2 : 0; }
 
-// ----------------------------------------------------------------- Philox4x64-10
+// ----------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
-// (SC'11): 10 rounds of two 64x64->128 multiplies and a word permutation, with
-// a Weyl key schedule.
-struct U64x4 {
-    uint64_t v[4];
+// (SC'11): 10 rounds of two 32x32->64 multiplies (one wide integer multiply
+// each) and a word permutation, with a Weyl key schedule.
+struct U32x4 {
+    uint32_t v[4];
 };
 
-__device__ __forceinline__ U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
-                                               uint64_t c3, uint64_t k0, uint64_t k1)
+__device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                               uint32_t k1)
 {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
         if (round > 0) {
             k0 += W0;
             k1 += W1;
         }
-        uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
-        uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
-        uint64_t n0 = hi1 ^ c1 ^ k0;
-        uint64_t n2 = hi0 ^ c3 ^ k1;
+        const uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
         c0 = n0;
-        c1 = lo1;
+        c1 = (uint32_t)p1;
         c2 = n2;
-        c3 = lo0;
+        c3 = (uint32_t)p0;
     }
-    U64x4 r;
+    U32x4 r;
     r.v[0] = c0; r.v[1] = c1; r.v[2] = c2; r.v[3] = c3;
     return r;
 }
 
 enum : uint32_t { kStreamQubit = 0, kStreamMeas = 1, kStreamCoin = 2 };
+constexpr uint32_t kMaxSweep = 1u << 22;   // sweep indices fit the counter's 22 bits
 
-__device__ __forceinline__ uint64_t stream_word3(uint32_t stream, uint32_t sweep, uint32_t block)
+// Block b of the random stream at (seed, stream, site, cycle, sweep, group): its
+// two 64-bit words are words 2b (outputs 0, 1) and 2b + 1 (outputs 2, 3).
+struct Words2 {
+    uint64_t w[2];
+};
+
+__device__ __forceinline__ Words2 stream_words(uint64_t seed, uint32_t stream, uint64_t site, uint32_t cycle,
+                                               uint32_t sweep, uint64_t group, uint32_t block)
 {
-    return ((uint64_t)stream << 48) | ((uint64_t)sweep << 8) | (uint64_t)block;
+    const U32x4 o = philox4x32_10((uint32_t)group, (uint32_t)site, cycle, (stream << 30) | (sweep << 8) | block,
+                                  (uint32_t)seed, (uint32_t)(seed >> 32));
+    Words2 r;
+    r.w[0] = (uint64_t)o.v[0] | ((uint64_t)o.v[1] << 32);
+    r.w[1] = (uint64_t)o.v[2] | ((uint64_t)o.v[3] << 32);
+    return r;
 }
 
 // 64 Bernoulli(P / 2^32) bits, one per sample of word `group`: lane j is set
-// iff U_j < P, with U_j the 32-bit integer whose bit 31-i is bit j of output
-// word i (word i = output i%4 of block i/4).  Evaluated as a bit-sliced
-// most-significant-first comparison that stops once every lane is decided.
+// iff U_j < P, with U_j the 32-bit integer whose bit 31-i is bit j of stream
+// word i.  Evaluated as a bit-sliced most-significant-first comparison that
+// stops once every lane is decided.
 __device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, uint32_t stream,
                                                    uint64_t site, uint32_t cycle, uint32_t sweep,
                                                    uint64_t group)
@@ -158,16 +170,16 @@ __device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, 
     if (thr >= (1ULL << 32)) return ~0ULL;
     uint64_t lt = 0, eq = ~0ULL;
 #pragma unroll 1
-    for (int blk = 0; blk < 8; ++blk) {
-        U64x4 w = philox4x64_10(group, site, cycle, stream_word3(stream, sweep, blk), seed, 0);
+    for (uint32_t blk = 0; blk < 16; ++blk) {
+        const Words2 w = stream_words(seed, stream, site, cycle, sweep, group, blk);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int bit = 31 - (4 * blk + i);
+        for (int i = 0; i < 2; ++i) {
+            const int bit = 31 - (int)(2 * blk + i);
             if ((thr >> bit) & 1ULL) {
-                lt |= eq & ~w.v[i];
-                eq &= w.v[i];
+                lt |= eq & ~w.w[i];
+                eq &= w.w[i];
             } else {
-                eq &= ~w.v[i];
+                eq &= ~w.w[i];
             }
         }
         if (eq == 0) break;
@@ -175,12 +187,21 @@ __device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, 
     return lt;
 }
 
-// p-flip coin words for 64 samples of the three edges at a site: output d of
-// block 0 of stream 2 keyed by the site is the coin word of its d-edge.
-__device__ __forceinline__ U64x4 coin_block(uint64_t seed, uint64_t site, uint32_t cycle, uint32_t sweep,
+// p-flip coin words for 64 samples of up to four variables keyed by one site:
+// stream-2 word d is the coin word of the site's d-th variable (d-edge of a
+// lattice site; variable 4 site + d of a generic code).
+struct U64x4 {
+    uint64_t v[4];
+};
+
+__device__ __forceinline__ U64x4 coin_words(uint64_t seed, uint64_t site, uint32_t cycle, uint32_t sweep,
                                             uint64_t group)
 {
-    return philox4x64_10(group, site, cycle, stream_word3(kStreamCoin, sweep, 0), seed, 0);
+    const Words2 a = stream_words(seed, kStreamCoin, site, cycle, sweep, group, 0);
+    const Words2 b = stream_words(seed, kStreamCoin, site, cycle, sweep, group, 1);
+    U64x4 r;
+    r.v[0] = a.w[0]; r.v[1] = a.w[1]; r.v[2] = b.w[0]; r.v[3] = b.w[1];
+    return r;
 }
 
 // ----------------------------------------------------------------- majority logic

@@ -68,7 +68,8 @@ t3d_status validate_cfg(const t3d_run_cfg* c)
     T3D_REQUIRE(c != nullptr, "cfg is NULL");
     T3D_REQUIRE(c->T >= 0, "T must be >= 0");
     T3D_REQUIRE(c->p >= 0.0 && c->p <= 1.0 && c->q >= 0.0 && c->q <= 1.0, "p, q must lie in [0,1]");
-    T3D_REQUIRE(c->n_apply >= 0, "n_apply must be >= 0");
+    T3D_REQUIRE(c->n_apply >= 0 && c->n_apply <= (int)kMaxSweep, "n_apply must lie in [0, 2^22]");
+    T3D_REQUIRE(!c->perfect_round || c->perfect_max_sweeps <= (int)kMaxSweep, "perfect_max_sweeps must be <= 2^22");
     size_t slen = strnlen(c->schedule, sizeof(c->schedule));
     T3D_REQUIRE(slen < sizeof(c->schedule), "schedule must be NUL-terminated");
     T3D_REQUIRE(c->n_apply == 0 || slen >= 1, "n_apply > 0 needs a schedule");

@@ -10,8 +10,8 @@
 // are 32 words x 8 indices.  The rule kernel keeps a vertical (bit-sliced)
 // counter of unsatisfied checks per variable and compares it with the
 // degree's majority and tie values; one thread decides four consecutive
-// variables, which share one Philox block for their coins (output v mod 4 of
-// the block keyed v / 4).  BP messages are FP32 on the Tanner edges in CSR
+// variables, which share their coins (word v mod 4 of the coin stream keyed
+// v / 4: two Philox blocks).  BP messages are FP32 on the Tanner edges in CSR
 // order, samples innermost ([edge][S]), double-buffered; an iteration is a
 // variable pass (totals T_v = prior_v + sum of incoming messages) and a
 // check pass (inputs T_v - M_{c->v}), four samples per thread, with the
@@ -118,7 +118,7 @@ __global__ void k_tg_decide(const G g, int64_t W, uint64_t* __restrict__ e, cons
     int64_t q, w;
     if (!index_word((g.n + 3) / 4, W, q, w)) return;
     U64x4 coins;
-    if (probabilistic) coins = coin_block(seed, (uint64_t)q, cycle, sweep, group0 + w);
+    if (probabilistic) coins = coin_words(seed, (uint64_t)q, cycle, sweep, group0 + w);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int64_t v = 4 * q + k;
@@ -462,6 +462,7 @@ extern "C" t3d_status toric3d_tanner_pflip(const t3d_tanner* g, int64_t n_sample
     T3D_REQUIRE(disjoint(e, (size_t)g->n_vars * words_for(n_samples) * 8, s, (size_t)g->n_checks * words_for(n_samples) * 8),
                 "e and s must not overlap");
     T3D_REQUIRE(n_apply >= 0, "n_apply must be >= 0");
+    T3D_REQUIRE((uint64_t)sweep0 + (uint64_t)n_apply <= kMaxSweep, "sweep indices must stay below 2^22");
     const size_t slen = schedule ? strnlen(schedule, 64) : 0;
     T3D_REQUIRE(n_apply == 0 || (slen >= 1 && slen < 64), "n_apply > 0 needs a schedule of 1..63 letters");
     for (size_t i = 0; i < slen; ++i)

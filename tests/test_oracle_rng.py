@@ -1,53 +1,115 @@
 """Pins of the oracle's random-number contract.
 
 The paper says only "random number in (0,1)" (Sec. 3.2) and nothing about how
-noise is sampled, so the generator is this project's reading: Philox4x64-10
-(Salmon et al., SC'11).  numpy ships an independent implementation of the same
-generator, which pins every output word exactly."""
+noise is sampled, so the generator is this project's reading: Philox4x32-10
+(Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+SC'11).  Two pins independent of the oracle: the generator's published
+known-answer vectors (the philox4x32 10-round entries of the Random123
+distribution's kat_vectors), and Triton's own implementation of the same
+generator (triton.language.random.philox_impl, run by Triton's CPU
+interpreter) on random counters and keys and on the counter shapes the
+library uses."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
 import oracle
 
+# Random123 kat_vectors, philox4x32 with 10 rounds: (counter, key, output)
+KAT = [
+    ([0x00000000, 0x00000000, 0x00000000, 0x00000000], [0x00000000, 0x00000000],
+     [0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8]),
+    ([0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff], [0xffffffff, 0xffffffff],
+     [0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd]),
+    ([0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344], [0xa4093822, 0x299f31d0],
+     [0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1]),
+]
 
-def _numpy_block(counter, key):
-    # numpy increments its 256-bit counter before producing a block
-    c = sum(int(x) << (64 * i) for i, x in enumerate(counter))
-    c = (c - 1) % (1 << 256)
-    c_prev = [(c >> (64 * i)) & ((1 << 64) - 1) for i in range(4)]
-    bg = np.random.Philox(key=np.array(key, dtype=np.uint64),
-                          counter=np.array(c_prev, dtype=np.uint64))
-    return bg.random_raw(4)
+
+@pytest.mark.parametrize("ctr,key,out", KAT)
+def test_philox_known_answers(ctr, key, out):
+    assert oracle.philox4x32(ctr, key).tolist() == out
 
 
-def test_philox_matches_numpy():
+_TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+from triton.language.random import philox_impl
+
+@triton.jit
+def k(ctr_ptr, key_ptr, out_ptr, N: tl.constexpr):
+    i = tl.arange(0, N)
+    c0 = tl.load(ctr_ptr + 4 * i); c1 = tl.load(ctr_ptr + 4 * i + 1)
+    c2 = tl.load(ctr_ptr + 4 * i + 2); c3 = tl.load(ctr_ptr + 4 * i + 3)
+    k0 = tl.load(key_ptr + 2 * i); k1 = tl.load(key_ptr + 2 * i + 1)
+    o0, o1, o2, o3 = philox_impl(c0, c1, c2, c3, k0, k1, 10)
+    tl.store(out_ptr + 4 * i, o0); tl.store(out_ptr + 4 * i + 1, o1)
+    tl.store(out_ptr + 4 * i + 2, o2); tl.store(out_ptr + 4 * i + 3, o3)
+
+data = json.loads(sys.stdin.read())
+n = len(data["key"]) // 2
+N = 1
+while N < n:
+    N *= 2
+ctr = torch.zeros(4 * N, dtype=torch.int64)
+ctr[:4 * n] = torch.tensor(data["ctr"], dtype=torch.int64)
+key = torch.zeros(2 * N, dtype=torch.int64)
+key[:2 * n] = torch.tensor(data["key"], dtype=torch.int64)
+out = torch.zeros(4 * N, dtype=torch.uint32)
+k[(1,)](ctr.to(torch.uint32), key.to(torch.uint32), out, N)
+print(json.dumps([int(x) & 0xffffffff for x in out[:4 * n].tolist()]))
+"""
+
+
+def _triton_blocks(ctrs, keys):
+    """Philox4x32-10 blocks from Triton's implementation, in a separate process (the
+    interpreter mode is process-wide)."""
+    pytest.importorskip("triton")
+    import json
+    r = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], capture_output=True, text=True, timeout=600,
+                       input=json.dumps({"ctr": [int(x) for c in ctrs for x in c],
+                                         "key": [int(x) for k in keys for x in k]}))
+    if r.returncode != 0:
+        pytest.skip("Triton's CPU interpreter is unavailable: " + r.stderr.strip().splitlines()[-1][:200])
+    flat = json.loads(r.stdout.strip().splitlines()[-1])
+    return [flat[4 * i:4 * i + 4] for i in range(len(ctrs))]
+
+
+def test_philox_matches_triton():
     rng = np.random.default_rng(123)
-    for _ in range(200):
-        ctr = rng.integers(1, 2 ** 63, 4, dtype=np.uint64)
-        key = rng.integers(0, 2 ** 63, 2, dtype=np.uint64)
-        assert np.array_equal(oracle.philox4x64(ctr, key), _numpy_block(ctr, key))
+    ctrs = rng.integers(0, 2 ** 32, (60, 4), dtype=np.uint64)
+    keys = rng.integers(0, 2 ** 32, (60, 2), dtype=np.uint64)
+    # the counter shapes the library uses: (group, site, cycle, stream<<30|sweep<<8|block), key (seed lo, seed hi)
+    shaped = [([1, 0, 1, 0], [0, 0]), ([5, 191, 3, (2 << 30) | (7 << 8)], [42, 0]),
+              ([1562, 98303, 32, (1 << 30) | 15], [5, 1 << 31]), ([15624, 331775, 1000, (2 << 30) | (63 << 8) | 1],
+                                                                  [0xdeadbeef, 0x12345678])]
+    ctrs = [list(c) for c in ctrs] + [c for c, _ in shaped]
+    keys = [list(k) for k in keys] + [k for _, k in shaped]
+    want = _triton_blocks(ctrs, keys)
+    for c, k, w in zip(ctrs, keys, want):
+        assert oracle.philox4x32(c, k).tolist() == w
 
 
-def test_philox_structured_counters_match_numpy():
-    # the counter shapes the library uses: (group, site, cycle, stream<<48|sweep<<8|blk)
-    for group, site, cycle, word3, seed in [(1, 0, 1, 0, 0), (5, 191, 3, (2 << 48) | (7 << 8), 42),
-                                            (1562, 98303, 32, (1 << 48) | 7, 2 ** 63 + 5)]:
-        ctr = np.array([group, site, cycle, word3], dtype=np.uint64)
-        key = np.array([seed, 0], dtype=np.uint64)
-        assert np.array_equal(oracle.philox4x64(ctr, key), _numpy_block(ctr, key))
+def _word(seed, stream, site, cycle, sweep, group, i):
+    """Word i of a stream position, assembled from single blocks as the contract states."""
+    out = oracle.philox4x32([group % 2 ** 32, site, cycle, (stream << 30) | (sweep << 8) | (i // 2)],
+                            [seed % 2 ** 32, seed >> 32])
+    j = 2 * (i % 2)
+    return int(out[j]) | (int(out[j + 1]) << 32)
 
 
 def test_uniform32_bit_assembly_uses_msb_first_words():
-    # U's bit (31-j) is bit `lane` of word j; word j = output j%4 of block j/4
-    seed, stream, site, cycle, sweep = 9, 1, 77, 4, 0
+    # U's bit (31-j) is bit `lane` of word j; word j = outputs 2(j%2), 2(j%2)+1 of block j/2
+    seed, stream, site, cycle, sweep = 9 + (3 << 32), 1, 77, 4, 0
     for sample in [64 * 3 + 0, 64 * 3 + 17, 64 * 3 + 63]:
         group, lane = sample // 64, sample % 64
         u = 0
-        for blk in range(8):
-            w = _numpy_block([group, site, cycle, (stream << 48) | (sweep << 8) | blk], [seed, 0])
-            for i in range(4):
-                j = 4 * blk + i
-                u |= ((int(w[i]) >> lane) & 1) << (31 - j)
+        for j in range(32):
+            u |= ((_word(seed, stream, site, cycle, sweep, group, j) >> lane) & 1) << (31 - j)
         assert oracle.uniform32(seed, stream, site, cycle, sweep, sample) == u
 
 
@@ -74,13 +136,13 @@ def test_bernoulli_is_u_less_than_threshold():
             assert oracle.bernoulli(p, seed, 0, 5, 2, 0, sample) == int(u < oracle.prob_to_threshold(p))
 
 
-def test_coin_is_bit_of_the_sites_block_and_fair():
-    """The coin of the d-edge at site r: output d of block 0 of stream 2 keyed by r."""
+def test_coin_is_bit_of_the_sites_words_and_fair():
+    """The coin of the d-edge at site r: word d of stream 2 keyed by r."""
     seed, L = 4, 3
     for sample in (0, 1, 63, 64, 200):
-        w = _numpy_block([sample // 64, 11, 3, (2 << 48) | (5 << 8)], [seed, 0])
         for d in range(3):
-            assert oracle.coin(seed, L, d * L ** 3 + 11, 3, 5, sample) == (int(w[d]) >> (sample % 64)) & 1
+            w = _word(seed, 2, 11, 3, 5, sample // 64, d)
+            assert oracle.coin(seed, L, d * L ** 3 + 11, 3, 5, sample) == (w >> (sample % 64)) & 1
     n = 20000
     heads = sum(oracle.coin(1, 7, i % 1029, 1, i // 1029, i) for i in range(n))
     assert abs(heads - n / 2) < 5 * (n / 4) ** 0.5

@@ -35,8 +35,8 @@ def test_toric_graph_reproduces_toric_oracle(L):
 
 @pytest.mark.parametrize("code", ["toric", "hgp"])
 def test_pflip_flips_majority_and_coin_chosen_ties(code):
-    """p-flip = the majority variables plus the tie variables whose coin (output v mod 4
-    of the block keyed v / 4) is 1; counts from the dense parity-check matrix."""
+    """p-flip = the majority variables plus the tie variables whose coin (word v mod 4
+    of the coin stream keyed v / 4) is 1; counts from the dense parity-check matrix."""
     if code == "toric":
         cptr, cvar = oracle.toric_tanner(3)
         n = 81
@@ -62,7 +62,7 @@ def test_pflip_flips_majority_and_coin_chosen_ties(code):
 
 
 def test_coin_key():
-    """The coin of variable v is output v mod 4 of the block keyed by site v / 4."""
+    """The coin of variable v is word v mod 4 of the coin stream keyed by site v / 4."""
     for v in (0, 1, 2, 3, 4, 7, 1001):
         for sample in (0, 5, 63, 64, 200):
             assert oracle.tanner_coin(9, v, 4, 2, sample) == oracle.lib().t3o_coin(9, v // 4, v % 4, 4, 2, sample)
