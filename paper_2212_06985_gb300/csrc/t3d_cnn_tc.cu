@@ -208,6 +208,12 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                  : "memory");
 }
 
+// Bring a global range toward the L2 ahead of its bulk copy (no completion to wait for).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -688,9 +694,9 @@ struct ColPos {
     int base, lo, hi;
 };
 
-__host__ __device__ inline int col_chunk_dx(bool bits_in, int p, int c) { return bits_in ? 2 * p - 1 + c : p - 1; }
+__host__ __device__ constexpr int col_chunk_dx(bool bits_in, int p, int c) { return bits_in ? 2 * p - 1 + c : p - 1; }
 
-__host__ __device__ inline bool col_reach(bool bits_in, int p, int jx)
+__host__ __device__ constexpr bool col_reach(bool bits_in, int p, int jx)
 {
     for (int c = 0; c < 2; ++c) {
         const int dx = col_chunk_dx(bits_in, p, c) - jx;
@@ -699,7 +705,7 @@ __host__ __device__ inline bool col_reach(bool bits_in, int p, int jx)
     return false;
 }
 
-__host__ __device__ inline ColPos col_pos(bool bits_in, int p, int b)
+__host__ __device__ constexpr ColPos col_pos(bool bits_in, int p, int b)
 {
     const int P = bits_in ? 2 : 4;
     int base = 0;
@@ -722,6 +728,21 @@ __host__ __device__ inline ColPos col_pos(bool bits_in, int p, int b)
             base += (4 - lo) + 4 + (hi + 1);
         }
     return r;
+}
+
+// The positions' table, evaluated at compile time so the issuer's unrolled loops
+// see constants.
+struct ColTable {
+    ColPos pos[16];
+};
+
+__host__ __device__ constexpr ColTable make_col_table(bool bits_in)
+{
+    ColTable t = {};
+    const int P = bits_in ? 2 : 4;
+    for (int b = 0; b < 4; ++b)
+        for (int p = 0; p < P; ++p) t.pos[b * P + p] = col_pos(bits_in, p, b);
+    return t;
 }
 
 __device__ __forceinline__ Unit col_unit_of(const TcArgs& a, int64_t u)
@@ -829,6 +850,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                 const Unit t = col_unit_of(a, u);
                 for (int zi = -1; zi <= L && ok; ++zi) {
                     const int zw = wrap(zi, L);
+                    // the tiles of input plane zi + 2 toward the L2, a ring's depth before their copies
+                    if (zi + 2 <= L) {
+                        const int zp = wrap(zi + 2, L);
+                        for (int yi = t.y - 1; yi <= t.y + 2; ++yi) {
+                            const int64_t row = ((int64_t)zp * L + wrap(yi, L)) * L;
+                            for (int i = 0; i < 4; ++i)
+                                bulk_prefetch_l2(a.in + ((row + wrap(t.x0 - 1 + i, L)) * a.Sp + t.m0) * in_row,
+                                                 tile_bytes);
+                        }
+                    }
                     for (int yi = t.y - 1; yi <= t.y + 2; ++yi) {
                         const int g = (int)(rseq % kColRows);
                         const uint32_t use = rseq / kColRows;
@@ -880,6 +911,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                     const int P1 = t1 - (zi - 1), P2 = t2 - (zi - 1);           // parts 0..2
                     const int s1 = (int)((qbase + t1) & 7);
                     const int wrap_at = s1 + (t2 - t1) > 7 ? t1 + (8 - s1) : -1;   // first plane in slot 0
+                    // the window of position (b, p): blocks 4 P1 .. 4 P2 + hi - lo of its sequence
+                    // into TMEM column 64 s1 + 16 lo, N = 16 (4 (P2 - P1) + hi - lo + 1)
+                    const uint64_t bdesc_plane = bdesc0 + (uint64_t)(128 * P1);
+                    const uint32_t idesc_plane = kIdescBase + ((uint32_t)(8 * (P2 - P1)) << 17);
+                    const uint32_t col_plane = tmem + (uint32_t)(s1 * kColPlaneCols);
+                    constexpr ColTable kTab = make_col_table(kBitsIn);
+#pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const int g = (int)(rseq % kColRows);
                         if (!wait_bar(full_bar(g), (rseq / kColRows) & 1u, abort_flag)) {
@@ -887,22 +925,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                             break;
                         }
                         const uint64_t adesc0 = smem_desc(ring + (uint32_t)g * kColRowBytes, a_lbo, a_sbo);
+                        if (wrap_at < 0) {
 #pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            const ColPos pos = s_pos[b * P + p];
-                            const uint64_t adesc = adesc0 + (uint64_t)(p * (kSlotBytes >> 4));
-                            auto issue = [&](int pa, int ja, int pz, int jz, int col) {
-                                // blocks (pa, ja) .. (pz, jz) of the sequence into TMEM column col
-                                const int b0 = 4 * pa + ja - pos.lo, nb = 4 * (pz - pa) + jz - ja + 1;
-                                mma_bf16_n(tmem + (uint32_t)col, adesc, bdesc0 + (uint64_t)(32 * (pos.base + b0)),
-                                           kIdescBase | ((uint32_t)(nb * 16 / 8) << 17));
-                            };
-                            if (wrap_at < 0) {
-                                issue(P1, pos.lo, P2, pos.hi, s1 * kColPlaneCols + pos.lo * kC);
-                            } else {
-                                const int Pw = wrap_at - (zi - 1);
-                                issue(P1, pos.lo, Pw - 1, 3, s1 * kColPlaneCols + pos.lo * kC);
-                                issue(Pw, 0, P2, pos.hi, 0);
+                            for (int p = 0; p < P; ++p) {
+                                const ColPos pos = kTab.pos[b * P + p];
+                                mma_bf16_n(col_plane + (uint32_t)(pos.lo * kC),
+                                           adesc0 + (uint64_t)(p * (kSlotBytes >> 4)),
+                                           bdesc_plane + (uint64_t)(32 * pos.base),
+                                           idesc_plane + ((uint32_t)(2 * (pos.hi - pos.lo + 1)) << 17));
+                            }
+                        } else {
+                            // the window crosses the ring's end: split at slot 0
+                            const int Pw = wrap_at - (zi - 1);
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                const ColPos pos = kTab.pos[b * P + p];
+                                const uint64_t adesc = adesc0 + (uint64_t)(p * (kSlotBytes >> 4));
+                                auto issue = [&](int pa, int ja, int pz, int jz, uint32_t col) {
+                                    // blocks (pa, ja) .. (pz, jz) of the sequence into TMEM column col
+                                    const int b0 = 4 * pa + ja - pos.lo, nb = 4 * (pz - pa) + jz - ja + 1;
+                                    mma_bf16_n(tmem + col, adesc, bdesc0 + (uint64_t)(32 * (pos.base + b0)),
+                                               kIdescBase | ((uint32_t)(nb * 2) << 17));
+                                };
+                                issue(P1, pos.lo, Pw - 1, 3, (uint32_t)(s1 * kColPlaneCols + pos.lo * kC));
+                                issue(Pw, 0, P2, pos.hi, 0u);
                             }
                         }
                         mma_commit(empty_bar(g));
