@@ -55,7 +55,10 @@ def test_bp_pflip_L32_full_size_sampled():
     checked = 0
     # S .. 64 W - 1 are the padding lanes of the last word: decoded like any sample (their own
     # keys), left out of the readout
-    for i in (0, 1, 63, 64, 25023, 25024, 77_777, S - 1, S):
+    # a lane is skipped when any of its 98,304 posteriors lies within 1e-4 of zero, which
+    # happens in roughly half the lanes; 20 candidates leave enough checked ones
+    for i in (0, 1, 2, 63, 64, 65, 127, 25023, 25024, 25025, 50_000, 50_047, 50_048, 77_777, 88_888,
+              99_900, 99_935, S - 2, S - 1, S):
         e0 = oracle.noise_batch(L, np.zeros((1, n), np.uint8), w.p, w.seed, i, 1)
         s0 = oracle.measure_batch(L, e0, w.q, w.seed, i, 1)
         _, llr = oracle.bp_batch(L, s0, w.p, w.q, True, w.bp_iters)
