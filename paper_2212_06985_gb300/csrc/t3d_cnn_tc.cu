@@ -418,46 +418,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     const uint32_t tile_bytes = kTileM * in_row;
 
     if (warp == kProducerWarp) {
-        if (lane == 0) {
-            // one row (fixed input y and z, x = x0-1 .. x0+fx) per slot group, one barrier phase each
-            uint32_t gseq = 0;
-            bool ok = true;
-            for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
-                const Unit t = unit_of(a, u);
-                for (int zi = -1; zi <= L && ok; ++zi) {
-                    const int zw = wrap(zi, L);
-                    for (int yi = t.y - 1; yi <= t.y + 1; ++yi) {
-                        const int g = (int)(gseq % kGroups);
-                        const uint32_t use = gseq / kGroups;
-                        if (use > 0 && !wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        // tiles x = x0-1 .. : pointer steps of one site, wrapping at x = L
-                        const int64_t row = ((int64_t)zw * L + wrap(yi, L)) * L;
-                        const int64_t site_bytes = a.Sp * in_row;
-                        const uint8_t* row_ptr = a.in + (row * a.Sp + t.m0) * in_row;
-                        int x = wrap(t.x0 - 1, L);
-                        const uint8_t* src = row_ptr + x * site_bytes;
-                        const int n_tiles = kBitsIn ? 2 * ((t.fx + 3) / 2) : t.fx + 2;
-                        const uint32_t dst_step = kBitsIn ? tile_bytes : (uint32_t)kSlotBytes;
-                        uint32_t dst = ring + (uint32_t)(g * kRowSlots) * kSlotBytes;
-                        mbar_arrive_expect_tx(full_bar(g), (uint32_t)n_tiles * tile_bytes);
-                        for (int i = 0; i < n_tiles; ++i) {
-                            bulk_load(dst, src, tile_bytes, full_bar(g));
-                            dst += dst_step;
-                            if (++x == L) {
-                                x = 0;
-                                src = row_ptr;
-                            } else {
-                                src += site_bytes;
-                            }
-                        }
-                        ++gseq;
+        // one row (fixed input y and z, x = x0-1 .. x0+fx) per slot group, one barrier phase each;
+        // lane i issues the row's tile i (bulk copies issued by many lanes at once move several
+        // times the bytes per clock of one issuing thread on GB300)
+        uint32_t gseq = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+            const Unit t = unit_of(a, u);
+            for (int zi = -1; zi <= L && ok; ++zi) {
+                const int zw = wrap(zi, L);
+                for (int yi = t.y - 1; yi <= t.y + 1; ++yi) {
+                    const int g = (int)(gseq % kGroups);
+                    const uint32_t use = gseq / kGroups;
+                    int good = 1;
+                    if (lane == 0 && use > 0) good = wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag) ? 1 : 0;
+                    if (!__shfl_sync(0xffffffffu, good, 0)) {
+                        ok = false;
+                        break;
                     }
+                    const int64_t row = ((int64_t)zw * L + wrap(yi, L)) * L;
+                    const int n_tiles = kBitsIn ? 2 * ((t.fx + 3) / 2) : t.fx + 2;
+                    const uint32_t dst_step = kBitsIn ? tile_bytes : (uint32_t)kSlotBytes;
+                    if (lane == 0) mbar_arrive_expect_tx(full_bar(g), (uint32_t)n_tiles * tile_bytes);
+                    __syncwarp();
+                    if (lane < n_tiles) {
+                        const int x = wrap(t.x0 - 1 + lane, L);   // x0 - 1 + lane < 2L
+                        bulk_load(ring + (uint32_t)(g * kRowSlots) * kSlotBytes + (uint32_t)lane * dst_step,
+                                  a.in + ((row + x) * a.Sp + t.m0) * in_row, tile_bytes, full_bar(g));
+                    }
+                    ++gseq;
                 }
             }
-            // copies still in flight land before the CTA exits
+        }
+        // copies still in flight land before the CTA exits
+        if (lane == 0) {
             const uint32_t last = gseq < (uint32_t)kGroups ? gseq : (uint32_t)kGroups;
             for (uint32_t g = 0; g < last; ++g) {
                 // the latest row issued on this group: the largest q < gseq with q % kGroups == g
@@ -673,14 +667,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
 // epilogue after it drains a plane (and once at the start), so every MMA
 // accumulates.  The first layer pairs x-adjacent input sites in one K = 16
 // operand (chunk c = site 2p - 1 + c of the row) as the line kernel does.
-constexpr int kColRows = 8;                               // input rows (4 tiles, one y and z) in flight
-constexpr int kColRowBytes = 4 * kSlotBytes;              // 16 KiB (first layer: 8 KiB used)
+constexpr int kColIn = 2;                                 // input planes (16 tiles each) in flight
+constexpr int kColInBytes = 16 * kSlotBytes;              // 64 KiB (first layer: 32 KiB used)
 constexpr int kColSlots = 8;                              // output planes resident in TMEM
 constexpr int kColPlaneCols = 4 * kC;                     // 64
 constexpr int kColWBlocks = 168;                          // windows of the 16 positions (hidden layers)
-constexpr int kColOffW = kColRows * kColRowBytes;
+constexpr int kColOffW = kColIn * kColInBytes;
 constexpr int kColOffBar = kColOffW + kColWBlocks * 512;
-constexpr int kColNumBars = 2 * kColRows + 2 * kColSlots + 1;   // full, empty, acc_full, acc_empty, done
+constexpr int kColNumBars = 2 * kColIn + 2 * kColSlots + 1;   // full, empty, acc_full, acc_empty, done
 constexpr int kColOffMisc = kColOffBar + kColNumBars * 8;
 constexpr int kColOffPos = kColOffMisc + 16;              // ColPos[16]
 constexpr int kColSmemBytes = kColOffPos + 16 * 12 + 1024;
@@ -767,10 +761,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
     const uint32_t wsm = ring + kColOffW;
     const uint32_t bars = ring + kColOffBar;
     auto full_bar = [&](int i) { return bars + 8u * (uint32_t)i; };
-    auto empty_bar = [&](int i) { return bars + 8u * (uint32_t)(kColRows + i); };
-    auto accf_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColRows + i); };
-    auto acce_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColRows + kColSlots + i); };
-    const uint32_t done_bar = bars + 8u * (uint32_t)(2 * kColRows + 2 * kColSlots);
+    auto empty_bar = [&](int i) { return bars + 8u * (uint32_t)(kColIn + i); };
+    auto accf_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColIn + i); };
+    auto acce_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColIn + kColSlots + i); };
+    const uint32_t done_bar = bars + 8u * (uint32_t)(2 * kColIn + 2 * kColSlots);
     uint32_t* misc = reinterpret_cast<uint32_t*>(sm + kColOffMisc);   // [0] TMEM base, [1] abort flag
     volatile uint32_t* abort_flag = misc + 1;
     ColPos* s_pos = reinterpret_cast<ColPos*>(sm + kColOffPos);   // [b * P + p]
@@ -811,7 +805,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
     }
     fence_proxy_async_smem();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kColRows; ++i) {
+        for (int i = 0; i < kColIn; ++i) {
             mbar_init(full_bar(i), 1);
             mbar_init(empty_bar(i), 1);
         }
@@ -843,53 +837,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
     const uint32_t tile_bytes = kTileM * in_row;
 
     if (warp == kProducerWarp) {
-        if (lane == 0) {
-            uint32_t rseq = 0;
-            bool ok = true;
-            for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
-                const Unit t = col_unit_of(a, u);
-                for (int zi = -1; zi <= L && ok; ++zi) {
-                    const int zw = wrap(zi, L);
-                    // the tiles of input plane zi + 2 toward the L2, a ring's depth before their copies
-                    if (zi + 2 <= L) {
-                        const int zp = wrap(zi + 2, L);
-                        for (int yi = t.y - 1; yi <= t.y + 2; ++yi) {
-                            const int64_t row = ((int64_t)zp * L + wrap(yi, L)) * L;
-                            for (int i = 0; i < 4; ++i)
-                                bulk_prefetch_l2(a.in + ((row + wrap(t.x0 - 1 + i, L)) * a.Sp + t.m0) * in_row,
-                                                 tile_bytes);
-                        }
-                    }
-                    for (int yi = t.y - 1; yi <= t.y + 2; ++yi) {
-                        const int g = (int)(rseq % kColRows);
-                        const uint32_t use = rseq / kColRows;
-                        if (use > 0 && !wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        const int64_t row = ((int64_t)zw * L + wrap(wrap(yi, L), L)) * L;
-                        uint32_t dst = ring + (uint32_t)g * kColRowBytes;
-                        mbar_arrive_expect_tx(full_bar(g), 4u * tile_bytes);
-                        for (int i = 0; i < 4; ++i) {
-                            const int xi = wrap(wrap(t.x0 - 1 + i, L), L);
-                            bulk_load(dst, a.in + ((row + xi) * a.Sp + t.m0) * in_row, tile_bytes, full_bar(g));
-                            dst += tile_bytes;
-                        }
-                        ++rseq;
-                    }
+        // one input plane (the 4 x 4 tiles around the column) per slot, one barrier phase
+        // each; lane 4 b + i issues the tile at (x0 - 1 + i, y0 - 1 + b)
+        uint32_t pseq = 0;
+        bool ok = true;
+        const int b = (lane >> 2) & 3, i = lane & 3;
+        for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
+            const Unit t = col_unit_of(a, u);
+            const int64_t xy = (int64_t)wrap(t.y - 1 + b, L) * L + wrap(t.x0 - 1 + i, L);
+            for (int zi = -1; zi <= L; ++zi) {
+                // the tiles of input plane zi + 2 toward the L2, a ring's depth before their copies
+                if (zi + 2 <= L && lane < 16)
+                    bulk_prefetch_l2(a.in + (((int64_t)wrap(zi + 2, L) * L * L + xy) * a.Sp + t.m0) * in_row,
+                                     tile_bytes);
+                const int g = (int)(pseq % kColIn);
+                const uint32_t use = pseq / kColIn;
+                int good = 1;
+                if (lane == 0 && use > 0) good = wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, good, 0)) {
+                    ok = false;
+                    break;
                 }
+                if (lane == 0) mbar_arrive_expect_tx(full_bar(g), 16u * tile_bytes);
+                __syncwarp();
+                if (lane < 16)
+                    bulk_load(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * tile_bytes,
+                              a.in + (((int64_t)wrap(zi, L) * L * L + xy) * a.Sp + t.m0) * in_row, tile_bytes,
+                              full_bar(g));
+                ++pseq;
             }
-            // copies still in flight land before the CTA exits
-            const uint32_t last = rseq < (uint32_t)kColRows ? rseq : (uint32_t)kColRows;
+        }
+        // copies still in flight land before the CTA exits
+        if (lane == 0) {
+            const uint32_t last = pseq < (uint32_t)kColIn ? pseq : (uint32_t)kColIn;
             for (uint32_t g = 0; g < last; ++g) {
-                const uint32_t q = rseq - 1 - ((rseq - 1 - g) % kColRows);
-                wait_bar(full_bar((int)g), (q / kColRows) & 1u, abort_flag, true);
+                const uint32_t q = pseq - 1 - ((pseq - 1 - g) % kColIn);
+                wait_bar(full_bar((int)g), (q / kColIn) & 1u, abort_flag, true);
             }
         }
         __syncwarp();
     } else if (warp == kIssuerWarp) {
         if (lane == 0) {
-            uint32_t rseq = 0;
+            uint32_t pseq = 0;
             int64_t qbase = 0;
             bool ok = true;
             const uint32_t a_lbo = kBitsIn ? 2048u : 128u, a_sbo = kBitsIn ? 128u : 256u;
@@ -917,14 +906,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                     const uint32_t idesc_plane = kIdescBase + ((uint32_t)(8 * (P2 - P1)) << 17);
                     const uint32_t col_plane = tmem + (uint32_t)(s1 * kColPlaneCols);
                     constexpr ColTable kTab = make_col_table(kBitsIn);
+                    const int g = (int)(pseq % kColIn);
+                    if (!wait_bar(full_bar(g), (pseq / kColIn) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
-                        const int g = (int)(rseq % kColRows);
-                        if (!wait_bar(full_bar(g), (rseq / kColRows) & 1u, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        const uint64_t adesc0 = smem_desc(ring + (uint32_t)g * kColRowBytes, a_lbo, a_sbo);
+                        const uint64_t adesc0 =
+                            smem_desc(ring + (uint32_t)g * kColInBytes + (uint32_t)b * 4u * tile_bytes, a_lbo, a_sbo);
                         if (wrap_at < 0) {
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
@@ -951,10 +941,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                                 issue(Pw, 0, P2, pos.hi, 0u);
                             }
                         }
-                        mma_commit(empty_bar(g));
-                        ++rseq;
                     }
-                    if (!ok) break;
+                    mma_commit(empty_bar(g));
+                    ++pseq;
                     // output plane zi - 1 has received its last contribution
                     if (zi - 1 >= 0) mma_commit(accf_bar((int)((qbase + zi - 1) & 7)));
                 }
