@@ -667,8 +667,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
 // epilogue after it drains a plane (and once at the start), so every MMA
 // accumulates.  The first layer pairs x-adjacent input sites in one K = 16
 // operand (chunk c = site 2p - 1 + c of the row) as the line kernel does.
-constexpr int kColIn = 4;                                 // input half-planes (8 tiles each) in flight
-constexpr int kColInBytes = 8 * kSlotBytes;               // 32 KiB (first layer: 16 KiB used)
+constexpr int kColIn = 2;                                 // input planes (16 tiles each) in flight
+constexpr int kColInBytes = 16 * kSlotBytes;              // 64 KiB (first layer: 32 KiB used)
 constexpr int kColSlots = 8;                              // output planes resident in TMEM
 constexpr int kColPlaneCols = 4 * kC;                     // 64
 constexpr int kColWBlocks = 168;                          // windows of the 16 positions (hidden layers)
@@ -837,41 +837,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
     const uint32_t tile_bytes = kTileM * in_row;
 
     if (warp == kProducerWarp) {
-        // one half input plane (rows b = 2h, 2h + 1 of the 4 x 4 tiles around the column) per
-        // slot, one barrier phase each; lane 4 b' + i issues the tile at (x0 - 1 + i, y0 - 1 + b),
-        // b = 2h + b'.  Many lanes issuing at once, and slots of this size, keep the copies
-        // ahead of the MMAs on GB300 (one thread issuing 4 KiB copies moves ~5 B/clk/SM).
+        // one input plane (the 4 x 4 tiles around the column) per slot, one barrier phase
+        // each; lane 4 b + i issues the tile at (x0 - 1 + i, y0 - 1 + b)
         uint32_t pseq = 0;
         bool ok = true;
         const int b = (lane >> 2) & 3, i = lane & 3;
         for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
             const Unit t = col_unit_of(a, u);
             const int64_t xy = (int64_t)wrap(t.y - 1 + b, L) * L + wrap(t.x0 - 1 + i, L);
-            const int64_t xy_h = (int64_t)wrap(t.y - 1 + (b & 1), L) * L + wrap(t.x0 - 1 + i, L);   // rows 0, 1
-            const int64_t xy_h2 = (int64_t)wrap(t.y + 1 + (b & 1), L) * L + wrap(t.x0 - 1 + i, L);  // rows 2, 3
-            for (int zi = -1; zi <= L && ok; ++zi) {
-                // the tiles of input plane zi + 2 toward the L2, ahead of their copies
+            for (int zi = -1; zi <= L; ++zi) {
+                // the tiles of input plane zi + 2 toward the L2, a ring's depth before their copies
                 if (zi + 2 <= L && lane < 16)
                     bulk_prefetch_l2(a.in + (((int64_t)wrap(zi + 2, L) * L * L + xy) * a.Sp + t.m0) * in_row,
                                      tile_bytes);
-                const int64_t zrow = (int64_t)wrap(zi, L) * L * L;
-                for (int h = 0; h < 2; ++h) {
-                    const int g = (int)(pseq % kColIn);
-                    const uint32_t use = pseq / kColIn;
-                    int good = 1;
-                    if (lane == 0 && use > 0) good = wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag) ? 1 : 0;
-                    if (!__shfl_sync(0xffffffffu, good, 0)) {
-                        ok = false;
-                        break;
-                    }
-                    if (lane == 0) mbar_arrive_expect_tx(full_bar(g), 8u * tile_bytes);
-                    __syncwarp();
-                    if (lane < 8)
-                        bulk_load(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * tile_bytes,
-                                  a.in + ((zrow + (h ? xy_h2 : xy_h)) * a.Sp + t.m0) * in_row, tile_bytes,
-                                  full_bar(g));
-                    ++pseq;
+                const int g = (int)(pseq % kColIn);
+                const uint32_t use = pseq / kColIn;
+                int good = 1;
+                if (lane == 0 && use > 0) good = wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, good, 0)) {
+                    ok = false;
+                    break;
                 }
+                if (lane == 0) mbar_arrive_expect_tx(full_bar(g), 16u * tile_bytes);
+                __syncwarp();
+                if (lane < 16)
+                    bulk_load(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * tile_bytes,
+                              a.in + (((int64_t)wrap(zi, L) * L * L + xy) * a.Sp + t.m0) * in_row, tile_bytes,
+                              full_bar(g));
+                ++pseq;
             }
         }
         // copies still in flight land before the CTA exits
@@ -913,18 +906,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                     const uint32_t idesc_plane = kIdescBase + ((uint32_t)(8 * (P2 - P1)) << 17);
                     const uint32_t col_plane = tmem + (uint32_t)(s1 * kColPlaneCols);
                     constexpr ColTable kTab = make_col_table(kBitsIn);
-                    int g = 0;
+                    const int g = (int)(pseq % kColIn);
+                    if (!wait_bar(full_bar(g), (pseq / kColIn) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
-                        if ((b & 1) == 0) {   // rows 2h, 2h + 1 arrive together
-                            g = (int)(pseq % kColIn);
-                            if (!wait_bar(full_bar(g), (pseq / kColIn) & 1u, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                        }
-                        const uint64_t adesc0 = smem_desc(
-                            ring + (uint32_t)g * kColInBytes + (uint32_t)(b & 1) * 4u * tile_bytes, a_lbo, a_sbo);
+                        const uint64_t adesc0 =
+                            smem_desc(ring + (uint32_t)g * kColInBytes + (uint32_t)b * 4u * tile_bytes, a_lbo, a_sbo);
                         if (wrap_at < 0) {
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
@@ -951,12 +941,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                                 issue(Pw, 0, P2, pos.hi, 0u);
                             }
                         }
-                        if (b & 1) {
-                            mma_commit(empty_bar(g));
-                            ++pseq;
-                        }
                     }
-                    if (!ok) break;
+                    mma_commit(empty_bar(g));
+                    ++pseq;
                     // output plane zi - 1 has received its last contribution
                     if (zi - 1 >= 0) mma_commit(accf_bar((int)((qbase + zi - 1) & 7)));
                 }
