@@ -354,6 +354,35 @@ __device__ __forceinline__ int wrap(int v, int L)
     return v < 0 ? v + L : (v >= L ? v - L : v);
 }
 
+// Activation layout: the tile of (site, 128-sample tile m) starts at byte
+// (m L^3 + site) tile_bytes, so a tile is contiguous and so are the tiles of
+// x-adjacent sites of one row (bulk copies of whole runs of a row move more
+// bytes per clock than one copy per tile).
+__device__ __forceinline__ int64_t tile_off(int64_t site, int64_t m0, int L3, uint32_t tile_bytes)
+{
+    return ((m0 >> 7) * L3 + site) * (int64_t)tile_bytes;
+}
+
+// Copy the tiles of sites row + wrap(x0 + i), i = 0 .. n - 1, to dst + i tile_bytes: one bulk
+// copy per run of consecutive sites (a row wraps at x = L at most once when n <= L + 2, twice
+// for the smallest lattices).  prefetch: bring them to the L2 instead.
+__device__ __forceinline__ void copy_row(uint32_t dst, const uint8_t* in, int64_t row, int x0, int n, int L, int L3,
+                                         int64_t m0, uint32_t tile_bytes, uint32_t bar, bool prefetch)
+{
+    int i = 0;
+    while (i < n) {
+        const int x = wrap(x0 + i, L);
+        int k = 1;
+        while (i + k < n && x + k < L && wrap(x0 + i + k, L) == x + k) ++k;
+        const uint8_t* src = in + tile_off(row + x, m0, L3, tile_bytes);
+        if (prefetch)
+            bulk_prefetch_l2(src, (uint32_t)k * tile_bytes);
+        else
+            bulk_load(dst + (uint32_t)i * tile_bytes, src, (uint32_t)k * tile_bytes, bar);
+        i += k;
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 template <bool kHead, bool kBitsIn>
 __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant__ TcArgs a)
@@ -418,9 +447,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     const uint32_t tile_bytes = kTileM * in_row;
 
     if (warp == kProducerWarp) {
-        // one row (fixed input y and z, x = x0-1 .. x0+fx) per slot group, one barrier phase each;
-        // lane i issues the row's tile i (bulk copies issued by many lanes at once move several
-        // times the bytes per clock of one issuing thread on GB300)
+        // one row (fixed input y and z, x = x0-1 .. x0+fx) per slot group, one barrier phase each,
+        // copied in runs of x-adjacent tiles (contiguous in the tile-major layout)
         uint32_t gseq = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
@@ -438,13 +466,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
                     }
                     const int64_t row = ((int64_t)zw * L + wrap(yi, L)) * L;
                     const int n_tiles = kBitsIn ? 2 * ((t.fx + 3) / 2) : t.fx + 2;
-                    const uint32_t dst_step = kBitsIn ? tile_bytes : (uint32_t)kSlotBytes;
-                    if (lane == 0) mbar_arrive_expect_tx(full_bar(g), (uint32_t)n_tiles * tile_bytes);
-                    __syncwarp();
-                    if (lane < n_tiles) {
-                        const int x = wrap(t.x0 - 1 + lane, L);   // x0 - 1 + lane < 2L
-                        bulk_load(ring + (uint32_t)(g * kRowSlots) * kSlotBytes + (uint32_t)lane * dst_step,
-                                  a.in + ((row + x) * a.Sp + t.m0) * in_row, tile_bytes, full_bar(g));
+                    if (lane == 0) {
+                        // the row's tiles land tile_bytes apart in the slot group, in runs of
+                        // consecutive sites
+                        mbar_arrive_expect_tx(full_bar(g), (uint32_t)n_tiles * tile_bytes);
+                        copy_row(ring + (uint32_t)(g * kRowSlots) * kSlotBytes, a.in, row, t.x0 - 1, n_tiles, L, a.L3,
+                                 t.m0, tile_bytes, full_bar(g), false);
                     }
                     ++gseq;
                 }
@@ -611,7 +638,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
 #pragma unroll
                             for (int c = 0; c < kC; c += 2)
                                 p[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
-                            uint8_t* dst = a.out + (site * a.Sp + t.m0) * 32 + (r >> 3) * 256 + (r & 7) * 16;
+                            uint8_t* dst = a.out + tile_off(site, t.m0, a.L3, 4096) + (r >> 3) * 256 + (r & 7) * 16;
                             *reinterpret_cast<uint4*>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
                             *reinterpret_cast<uint4*>(dst + 128) = make_uint4(p[4], p[5], p[6], p[7]);
                         } else {
@@ -837,19 +864,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
     const uint32_t tile_bytes = kTileM * in_row;
 
     if (warp == kProducerWarp) {
-        // one input plane (the 4 x 4 tiles around the column) per slot, one barrier phase
-        // each; lane 4 b + i issues the tile at (x0 - 1 + i, y0 - 1 + b)
+        // one input plane (the 4 x 4 tiles around the column) per slot, one barrier phase each;
+        // lane b copies row b (yi = y0 - 1 + b): its four x-adjacent tiles are contiguous, one
+        // 16 KiB bulk copy (two where the row wraps)
         uint32_t pseq = 0;
         bool ok = true;
-        const int b = (lane >> 2) & 3, i = lane & 3;
         for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
             const Unit t = col_unit_of(a, u);
-            const int64_t xy = (int64_t)wrap(t.y - 1 + b, L) * L + wrap(t.x0 - 1 + i, L);
+            const int yb = wrap(t.y - 1 + (lane & 3), L);
             for (int zi = -1; zi <= L; ++zi) {
                 // the tiles of input plane zi + 2 toward the L2, a ring's depth before their copies
-                if (zi + 2 <= L && lane < 16)
-                    bulk_prefetch_l2(a.in + (((int64_t)wrap(zi + 2, L) * L * L + xy) * a.Sp + t.m0) * in_row,
-                                     tile_bytes);
+                if (zi + 2 <= L && lane < 4)
+                    copy_row(0, a.in, ((int64_t)wrap(zi + 2, L) * L + yb) * L, t.x0 - 1, 4, L, a.L3, t.m0,
+                             tile_bytes, 0, true);
                 const int g = (int)(pseq % kColIn);
                 const uint32_t use = pseq / kColIn;
                 int good = 1;
@@ -860,10 +887,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                 }
                 if (lane == 0) mbar_arrive_expect_tx(full_bar(g), 16u * tile_bytes);
                 __syncwarp();
-                if (lane < 16)
-                    bulk_load(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * tile_bytes,
-                              a.in + (((int64_t)wrap(zi, L) * L * L + xy) * a.Sp + t.m0) * in_row, tile_bytes,
-                              full_bar(g));
+                if (lane < 4)
+                    copy_row(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * 4u * tile_bytes, a.in,
+                             ((int64_t)wrap(zi, L) * L + yb) * L, t.x0 - 1, 4, L, a.L3, t.m0, tile_bytes, full_bar(g),
+                             false);
                 ++pseq;
             }
         }
@@ -1004,7 +1031,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
 #pragma unroll
                         for (int c = 0; c < kC; c += 2)
                             pk[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
-                        uint8_t* dst = a.out + (site * a.Sp + t.m0) * 32 + (r >> 3) * 256 + (r & 7) * 16;
+                        uint8_t* dst = a.out + tile_off(site, t.m0, a.L3, 4096) + (r >> 3) * 256 + (r & 7) * 16;
                         *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                     } else {
@@ -1062,7 +1089,9 @@ __global__ void k_expand_bits(int L3, int64_t Sp, int64_t W, int64_t words, cons
         }
     }
     constexpr uint32_t one = 0x3F80u;   // BF16 1.0
-    uint4* dst = out + site * Sp + m0 + lane;
+    // tile-major layout: samples m0 .. m0 + 127 in tile m0 / 128 of the site, the next 128 in
+    // the next tile (L3 tiles further)
+    uint4* dst = out + ((m0 >> 7) * L3 + site) * kTileM + lane;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         if (m0 + 32 * j >= Sp) break;
@@ -1070,7 +1099,8 @@ __global__ void k_expand_bits(int L3, int64_t Sp, int64_t W, int64_t words, cons
         uint32_t h[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) h[c] = ((__shfl_sync(0xffffffffu, half, c * 4 + (j >> 1)) >> lane) & 1u) * one;
-        dst[32 * j] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), 0u);
+        dst[(j >> 2) * (int64_t)L3 * kTileM + 32 * (j & 3)] =
+            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), 0u);
     }
 }
 
