@@ -865,18 +865,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
 
     if (warp == kProducerWarp) {
         // one input plane (the 4 x 4 tiles around the column) per slot, one barrier phase each;
-        // lane b copies row b (yi = y0 - 1 + b): its four x-adjacent tiles are contiguous, one
-        // 16 KiB bulk copy (two where the row wraps)
+        // lane 4 b + i copies the tile at (x0 - 1 + i, y0 - 1 + b).  Sixteen lanes issuing 4 KiB
+        // copies at once measured faster here than four lanes issuing a row's 16 KiB each.
         uint32_t pseq = 0;
         bool ok = true;
+        const int b = (lane >> 2) & 3, i = lane & 3;
         for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
             const Unit t = col_unit_of(a, u);
-            const int yb = wrap(t.y - 1 + (lane & 3), L);
+            const int64_t xy = (int64_t)wrap(t.y - 1 + b, L) * L + wrap(t.x0 - 1 + i, L);
             for (int zi = -1; zi <= L; ++zi) {
                 // the tiles of input plane zi + 2 toward the L2, a ring's depth before their copies
-                if (zi + 2 <= L && lane < 4)
-                    copy_row(0, a.in, ((int64_t)wrap(zi + 2, L) * L + yb) * L, t.x0 - 1, 4, L, a.L3, t.m0,
-                             tile_bytes, 0, true);
+                if (zi + 2 <= L && lane < 16)
+                    bulk_prefetch_l2(a.in + tile_off((int64_t)wrap(zi + 2, L) * L * L + xy, t.m0, a.L3, tile_bytes),
+                                     tile_bytes);
                 const int g = (int)(pseq % kColIn);
                 const uint32_t use = pseq / kColIn;
                 int good = 1;
@@ -887,10 +888,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                 }
                 if (lane == 0) mbar_arrive_expect_tx(full_bar(g), 16u * tile_bytes);
                 __syncwarp();
-                if (lane < 4)
-                    copy_row(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * 4u * tile_bytes, a.in,
-                             ((int64_t)wrap(zi, L) * L + yb) * L, t.x0 - 1, 4, L, a.L3, t.m0, tile_bytes, full_bar(g),
-                             false);
+                if (lane < 16)
+                    bulk_load(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * tile_bytes,
+                              a.in + tile_off((int64_t)wrap(zi, L) * L * L + xy, t.m0, a.L3, tile_bytes), tile_bytes,
+                              full_bar(g));
                 ++pseq;
             }
         }
