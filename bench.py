@@ -328,10 +328,14 @@ def learned_leg(args, t3d, w, S, sample0, dev, stream, barrier, world, peaks):
 # the flip words (0.875 B).
 SWEEP_BYTES = {"noise": 0.25, "syndrome": 0.25, "flip": 0.5, "pflip": 0.875}
 # Warp instructions per 64-sample word of each qubit (noise), check (syndrome)
-# or site (one p-flip application) at p = q = 4%, from one ncu capture of the
-# current kernels (smsp__inst_executed.sum over the launch's words); None until
-# captured.  The Philox arithmetic binds these kernels on the issue rate.
-SWEEP_INST = {"noise": None, "syndrome": None, "pflip": None}
+# or site (the decision pass of one p-flip application) at p = q = 4%, from one
+# ncu capture of the current kernels (smsp__inst_executed.sum / (units x words),
+# L = 32, 8192 samples: 298.2 M, 341.0 M and 67.1 M instructions).  The Philox
+# arithmetic binds these kernels on the instruction issue rate.
+SWEEP_INST_P = 0.04
+SWEEP_INST = {"noise": 298.2e6 / (98304 * 128), "syndrome": 341.0e6 / (98304 * 128), "pflip": 67.1e6 / (32768 * 128)}
+# The p-flip syndrome pass reads the flip words and updates s in place (0.375 B).
+PFLIP_APPLY_BYTES = 0.375
 
 
 def sweep_roofline(prof, w, qubits, S, steps, ms, hbm_peak, peak_source, clk):
@@ -357,8 +361,24 @@ def sweep_roofline(prof, w, qubits, S, steps, ms, hbm_peak, peak_source, clk):
            "traffic": None, "peak_source": peak_source}
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     units = {"noise": qubits, "syndrome": qubits, "pflip": qubits // 3}   # edges, faces, sites
-    if SWEEP_INST.get(dom):
-        peak = 152 * 4 * sm_mhz * 1e6 / 1e9
+    issue_peak = 152 * 4 * sm_mhz * 1e6                  # warp instructions per second
+    inst_known = abs(w.p - SWEEP_INST_P) < 1e-12 and abs(w.q - SWEEP_INST_P) < 1e-12
+    if inst_known:
+        # the cycle's bound: every kernel at the slower of its HBM and issue bounds
+        hbm = hbm_peak * 1e9
+        b_noise = max(SWEEP_BYTES["noise"] * qubits * S / hbm, SWEEP_INST["noise"] * units["noise"] * words / issue_peak)
+        b_syn = max(SWEEP_BYTES["syndrome"] * qubits * S / hbm,
+                    SWEEP_INST["syndrome"] * units["syndrome"] * words / issue_peak)
+        b_flip = SWEEP_BYTES["flip"] * qubits * S / hbm
+        b_pflip = (max((SWEEP_BYTES["pflip"] - PFLIP_APPLY_BYTES) * qubits * S / hbm,
+                       SWEEP_INST["pflip"] * units["pflip"] * words / issue_peak) + PFLIP_APPLY_BYTES * qubits * S / hbm)
+        bound_s = b_noise + b_syn + per_step["flip"] * b_flip + per_step["pflip"] * b_pflip
+        out["cycle_bound_ms"] = 1e3 * bound_s
+        out["cycle_roofline_frac"] = bound_s / (ms / 1e3 / steps)
+        out["cycle_roofline"] = ("sum over the cycle's kernels of max(algorithmic bytes / HBM peak, warp "
+                                 "instructions / issue peak), decode kernels only (the readout is extra)")
+    if inst_known and SWEEP_INST.get(dom):
+        peak = issue_peak / 1e9
         achieved = SWEEP_INST[dom] * units[dom] * words / t_app / 1e9
         out.update(bound="alu", achieved=achieved, peak=peak, unit="Ginst/s", frac=achieved / peak,
                    peak_derivation=f"152 SMs x 4 schedulers x 1 warp instruction/clock x {sm_mhz:.0f} MHz")
