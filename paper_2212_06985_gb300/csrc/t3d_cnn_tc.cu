@@ -888,10 +888,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                 }
                 if (lane == 0) mbar_arrive_expect_tx(full_bar(g), 16u * tile_bytes);
                 __syncwarp();
-                if (lane < 16)
+                if (kBitsIn) {
+                    // 2 KiB tiles: lane b copies row b's four contiguous tiles (8 KiB) in one run
+                    if (lane < 4)
+                        copy_row(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * 4u * tile_bytes, a.in,
+                                 ((int64_t)wrap(zi, L) * L + wrap(t.y - 1 + lane, L)) * L, t.x0 - 1, 4, L, a.L3, t.m0,
+                                 tile_bytes, full_bar(g), false);
+                } else if (lane < 16) {
                     bulk_load(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * tile_bytes,
                               a.in + tile_off((int64_t)wrap(zi, L) * L * L + xy, t.m0, a.L3, tile_bytes), tile_bytes,
                               full_bar(g));
+                }
                 ++pseq;
             }
         }
