@@ -41,7 +41,7 @@ VALUE_IS = "BP+p-flip; learned_pflip.value = learned+p-flip, learned_pflip.vs_bp
 # ncu capture of the current k_bp_step (L = 32, 1024 samples; traffic grows in
 # proportion to the samples a launch covers, so it scales to full launches).
 # Set to None when the kernel changes until it is captured again.
-BP_STEP_TRAFFIC = {"first_iteration": 15.68, "full_iteration": 31.94}
+BP_STEP_TRAFFIC = {"first_iteration": 15.69, "full_iteration": 31.90}
 UNIT = "qubit-cycles/s"
 
 
