@@ -707,9 +707,6 @@ constexpr int kColOffPos = kColOffMisc + 16;              // ColPos[16]
 constexpr int kColSmemBytes = kColOffPos + 16 * 12 + 1024;
 static_assert(kColSmemBytes <= 227 * 1024, "shared memory budget");
 static_assert(kColSlots * kColPlaneCols == 512, "TMEM ring");
-constexpr int kColProducerWarp = 8;                       // warps 0-7: two epilogue groups of four
-constexpr int kColIssuerWarp = 9;
-constexpr int kColThreads = 32 * (kColIssuerWarp + 1);   // 320
 
 // Operand position p of a row (hidden: the site x0 - 1 + p; first layer: the
 // pair x0 - 1 + 2p, x0 + 2p) at row b (yi = y0 - 1 + b): the column sites in
@@ -783,7 +780,7 @@ __device__ __forceinline__ Unit col_unit_of(const TcArgs& a, int64_t u)
 }
 
 template <bool kHead, bool kBitsIn>
-__global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_constant__ TcArgs a)
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constant__ TcArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -847,7 +844,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_consta
         misc[1] = 0;
         fence_mbar_init();
     }
-    if (warp == kColIssuerWarp) tmem_alloc(smem_u32(misc), kTmemCols);
+    if (warp == kIssuerWarp) tmem_alloc(smem_u32(misc), kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -866,7 +863,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_consta
     const uint32_t in_row = kBitsIn ? 16u : 32u;
     const uint32_t tile_bytes = kTileM * in_row;
 
-    if (warp == kColProducerWarp) {
+    if (warp == kProducerWarp) {
         // one input plane (the 4 x 4 tiles around the column) per slot, one barrier phase each;
         // lane 4 b + i copies the tile at (x0 - 1 + i, y0 - 1 + b).  Sixteen lanes issuing 4 KiB
         // copies at once measured faster here than four lanes issuing a row's 16 KiB each.
@@ -914,7 +911,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_consta
             }
         }
         __syncwarp();
-    } else if (warp == kColIssuerWarp) {
+    } else if (warp == kIssuerWarp) {
         if (lane == 0) {
             uint32_t pseq = 0;
             int64_t qbase = 0;
@@ -993,11 +990,8 @@ __global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_consta
         }
         __syncwarp();
     } else {
-        // epilogue: two groups of four warps drain alternate planes (one group's TMEM loads and
-        // stores overlap the other's arithmetic); warp w owns TMEM lanes (= tile rows =
-        // samples) 32 (w mod 4) .. + 31
-        const int ew = warp & 3, grp = warp >> 2;
-        const int r = ew * 32 + lane;
+        // epilogue: warp w owns TMEM lanes (= tile rows = samples) 32w .. 32w + 31
+        const int r = warp * 32 + lane;
         float bias[kC];
 #pragma unroll
         for (int c = 0; c < kC; ++c) bias[c] = a.bias[c];
@@ -1016,7 +1010,6 @@ __global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_consta
             const int64_t sample = t.m0 + r;
             const bool valid = sample < a.n_samples;
             for (int zo = 0; zo < L; ++zo, ++q) {
-                if ((int)(q & 1) != grp) continue;
                 const int s = (int)(q & 7);
                 int got = 1;
                 if (lane == 0) got = wait_bar(accf_bar(s), (uint32_t)(q >> 3) & 1u, abort_flag) ? 1 : 0;
@@ -1026,7 +1019,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_consta
                     break;
                 }
                 tc_fence_after();
-                const uint32_t lane_base = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(s * kColPlaneCols);
+                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kColPlaneCols);
                 uint32_t raw[4][16];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) tmem_ld16(lane_base + (uint32_t)(j * kC), raw[j]);
@@ -1057,8 +1050,8 @@ __global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_consta
 #pragma unroll
                             for (int d = 0; d < 3; ++d) z[d] = fmaf(y, w4[d * kC + c], z[d]);
                         }
-                        const int64_t wd = (t.m0 + ew * 32) / 64;
-                        const int hw = ew & 1;
+                        const int64_t wd = (t.m0 + warp * 32) / 64;
+                        const int hw = warp & 1;
 #pragma unroll
                         for (int d = 0; d < 3; ++d) {
                             if (a.logits && valid)
@@ -1077,7 +1070,7 @@ __global__ void __launch_bounds__(kColThreads, 1) k_conv_col(const __grid_consta
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == kColIssuerWarp) {
+    if (warp == kIssuerWarp) {
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
     }
@@ -1145,7 +1138,7 @@ t3d_status launch_conv_col(const TcArgs& a, cudaStream_t st)
 {
     const int grid = (int)std::min<int64_t>(a.n_units, sm_count());
     ProfScope prof(T3D_K_CNN, st);
-    k_conv_col<kHead, kBitsIn><<<grid, kColThreads, kColSmemBytes, st>>>(a);
+    k_conv_col<kHead, kBitsIn><<<grid, kTcThreads, kColSmemBytes, st>>>(a);
     T3D_LAUNCH_CHECK("tensor-core convolution (2 x 2 columns)");
     return T3D_OK;
 }
