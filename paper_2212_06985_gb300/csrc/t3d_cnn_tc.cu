@@ -874,10 +874,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
             const Unit t = col_unit_of(a, u);
             const int64_t xy = (int64_t)wrap(t.y - 1 + b, L) * L + wrap(t.x0 - 1 + i, L);
             for (int zi = -1; zi <= L; ++zi) {
-                // the tiles of input plane zi + 2 toward the L2, a ring's depth before their copies
-                if (zi + 2 <= L && lane < 16)
-                    bulk_prefetch_l2(a.in + tile_off((int64_t)wrap(zi + 2, L) * L * L + xy, t.m0, a.L3, tile_bytes),
-                                     tile_bytes);
                 const int g = (int)(pseq % kColIn);
                 const uint32_t use = pseq / kColIn;
                 int good = 1;
