@@ -694,14 +694,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
 // epilogue after it drains a plane (and once at the start), so every MMA
 // accumulates.  The first layer pairs x-adjacent input sites in one K = 16
 // operand (chunk c = site 2p - 1 + c of the row) as the line kernel does.
-constexpr int kColIn = 2;                                 // input planes (16 tiles each) in flight
-constexpr int kColInBytes = 16 * kSlotBytes;              // 64 KiB (first layer: 32 KiB used)
+// Input ring of 128 KiB: two planes of 16 x 4 KiB tiles (hidden layers) or four of 16 x 2 KiB
+// (first layer).
+constexpr int kColRingBytes = 32 * kSlotBytes;
+__host__ __device__ constexpr int col_in_slots(bool bits_in) { return bits_in ? 4 : 2; }
+constexpr int kColInMax = 4;
 constexpr int kColSlots = 8;                              // output planes resident in TMEM
 constexpr int kColPlaneCols = 4 * kC;                     // 64
 constexpr int kColWBlocks = 168;                          // windows of the 16 positions (hidden layers)
-constexpr int kColOffW = kColIn * kColInBytes;
+constexpr int kColOffW = kColRingBytes;
 constexpr int kColOffBar = kColOffW + kColWBlocks * 512;
-constexpr int kColNumBars = 2 * kColIn + 2 * kColSlots + 1;   // full, empty, acc_full, acc_empty, done
+constexpr int kColNumBars = 2 * kColInMax + 2 * kColSlots + 1;   // full, empty, acc_full, acc_empty, done
 constexpr int kColOffMisc = kColOffBar + kColNumBars * 8;
 constexpr int kColOffPos = kColOffMisc + 16;              // ColPos[16]
 constexpr int kColSmemBytes = kColOffPos + 16 * 12 + 1024;
@@ -787,11 +790,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
     const uint32_t ring = smem_u32(sm);
     const uint32_t wsm = ring + kColOffW;
     const uint32_t bars = ring + kColOffBar;
+    constexpr int kColIn = col_in_slots(kBitsIn);
+    constexpr uint32_t kColInBytes = (uint32_t)(kColRingBytes / kColIn);
     auto full_bar = [&](int i) { return bars + 8u * (uint32_t)i; };
-    auto empty_bar = [&](int i) { return bars + 8u * (uint32_t)(kColIn + i); };
-    auto accf_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColIn + i); };
-    auto acce_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColIn + kColSlots + i); };
-    const uint32_t done_bar = bars + 8u * (uint32_t)(2 * kColIn + 2 * kColSlots);
+    auto empty_bar = [&](int i) { return bars + 8u * (uint32_t)(kColInMax + i); };
+    auto accf_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColInMax + i); };
+    auto acce_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kColInMax + kColSlots + i); };
+    const uint32_t done_bar = bars + 8u * (uint32_t)(2 * kColInMax + 2 * kColSlots);
     uint32_t* misc = reinterpret_cast<uint32_t*>(sm + kColOffMisc);   // [0] TMEM base, [1] abort flag
     volatile uint32_t* abort_flag = misc + 1;
     ColPos* s_pos = reinterpret_cast<ColPos*>(sm + kColOffPos);   // [b * P + p]
