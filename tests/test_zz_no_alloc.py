@@ -45,3 +45,31 @@ def test_noalloc_flip_rejects_sizes_beyond_its_scratch():
     s = torch.zeros_like(e)
     with pytest.raises(t3d.T3DError, match="built-in scratch"):
         t3d.toric3d_flip_noalloc(L, e, s, 1)
+
+
+def test_noalloc_flip_replayed_from_a_captured_graph():
+    # the use the entry point exists for: after one eager call (which looks up the scratch
+    # address outside any capture), a call captured on a side stream into a CUDA graph and
+    # replayed, each replay checked against toric3d_flip with a workspace
+    L, S, sweeps = 6, 500, 3
+    ebits, sbits = _noisy(L, S, seed=11)
+    e_ref, s_ref = upload_bits(ebits), upload_bits(sbits)
+    e_na, s_na = upload_bits(ebits), upload_bits(sbits)
+    work = workspace(t3d.toric3d_flip_workspace_bytes(L, e_ref.shape[1]))
+    t3d.toric3d_flip(L, e_ref, s_ref, 1, work)
+    t3d.toric3d_flip_noalloc(L, e_na, s_na, 1)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        t3d.toric3d_flip_noalloc(L, e_na, s_na, sweeps, stream=side)
+    torch.cuda.synchronize()
+    # capturing ran nothing: the states still match after the eager call
+    assert np.array_equal(download_bits(e_na, S), download_bits(e_ref, S))
+    for replay in range(2):
+        graph.replay()
+        t3d.toric3d_flip(L, e_ref, s_ref, sweeps, work)
+        torch.cuda.synchronize()
+        assert np.array_equal(download_bits(e_na, S), download_bits(e_ref, S)), replay
+        assert np.array_equal(download_bits(s_na, S), download_bits(s_ref, S)), replay
