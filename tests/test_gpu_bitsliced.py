@@ -85,8 +85,9 @@ def test_plain_flip_entry_point():
 
 
 @pytest.mark.parametrize("L,S,density", [(2, 200, 0.4), (3, 500, 0.3), (4, 1000, 0.45), (5, 99, 0.5),
-                                         (8, 130, 0.5)])
+                                         (8, 130, 0.5), (6, 5000, 0.45), (16, 700, 0.5)])
 def test_logical_matches_oracle(L, S, density):
+    # 5000 samples: 79 words, ten word tiles with a ragged last one; L = 16: 256 lines per axis
     n = 3 * L ** 3
     ebits = inp.random_bits(S, n, density, seed=L)
     e = upload_bits(ebits)
