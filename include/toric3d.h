@@ -101,6 +101,28 @@ size_t toric3d_flip_workspace_bytes(int L, int64_t words);
 t3d_status toric3d_flip(int L, int64_t words, uint64_t* e, uint64_t* s, int sweeps, void* work,
                         size_t work_bytes, t3d_stream stream);
 
+/* Workspace for toric3d_flip_until_clear: the syndrome copy of toric3d_flip plus
+ * 256 bytes of flags. */
+size_t toric3d_flip_until_clear_workspace_bytes(int L, int64_t words);
+
+/*
+ * Parallel flip until the syndrome clears (Sec. 3.1: the decoder repeats the
+ * flip until no check is unsatisfied or a sweep limit is reached): at most
+ * max_sweeps applications of the toric3d_flip rule; once an application
+ * leaves no unsatisfied check anywhere in the batch, the remaining ones do no
+ * work (each checks a device flag at its start, so nothing waits on the host
+ * and the call can be captured in a CUDA graph).  The results equal those of
+ * toric3d_flip with max_sweeps sweeps: a sample whose syndrome is clear flips
+ * nothing.  sweeps_done (device int32, nullable) receives the number of
+ * applications that ran from a syndrome with an unsatisfied check: 0 for a
+ * clear input, max_sweeps when the batch never clears.  work: >=
+ * toric3d_flip_until_clear_workspace_bytes(L, words) bytes, 16-byte aligned,
+ * contents not preserved.  0 <= max_sweeps <= 2^22.
+ */
+t3d_status toric3d_flip_until_clear(int L, int64_t words, uint64_t* e, uint64_t* s, int max_sweeps,
+                                    int32_t* sweeps_done, void* work, size_t work_bytes,
+                                    t3d_stream stream);
+
 /*
  * toric3d_flip without a workspace argument, for callers that cannot give the
  * library device memory: a decoder in a control loop whose device memory is
@@ -361,8 +383,9 @@ t3d_status toric3d_unpack(int64_t n_bits, int64_t n_samples, const uint64_t* wor
  * cube meta-checks as in toric3d_bp_meta) with its hard decision, then n_apply flip/p-flip
  * applications cycling through `schedule` (application k keys the coins with
  * sweep index k).  Optionally a final noiseless measurement (cycle0+T+1)
- * decoded by up to perfect_max_sweeps flip applications.  Finally the
- * logical readout into mask / counts8.
+ * decoded by up to perfect_max_sweeps flip applications, the ones after an
+ * item's syndrome clears skipped on the device as in toric3d_flip_until_clear
+ * (same results).  Finally the logical readout into mask / counts8.
  */
 typedef struct {
     int32_t L;

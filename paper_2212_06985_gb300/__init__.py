@@ -32,6 +32,7 @@ __all__ = [
     "EXPORTED_SYMBOLS", "replica_sample0", "BatchItem", "make_batch", "toric3d_run_batch",
     "toric3d_run_batch_workspace_bytes", "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm",
     "toric3d_autotune_batch", "toric3d_flip_noalloc", "toric3d_gate_workspace_bytes", "toric3d_gate",
+    "toric3d_flip_until_clear_workspace_bytes", "toric3d_flip_until_clear",
     "toric3d_bp_meta_workspace_bytes", "toric3d_bp_meta", "toric3d_bp_meta_message_bytes", "toric3d_bp_meta_step",
     "toric3d_tanner_bytes", "toric3d_tanner_prepare", "toric3d_tanner_noise", "toric3d_tanner_syndrome",
     "toric3d_tanner_flip_workspace_bytes", "toric3d_tanner_pflip", "toric3d_tanner_bp_workspace_bytes",
@@ -47,6 +48,7 @@ EXPORTED_SYMBOLS = [
     "toric3d_run_cycles", "toric3d_run_batch_workspace_bytes", "toric3d_run_batch",
     "toric3d_set_blocks_per_sm", "toric3d_get_blocks_per_sm", "toric3d_autotune_batch",
     "toric3d_profile_enable", "toric3d_profile_reset", "toric3d_profile_read", "toric3d_flip_noalloc",
+    "toric3d_flip_until_clear_workspace_bytes", "toric3d_flip_until_clear",
     "toric3d_cnn_param_count", "toric3d_cnn_blob_bytes", "toric3d_cnn_prepare", "toric3d_cnn_workspace_bytes",
     "toric3d_cnn_decode", "toric3d_cnn_train_workspace_bytes", "toric3d_cnn_train_step",
     "toric3d_gate_workspace_bytes", "toric3d_gate", "toric3d_cnn_status", "toric3d_cnn_debug_wait_limit",
@@ -155,6 +157,8 @@ def _declare(h):
         "toric3d_flip_workspace_bytes": (sz, [i32, i64]),
         "toric3d_flip": (i32, [i32, i64, _P, _P, i32, _P, sz, _P]),
         "toric3d_flip_noalloc": (i32, [i32, i64, _P, _P, i32, _P]),
+        "toric3d_flip_until_clear_workspace_bytes": (sz, [i32, i64]),
+        "toric3d_flip_until_clear": (i32, [i32, i64, _P, _P, i32, _P, _P, sz, _P]),
         "toric3d_pflip": (i32, [i32, i64, _P, _P, ctypes.c_char_p, i32, u32, u64, u64, u32, _P, sz, _P]),
         "toric3d_bp_message_bytes": (sz, [i32, i64]),
         "toric3d_bp_step": (i32, [i32, i64, _P, dbl, dbl, _P, _P, _P]),
@@ -281,6 +285,18 @@ def toric3d_syndrome(L, e, s, q, seed, sample0, cycle, stream=None):
 def toric3d_flip(L, e, s, sweeps, work, stream=None):
     _check(lib().toric3d_flip(L, e.shape[-1], _ptr(e), _ptr(s), sweeps, _ptr(work),
                               work.numel() * work.element_size(), _stream(stream)))
+
+
+def toric3d_flip_until_clear_workspace_bytes(L, words):
+    return lib().toric3d_flip_until_clear_workspace_bytes(L, words)
+
+
+def toric3d_flip_until_clear(L, e, s, max_sweeps, work, sweeps_done=None, stream=None):
+    """Up to max_sweeps flip applications, the ones after the batch's syndrome cleared
+    skipped on the device; sweeps_done: optional one-element int32 device tensor."""
+    _check(lib().toric3d_flip_until_clear(L, e.shape[-1], _ptr(e), _ptr(s), max_sweeps,
+                                          _ptr(sweeps_done) if sweeps_done is not None else None,
+                                          _ptr(work), work.numel() * work.element_size(), _stream(stream)))
 
 
 def toric3d_flip_noalloc(L, e, s, sweeps, stream=None):

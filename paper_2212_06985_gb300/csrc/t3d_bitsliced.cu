@@ -121,6 +121,44 @@ __device__ __forceinline__ Moves site_moves(const Lattice& lat, int site)
     return m;
 }
 
+// Flip until clear (ItemDesc::stop): whether application d.stop_k runs -- the first
+// always does, a later one only if the previous one left an unsatisfied check in the
+// item.  The decision is the same for every thread of the launch.  The thread of local
+// block 0 also clears the flag slot the next application writes and counts the
+// applications after the first that run.
+__device__ __forceinline__ bool stop_run(const ItemDesc& d, int64_t lb)
+{
+    if (!d.stop) return true;
+    const int k = d.stop_k;
+    const bool run = k == 0 || *(volatile uint32_t*)&d.stop[(k + 2) % 3] != 0;
+    if (lb == 0 && threadIdx.x == 0) {
+        d.stop[(k + 1) % 3] = 0;
+        if (run && k > 0) d.stop[3] += 1u;
+    }
+    return run;
+}
+
+// Flip until clear, per thread: note an unsatisfied check left in the output (nz) and, in
+// the first application, one found in the input (nzin).  The flag is read before the
+// atomic so that a launch makes few atomics once the flag is up.
+__device__ __forceinline__ void stop_note(const ItemDesc& d, uint64_t nz, uint64_t nzin)
+{
+    uint32_t* out = &d.stop[d.stop_k % 3];
+    if (nz && *(volatile uint32_t*)out == 0) atomicOr(out, 1u);
+    if (d.stop_k == 0 && nzin && *(volatile uint32_t*)&d.stop[4] == 0) atomicOr(&d.stop[4], 1u);
+}
+
+// The same for a whole block (every thread of the block calls it).
+__device__ __forceinline__ void stop_note_block(const ItemDesc& d, uint64_t nz, uint64_t nzin)
+{
+    const int out = __syncthreads_or(nz != 0);
+    const int in = d.stop_k == 0 ? __syncthreads_or(nzin != 0) : 0;
+    if (threadIdx.x == 0) {
+        if (out) atomicOr(&d.stop[d.stop_k % 3], 1u);
+        if (in) atomicOr(&d.stop[4], 1u);
+    }
+}
+
 // One synchronous flip application for the three faces at a site, reading the
 // item's s and writing its tmp (64 registers: four blocks per SM).  The thread
 // of site r decides the nine edges its faces touch -- (x,r), (y,r),
@@ -133,6 +171,7 @@ __global__ void __launch_bounds__(kThreads, 4)
 k_flip(const __grid_constant__ ItemTable tab)
 {
     for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
+        if (!stop_run(d, lb)) return;   // the item's syndrome has cleared
         const Lattice lat = d.lat;
         int r;
         int64_t w;
@@ -170,9 +209,12 @@ k_flip(const __grid_constant__ ItemTable tab)
         const uint64_t fx0 = f[0], fy0 = f[1], fz0 = f[2], fxy = f[3], fxz = f[4], fyx = f[5], fyz = f[6],
                        fzx = f[7], fzy = f[8];
         uint64_t* __restrict__ q0 = s_out + (int64_t)r * W + w;
-        q0[0] = s0 ^ fy0 ^ fyz ^ fz0 ^ fzy;
-        q0[L3W] = s1 ^ fx0 ^ fxz ^ fz0 ^ fzx;
-        q0[2 * L3W] = s2 ^ fx0 ^ fxy ^ fy0 ^ fyx;
+        const uint64_t n0 = s0 ^ fy0 ^ fyz ^ fz0 ^ fzy, n1 = s1 ^ fx0 ^ fxz ^ fz0 ^ fzx,
+                       n2 = s2 ^ fx0 ^ fxy ^ fy0 ^ fyx;
+        q0[0] = n0;
+        q0[L3W] = n1;
+        q0[2 * L3W] = n2;
+        if (d.stop) stop_note(d, n0 | n1 | n2, s0 | s1 | s2);
         uint64_t* __restrict__ e0 = e + (int64_t)r * W + w;
         if (fx0) e0[0] ^= fx0;
         if (fy0) e0[L3W] ^= fy0;
@@ -202,9 +244,11 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
 {
     __shared__ uint64_t sm[kTileSlots * kTileWords];
     for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
+        if (!stop_run(d, lb)) return;   // the item's syndrome has cleared (uniform over the launch)
         __syncthreads();   // the previous block's last step may still read the rings
         const Lattice lat = d.lat;
         const int L = lat.L, Wt = d.tx;
+        uint64_t nz = 0, nzin = 0;   // flip until clear: unsatisfied checks written / read
         const int64_t W = d.W, nw = d.nw ? d.nw : d.W, L3W = (int64_t)lat.L3 * W;
         const int z = (int)(lb % L);
         const int64_t w = (lb / L) * Wt + (threadIdx.x & (Wt - 1));
@@ -282,9 +326,13 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
                     uint64_t f[9];
 #pragma unroll
                     for (int k = 0; k < 9; ++k) f[k] = at_least_three(q[k][0], q[k][1], q[k][2], q[k][3]);
-                    q0[0] = s0 ^ f[1] ^ f[6] ^ f[2] ^ f[8];
-                    q0[L3W] = s1 ^ f[0] ^ f[4] ^ f[2] ^ f[7];
-                    q0[2 * L3W] = s2 ^ f[0] ^ f[3] ^ f[1] ^ f[5];
+                    const uint64_t n0 = s0 ^ f[1] ^ f[6] ^ f[2] ^ f[8], n1 = s1 ^ f[0] ^ f[4] ^ f[2] ^ f[7],
+                                   n2 = s2 ^ f[0] ^ f[3] ^ f[1] ^ f[5];
+                    q0[0] = n0;
+                    q0[L3W] = n1;
+                    q0[2 * L3W] = n2;
+                    nz |= n0 | n1 | n2;
+                    nzin |= s0 | s1 | s2;
                     uint64_t* __restrict__ e0 = d.e + own;   // this thread alone writes its site's edges
                     if (f[0]) e0[0] = e0v ^ f[0];
                     if (f[1]) e0[L3W] = e1v ^ f[1];
@@ -293,6 +341,7 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
             }
             __syncthreads();
         }
+        if (d.stop) stop_note_block(d, nz, nzin);
     });
 }
 
@@ -572,6 +621,21 @@ __global__ void k_gate_decide(int64_t W, int Y, const uint64_t* __restrict__ par
     if (flag && n_flagged) atomicAdd(n_flagged, 1ULL);
 }
 
+// Flip until clear, after the last application: if the item's syndrome cleared (the last
+// application left no unsatisfied check, or did not run), its s is all zero -- the
+// applications that did not run left stale words in the ping-pong buffers, so s is
+// written as zero here -- and the number of applications that ran goes to *sweeps_done:
+// the first if its input had an unsatisfied check, and every later one that ran.
+__global__ void k_flip_finish(const __grid_constant__ ItemDesc d, int n_apply, int32_t* __restrict__ sweeps_done)
+{
+    const uint32_t* st = d.stop;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && sweeps_done) *sweeps_done = (int32_t)(st[4] + st[3]);
+    if (st[(n_apply - 1) % 3] != 0) return;
+    const int64_t n = (int64_t)3 * d.lat.L3 * d.W;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d.s[i] = 0;
+}
+
 __global__ void k_pack(int64_t n_bits, int64_t n_samples, int64_t W, const uint8_t* __restrict__ bits,
                        uint64_t* __restrict__ words)
 {
@@ -664,6 +728,8 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
     int swaps = 0;
     for (int k = 0; k < n_apply; ++k) {
         const bool pk = schedule[k % slen] == 'P';
+        for (int i = 0; i < t.n; ++i) t.it[i].stop_k = k;
+        for (int i = 0; i < tt.n; ++i) tt.it[i].stop_k = k;
         ProfScope prof(pk ? T3D_K_PFLIP : T3D_K_FLIP, st);
         if (pk) {
             k_pflip_decide<<<persistent_grid((const void*)k_pflip_decide, kThreads, T3D_K_PFLIP, t.prefix[t.n], has_live(t)),
@@ -694,6 +760,28 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
             T3D_CUDA_CHECK(cudaMemcpy2DAsync(d.s, pitch, d.tmp, pitch, width, (size_t)3 * d.lat.L3,
                                              cudaMemcpyDeviceToDevice, st));
         }
+    }
+    return T3D_OK;
+}
+
+t3d_status launch_flip_until_clear(ItemTable& tab, int max_sweeps, int32_t* sweeps_done, cudaStream_t st)
+{
+    if (max_sweeps <= 0) {
+        if (sweeps_done) T3D_CUDA_CHECK(cudaMemsetAsync(sweeps_done, 0, sizeof(int32_t), st));
+        return T3D_OK;
+    }
+    for (int i = 0; i < tab.n; ++i) {
+        T3D_REQUIRE(tab.it[i].stop != nullptr, "flip until clear: item %d has no flag words", i);
+        T3D_CUDA_CHECK(cudaMemsetAsync(tab.it[i].stop, 0, kStopWords * sizeof(uint32_t), st));
+    }
+    T3D_TRY(launch_sweeps(tab, "F", 1, max_sweeps, 0, 0, 0, st));
+    ProfScope prof(T3D_K_FLIP, st);
+    for (int i = 0; i < tab.n; ++i) {
+        const ItemDesc& d = tab.it[i];
+        const int64_t n = (int64_t)3 * d.lat.L3 * d.W;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+        k_flip_finish<<<grid, 256, 0, st>>>(d, max_sweeps, i == 0 ? sweeps_done : nullptr);
+        T3D_LAUNCH_CHECK("flip until clear: finish");
     }
     return T3D_OK;
 }
@@ -940,6 +1028,31 @@ extern "C" t3d_status toric3d_flip(int L, int64_t words, uint64_t* e, uint64_t* 
 {
     clear_error();
     return sweeps_common(L, words, e, s, "F", sweeps, 0, 0, 0, 0, work, work_bytes, stream);
+}
+
+extern "C" size_t toric3d_flip_until_clear_workspace_bytes(int L, int64_t words)
+{
+    const size_t b = toric3d_flip_workspace_bytes(L, words);
+    return b ? (b + 255) / 256 * 256 + 256 : 0;
+}
+
+extern "C" t3d_status toric3d_flip_until_clear(int L, int64_t words, uint64_t* e, uint64_t* s, int max_sweeps,
+                                               int32_t* sweeps_done, void* work, size_t work_bytes,
+                                               t3d_stream stream)
+{
+    clear_error();
+    T3D_TRY(check_lattice(L));
+    T3D_REQUIRE(words >= 1 && words <= 65535LL * 32, "words=%lld out of range", (long long)words);
+    T3D_TRY(check_words(e, "e"));
+    T3D_TRY(check_words(s, "s"));
+    T3D_REQUIRE(max_sweeps >= 0 && (uint64_t)max_sweeps <= kMaxSweep, "max_sweeps must be in [0, 2^22]");
+    T3D_REQUIRE(sweeps_done == nullptr || aligned(sweeps_done, 4), "sweeps_done must be 4-byte aligned");
+    T3D_REQUIRE(work != nullptr && aligned(work, 16), "work must be a 16-byte aligned device pointer");
+    const size_t need = toric3d_flip_until_clear_workspace_bytes(L, words);
+    T3D_REQUIRE(work_bytes >= need, "workspace too small: %zu < %zu", work_bytes, need);
+    ItemTable tab = single_item(L, words, words * 64, 0, e, s, static_cast<uint64_t*>(work));
+    tab.it[0].stop = reinterpret_cast<uint32_t*>(static_cast<char*>(work) + need - 256);
+    return launch_flip_until_clear(tab, max_sweeps, sweeps_done, as_stream(stream));
 }
 
 extern "C" t3d_status toric3d_pflip(int L, int64_t words, uint64_t* e, uint64_t* s,

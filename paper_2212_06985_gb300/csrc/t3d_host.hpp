@@ -107,6 +107,11 @@ t3d_status launch_syndrome(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t
                            cudaStream_t st);
 // n_apply applications cycling through `schedule`; uses each item's e, s and
 // tmp and leaves the result in s.
+// Flip until clear: up to max_sweeps flip applications, each item's stop after its syndrome
+// clears (every item needs ItemDesc::stop, kStopWords words of device memory); the count of
+// applications of item 0 that ran goes to *sweeps_done (device, nullable).
+constexpr int kStopWords = 8;
+t3d_status launch_flip_until_clear(ItemTable& tab, int max_sweeps, int32_t* sweeps_done, cudaStream_t st);
 t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_apply,
                          uint32_t sweep0, uint64_t seed, uint32_t cycle, cudaStream_t st);
 t3d_status launch_logical(ItemTable& tab, cudaStream_t st);

@@ -43,6 +43,12 @@ struct ItemDesc {
     const uint32_t* wsrc; // device, nullable
     int64_t live_bpu;     // blocks per unit of live_wpu words (set by each launcher)
     int live_wpu;
+    // Flip until clear (nullable): stop[0..2] a ring of "an unsatisfied check is left" flags of
+    // the applications (application k writes slot k % 3), stop[3] the applications after the
+    // first that ran, stop[4] whether the first application's input had an unsatisfied check.
+    // Application k runs only if application k - 1 left an unsatisfied check in the item.
+    uint32_t* stop;
+    int stop_k;           // index of the application being launched
     int tx;               // bit-sliced kernels: words per thread-block row (power of 2)
     int64_t blocks;       // thread blocks this item needs in the current launch
 };

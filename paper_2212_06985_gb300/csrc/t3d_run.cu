@@ -46,6 +46,7 @@ struct Plan {
     unsigned long long* n_fallback[kMaxItems];
     void* cnn_work[kMaxItems];
     int64_t cnn_chunk[kMaxItems];  // pre-decoder chunk, words
+    uint32_t* stop[kMaxItems];     // perfect round: the flags of the flip until clear
 };
 
 bool learned(const t3d_run_cfg& c) { return c.cnn_blob != nullptr; }
@@ -179,6 +180,7 @@ size_t batch_workspace_bytes(const t3d_run_cfg& c, const t3d_batch_item* items, 
 {
     size_t total = 0;
     for (int i = 0; i < n; ++i) total += 2 * round_up(state_bytes(items[i].L, items[i].n_samples));
+    if (c.perfect_round) total += (size_t)n * round_up(kStopWords * sizeof(uint32_t));
     if (learned(c))
         for (int i = 0; i < n; ++i) total += learned_bytes(c, items[i].L, items[i].n_samples);
     if (needs_bp(c)) {
@@ -213,6 +215,13 @@ t3d_status plan_workspace(const t3d_run_cfg& c, const t3d_batch_item* items, int
         d.mask = items[i].mask;
         d.counts8 = reinterpret_cast<unsigned long long*>(items[i].counts8);
         used += 2 * sb;
+    }
+    if (c.perfect_round) {
+        for (int i = 0; i < n; ++i) {
+            T3D_REQUIRE(used + round_up(kStopWords * sizeof(uint32_t)) <= work_bytes, "workspace too small");
+            pl.stop[i] = reinterpret_cast<uint32_t*>(base + used);
+            used += round_up(kStopWords * sizeof(uint32_t));
+        }
     }
     if (learned(c)) {
         for (int i = 0; i < n; ++i) {
@@ -364,8 +373,12 @@ t3d_status enqueue_run(const t3d_run_cfg& c, const Plan& pl, cudaStream_t st)
         tab = pl.items;
         T3D_TRY(launch_syndrome(tab, 0, c.seed, cycle, st));
         if (c.perfect_max_sweeps > 0) {
+            // flip until every item's syndrome clears, at most perfect_max_sweeps applications
+            // (the applications after an item clears do no work; the results are those of
+            // perfect_max_sweeps applications)
             tab = pl.items;
-            T3D_TRY(launch_sweeps(tab, "F", 1, c.perfect_max_sweeps, 0, c.seed, cycle, st));
+            for (int i = 0; i < tab.n; ++i) tab.it[i].stop = pl.stop[i];
+            T3D_TRY(launch_flip_until_clear(tab, c.perfect_max_sweeps, nullptr, st));
         }
     }
     bool readout = false;

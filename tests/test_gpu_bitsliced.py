@@ -135,3 +135,43 @@ def test_exhaustive_L2_flip_and_pflip_over_all_syndromes(start):
         we, ws = oracle.flip_batch(L, zeros, sbits, probabilistic, 3, start, 2, 5)
         assert np.array_equal(download_bits(e, CHUNK), we)
         assert np.array_equal(download_bits(s, CHUNK), ws)
+
+
+# ------------------------------------------------------------------ flip until clear
+@pytest.mark.parametrize("L,S,p,max_sweeps", [(4, 1000, 0.01, 32), (6, 3000, 0.02, 32), (8, 200, 0.06, 5),
+                                              (33, 64, 0.004, 8)])
+def test_flip_until_clear_matches_fixed_sweeps_and_counts_the_sweeps(L, S, p, max_sweeps):
+    # L = 33 takes the one-thread-per-site flip kernel, the others the shared-memory one; the
+    # (8, 0.06, 5) case does not clear, so every application runs
+    n = 3 * L ** 3
+    ebits = inp.random_bits(S, n, p, seed=100 + L)
+    sbits = oracle.syndrome_batch(L, ebits)
+    e_fix, s_fix = upload_bits(ebits), upload_bits(sbits)
+    e_stop, s_stop = upload_bits(ebits), upload_bits(sbits)
+    W = e_fix.shape[1]
+    t3d.toric3d_flip(L, e_fix, s_fix, max_sweeps, workspace(t3d.toric3d_flip_workspace_bytes(L, W)))
+    done = torch.full((1,), -7, dtype=torch.int32, device=dev())
+    t3d.toric3d_flip_until_clear(L, e_stop, s_stop, max_sweeps,
+                                 workspace(t3d.toric3d_flip_until_clear_workspace_bytes(L, W)), done)
+    torch.cuda.synchronize()
+    assert np.array_equal(download_bits(e_stop, S), download_bits(e_fix, S))
+    assert np.array_equal(download_bits(s_stop, S), download_bits(s_fix, S))
+    # the oracle's count: applications that start from a syndrome with an unsatisfied check
+    we, ws, count = ebits, sbits, 0
+    while count < max_sweeps and ws.any():
+        we, ws = oracle.flip_batch(L, we, ws)
+        count += 1
+    assert int(done.item()) == count
+    assert np.array_equal(download_bits(e_stop, S), we)
+
+
+def test_flip_until_clear_on_a_clear_syndrome_runs_no_sweep():
+    L, S = 5, 300
+    ebits = inp.random_bits(S, 3 * L ** 3, 0.0, seed=3)
+    e, s = upload_bits(ebits), upload_bits(ebits)
+    done = torch.full((1,), -7, dtype=torch.int32, device=dev())
+    t3d.toric3d_flip_until_clear(L, e, s, 16, workspace(t3d.toric3d_flip_until_clear_workspace_bytes(L, e.shape[1])),
+                                 done)
+    torch.cuda.synchronize()
+    assert int(done.item()) == 0
+    assert not download_bits(e, S).any() and not download_bits(s, S).any()
