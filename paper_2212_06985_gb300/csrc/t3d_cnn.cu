@@ -8,19 +8,16 @@
 // parameters.  Input channels of site r: s_{t-1}(n, r) and s_t(n, r) for the
 // three face normals n, as 0/1.  Output d of site r: the edge (d, r).
 //
-// Layout: activations are BF16 [site][sample][16] (32 bytes per site and
-// sample), so a 3x3x3 convolution is 27 accumulated GEMMs of
-// (samples x 16 input channels) . (16 x 16 output channels): one warp computes
-// 32 samples x 16 channels of one site with mma.sync m16n8k16 (BF16 inputs,
-// FP32 accumulation), reading the neighbour site's 32 x 16 input tile directly
-// as A fragments and the offset's 16 x 16 weights from shared memory.
-// Hidden activations are rounded to BF16 between layers; the head reads the
-// third layer's output in FP32.
+// The convolutions of inference and training run on the tcgen05 tensor
+// cores (t3d_cnn_tc.cu): activations are BF16 and tile-major, FP32
+// accumulation in TMEM; hidden activations are rounded to BF16 between layers
+// and the head reads the third layer's output in FP32.
 //
-// Training: forward with the labels fused into the third layer's epilogue
-// (BCE gradient, head gradient, ReLU mask), backward data by the same
-// tensor-core convolution with flipped and transposed weights, weight and
-// bias gradients by a CUDA-core reduction, Adam.
+// Training: the forward pass with the labels in the third layer's epilogue
+// (BCE gradient, the head's gradients, the ReLU mask), backward data by the
+// same tensor-core convolution with flipped and transposed weights and a
+// masking epilogue, weight and bias gradients by a CUDA-core reduction over
+// sites and samples, Adam.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -35,8 +32,7 @@
 namespace t3d {
 namespace cnn {
 
-constexpr int kThreads = 256;   // 8 warps
-constexpr int kTile = 32;       // samples per warp tile
+constexpr int kTile = 128;      // samples per tensor-core tile
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -50,16 +46,6 @@ __device__ __forceinline__ float2 unpack_bf16(uint32_t u)
     return __bfloat1622float2(v);
 }
 
-// D (16x8, f32) += A (16x16, bf16, row) * B (16x8, bf16, col).
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2])
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // Neighbour site r + (dx, dy, dz) with periodic wrap.
 __device__ __forceinline__ int neighbour(const Lattice& lat, const Coord& rc, int k)
 {
@@ -71,318 +57,27 @@ __device__ __forceinline__ int neighbour(const Lattice& lat, const Coord& rc, in
     return (z * lat.L + y) * lat.L + x;
 }
 
-enum InMode { kInBits = 0, kInAct = 1 };
-enum OutMode { kOutRelu = 0, kOutMask = 1, kOutHeadDecide = 2, kOutHeadTrain = 3 };
-
-struct ConvArgs {
-    Lattice lat;
-    int64_t Sp;                    // padded samples of the activation buffers (multiple of 32)
-    int64_t n_samples;             // valid samples
-    int64_t W;                     // words per bit-sliced row
-    const uint64_t* s_prev;        // kInBits
-    const uint64_t* s_cur;
-    const uint32_t* x;             // kInAct: BF16 pairs [site][Sp][8]
-    const __nv_bfloat16* w;        // [27][co][ci]
-    const float* bias;             // [16] (relu / head modes)
-    const float* w4;               // [3][16] head
-    const float* b4;               // [3]
-    uint32_t* y;                   // BF16 output [site][Sp][8] (relu / mask / head-train dPre)
-    const uint32_t* mask;          // kOutMask: forward activation whose sign gates the gradient
-    uint32_t* e32;                 // head decide: error words as 32-bit halves
-    uint32_t* dec32;               // head decide: decision words, [word][site][8] 32-bit halves
-    float* logits;                 // optional [3][L^3][n_samples]
-    const uint64_t* label;         // head train: bit-sliced e_t
-    float inv_n;                   // head train: 1 / (3 L^3 n_samples)
-    float* grad_w4;                // head train: [3][16] accumulated
-    float* grad_b4;                // [3]
-    float* loss;                   // [1]
-};
-
-template <int kIn, int kOut>
-__global__ void __launch_bounds__(kThreads)
-k_conv(const ConvArgs a)
+// Element pair (c, c + 1), c even, of sample s at site r in a tile-major buffer of
+// 16 channels ([sample/8][channel/8][8 samples][8 channels] per 128-sample tile) or
+// of 8 ([sample][8]), as one 32-bit word.
+__device__ __forceinline__ uint32_t tile_pair(const uint8_t* buf, int L3, int channels, int r, int64_t s, int c)
 {
-    __shared__ __align__(16) __nv_bfloat16 sw[kOff][kC][kC];
-    __shared__ float sred[kThreads / 32][3 * kC + 3 + 1];
-    for (int i = threadIdx.x; i < kOff * kC * kC / 2; i += blockDim.x)
-        reinterpret_cast<uint32_t*>(&sw[0][0][0])[i] = reinterpret_cast<const uint32_t*>(a.w)[i];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int r = blockIdx.x * (kThreads / 32) + warp;
-    const int64_t m0 = (int64_t)blockIdx.y * kTile;
-    const bool active = r < a.lat.L3;
-    float acc[2][2][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) acc[mt][nt][i] = 0.0f;
-    if (active) {
-        const Coord rc = site_coord(a.lat, r);
-        for (int k = 0; k < kOff; ++k) {
-            const int rn = neighbour(a.lat, rc, k);
-            uint32_t A[2][4];
-            if (kIn == kInAct) {
-                const uint32_t* base = a.x + ((int64_t)rn * a.Sp + m0) * (kC / 2);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const uint32_t* row0 = base + (mt * 16 + g) * (kC / 2);
-                    const uint32_t* row8 = row0 + 8 * (kC / 2);
-                    A[mt][0] = row0[t];
-                    A[mt][1] = row8[t];
-                    A[mt][2] = row0[t + 4];
-                    A[mt][3] = row8[t + 4];
-                }
-            } else {
-                // channel c < 3: s_{t-1}(n = c); 3 <= c < 6: s_t(n = c - 3); others zero
-                const int64_t wd = m0 / 64;
-                const int sh = (int)(m0 % 64);
-                uint64_t wp[3], wc[3];
-#pragma unroll
-                for (int n = 0; n < 3; ++n) {
-                    wp[n] = a.s_prev[((int64_t)n * a.lat.L3 + rn) * a.W + wd] >> sh;
-                    wc[n] = a.s_cur[((int64_t)n * a.lat.L3 + rn) * a.W + wd] >> sh;
-                }
-                auto bitv = [&](int c, int row) -> float {
-                    uint64_t w = c < 3 ? wp[c] : wc[c - 3];
-                    return ((w >> row) & 1ULL) ? 1.0f : 0.0f;
-                };
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int ra = mt * 16 + g, rb = ra + 8;
-                    const int c0 = 2 * t, c1 = 2 * t + 1;
-                    A[mt][0] = c0 < kInC ? pack_bf16(bitv(c0, ra), c1 < kInC ? bitv(c1, ra) : 0.0f) : 0u;
-                    A[mt][1] = c0 < kInC ? pack_bf16(bitv(c0, rb), c1 < kInC ? bitv(c1, rb) : 0.0f) : 0u;
-                    A[mt][2] = 0u;  // channels 8..15
-                    A[mt][3] = 0u;
-                }
-            }
-            uint32_t B[2][2];
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const uint32_t* wrow = reinterpret_cast<const uint32_t*>(&sw[k][nt * 8 + g][0]);
-                B[nt][0] = wrow[t];
-                B[nt][1] = wrow[t + 4];
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) mma_bf16(acc[mt][nt], A[mt], B[nt]);
-        }
-    }
-    // this thread holds rows {mt*16 + g, mt*16 + g + 8} x channels {nt*8 + 2t, nt*8 + 2t + 1}
-    if (kOut == kOutRelu || kOut == kOutMask) {
-        if (!active) return;
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int64_t row = m0 + mt * 16 + g + 8 * half;
-                uint32_t* out = a.y + ((int64_t)r * a.Sp + row) * (kC / 2);
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const int c = nt * 8 + 2 * t;
-                    float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
-                    if (kOut == kOutRelu) {
-                        v0 = fmaxf(v0 + a.bias[c], 0.0f);
-                        v1 = fmaxf(v1 + a.bias[c + 1], 0.0f);
-                    } else {
-                        const float2 m = unpack_bf16(a.mask[((int64_t)r * a.Sp + row) * (kC / 2) + c / 2]);
-                        v0 = m.x > 0.0f ? v0 : 0.0f;
-                        v1 = m.y > 0.0f ? v1 : 0.0f;
-                    }
-                    out[c / 2] = pack_bf16(v0, v1);
-                }
-            }
-        return;
-    }
-    // head: y3 = relu(acc + b3) in FP32; z_d = sum_c y3_c w4[d][c] + b4[d]
-    float y3[2][2][2][2];  // [mt][half][nt][j]
-    float z[2][2][3];      // [mt][half][d]
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) z[mt][half][d] = 0.0f;
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int c = nt * 8 + 2 * t + j;
-                    const float v = fmaxf(acc[mt][nt][2 * half + j] + a.bias[c], 0.0f);
-                    y3[mt][half][nt][j] = v;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) z[mt][half][d] += v * a.w4[d * kC + c];
-                }
-        }
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int half = 0; half < 2; ++half)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                float v = z[mt][half][d];
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                z[mt][half][d] = v + a.b4[d];
-            }
-    // the logit of sample row l (= mt*16 + half*8 + g) into lane l
-    float zl[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        float cand[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) cand[q] = __shfl_sync(0xffffffffu, z[q >> 1][q & 1][d], 4 * (lane & 7));
-        const int q = lane >> 3;
-        zl[d] = q == 0 ? cand[0] : (q == 1 ? cand[1] : (q == 2 ? cand[2] : cand[3]));
-    }
-    const int64_t sample = m0 + lane;
-    const bool valid = active && sample < a.n_samples;
-    if (a.logits && valid) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) a.logits[((int64_t)d * a.lat.L3 + r) * a.n_samples + sample] = zl[d];
-    }
-    if (kOut == kOutHeadDecide) {
-        const int64_t wd = m0 / 64;
-        const int hw = (int)((m0 / 32) & 1);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const uint32_t bits = __ballot_sync(0xffffffffu, valid && zl[d] > 0.0f);
-            if (active && lane == 0) {
-                if (bits) a.e32[2 * (((int64_t)d * a.lat.L3 + r) * a.W + wd) + hw] ^= bits;
-                a.dec32[(wd * a.lat.L3 + r) * 8 + 2 * d + hw] = bits;
-            }
-        }
-        return;
-    }
-    // training: BCE gradient dz = (sigmoid(z) - y) / N, loss, head gradients, dPre3
-    float dzl[3];
-    float loss = 0.0f;
-    {
-        const int64_t wd = m0 / 64;
-        const int sh = (int)(m0 % 64);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            float y = 0.0f;
-            if (active) y = (float)((a.label[((int64_t)d * a.lat.L3 + r) * a.W + wd] >> (sh + lane)) & 1ULL);
-            const float zz = zl[d];
-            const float sig = 1.0f / (1.0f + expf(-zz));
-            dzl[d] = valid ? (sig - y) * a.inv_n : 0.0f;
-            if (valid) loss += fmaxf(zz, 0.0f) - zz * y + log1pf(expf(-fabsf(zz)));
-        }
-    }
-    // back to fragment rows: the dz of rows held by this lane
-    float dz[2][2][3];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int half = 0; half < 2; ++half)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) dz[mt][half][d] = __shfl_sync(0xffffffffu, dzl[d], mt * 16 + half * 8 + g);
-    float gw4[3][4], gb4[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        gb4[d] = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) gw4[d][i] = 0.0f;
-    }
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int64_t row = m0 + mt * 16 + g + 8 * half;
-            uint32_t* out = a.y + ((int64_t)r * a.Sp + row) * (kC / 2);
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                float dv[2];
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int c = nt * 8 + 2 * t + j;
-                    float dy = 0.0f;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        dy += dz[mt][half][d] * a.w4[d * kC + c];
-                        gw4[d][nt * 2 + j] += y3[mt][half][nt][j] * dz[mt][half][d];
-                    }
-                    dv[j] = y3[mt][half][nt][j] > 0.0f ? dy : 0.0f;
-                }
-                if (active) out[(nt * 8 + 2 * t) / 2] = pack_bf16(dv[0], dv[1]);
-            }
-        }
-    // t == 0 lanes of each group hold rows' dz for bias: sum dz over the warp's 32 rows once
-#pragma unroll
-    for (int d = 0; d < 3; ++d) gb4[d] = dzl[d];
-    // reduce over the warp: head weights over groups (lanes with equal t), bias and loss over all
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float v = gw4[d][i];
-            v += __shfl_xor_sync(0xffffffffu, v, 4);
-            v += __shfl_xor_sync(0xffffffffu, v, 8);
-            v += __shfl_xor_sync(0xffffffffu, v, 16);
-            gw4[d][i] = v;
-        }
-        float b = gb4[d];
-        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-        gb4[d] = b;
-    }
-    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
-    if (lane < 4) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) sred[warp][d * kC + (i >> 1) * 8 + 2 * lane + (i & 1)] = gw4[d][i];
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) sred[warp][3 * kC + d] = gb4[d];
-        sred[warp][3 * kC + 3] = loss;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3 * kC + 4) {
-        float v = 0.0f;
-        for (int wi = 0; wi < kThreads / 32; ++wi) v += sred[wi][threadIdx.x];
-        if (threadIdx.x < 3 * kC) atomicAdd(&a.grad_w4[threadIdx.x], v);
-        else if (threadIdx.x < 3 * kC + 3) atomicAdd(&a.grad_b4[threadIdx.x - 3 * kC], v);
-        else atomicAdd(a.loss, v);
-    }
-}
-
-// Input features for training (BF16 [site][Sp][16]): the six syndrome bits.
-__global__ void k_features(Lattice lat, int64_t Sp, int64_t W, const uint64_t* __restrict__ s_prev,
-                           const uint64_t* __restrict__ s_cur, uint32_t* __restrict__ x)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // (site, sample)
-    if (i >= (int64_t)lat.L3 * Sp) return;
-    const int r = (int)(i / Sp);
-    const int64_t s = i - (int64_t)r * Sp;
-    float v[kInC];
-#pragma unroll
-    for (int n = 0; n < 3; ++n) {
-        v[n] = (float)((s_prev[((int64_t)n * lat.L3 + r) * W + s / 64] >> (s % 64)) & 1ULL);
-        v[3 + n] = (float)((s_cur[((int64_t)n * lat.L3 + r) * W + s / 64] >> (s % 64)) & 1ULL);
-    }
-    uint32_t* out = x + i * (kC / 2);
-    out[0] = pack_bf16(v[0], v[1]);
-    out[1] = pack_bf16(v[2], v[3]);
-    out[2] = pack_bf16(v[4], v[5]);
-#pragma unroll
-    for (int c = 3; c < kC / 2; ++c) out[c] = 0u;
+    const int64_t tile = ((s >> 7) * L3 + r) * (int64_t)(256 * channels);
+    const int m = (int)(s & 127);
+    const int64_t off = channels == 16 ? (m >> 3) * 256 + (c >> 3) * 128 + (m & 7) * 16 + (c & 7) * 2 : m * 16 + c * 2;
+    return *reinterpret_cast<const uint32_t*>(buf + tile + off);
 }
 
 // Weight and bias gradients of one convolution layer (CUDA cores):
 // gw[k][co][ci] = sum over sites r and samples s of x[r + off_k][s][ci] dpre[r][s][co],
 // gb[co] = sum dpre[r][s][co].  Block (k, sample chunk of 64); thread (co, ci);
-// partial sums per chunk go to part[chunk][k][co][ci] (+ bias at k = 27).
+// partial sums per chunk go to part[chunk][k][co][ci] (+ bias at k = 27).  x has
+// x_ch channels (8: the first layer's input, 16: hidden), dpre 16; both tile-major.
 constexpr int kChunk = 64;
 
 __global__ void __launch_bounds__(256)
-k_wgrad(Lattice lat, int64_t Sp, int64_t n_samples, const uint32_t* __restrict__ x,
-        const uint32_t* __restrict__ dpre, float* __restrict__ part)
+k_wgrad(Lattice lat, int64_t n_samples, const uint8_t* __restrict__ x, int x_ch, const uint8_t* __restrict__ dpre,
+        float* __restrict__ part)
 {
     __shared__ float sx[kChunk][kC + 1];
     __shared__ float sd[kChunk][kC + 1];
@@ -395,8 +90,9 @@ k_wgrad(Lattice lat, int64_t Sp, int64_t n_samples, const uint32_t* __restrict__
         for (int i = threadIdx.x; i < kChunk * (kC / 2); i += blockDim.x) {
             const int s = i / (kC / 2), c2 = i % (kC / 2);
             const bool ok = s0 + s < n_samples;
-            const float2 vx = ok ? unpack_bf16(x[((int64_t)rn * Sp + s0 + s) * (kC / 2) + c2]) : make_float2(0, 0);
-            const float2 vd = ok ? unpack_bf16(dpre[((int64_t)r * Sp + s0 + s) * (kC / 2) + c2]) : make_float2(0, 0);
+            const float2 vx = ok && 2 * c2 < x_ch ? unpack_bf16(tile_pair(x, lat.L3, x_ch, rn, s0 + s, 2 * c2))
+                                                  : make_float2(0, 0);
+            const float2 vd = ok ? unpack_bf16(tile_pair(dpre, lat.L3, kC, r, s0 + s, 2 * c2)) : make_float2(0, 0);
             sx[s][2 * c2] = vx.x;
             sx[s][2 * c2 + 1] = vx.y;
             sd[s][2 * c2] = vd.x;
@@ -493,10 +189,8 @@ __global__ void k_dec_apply(Lattice lat, int64_t W, int64_t words, const uint64_
 }
 
 int64_t padded(int64_t n) { return (n + kTile - 1) / kTile * kTile; }
-size_t act_bytes(int L, int64_t n) { return (size_t)L * L * L * (size_t)padded(n) * kC * 2; }
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
-dim3 conv_grid(int L, int64_t n) { return dim3((unsigned)((L * L * L + 7) / 8), (unsigned)(padded(n) / kTile)); }
 
 }  // namespace cnn
 }  // namespace t3d
@@ -540,7 +234,8 @@ static t3d_status cnn_checks(int L, int64_t n_samples)
 {
     T3D_TRY(check_lattice(L));
     T3D_REQUIRE(L <= 128, "the pre-decoder supports L <= 128");
-    T3D_REQUIRE(n_samples >= 1 && padded(n_samples) / kTile <= 65535, "n_samples out of range");
+    // (the weight-gradient grid has one row per 64 samples; 2,097,120 samples in all)
+    T3D_REQUIRE(n_samples >= 1 && padded(n_samples) <= 65535LL * 32, "n_samples out of range");
     return T3D_OK;
 }
 
@@ -603,9 +298,8 @@ extern "C" t3d_status toric3d_cnn_decode(int L, int64_t n_samples, const uint64_
 extern "C" size_t toric3d_cnn_train_workspace_bytes(int L, int64_t n_samples)
 {
     if (L < 2 || L > 128 || n_samples < 1) return 0;
-    const size_t ab = round256(act_bytes(L, n_samples));
     const size_t part = round256((size_t)((padded(n_samples) + kChunk - 1) / kChunk) * (kOff + 1) * kC * kC * 4);
-    return 5 * ab + part + round256(kParams * 4) + 256;
+    return tc_act_bytes(L, n_samples, 8) + 4 * tc_act_bytes(L, n_samples, kC) + part + round256(kParams * 4) + 256;
 }
 
 extern "C" t3d_status toric3d_cnn_train_step(int L, int64_t n_samples, const uint64_t* s_prev,
@@ -625,80 +319,37 @@ extern "C" t3d_status toric3d_cnn_train_step(int L, int64_t n_samples, const uin
     T3D_REQUIRE(work_bytes >= toric3d_cnn_train_workspace_bytes(L, n_samples), "workspace too small");
     cudaStream_t st = as_stream(stream);
     Blob* b = static_cast<Blob*>(blob);
-    char* base = static_cast<char*>(work);
-    const size_t ab = round256(act_bytes(L, n_samples));
-    uint32_t* x0 = reinterpret_cast<uint32_t*>(base);
-    uint32_t* y1 = reinterpret_cast<uint32_t*>(base + ab);
-    uint32_t* y2 = reinterpret_cast<uint32_t*>(base + 2 * ab);
-    uint32_t* g3 = reinterpret_cast<uint32_t*>(base + 3 * ab);   // dPre3, later dPre1
-    uint32_t* g2 = reinterpret_cast<uint32_t*>(base + 4 * ab);   // dPre2
+    uint8_t* base = static_cast<uint8_t*>(work);
+    const size_t xb = tc_act_bytes(L, n_samples, 8), ab = tc_act_bytes(L, n_samples, kC);
+    uint8_t* x0 = base;                 // the syndrome features
+    uint8_t* y1 = base + xb;
+    uint8_t* y2 = y1 + ab;
+    uint8_t* g3 = y2 + ab;              // dPre3, later dPre1
+    uint8_t* g2 = g3 + ab;              // dPre2
     const int chunks = (int)((padded(n_samples) + kChunk - 1) / kChunk);
-    float* part = reinterpret_cast<float*>(base + 5 * ab);
-    float* grads = reinterpret_cast<float*>(base + 5 * ab +
-                                            round256((size_t)chunks * (kOff + 1) * kC * kC * 4));
+    float* part = reinterpret_cast<float*>(g2 + ab);
+    float* grads = reinterpret_cast<float*>(g2 + ab + round256((size_t)chunks * (kOff + 1) * kC * kC * 4));
     if (grads_out) grads = grads_out;
     const Lattice lat = make_lattice_host(L);
-    const int64_t Sp = padded(n_samples), W = words_for(n_samples);
+    const int64_t W = words_for(n_samples);
     T3D_CUDA_CHECK(cudaMemsetAsync(grads, 0, kParams * sizeof(float), st));
     T3D_CUDA_CHECK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
-    const dim3 grid = conv_grid(L, n_samples);
-    ProfScope prof(T3D_K_CNN, st);
-    k_features<<<(unsigned)(((int64_t)lat.L3 * Sp + 255) / 256), 256, 0, st>>>(lat, Sp, W, s_prev, s, x0);
-    ConvArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.lat = lat;
-    a.Sp = Sp;
-    a.n_samples = n_samples;
-    a.W = W;
-    a.s_prev = s_prev;
-    a.s_cur = s;
-    // forward
-    a.w = &b->wf[0][0][0][0];
-    a.bias = b->bias[0];
-    a.y = y1;
-    k_conv<kInBits, kOutRelu><<<grid, kThreads, 0, st>>>(a);
-    a.x = y1;
-    a.w = &b->wf[1][0][0][0];
-    a.bias = b->bias[1];
-    a.y = y2;
-    k_conv<kInAct, kOutRelu><<<grid, kThreads, 0, st>>>(a);
-    a.x = y2;
-    a.w = &b->wf[2][0][0][0];
-    a.bias = b->bias[2];
-    a.w4 = &b->w4[0][0];
-    a.b4 = b->b4;
-    a.y = g3;
-    a.label = e_label;
-    a.inv_n = 1.0f / (3.0f * (float)lat.L3 * (float)n_samples);
-    a.grad_w4 = grads + P_W4;
-    a.grad_b4 = grads + P_B4;
-    a.loss = loss_out;
-    k_conv<kInAct, kOutHeadTrain><<<grid, kThreads, 0, st>>>(a);
-    T3D_LAUNCH_CHECK("cnn forward");
+    // forward, with the BCE gradient and the head's gradients in the last layer's epilogue
+    T3D_TRY(tc_train_forward(L, n_samples, W, s_prev, s, e_label, b, x0, y1, y2, g3, grads + P_W4, grads + P_B4,
+                             loss_out, st));
     // backward: layer 3 weights, then data gradient into layer 2 (masked by y2 > 0), ...
+    ProfScope prof(T3D_K_CNN, st);
     const dim3 wg(kOff + 1, (unsigned)chunks);
     const int red = ((kOff + 1) * kC * kC + 255) / 256;
-    k_wgrad<<<wg, 256, 0, st>>>(lat, Sp, n_samples, y2, g3, part);
+    k_wgrad<<<wg, 256, 0, st>>>(lat, n_samples, y2, kC, g3, part);
     k_wgrad_reduce<<<red, 256, 0, st>>>(chunks, part, grads + P_W3, grads + P_B3, kC);
-    ConvArgs bk;
-    std::memset(&bk, 0, sizeof(bk));
-    bk.lat = lat;
-    bk.Sp = Sp;
-    bk.n_samples = n_samples;
-    bk.W = W;
-    bk.x = g3;
-    bk.w = &b->wt[2][0][0][0];
-    bk.mask = y2;
-    bk.y = g2;
-    k_conv<kInAct, kOutMask><<<grid, kThreads, 0, st>>>(bk);
-    k_wgrad<<<wg, 256, 0, st>>>(lat, Sp, n_samples, y1, g2, part);
+    T3D_LAUNCH_CHECK("cnn weight gradient");
+    T3D_TRY(tc_backward_data(L, n_samples, &b->wt[2][0][0][0], g3, y2, g2, st));
+    k_wgrad<<<wg, 256, 0, st>>>(lat, n_samples, y1, kC, g2, part);
     k_wgrad_reduce<<<red, 256, 0, st>>>(chunks, part, grads + P_W2, grads + P_B2, kC);
-    bk.x = g2;
-    bk.w = &b->wt[1][0][0][0];
-    bk.mask = y1;
-    bk.y = g3;  // dPre1
-    k_conv<kInAct, kOutMask><<<grid, kThreads, 0, st>>>(bk);
-    k_wgrad<<<wg, 256, 0, st>>>(lat, Sp, n_samples, x0, g3, part);
+    T3D_LAUNCH_CHECK("cnn weight gradient");
+    T3D_TRY(tc_backward_data(L, n_samples, &b->wt[1][0][0][0], g2, y1, g3, st));   // dPre1
+    k_wgrad<<<wg, 256, 0, st>>>(lat, n_samples, x0, 8, g3, part);
     k_wgrad_reduce<<<red, 256, 0, st>>>(chunks, part, grads + P_W1, grads + P_B1, kInC);
     T3D_LAUNCH_CHECK("cnn backward");
     if (lr > 0.0f) {

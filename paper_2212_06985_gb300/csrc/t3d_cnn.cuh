@@ -51,5 +51,23 @@ t3d_status tc_prepare();
 t3d_status tc_status();
 t3d_status tc_set_wait_limit(uint64_t ns);
 
+// Training on the same tensor-core convolutions.  Activations and gradients are
+// tile-major: the 128-sample tile t of site r is one block at byte
+// (t L^3 + r) * (256 * channels), [sample/8][channel/8][8 samples][8 channels]
+// BF16 for 16 channels, [sample][8] for the first layer's 8 (6 used).
+// tc_act_bytes: one such buffer.
+size_t tc_act_bytes(int L, int64_t n_samples, int channels);
+// Forward pass with the labels: x0 (8 channels) the syndrome features, y1 and y2
+// the hidden activations, g3 the gradient at the third layer's pre-activation of
+// the mean BCE; the head's gradients and the summed BCE are added to grad_w4
+// [3][16], grad_b4 [3] and loss [1].
+t3d_status tc_train_forward(int L, int64_t n_samples, int64_t W, const uint64_t* s_prev, const uint64_t* s,
+                            const uint64_t* label, const Blob* blob, uint8_t* x0, uint8_t* y1, uint8_t* y2,
+                            uint8_t* g3, float* grad_w4, float* grad_b4, float* loss, cudaStream_t st);
+// Backward data through one convolution: g_out = conv(g_in; wt) where the forward
+// activation mask_act is non-zero, else 0 (wt: the transposed, flipped weights).
+t3d_status tc_backward_data(int L, int64_t n_samples, const __nv_bfloat16* wt, const uint8_t* g_in,
+                            const uint8_t* mask_act, uint8_t* g_out, cudaStream_t st);
+
 }  // namespace cnn
 }  // namespace t3d

@@ -1,42 +1,38 @@
-// Inference forward pass of the learned pre-decoder on the fifth-generation
-// tensor cores (tcgen05 MMA with TMEM accumulators, operands staged in shared
-// memory by bulk asynchronous copies).
+// The learned pre-decoder's convolutions on the fifth-generation tensor cores
+// (tcgen05 MMA with TMEM accumulators, operands staged in shared memory): the
+// inference forward pass, and for training the forward pass with the loss and
+// the backward-data passes (the same kernel with another epilogue).
 //
-// A 3x3x3 convolution with 16 output channels has a small GEMM N (16), and a
-// tcgen05.mma with M = 128, K = 16 takes as long for N = 16 as for N = 128
-// (measured on GB300: about 53 cycles from one issuing thread at N = 16, 64 at
-// N = 128, 128 at N = 256, the last two at the tensor peak).  So every MMA here
-// computes 8 output sites at once:
-//   D[sample][(r, co)] += A_i[sample][ci] . B[(r, co)][ci],   M = N = 128, K = 16,
-// where A_i is the 128-sample activation tile of one input site i, the 128
-// columns of D are 8 consecutive output sites along x (r = 7 - (x - x0)) times 16
-// channels, and B stacks, for each of the 8 outputs, the weights of the offset
-// that connects it to i (zero where i is not its neighbour).  For a fixed
-// (dy, dz) these stacks are strided views of one zero-padded strip of weight
-// blocks [0 x 7, W(dx=-1), W(0), W(+1), 0 x 7]: the view for input offset
-// a = x_i - x0 starts a blocks further along the strip.  Nine strips (one per
-// (dy, dz), sharing their zero padding) take 97 blocks of 512 bytes.
+// Each 3x3x3 convolution (16 output channels) is a sum of GEMMs over the input
+// sites: for an input site i and every output site o within one step of it,
+//   D_o[sample][co] += A_i[sample][ci] . W(i - o)[co][ci],   M = 128, K = 16,
+// where A_i is the 128-sample activation tile of site i.  A tcgen05.mma with
+// M = 128, K = 16 takes about as long for N = 16 as for N = 64 (the issue
+// floor, about 53 cycles; N = 128 takes 64 and N = 256 128, the bf16 peak), so
+// one MMA serves every output of a work unit that an input tile reaches: its N
+// stacks those outputs' weight blocks (the column kernel below).
 //
-// Work unit: one 128-sample tile x one line of 8 output sites (x0..x0+7, y)
-// running through all L planes in z.  The CTA streams the unit's input tiles
-// plane by plane (input planes z = -1 .. L, each with the 10 x 3 sites
-// (x0-1..x0+8, y-1..y+1) around the line, periodic wrap); each input tile is
-// loaded into shared memory once and multiplied into the (up to) three output
-// planes z-1, z, z+1 it touches, one MMA each.  TMEM holds the accumulators of
-// four output planes (4 x 128 columns): while input plane z is multiplied,
-// outputs z-1, z, z+1 accumulate and the epilogue drains plane z-2.
+// Work unit: one 128-sample tile x one 2 x 2 column of output sites running
+// through all L planes in z.  The CTA streams the unit's input planes
+// z = -1 .. L, each the 4 x 4 input sites around the column (periodic wrap);
+// each input tile reaches shared memory once and is multiplied, by one MMA,
+// into every column site of the three output planes it touches.  TMEM keeps a
+// ring of eight output planes; the epilogue drains a plane once its last
+// input plane has been multiplied.
 //
 // Warp roles (192 threads, one CTA per SM):
 //   warps 0-3  epilogue: tcgen05.ld of a finished plane (warp w reads TMEM lanes
-//              32w..32w+31 = samples), bias + ReLU + BF16 store of the next
-//              layer's input, or for the last layer the 16 -> 3 head and the
-//              hard decisions;
-//   warp 4     producer: one thread issues the bulk copies of input tiles into
-//              a ring of shared-memory slots;
+//              32w..32w+31 = samples), then by mode (TcMode): bias + ReLU +
+//              BF16 store of the next layer's input; the 16 -> 3 head and the
+//              hard decisions; the head with the BCE gradient, the head's
+//              gradients and the gradient at the pre-activation; or the
+//              backward-data gradient gated by the forward activation;
+//   warp 4     producer: sixteen lanes issue the bulk copies of a plane's 16
+//              tiles at once (first layer: four lanes copy a row's four 2 KiB
+//              tiles each as one run) into a ring of shared-memory slots;
 //   warp 5     MMA issuer: one thread issues the MMAs and commits their
-//              completion to the row's "empty" barrier and to the plane's
-//              "accumulators full" barrier (the code takes kIssuers threads
-//              owning alternate planes; two were slower than one on GB300).
+//              completion to the slot's "empty" barrier and to the output
+//              plane's "accumulators full" barrier.
 // Every wait is bounded (one second; toric3d_cnn_debug_wait_limit shortens the
 // waits that may give up, so a test can make them run out); a wait that gives
 // up sets the device error flag and the CTA winds down (waiting, again bounded
@@ -45,13 +41,14 @@
 //
 // Shared-memory operand layout ("no swizzle", K-major): core matrices of 8 rows
 // x 16 bytes stored contiguously.  Hidden activations in global memory use the
-// same layout, [site][sample/8][channel/8][8 samples][8 channels] BF16, so a
-// tile (site, 128 samples) is one contiguous 4 KiB block: K-direction core
-// matrix stride (LBO) 128 B, M-direction stride (SBO) 256 B.  The first
-// layer's input (6 of 8 channels used) is stored as [site][sample][8]
-// (2 KiB per tile, SBO 128 B); two x-adjacent sites fill one 4 KiB slot as the
-// two K chunks of one operand (LBO 2 KiB), see pair_start.  Weight blocks:
-// [co/8][ci/8][co%8][ci%8] (512 B, LBO 128 B, SBO 256 B).
+// same layout, [sample/8][channel/8][8 samples][8 channels] BF16 per tile, and
+// the tile of (site, 128-sample tile m) starts at byte (m L^3 + site) 4096, so
+// a tile is one contiguous 4 KiB block (K-direction core-matrix stride (LBO)
+// 128 B, M-direction stride (SBO) 256 B).  The first layer's input tile (6 of 8
+// channels used: s_{t-1} then s_t of the three faces) is [sample][8], 2 KiB
+// (SBO 128 B); two x-adjacent sites form one K = 16 operand as its two K chunks
+// (LBO 2 KiB).  Weight blocks: [co/8][ci/8][co%8][ci%8] (512 B, LBO 128 B,
+// SBO 256 B).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -69,54 +66,27 @@ namespace cnn {
 namespace {
 
 constexpr int kTileM = 128;                         // samples per tile (MMA M)
-constexpr int kLine = 8;                            // output sites per MMA (N = 8 x 16)
-constexpr int kN = kLine * kC;                      // 128
-constexpr int kPlanes = 4;                          // output planes resident in TMEM
-constexpr uint32_t kTmemCols = kPlanes * kN;        // 512
-constexpr int kRowSlots = kLine + 2;                // input tiles of one row (x0-1 .. x0+8)
-constexpr int kGroups = 4;                          // rows in flight; each row has one full / empty barrier
-constexpr int kRing = kRowSlots * kGroups;          // 40 shared-memory input slots
-constexpr int kSlotBytes = 4096;
-constexpr int kStripPad = 7;                        // zero blocks between strips
-constexpr int kStripBlocks = kStripPad + 9 * (3 + kStripPad);   // 97
-constexpr int kWBytes = kStripBlocks * 512;         // 49,664 B
+constexpr uint32_t kTmemCols = 512;
+constexpr int kSlotBytes = 4096;                    // one hidden-layer tile
 constexpr int kEpiWarps = 4;
-constexpr int kEpiBatch = 4;                        // TMEM loads in flight per epilogue thread
 constexpr int kProducerWarp = 4;
-constexpr int kIssuerWarp = 5;                      // .. kIssuerWarp + kIssuers - 1
-constexpr int kIssuers = 1;                         // two issuers measured slower on GB300
-constexpr int kTcThreads = 32 * (kIssuerWarp + kIssuers);
+constexpr int kIssuerWarp = 5;
+constexpr int kTcThreads = 32 * (kIssuerWarp + 1);
 constexpr uint64_t kWaitNs = 1000000000ull;         // bound of every wait
-
-// Dynamic shared memory: ring | weight strips | barriers | misc.
-constexpr int kOffW = kRing * kSlotBytes;
-constexpr int kOffBar = kOffW + kWBytes;
-constexpr int kNumBars = 2 * kGroups + 2 * kPlanes + kIssuers;   // full, empty, acc_full, acc_empty, done
-constexpr int kOffMisc = kOffBar + kNumBars * 8;
-constexpr int kSmemBytes = kOffMisc + 16 + 1024;        // + alignment slack
-static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
-
-// Block index of W(dx = -1, dy, dz) in the strips; s = (dz + 1) * 3 + (dy + 1).
-__host__ __device__ constexpr int strip_start(int s) { return kStripPad + s * (3 + kStripPad); }
-
-// First layer (8 input channels per site): two x-adjacent input sites share
-// one K = 16 tile (K chunk 0 = site x, chunk 1 = site x + 1), and the pair
-// strip of (dy, dz) holds blocks [W(t) | W(t + 1)] for first-site offsets
-// t = -2 .. 1 (W = 0 outside -1..1) between 6 zero blocks; the view for the
-// pair starting at input offset xa begins at pair_start(s) + xa - 5.
-constexpr int kPairPad = 6;
-__host__ __device__ constexpr int pair_start(int s) { return kPairPad + s * (4 + kPairPad); }
-static_assert(kPairPad + 9 * (4 + kPairPad) <= kStripBlocks, "pair strips fit the strip area");
-
-// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
-// bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
 
 __device__ unsigned int g_tc_error;   // bit 0: a bounded wait gave up
 // bound of the waits that may give up (the wind-down drains always use kWaitNs)
 __device__ unsigned long long g_tc_wait_ns = kWaitNs;
+
+// What the epilogue makes of a finished output plane.
+enum TcMode {
+    kTcRelu = 0,        // bias + ReLU, BF16 activations for the next layer
+    kTcHead = 1,        // bias + ReLU, the 16 -> 3 head, hard decisions (and optional logits)
+    kTcHeadTrain = 2,   // training: the head, the BCE gradient against the labels, the head's
+                        // gradients and the loss, and the gradient at the layer's pre-activation
+    kTcMask = 3,        // backward data: the gradient gated by the forward activation's sign
+};
+__host__ __device__ constexpr bool tc_head(int mode) { return mode == kTcHead || mode == kTcHeadTrain; }
 
 struct TcArgs {
     int L, L3;
@@ -124,17 +94,22 @@ struct TcArgs {
     int64_t n_samples;
     int64_t W;                  // row stride of the bit-sliced arrays (words)
     int64_t words;              // words of this pass
-    int nbx;                    // line kernel: lines of 8 sites along x
-    int ncx;                    // column kernel: 2 x 2 columns per axis (ceil(L / 2))
+    int ncx;                    // 2 x 2 columns per axis (ceil(L / 2))
     int64_t n_units;
     const uint8_t* in;          // input activations
-    uint8_t* out;               // hidden layers: output activations
+    uint8_t* out;               // output activations / gradients (all modes but kTcHead)
     const __nv_bfloat16* w;     // [27][co][ci]
     const float* bias;          // [16]
     const float* w4;            // head [3][16]
     const float* b4;            // [3]
-    uint32_t* dec32;            // head: decision words [word][site][8] 32-bit halves
-    float* logits;              // head: optional [3][L^3][n_samples]
+    uint32_t* dec32;            // kTcHead: decision words [word][site][8] 32-bit halves
+    float* logits;              // kTcHead: optional [3][L^3][n_samples]
+    const uint64_t* label;      // kTcHeadTrain: bit-sliced labels [3][L^3][W]
+    float inv_n;                // kTcHeadTrain: 1 / (3 L^3 n_samples)
+    float* grad_w4;             // kTcHeadTrain: [3][16], accumulated
+    float* grad_b4;             // kTcHeadTrain: [3], accumulated
+    float* loss;                // kTcHeadTrain: [1], accumulated
+    const uint8_t* mask_act;    // kTcMask: the forward activation at the output sites
 };
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -208,12 +183,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                  : "memory");
 }
 
-// Bring a global range toward the L2 ahead of its bulk copy (no completion to wait for).
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -255,20 +224,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            (1ull << 46);
 }
 
-// D (+)= A . B^T; accumulate = 0 overwrites D.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n"
-        ".reg .pred pa;\n"
-        "setp.ne.b32 pa, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n"
-        "}\n" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(kIdesc), "r"(accumulate)
-        : "memory");
-}
-
-// The same with an instruction descriptor chosen per MMA (N varies).
+// D += A . B^T with the instruction descriptor of this MMA (N varies).
 __device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc)
 {
     asm volatile(
@@ -331,22 +287,8 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 // ------------------------------------------------------------------ schedule
 struct Unit {
     int64_t m0;      // first sample of the tile
-    int x0, y;       // line origin
-    int fx;          // line length (clipped at the lattice edge)
+    int x0, y;       // column origin (even)
 };
-
-__device__ __forceinline__ Unit unit_of(const TcArgs& a, int64_t u)
-{
-    const int64_t lines = (int64_t)a.nbx * a.L;
-    const int64_t tile = u / lines;
-    const int rem = (int)(u - tile * lines);
-    Unit t;
-    t.m0 = tile * kTileM;
-    t.y = rem / a.nbx;
-    t.x0 = (rem % a.nbx) * kLine;
-    t.fx = min(kLine, a.L - t.x0);
-    return t;
-}
 
 // v in [-L, 2L): periodic coordinate
 __device__ __forceinline__ int wrap(int v, int L)
@@ -365,313 +307,18 @@ __device__ __forceinline__ int64_t tile_off(int64_t site, int64_t m0, int L3, ui
 
 // Copy the tiles of sites row + wrap(x0 + i), i = 0 .. n - 1, to dst + i tile_bytes: one bulk
 // copy per run of consecutive sites (a row wraps at x = L at most once when n <= L + 2, twice
-// for the smallest lattices).  prefetch: bring them to the L2 instead.
+// for the smallest lattices).
 __device__ __forceinline__ void copy_row(uint32_t dst, const uint8_t* in, int64_t row, int x0, int n, int L, int L3,
-                                         int64_t m0, uint32_t tile_bytes, uint32_t bar, bool prefetch)
+                                         int64_t m0, uint32_t tile_bytes, uint32_t bar)
 {
     int i = 0;
     while (i < n) {
         const int x = wrap(x0 + i, L);
         int k = 1;
         while (i + k < n && x + k < L && wrap(x0 + i + k, L) == x + k) ++k;
-        const uint8_t* src = in + tile_off(row + x, m0, L3, tile_bytes);
-        if (prefetch)
-            bulk_prefetch_l2(src, (uint32_t)k * tile_bytes);
-        else
-            bulk_load(dst + (uint32_t)i * tile_bytes, src, (uint32_t)k * tile_bytes, bar);
+        bulk_load(dst + (uint32_t)i * tile_bytes, in + tile_off(row + x, m0, L3, tile_bytes), (uint32_t)k * tile_bytes,
+                  bar);
         i += k;
-    }
-}
-
-// ------------------------------------------------------------------ kernel
-template <bool kHead, bool kBitsIn>
-__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant__ TcArgs a)
-{
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const uint32_t ring = smem_u32(sm);
-    const uint32_t wsm = ring + kOffW;
-    const uint32_t bars = ring + kOffBar;
-    auto full_bar = [&](int i) { return bars + 8u * (uint32_t)i; };
-    auto empty_bar = [&](int i) { return bars + 8u * (uint32_t)(kGroups + i); };
-    auto accf_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kGroups + i); };
-    auto acce_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kGroups + kPlanes + i); };
-    auto done_bar = [&](int i) { return bars + 8u * (uint32_t)(2 * kGroups + 2 * kPlanes + i); };
-    uint32_t* misc = reinterpret_cast<uint32_t*>(sm + kOffMisc);   // [0] TMEM base, [1] abort flag
-    volatile uint32_t* abort_flag = misc + 1;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // weight strips: zero everything, then W(dx, dy, dz) at block strip_start(s) + dx + 1 in the
-    // B-operand layout [co/8][ci/8][co%8][ci%8]; first layer: the pair strips
-    for (int i = threadIdx.x; i < kWBytes / 16; i += blockDim.x)
-        reinterpret_cast<uint4*>(sm + kOffW)[i] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < kOff * kC * kC; i += blockDim.x) {
-        const int k = i >> 8, co = (i >> 4) & 15, ci = i & 15;
-        const int st = k / 3, dx = k % 3 - 1;   // st = (dz + 1) * 3 + (dy + 1)
-        const __nv_bfloat16 w = a.w[i];
-        const int row = (co >> 3) * 256 + (co & 7) * 16;
-        if (kBitsIn) {
-            if (ci >= 8) continue;   // no such input channel
-            // chunk 0 of the block with t = dx, chunk 1 of the block with t = dx - 1
-            *reinterpret_cast<__nv_bfloat16*>(sm + kOffW + (pair_start(st) + dx + 2) * 512 + row + ci * 2) = w;
-            *reinterpret_cast<__nv_bfloat16*>(sm + kOffW + (pair_start(st) + dx + 1) * 512 + row + 128 + ci * 2) = w;
-        } else {
-            const int off = (strip_start(st) + dx + 1) * 512 + row + (ci >> 3) * 128 + (ci & 7) * 2;
-            *reinterpret_cast<__nv_bfloat16*>(sm + kOffW + off) = w;
-        }
-    }
-    fence_proxy_async_smem();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < kGroups; ++i) {
-            mbar_init(full_bar(i), 1);
-            mbar_init(empty_bar(i), kIssuers);   // one commit per issuer
-        }
-        for (int i = 0; i < kPlanes; ++i) {
-            mbar_init(accf_bar(i), 1);
-            mbar_init(acce_bar(i), kEpiWarps);
-        }
-        for (int i = 0; i < kIssuers; ++i) mbar_init(done_bar(i), 1);
-        misc[1] = 0;
-        fence_mbar_init();
-    }
-    if (warp == kIssuerWarp) tmem_alloc(smem_u32(misc), kTmemCols);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = misc[0];
-
-    const int L = a.L;
-    const uint32_t in_row = kBitsIn ? 16u : 32u;
-    const uint32_t tile_bytes = kTileM * in_row;
-
-    if (warp == kProducerWarp) {
-        // one row (fixed input y and z, x = x0-1 .. x0+fx) per slot group, one barrier phase each,
-        // copied in runs of x-adjacent tiles (contiguous in the tile-major layout)
-        uint32_t gseq = 0;
-        bool ok = true;
-        for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
-            const Unit t = unit_of(a, u);
-            for (int zi = -1; zi <= L && ok; ++zi) {
-                const int zw = wrap(zi, L);
-                for (int yi = t.y - 1; yi <= t.y + 1; ++yi) {
-                    const int g = (int)(gseq % kGroups);
-                    const uint32_t use = gseq / kGroups;
-                    int good = 1;
-                    if (lane == 0 && use > 0) good = wait_bar(empty_bar(g), (use - 1) & 1u, abort_flag) ? 1 : 0;
-                    if (!__shfl_sync(0xffffffffu, good, 0)) {
-                        ok = false;
-                        break;
-                    }
-                    const int64_t row = ((int64_t)zw * L + wrap(yi, L)) * L;
-                    const int n_tiles = kBitsIn ? 2 * ((t.fx + 3) / 2) : t.fx + 2;
-                    if (lane == 0) {
-                        // the row's tiles land tile_bytes apart in the slot group, in runs of
-                        // consecutive sites
-                        mbar_arrive_expect_tx(full_bar(g), (uint32_t)n_tiles * tile_bytes);
-                        copy_row(ring + (uint32_t)(g * kRowSlots) * kSlotBytes, a.in, row, t.x0 - 1, n_tiles, L, a.L3,
-                                 t.m0, tile_bytes, full_bar(g), false);
-                    }
-                    ++gseq;
-                }
-            }
-        }
-        // copies still in flight land before the CTA exits
-        if (lane == 0) {
-            const uint32_t last = gseq < (uint32_t)kGroups ? gseq : (uint32_t)kGroups;
-            for (uint32_t g = 0; g < last; ++g) {
-                // the latest row issued on this group: the largest q < gseq with q % kGroups == g
-                const uint32_t q = gseq - 1 - ((gseq - 1 - g) % kGroups);
-                wait_bar(full_bar((int)g), (q / kGroups) & 1u, abort_flag, true);
-            }
-        }
-        __syncwarp();
-    } else if (warp >= kIssuerWarp && warp < kIssuerWarp + kIssuers) {
-        // issuer iss owns the output planes with sequence number q = iss (mod kIssuers): every
-        // accumulator is written by one thread, in program order
-        const int iss = warp - kIssuerWarp;
-        if (lane == 0) {
-            uint32_t gseq = 0;
-            int64_t qbase = 0;
-            bool ok = true;
-            // first layer: K chunk 1 is the pair's second site, 2 KiB further
-            const uint32_t a_lbo = kBitsIn ? 2048u : 128u, a_sbo = kBitsIn ? 128u : 256u;
-            const uint64_t bdesc0 = smem_desc(wsm, 128u, 256u);   // + 32 per 512-byte block
-            for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
-                const Unit t = unit_of(a, u);
-                const bool full = t.fx == kLine;
-                for (int zi = -1; zi <= L && ok; ++zi) {
-                    // output plane zi + 1 is first written by this input plane
-                    if (zi + 1 <= L - 1 && (int)((qbase + zi + 1) % kIssuers) == iss) {
-                        const int64_t q = qbase + zi + 1;
-                        const uint32_t v = (uint32_t)(q >> 2);
-                        if (v > 0 && !wait_bar(acce_bar((int)(q & 3)), (v - 1) & 1u, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                    }
-                    // TMEM column of output plane zi - dz (i = dz + 1), or -1 outside [0, L)
-                    int colb[3];
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        const int zo = zi - (i - 1);
-                        colb[i] = (zo >= 0 && zo < L && (int)((qbase + zo) % kIssuers) == iss)
-                                      ? (int)((qbase + zo) & 3) * kN
-                                      : -1;
-                    }
-                    // one tile: input offset xa = x_i - x0 in [-1, 8], dy; the MMA into plane
-                    // zi + 1 from the plane's first tile (xa = -1, dy = -1) overwrites D.
-                    auto tile_mmas = [&](int xa, int dyi, uint64_t adesc) {
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) {
-                            if (colb[i] < 0) continue;
-                            const int blk = strip_start(i * 3 + dyi) + xa - 6;
-                            const uint32_t acc = (i == 0 && dyi == 0 && xa == -1) ? 0u : 1u;
-                            mma_bf16(tmem + (uint32_t)colb[i], adesc, bdesc0 + (uint64_t)(32 * blk), acc);
-                        }
-                    };
-                    // the three rows of the plane, each one slot group behind one barrier
-                    auto row_mmas = [&](int dyi) {
-                        const int g = (int)(gseq % kGroups);
-                        // the copies and the MMAs meet through the barrier (both in the async proxy)
-                        if (ok && !wait_bar(full_bar(g), (gseq / kGroups) & 1u, abort_flag)) ok = false;
-                        if (!ok) return;
-                        const uint64_t adesc0 =
-                            smem_desc(ring + (uint32_t)(g * kRowSlots) * kSlotBytes, a_lbo, a_sbo);
-                        if (kBitsIn) {
-                            // pair p: sites x0-1+2p, x0+2p (4 KiB slot p); view pair_start + xa - 5
-                            auto pair_mmas = [&](int p) {
-                                const int xa = 2 * p - 1;
-#pragma unroll
-                                for (int i = 0; i < 3; ++i) {
-                                    if (colb[i] < 0) continue;
-                                    const int blk = pair_start(i * 3 + dyi) + xa - 5;
-                                    const uint32_t acc = (i == 0 && dyi == 0 && p == 0) ? 0u : 1u;
-                                    mma_bf16(tmem + (uint32_t)colb[i], adesc0 + (uint64_t)(p * (kSlotBytes >> 4)),
-                                             bdesc0 + (uint64_t)(32 * blk), acc);
-                                }
-                            };
-                            if (full) {
-#pragma unroll
-                                for (int p = 0; p < (kLine + 2) / 2; ++p) pair_mmas(p);
-                            } else {
-                                for (int p = 0; p < (t.fx + 3) / 2; ++p) pair_mmas(p);
-                            }
-                        } else if (full) {
-#pragma unroll
-                            for (int xa = -1; xa <= kLine; ++xa)
-                                tile_mmas(xa, dyi, adesc0 + (uint64_t)((xa + 1) * (kSlotBytes >> 4)));
-                        } else {
-                            for (int xa = -1; xa <= t.fx; ++xa)
-                                tile_mmas(xa, dyi, adesc0 + (uint64_t)((xa + 1) * (kSlotBytes >> 4)));
-                        }
-                        mma_commit(empty_bar(g));
-                        ++gseq;
-                    };
-                    row_mmas(0);
-                    row_mmas(1);
-                    row_mmas(2);
-                    if (!ok) break;
-                    // output plane zi - 1 has received its last contribution
-                    if (zi - 1 >= 0 && zi - 1 <= L - 1 && (int)((qbase + zi - 1) % kIssuers) == iss)
-                        mma_commit(accf_bar((int)((qbase + zi - 1) & 3)));
-                }
-                qbase += L;
-            }
-            // every MMA issued has completed before TMEM is released
-            mma_commit(done_bar(iss));
-            wait_bar(done_bar(iss), 0, abort_flag, true);
-        }
-        __syncwarp();
-    } else {
-        // epilogue: warp w owns TMEM lanes (= tile rows = samples) 32w .. 32w + 31
-        const int r = warp * 32 + lane;
-        float bias[kC];
-#pragma unroll
-        for (int c = 0; c < kC; ++c) bias[c] = a.bias[c];
-        float w4[kHead ? 3 * kC : 1];
-        float b4[3] = {0.0f, 0.0f, 0.0f};
-        if (kHead) {
-#pragma unroll
-            for (int i = 0; i < 3 * kC; ++i) w4[i] = a.w4[i];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) b4[d] = a.b4[d];
-        }
-        int64_t q = 0;
-        bool ok = true;
-        for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
-            const Unit t = unit_of(a, u);
-            const int64_t sample = t.m0 + r;
-            const bool valid = sample < a.n_samples;
-            for (int zo = 0; zo < L; ++zo, ++q) {
-                const int s = (int)(q & 3);
-                // one lane waits; the warp stays converged for the .sync.aligned TMEM loads
-                int got = 1;
-                if (lane == 0) got = wait_bar(accf_bar(s), (uint32_t)(q >> 2) & 1u, abort_flag) ? 1 : 0;
-                got = __shfl_sync(0xffffffffu, got, 0);
-                if (!got) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                // four outputs per batch of TMEM loads, one wait per batch
-                for (int ob = 0; ob < t.fx; ob += kEpiBatch) {
-                    uint32_t raw[kEpiBatch][16];
-#pragma unroll
-                    for (int j = 0; j < kEpiBatch; ++j)
-                        if (ob + j < t.fx)
-                            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) +
-                                          (uint32_t)(s * kN + (kLine - 1 - (ob + j)) * kC),
-                                      raw[j]);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < kEpiBatch; ++j) {
-                        if (ob + j >= t.fx) continue;
-                        const int64_t site = ((int64_t)zo * L + t.y) * L + (t.x0 + ob + j);
-                        float v[16];
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(raw[j][c]);
-                        if (!kHead) {
-                            uint32_t p[8];
-#pragma unroll
-                            for (int c = 0; c < kC; c += 2)
-                                p[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
-                            uint8_t* dst = a.out + tile_off(site, t.m0, a.L3, 4096) + (r >> 3) * 256 + (r & 7) * 16;
-                            *reinterpret_cast<uint4*>(dst) = make_uint4(p[0], p[1], p[2], p[3]);
-                            *reinterpret_cast<uint4*>(dst + 128) = make_uint4(p[4], p[5], p[6], p[7]);
-                        } else {
-                            float z[3] = {b4[0], b4[1], b4[2]};
-#pragma unroll
-                            for (int c = 0; c < kC; ++c) {
-                                const float y = fmaxf(v[c] + bias[c], 0.0f);
-#pragma unroll
-                                for (int d = 0; d < 3; ++d) z[d] = fmaf(y, w4[d * kC + c], z[d]);
-                            }
-                            const int64_t wd = (t.m0 + warp * 32) / 64;
-                            const int hw = warp & 1;
-#pragma unroll
-                            for (int d = 0; d < 3; ++d) {
-                                if (a.logits && valid)
-                                    a.logits[((int64_t)d * a.L3 + site) * a.n_samples + sample] = z[d];
-                                const uint32_t bits = __ballot_sync(0xffffffffu, valid && z[d] > 0.0f);
-                                if (lane == 0 && wd < a.words) a.dec32[(wd * a.L3 + site) * 8 + 2 * d + hw] = bits;
-                            }
-                        }
-                    }
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acce_bar(s));
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == kIssuerWarp) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -689,11 +336,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
 // one per-position sequence of weight blocks [plane zi - 1: sites lo..3 |
 // plane zi: 0..3 | plane zi + 1: 0..hi], W(xi - xo, yi - yo, zi - zo) or zero
 // where the site is out of reach; of the blocks multiplied 64% are non-zero
-// (108 of 168 per plane; the line kernel: 30%).  A window that would cross
+// (108 of 168 per plane).  A window that would cross
 // the ring's end is split in two MMAs.  TMEM columns are zeroed by the
 // epilogue after it drains a plane (and once at the start), so every MMA
 // accumulates.  The first layer pairs x-adjacent input sites in one K = 16
-// operand (chunk c = site 2p - 1 + c of the row) as the line kernel does.
+// operand (chunk c = site 2p - 1 + c of the row; LBO 2 KiB steps to the second site).
 // Input ring of 128 KiB: two planes of 16 x 4 KiB tiles (hidden layers) or four of 16 x 2 KiB
 // (first layer).
 constexpr int kColRingBytes = 32 * kSlotBytes;
@@ -778,11 +425,10 @@ __device__ __forceinline__ Unit col_unit_of(const TcArgs& a, int64_t u)
     t.m0 = tile * kTileM;
     t.y = (rem / a.ncx) * 2;
     t.x0 = (rem % a.ncx) * 2;
-    t.fx = 0;
     return t;
 }
 
-template <bool kHead, bool kBitsIn>
+template <int kMode, bool kBitsIn>
 __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constant__ TcArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -894,7 +540,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                     if (lane < 4)
                         copy_row(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * 4u * tile_bytes, a.in,
                                  ((int64_t)wrap(zi, L) * L + wrap(t.y - 1 + lane, L)) * L, t.x0 - 1, 4, L, a.L3, t.m0,
-                                 tile_bytes, full_bar(g), false);
+                                 tile_bytes, full_bar(g));
                 } else if (lane < 16) {
                     bulk_load(ring + (uint32_t)g * kColInBytes + (uint32_t)lane * tile_bytes,
                               a.in + tile_off((int64_t)wrap(zi, L) * L * L + xy, t.m0, a.L3, tile_bytes), tile_bytes,
@@ -993,9 +639,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
     } else {
         // epilogue: warp w owns TMEM lanes (= tile rows = samples) 32w .. 32w + 31
         const int r = warp * 32 + lane;
+        constexpr bool kHead = tc_head(kMode);
         float bias[kC];
 #pragma unroll
-        for (int c = 0; c < kC; ++c) bias[c] = a.bias[c];
+        for (int c = 0; c < kC; ++c) bias[c] = kMode == kTcMask ? 0.0f : a.bias[c];
         float w4[kHead ? 3 * kC : 1];
         float b4[3] = {0.0f, 0.0f, 0.0f};
         if (kHead) {
@@ -1004,6 +651,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
 #pragma unroll
             for (int d = 0; d < 3; ++d) b4[d] = a.b4[d];
         }
+        // training: this thread's share of the head's gradients and of the loss
+        constexpr int kAcc = kMode == kTcHeadTrain ? 3 * kC + 3 + 1 : 1;
+        float acc[kAcc];
+#pragma unroll
+        for (int i = 0; i < kAcc; ++i) acc[i] = 0.0f;
         int64_t q = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; u < a.n_units && ok; u += gridDim.x) {
@@ -1032,33 +684,81 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                     const int xo = t.x0 + (j & 1), yo = t.y + (j >> 1);
                     if (xo >= L || yo >= L) continue;   // the odd lattice's last column
                     const int64_t site = ((int64_t)zo * L + yo) * L + xo;
+                    const int64_t row_off = tile_off(site, t.m0, a.L3, 4096) + (r >> 3) * 256 + (r & 7) * 16;
                     float v[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) v[c] = __uint_as_float(raw[j][c]);
-                    if (!kHead) {
+                    if (kMode == kTcRelu || kMode == kTcMask) {
                         uint32_t pk[8];
+                        if (kMode == kTcRelu) {
 #pragma unroll
-                        for (int c = 0; c < kC; c += 2)
-                            pk[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
-                        uint8_t* dst = a.out + tile_off(site, t.m0, a.L3, 4096) + (r >> 3) * 256 + (r & 7) * 16;
+                            for (int c = 0; c < kC; c += 2)
+                                pk[c / 2] = pack2(fmaxf(v[c] + bias[c], 0.0f), fmaxf(v[c + 1] + bias[c + 1], 0.0f));
+                        } else {
+                            // the gradient passes where the forward activation (a ReLU output,
+                            // so never negative) is non-zero
+                            const uint4 m0v = *reinterpret_cast<const uint4*>(a.mask_act + row_off);
+                            const uint4 m1v = *reinterpret_cast<const uint4*>(a.mask_act + row_off + 128);
+                            const uint32_t mw[8] = {m0v.x, m0v.y, m0v.z, m0v.w, m1v.x, m1v.y, m1v.z, m1v.w};
+#pragma unroll
+                            for (int c = 0; c < kC; c += 2)
+                                pk[c / 2] = pack2((mw[c / 2] & 0x7FFFu) ? v[c] : 0.0f,
+                                                  (mw[c / 2] & 0x7FFF0000u) ? v[c + 1] : 0.0f);
+                        }
+                        uint8_t* dst = a.out + row_off;
                         *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                     } else {
+                        float y3[kC];
                         float z[3] = {b4[0], b4[1], b4[2]};
 #pragma unroll
                         for (int c = 0; c < kC; ++c) {
-                            const float y = fmaxf(v[c] + bias[c], 0.0f);
+                            y3[c] = fmaxf(v[c] + bias[c], 0.0f);
 #pragma unroll
-                            for (int d = 0; d < 3; ++d) z[d] = fmaf(y, w4[d * kC + c], z[d]);
+                            for (int d = 0; d < 3; ++d) z[d] = fmaf(y3[c], w4[d * kC + c], z[d]);
                         }
                         const int64_t wd = (t.m0 + warp * 32) / 64;
                         const int hw = warp & 1;
+                        if (kMode == kTcHead) {
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            if (a.logits && valid)
-                                a.logits[((int64_t)d * a.L3 + site) * a.n_samples + sample] = z[d];
-                            const uint32_t bits = __ballot_sync(0xffffffffu, valid && z[d] > 0.0f);
-                            if (lane == 0 && wd < a.words) a.dec32[(wd * a.L3 + site) * 8 + 2 * d + hw] = bits;
+                            for (int d = 0; d < 3; ++d) {
+                                if (a.logits && valid)
+                                    a.logits[((int64_t)d * a.L3 + site) * a.n_samples + sample] = z[d];
+                                const uint32_t bits = __ballot_sync(0xffffffffu, valid && z[d] > 0.0f);
+                                if (lane == 0 && wd < a.words) a.dec32[(wd * a.L3 + site) * 8 + 2 * d + hw] = bits;
+                            }
+                        } else {
+                            // binary cross-entropy of the logits against the labels (the mean over
+                            // edges and samples is what training minimises): dL/dz = (sigmoid(z) - y) / N
+                            float dz[3];
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) {
+                                const uint64_t lw = wd < a.words ? a.label[((int64_t)d * a.L3 + site) * a.W + wd] : 0ull;
+                                const float yv = (float)((uint32_t)(lw >> (32 * hw + lane)) & 1u);
+                                const float sig = 1.0f / (1.0f + expf(-z[d]));
+                                dz[d] = valid ? (sig - yv) * a.inv_n : 0.0f;
+                                if (valid) acc[3 * kC + 3] += fmaxf(z[d], 0.0f) - z[d] * yv + log1pf(expf(-fabsf(z[d])));
+                                acc[3 * kC + d] += dz[d];
+                            }
+                            uint32_t pk[8];
+#pragma unroll
+                            for (int c = 0; c < kC; c += 2) {
+                                float g2[2];
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    float dy = 0.0f;
+#pragma unroll
+                                    for (int d = 0; d < 3; ++d) {
+                                        dy = fmaf(dz[d], w4[d * kC + c + h], dy);
+                                        acc[d * kC + c + h] = fmaf(y3[c + h], dz[d], acc[d * kC + c + h]);
+                                    }
+                                    g2[h] = y3[c + h] > 0.0f ? dy : 0.0f;
+                                }
+                                pk[c / 2] = pack2(g2[0], g2[1]);
+                            }
+                            uint8_t* dst = a.out + row_off;
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                         }
                     }
                 }
@@ -1066,6 +766,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_col(const __grid_constan
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acce_bar(s));
+            }
+        }
+        if (kMode == kTcHeadTrain) {
+            // the warp's sums, then one atomic per value and warp
+#pragma unroll
+            for (int i = 0; i < kAcc; ++i) {
+                float x = acc[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0 && x != 0.0f) {
+                    float* dst = i < 3 * kC ? a.grad_w4 + i : (i < 3 * kC + 3 ? a.grad_b4 + (i - 3 * kC) : a.loss);
+                    atomicAdd(dst, x);
+                }
             }
         }
     }
@@ -1124,34 +837,40 @@ int sm_count()
     return n > 0 ? n : 1;
 }
 
-template <bool kHead, bool kBitsIn>
-t3d_status launch_conv(const TcArgs& a, cudaStream_t st)
-{
-    const int grid = (int)std::min<int64_t>(a.n_units, sm_count());
-    ProfScope prof(T3D_K_CNN, st);
-    k_conv_tc<kHead, kBitsIn><<<grid, kTcThreads, kSmemBytes, st>>>(a);
-    T3D_LAUNCH_CHECK("tensor-core convolution");
-    return T3D_OK;
-}
-
-template <bool kHead, bool kBitsIn>
+template <int kMode, bool kBitsIn>
 t3d_status launch_conv_col(const TcArgs& a, cudaStream_t st)
 {
     const int grid = (int)std::min<int64_t>(a.n_units, sm_count());
     ProfScope prof(T3D_K_CNN, st);
-    k_conv_col<kHead, kBitsIn><<<grid, kTcThreads, kColSmemBytes, st>>>(a);
-    T3D_LAUNCH_CHECK("tensor-core convolution (2 x 2 columns)");
+    k_conv_col<kMode, kBitsIn><<<grid, kTcThreads, kColSmemBytes, st>>>(a);
+    T3D_LAUNCH_CHECK("tensor-core convolution");
     return T3D_OK;
 }
 
-// The line kernel stays selectable (T3D_CNN_LINES=1 in the environment) for comparisons.
-bool use_line_kernel()
+// Arguments shared by every convolution of a pass over n_samples samples.
+TcArgs base_args(int L, int64_t n_samples, int64_t W)
 {
-    static const bool lines = [] {
-        const char* v = std::getenv("T3D_CNN_LINES");
-        return v && v[0] == '1';
-    }();
-    return lines;
+    TcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const int64_t Sp = tc_padded(n_samples);
+    a.L = L;
+    a.L3 = L * L * L;
+    a.Sp = Sp;
+    a.n_samples = n_samples;
+    a.W = W;
+    a.words = words_for(n_samples);
+    a.ncx = (L + 1) / 2;
+    a.n_units = (Sp / kTileM) * a.ncx * a.ncx;
+    return a;
+}
+
+t3d_status expand_bits(const TcArgs& a, const uint64_t* s_prev, const uint64_t* s, uint8_t* x0, cudaStream_t st)
+{
+    ProfScope prof(T3D_K_CNN, st);
+    const dim3 grid((unsigned)((a.L3 + 7) / 8), (unsigned)((a.Sp + 255) / 256));
+    k_expand_bits<<<grid, 256, 0, st>>>(a.L3, a.Sp, a.W, a.words, s_prev, s, reinterpret_cast<uint4*>(x0));
+    T3D_LAUNCH_CHECK("pre-decoder input expansion");
+    return T3D_OK;
 }
 
 }  // namespace
@@ -1165,66 +884,46 @@ t3d_status tc_prepare()
     T3D_REQUIRE(dev >= 0 && dev < 64, "device %d outside the 64 supported", dev);
     std::lock_guard<std::mutex> lock(mu);
     if (!configured[dev]) {
-        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kSmemBytes));
-        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kSmemBytes));
-        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_tc<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kSmemBytes));
-        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kColSmemBytes));
-        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kColSmemBytes));
-        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kColSmemBytes));
+        const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<kTcRelu, true>, attr, kColSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<kTcRelu, false>, attr, kColSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<kTcHead, false>, attr, kColSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<kTcHeadTrain, false>, attr, kColSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<kTcMask, false>, attr, kColSmemBytes));
         configured[dev] = true;
     }
     return T3D_OK;
 }
 
+size_t tc_act_bytes(int L, int64_t n_samples, int channels)
+{
+    return r256((size_t)L * L * L * (size_t)tc_padded(n_samples) * 2 * (size_t)channels);
+}
+
 size_t tc_workspace_bytes(int L, int64_t n_samples)
 {
-    const size_t sites = (size_t)L * L * L, Sp = (size_t)tc_padded(n_samples);
-    return r256(sites * Sp * 16) + 2 * r256(sites * Sp * 32);
+    return tc_act_bytes(L, n_samples, 8) + 2 * tc_act_bytes(L, n_samples, kC);
 }
 
 t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t* s_prev, const uint64_t* s,
                              uint64_t* dec, const Blob* blob, float* logits_out, void* work, cudaStream_t st)
 {
-    const int64_t Sp = tc_padded(n_samples), L3 = (int64_t)L * L * L;
-    uint8_t* base = static_cast<uint8_t*>(work);
-    uint8_t* in0 = base;
-    uint8_t* act0 = in0 + r256((size_t)L3 * Sp * 16);
-    uint8_t* act1 = act0 + r256((size_t)L3 * Sp * 32);
-    TcArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.L = L;
-    a.L3 = (int)L3;
-    a.Sp = Sp;
-    a.n_samples = n_samples;
-    a.W = W;
-    a.words = words_for(n_samples);
-    a.nbx = (L + kLine - 1) / kLine;
-    a.ncx = (L + 1) / 2;
-    const bool lines = use_line_kernel();
-    a.n_units = lines ? (Sp / kTileM) * a.nbx * L : (Sp / kTileM) * a.ncx * a.ncx;
+    uint8_t* in0 = static_cast<uint8_t*>(work);
+    uint8_t* act0 = in0 + tc_act_bytes(L, n_samples, 8);
+    uint8_t* act1 = act0 + tc_act_bytes(L, n_samples, kC);
     T3D_TRY(tc_prepare());
-    {
-        ProfScope prof(T3D_K_CNN, st);
-        const dim3 grid((unsigned)((L3 + 7) / 8), (unsigned)((Sp + 255) / 256));
-        k_expand_bits<<<grid, 256, 0, st>>>((int)L3, Sp, W, a.words, s_prev, s, reinterpret_cast<uint4*>(in0));
-        T3D_LAUNCH_CHECK("pre-decoder input expansion");
-    }
+    TcArgs a = base_args(L, n_samples, W);
+    T3D_TRY(expand_bits(a, s_prev, s, in0, st));
     a.in = in0;
     a.out = act0;
     a.w = &blob->wf[0][0][0][0];
     a.bias = blob->bias[0];
-    T3D_TRY((lines ? launch_conv<false, true>(a, st) : launch_conv_col<false, true>(a, st)));
+    T3D_TRY((launch_conv_col<kTcRelu, true>(a, st)));
     a.in = act0;
     a.out = act1;
     a.w = &blob->wf[1][0][0][0];
     a.bias = blob->bias[1];
-    T3D_TRY((lines ? launch_conv<false, false>(a, st) : launch_conv_col<false, false>(a, st)));
+    T3D_TRY((launch_conv_col<kTcRelu, false>(a, st)));
     a.in = act1;
     a.out = nullptr;
     a.w = &blob->wf[2][0][0][0];
@@ -1233,8 +932,52 @@ t3d_status launch_forward_tc(int L, int64_t n_samples, int64_t W, const uint64_t
     a.b4 = blob->b4;
     a.dec32 = reinterpret_cast<uint32_t*>(dec);
     a.logits = logits_out;
-    T3D_TRY((lines ? launch_conv<true, false>(a, st) : launch_conv_col<true, false>(a, st)));
+    T3D_TRY((launch_conv_col<kTcHead, false>(a, st)));
     return T3D_OK;
+}
+
+t3d_status tc_train_forward(int L, int64_t n_samples, int64_t W, const uint64_t* s_prev, const uint64_t* s,
+                            const uint64_t* label, const Blob* blob, uint8_t* x0, uint8_t* y1, uint8_t* y2,
+                            uint8_t* g3, float* grad_w4, float* grad_b4, float* loss, cudaStream_t st)
+{
+    T3D_TRY(tc_prepare());
+    TcArgs a = base_args(L, n_samples, W);
+    T3D_TRY(expand_bits(a, s_prev, s, x0, st));
+    a.in = x0;
+    a.out = y1;
+    a.w = &blob->wf[0][0][0][0];
+    a.bias = blob->bias[0];
+    T3D_TRY((launch_conv_col<kTcRelu, true>(a, st)));
+    a.in = y1;
+    a.out = y2;
+    a.w = &blob->wf[1][0][0][0];
+    a.bias = blob->bias[1];
+    T3D_TRY((launch_conv_col<kTcRelu, false>(a, st)));
+    a.in = y2;
+    a.out = g3;
+    a.w = &blob->wf[2][0][0][0];
+    a.bias = blob->bias[2];
+    a.w4 = &blob->w4[0][0];
+    a.b4 = blob->b4;
+    a.label = label;
+    a.inv_n = 1.0f / (3.0f * (float)a.L3 * (float)n_samples);
+    a.grad_w4 = grad_w4;
+    a.grad_b4 = grad_b4;
+    a.loss = loss;
+    T3D_TRY((launch_conv_col<kTcHeadTrain, false>(a, st)));
+    return T3D_OK;
+}
+
+t3d_status tc_backward_data(int L, int64_t n_samples, const __nv_bfloat16* wt, const uint8_t* g_in,
+                            const uint8_t* mask_act, uint8_t* g_out, cudaStream_t st)
+{
+    T3D_TRY(tc_prepare());
+    TcArgs a = base_args(L, n_samples, words_for(n_samples));
+    a.in = g_in;
+    a.out = g_out;
+    a.w = wt;
+    a.mask_act = mask_act;
+    return launch_conv_col<kTcMask, false>(a, st);
 }
 
 t3d_status tc_set_wait_limit(uint64_t ns)
