@@ -57,74 +57,6 @@ __device__ __forceinline__ int neighbour(const Lattice& lat, const Coord& rc, in
     return (z * lat.L + y) * lat.L + x;
 }
 
-// Element pair (c, c + 1), c even, of sample s at site r in a tile-major buffer of
-// 16 channels ([sample/8][channel/8][8 samples][8 channels] per 128-sample tile) or
-// of 8 ([sample][8]), as one 32-bit word.
-__device__ __forceinline__ uint32_t tile_pair(const uint8_t* buf, int L3, int channels, int r, int64_t s, int c)
-{
-    const int64_t tile = ((s >> 7) * L3 + r) * (int64_t)(256 * channels);
-    const int m = (int)(s & 127);
-    const int64_t off = channels == 16 ? (m >> 3) * 256 + (c >> 3) * 128 + (m & 7) * 16 + (c & 7) * 2 : m * 16 + c * 2;
-    return *reinterpret_cast<const uint32_t*>(buf + tile + off);
-}
-
-// Weight and bias gradients of one convolution layer (CUDA cores):
-// gw[k][co][ci] = sum over sites r and samples s of x[r + off_k][s][ci] dpre[r][s][co],
-// gb[co] = sum dpre[r][s][co].  Block (k, sample chunk of 64); thread (co, ci);
-// partial sums per chunk go to part[chunk][k][co][ci] (+ bias at k = 27).  x has
-// x_ch channels (8: the first layer's input, 16: hidden), dpre 16; both tile-major.
-constexpr int kChunk = 64;
-
-__global__ void __launch_bounds__(256)
-k_wgrad(Lattice lat, int64_t n_samples, const uint8_t* __restrict__ x, int x_ch, const uint8_t* __restrict__ dpre,
-        float* __restrict__ part)
-{
-    __shared__ float sx[kChunk][kC + 1];
-    __shared__ float sd[kChunk][kC + 1];
-    const int k = blockIdx.x;            // 0..26, 27 = bias
-    const int64_t s0 = (int64_t)blockIdx.y * kChunk;
-    const int co = threadIdx.x / kC, ci = threadIdx.x % kC;
-    float acc = 0.0f;
-    for (int r = 0; r < lat.L3; ++r) {
-        const int rn = (k < kOff) ? neighbour(lat, site_coord(lat, r), k) : r;
-        for (int i = threadIdx.x; i < kChunk * (kC / 2); i += blockDim.x) {
-            const int s = i / (kC / 2), c2 = i % (kC / 2);
-            const bool ok = s0 + s < n_samples;
-            const float2 vx = ok && 2 * c2 < x_ch ? unpack_bf16(tile_pair(x, lat.L3, x_ch, rn, s0 + s, 2 * c2))
-                                                  : make_float2(0, 0);
-            const float2 vd = ok ? unpack_bf16(tile_pair(dpre, lat.L3, kC, r, s0 + s, 2 * c2)) : make_float2(0, 0);
-            sx[s][2 * c2] = vx.x;
-            sx[s][2 * c2 + 1] = vx.y;
-            sd[s][2 * c2] = vd.x;
-            sd[s][2 * c2 + 1] = vd.y;
-        }
-        __syncthreads();
-        if (k < kOff) {
-#pragma unroll 8
-            for (int s = 0; s < kChunk; ++s) acc += sx[s][ci] * sd[s][co];
-        } else if (ci == 0) {
-            for (int s = 0; s < kChunk; ++s) acc += sd[s][co];
-        }
-        __syncthreads();
-    }
-    part[((int64_t)blockIdx.y * (kOff + 1) + k) * kC * kC + co * kC + ci] = acc;
-}
-
-__global__ void k_wgrad_reduce(int chunks, const float* __restrict__ part, float* __restrict__ gw,
-                               float* __restrict__ gb, int c_in)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;   // (k, co, ci) or bias
-    if (i >= (kOff + 1) * kC * kC) return;
-    float v = 0.0f;
-    for (int c = 0; c < chunks; ++c) v += part[(int64_t)c * (kOff + 1) * kC * kC + i];
-    const int k = i / (kC * kC), co = (i / kC) % kC, ci = i % kC;
-    if (k < kOff) {
-        if (ci < c_in) gw[(co * c_in + ci) * kOff + k] = v;   // PyTorch order [co][ci][k]
-    } else if (ci == 0) {
-        gb[co] = v;
-    }
-}
-
 // FP32 master -> blob (forward weights, transposed-flipped weights, biases, head).
 __global__ void k_prepare(const float* __restrict__ p, Blob* __restrict__ blob)
 {
@@ -298,8 +230,8 @@ extern "C" t3d_status toric3d_cnn_decode(int L, int64_t n_samples, const uint64_
 extern "C" size_t toric3d_cnn_train_workspace_bytes(int L, int64_t n_samples)
 {
     if (L < 2 || L > 128 || n_samples < 1) return 0;
-    const size_t part = round256((size_t)((padded(n_samples) + kChunk - 1) / kChunk) * (kOff + 1) * kC * kC * 4);
-    return tc_act_bytes(L, n_samples, 8) + 4 * tc_act_bytes(L, n_samples, kC) + part + round256(kParams * 4) + 256;
+    // features, y1, y2, two gradient buffers, two channel-major copies, the ones tile, grads
+    return tc_act_bytes(L, n_samples, 8) + 6 * tc_act_bytes(L, n_samples, kC) + 4096 + round256(kParams * 4) + 256;
 }
 
 extern "C" t3d_status toric3d_cnn_train_step(int L, int64_t n_samples, const uint64_t* s_prev,
@@ -326,32 +258,24 @@ extern "C" t3d_status toric3d_cnn_train_step(int L, int64_t n_samples, const uin
     uint8_t* y2 = y1 + ab;
     uint8_t* g3 = y2 + ab;              // dPre3, later dPre1
     uint8_t* g2 = g3 + ab;              // dPre2
-    const int chunks = (int)((padded(n_samples) + kChunk - 1) / kChunk);
-    float* part = reinterpret_cast<float*>(g2 + ab);
-    float* grads = reinterpret_cast<float*>(g2 + ab + round256((size_t)chunks * (kOff + 1) * kC * kC * 4));
+    uint8_t* xt = g2 + ab;              // channel-major copies for the weight gradients
+    uint8_t* dt = xt + ab;
+    uint8_t* ones = dt + ab;
+    float* grads = reinterpret_cast<float*>(ones + 4096);
     if (grads_out) grads = grads_out;
-    const Lattice lat = make_lattice_host(L);
     const int64_t W = words_for(n_samples);
     T3D_CUDA_CHECK(cudaMemsetAsync(grads, 0, kParams * sizeof(float), st));
     T3D_CUDA_CHECK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
+    T3D_TRY(tc_fill_ones(ones, st));
     // forward, with the BCE gradient and the head's gradients in the last layer's epilogue
     T3D_TRY(tc_train_forward(L, n_samples, W, s_prev, s, e_label, b, x0, y1, y2, g3, grads + P_W4, grads + P_B4,
                              loss_out, st));
-    // backward: layer 3 weights, then data gradient into layer 2 (masked by y2 > 0), ...
-    ProfScope prof(T3D_K_CNN, st);
-    const dim3 wg(kOff + 1, (unsigned)chunks);
-    const int red = ((kOff + 1) * kC * kC + 255) / 256;
-    k_wgrad<<<wg, 256, 0, st>>>(lat, n_samples, y2, kC, g3, part);
-    k_wgrad_reduce<<<red, 256, 0, st>>>(chunks, part, grads + P_W3, grads + P_B3, kC);
-    T3D_LAUNCH_CHECK("cnn weight gradient");
+    // backward: layer 3's weights, the data gradient into layer 2 (gated by y2 > 0), ...
+    T3D_TRY(tc_weight_grad(L, n_samples, kC, kC, y2, g3, xt, dt, ones, grads + P_W3, grads + P_B3, st));
     T3D_TRY(tc_backward_data(L, n_samples, &b->wt[2][0][0][0], g3, y2, g2, st));
-    k_wgrad<<<wg, 256, 0, st>>>(lat, n_samples, y1, kC, g2, part);
-    k_wgrad_reduce<<<red, 256, 0, st>>>(chunks, part, grads + P_W2, grads + P_B2, kC);
-    T3D_LAUNCH_CHECK("cnn weight gradient");
+    T3D_TRY(tc_weight_grad(L, n_samples, kC, kC, y1, g2, xt, dt, ones, grads + P_W2, grads + P_B2, st));
     T3D_TRY(tc_backward_data(L, n_samples, &b->wt[1][0][0][0], g2, y1, g3, st));   // dPre1
-    k_wgrad<<<wg, 256, 0, st>>>(lat, n_samples, x0, 8, g3, part);
-    k_wgrad_reduce<<<red, 256, 0, st>>>(chunks, part, grads + P_W1, grads + P_B1, kInC);
-    T3D_LAUNCH_CHECK("cnn backward");
+    T3D_TRY(tc_weight_grad(L, n_samples, 8, kInC, x0, g3, xt, dt, ones, grads + P_W1, grads + P_B1, st));
     if (lr > 0.0f) {
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);

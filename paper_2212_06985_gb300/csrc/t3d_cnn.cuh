@@ -68,6 +68,13 @@ t3d_status tc_train_forward(int L, int64_t n_samples, int64_t W, const uint64_t*
 // activation mask_act is non-zero, else 0 (wt: the transposed, flipped weights).
 t3d_status tc_backward_data(int L, int64_t n_samples, const __nv_bfloat16* wt, const uint8_t* g_in,
                             const uint8_t* mask_act, uint8_t* g_out, cudaStream_t st);
+// Weight and bias gradients of one convolution on the tensor cores: x (x_ch = 8 or 16
+// channels) and d (16) tile-major; xt, dt scratch of tc_act_bytes(L, n_samples, 16) for
+// their channel-major copies; ones: a 4 KiB tile of BF16 ones (tc_fill_ones).  Adds
+// gw[co][ci][27] (ci < cin_kept) and gb[16].
+t3d_status tc_fill_ones(uint8_t* tile, cudaStream_t st);
+t3d_status tc_weight_grad(int L, int64_t n_samples, int x_ch, int cin_kept, const uint8_t* x, const uint8_t* d,
+                          uint8_t* xt, uint8_t* dt, const uint8_t* ones, float* gw, float* gb, cudaStream_t st);
 
 }  // namespace cnn
 }  // namespace t3d

@@ -176,6 +176,29 @@ __device__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t* abort
     }
 }
 
+// Wait for phase 0 of a barrier that completes only at the end of a long launch: gives up
+// (error flag, abort) once *progress has not changed for g_tc_wait_ns.
+__device__ bool wait_bar_progress(uint32_t bar, volatile uint32_t* progress, volatile uint32_t* abort_flag)
+{
+    uint64_t t0 = global_ns();
+    uint32_t last = *progress;
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, 0)) return true;
+        if (*abort_flag) return false;
+        const uint32_t now_p = *progress;
+        const uint64_t now = global_ns();
+        if (now_p != last) {
+            last = now_p;
+            t0 = now;
+        } else if (now - t0 > *(volatile unsigned long long*)&g_tc_wait_ns) {
+            *abort_flag = 1;
+            atomicOr(&g_tc_error, 1u);
+            return false;
+        }
+    }
+}
+
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -231,6 +254,19 @@ __device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t a_desc, uin
         "{\n"
         ".reg .pred pa;\n"
         "setp.ne.b32 pa, 1, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc)
+        : "memory");
+}
+
+// D = A . B^T, not accumulating (the first MMA into an accumulator).
+__device__ __forceinline__ void mma_bf16_overwrite(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc)
+{
+    asm volatile(
+        "{\n"
+        ".reg .pred pa;\n"
+        "setp.ne.b32 pa, 0, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n"
         "}\n" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc)
@@ -826,6 +862,241 @@ __global__ void k_expand_bits(int L3, int64_t Sp, int64_t W, int64_t words, cons
     }
 }
 
+// ------------------------------------------------------------------ weight gradients
+// Weight and bias gradients of one convolution as a GEMM over samples:
+//   G[(k, ci)][co] = sum over sites r and samples s of x[r + off_k][s][ci] . d[r][s][co],
+// M = 128 rows (8 offsets x 16 input channels; the first layer 16 x 8), N = 16 output
+// channels, K = 16 samples per MMA.  The reduction runs over samples, so both operands are
+// channel-major copies of the tiles (k_channel_major): a tile of C channels x 128 samples is
+// [C/8][sample/8][8 channels][8 samples] BF16, K-major core matrices with LBO 128 B (the next
+// 8 samples) and SBO 2048 B (the next 8 channels -- also the step to the next tile of an M
+// group, so the 8 (16) neighbour tiles of a group sit at a uniform stride).  The 28th
+// "offset" is a tile of ones: its rows give the bias gradient sum d[r][s][co].  Work item:
+// one (128-sample tile, site); per item the d tile and, per M group, its neighbour tiles are
+// copied into rings of slots, and the group's accumulator in TMEM (16 columns) takes 8 MMAs.
+// The accumulators live for the whole launch and are added to the gradients at the end.
+// Rows beyond offset 27 multiply whatever the slot holds and are never read.
+constexpr int kWgX = 6;                       // group slots, 32 KiB each
+constexpr int kWgD = 4;                       // d-tile slots, 4 KiB each
+constexpr int kWgOffD = kWgX * 32768;
+constexpr int kWgOffBar = kWgOffD + kWgD * 4096;
+constexpr int kWgNumBars = 2 * kWgX + 2 * kWgD + 1;   // x full, x empty, d full, d empty, done
+constexpr int kWgOffMisc = kWgOffBar + kWgNumBars * 8;
+constexpr int kWgSmemBytes = kWgOffMisc + 16 + 1024;
+static_assert(kWgSmemBytes <= 227 * 1024, "shared memory budget");
+
+struct WgArgs {
+    int L, L3;
+    int64_t n_items;            // 128-sample tiles x L^3 sites
+    const uint8_t* xt;          // channel-major x tiles (kCin channels)
+    const uint8_t* dt;          // channel-major d tiles (16 channels)
+    const uint8_t* ones;        // one x tile of BF16 ones
+    int cin;                    // input channels kept in gw (6 for the first layer)
+    float* gw;                  // [co][cin][27], accumulated
+    float* gb;                  // [16], accumulated
+};
+
+// Site r + offset k (k = (dz + 1) 9 + (dy + 1) 3 + (dx + 1)), periodic.
+__device__ __forceinline__ int64_t wg_neighbour(int r, int k, int L)
+{
+    const int x = r % L, y = (r / L) % L, z = r / (L * L);
+    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+    return ((int64_t)wrap(z + dz, L) * L + wrap(y + dy, L)) * L + wrap(x + dx, L);
+}
+
+template <int kCin>
+__global__ void __launch_bounds__(kTcThreads, 1) k_wgrad_tc(const __grid_constant__ WgArgs a)
+{
+    constexpr uint32_t kTileB = kCin * 256;
+    constexpr int kPer = 128 / kCin;                         // offsets per M group
+    constexpr int kGroups = (kOff + 1 + kPer - 1) / kPer;    // 4, or 2 for the first layer
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t base = smem_u32(sm);
+    const uint32_t bars = base + kWgOffBar;
+    auto xfull = [&](int i) { return bars + 8u * (uint32_t)i; };
+    auto xempty = [&](int i) { return bars + 8u * (uint32_t)(kWgX + i); };
+    auto dfull = [&](int i) { return bars + 8u * (uint32_t)(2 * kWgX + i); };
+    auto dempty = [&](int i) { return bars + 8u * (uint32_t)(2 * kWgX + kWgD + i); };
+    const uint32_t done_bar = bars + 8u * (uint32_t)(2 * kWgX + 2 * kWgD);
+    uint32_t* misc = reinterpret_cast<uint32_t*>(sm + kWgOffMisc);   // [0] TMEM base, [1] abort, [2] progress
+    volatile uint32_t* abort_flag = misc + 1;
+    volatile uint32_t* progress = misc + 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        misc[2] = 0;
+        for (int i = 0; i < kWgX; ++i) {
+            mbar_init(xfull(i), 1);
+            mbar_init(xempty(i), 1);
+        }
+        for (int i = 0; i < kWgD; ++i) {
+            mbar_init(dfull(i), 1);
+            mbar_init(dempty(i), 1);
+        }
+        mbar_init(done_bar, 1);
+        misc[1] = 0;
+        fence_mbar_init();
+    }
+    if (warp == kIssuerWarp) tmem_alloc(smem_u32(misc), 64);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = misc[0];
+    const int L = a.L;
+
+    if (warp == kProducerWarp) {
+        uint32_t xs = 0, ds = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < a.n_items && ok; u += gridDim.x) {
+            const int64_t t = u / a.L3;
+            const int r = (int)(u - t * a.L3);
+            {
+                const int g = (int)(ds % kWgD);
+                const uint32_t use = ds / kWgD;
+                int good = 1;
+                if (lane == 0 && use > 0) good = wait_bar(dempty(g), (use - 1) & 1u, abort_flag) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, good, 0)) break;
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(dfull(g), 4096u);
+                    bulk_load(base + kWgOffD + (uint32_t)g * 4096u, a.dt + (t * a.L3 + r) * 4096, 4096u, dfull(g));
+                }
+                ++ds;
+            }
+            for (int grp = 0; grp < kGroups; ++grp) {
+                const int g = (int)(xs % kWgX);
+                const uint32_t use = xs / kWgX;
+                int good = 1;
+                if (lane == 0 && use > 0) good = wait_bar(xempty(g), (use - 1) & 1u, abort_flag) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, good, 0)) {
+                    ok = false;
+                    break;
+                }
+                const int k0 = grp * kPer;
+                const int n_real = min(kPer, kOff + 1 - k0);     // offsets and the ones tile
+                if (lane == 0) mbar_arrive_expect_tx(xfull(g), (uint32_t)n_real * kTileB);
+                __syncwarp();
+                if (lane < n_real) {
+                    const int k = k0 + lane;
+                    const uint8_t* src = k < kOff ? a.xt + (t * a.L3 + wg_neighbour(r, k, L)) * kTileB : a.ones;
+                    bulk_load(base + (uint32_t)g * 32768u + (uint32_t)lane * kTileB, src, kTileB, xfull(g));
+                }
+                ++xs;
+            }
+        }
+        // copies still in flight land before the CTA exits
+        if (lane == 0) {
+            const uint32_t lx = xs < (uint32_t)kWgX ? xs : (uint32_t)kWgX;
+            for (uint32_t g = 0; g < lx; ++g) {
+                const uint32_t q = xs - 1 - ((xs - 1 - g) % kWgX);
+                wait_bar(xfull((int)g), (q / kWgX) & 1u, abort_flag, true);
+            }
+            const uint32_t ld = ds < (uint32_t)kWgD ? ds : (uint32_t)kWgD;
+            for (uint32_t g = 0; g < ld; ++g) {
+                const uint32_t q = ds - 1 - ((ds - 1 - g) % kWgD);
+                wait_bar(dfull((int)g), (q / kWgD) & 1u, abort_flag, true);
+            }
+        }
+        __syncwarp();
+    } else if (warp == kIssuerWarp) {
+        if (lane == 0) {
+            constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) |
+                                        ((uint32_t)(kTileM >> 4) << 24);
+            uint32_t xs = 0, ds = 0;
+            bool ok = true, first = true;
+            for (int64_t u = blockIdx.x; u < a.n_items && ok; u += gridDim.x) {
+                const int gd = (int)(ds % kWgD);
+                if (!wait_bar(dfull(gd), (ds / kWgD) & 1u, abort_flag)) break;
+                tc_fence_after();
+                const uint64_t bdesc = smem_desc(base + kWgOffD + (uint32_t)gd * 4096u, 128u, 2048u);
+                for (int grp = 0; grp < kGroups; ++grp) {
+                    const int g = (int)(xs % kWgX);
+                    if (!wait_bar(xfull(g), (xs / kWgX) & 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t adesc = smem_desc(base + (uint32_t)g * 32768u, 128u, 2048u);
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        // 16 samples per step: two core matrices (256 B) further along K
+                        const uint64_t step = (uint64_t)((kk * 256) >> 4);
+                        if (first && kk == 0)
+                            mma_bf16_overwrite(tmem + (uint32_t)(grp * 16), adesc + step, bdesc + step, kIdesc);
+                        else
+                            mma_bf16_n(tmem + (uint32_t)(grp * 16), adesc + step, bdesc + step, kIdesc);
+                    }
+                    mma_commit(xempty(g));
+                    ++xs;
+                }
+                first = false;
+                mma_commit(dempty(gd));
+                ++ds;
+                *progress = ds;
+            }
+            mma_commit(done_bar);
+            wait_bar(done_bar, 0, abort_flag, true);
+        }
+        __syncwarp();
+    } else if (warp < kEpiWarps) {
+        // every MMA has completed: add the accumulators to the gradients; TMEM lane = M row
+        int got = 1;
+        if (lane == 0) got = wait_bar_progress(done_bar, progress, abort_flag) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        tc_fence_after();
+        if (got && !*abort_flag) {
+            const int row = warp * 32 + lane;
+#pragma unroll
+            for (int grp = 0; grp < kGroups; ++grp) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(grp * 16), v);
+                tmem_wait_ld();
+                const int k = grp * kPer + row / kCin, ci = row % kCin;
+                if (k < kOff && ci < a.cin) {
+#pragma unroll
+                    for (int co = 0; co < 16; ++co)
+                        atomicAdd(&a.gw[(co * a.cin + ci) * kOff + k], __uint_as_float(v[co]));
+                } else if (k == kOff && ci == 0) {
+#pragma unroll
+                    for (int co = 0; co < 16; ++co) atomicAdd(&a.gb[co], __uint_as_float(v[co]));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kIssuerWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 64);
+    }
+}
+
+// Channel-major copy of C-channel tiles (k_wgrad_tc's operands): the element (sample m,
+// channel c) of a tile moves from the tile-major place ([m/8][c/8][8][8] for 16 channels,
+// [m][8] for 8) to [c/8][m/8][8 channels][8 samples].  One block per tile.
+template <int kCh>
+__global__ void __launch_bounds__(256) k_channel_major(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst)
+{
+    constexpr int kN = kCh * 128;
+    __shared__ uint16_t tile[kN];
+    const int64_t t = blockIdx.x;
+    for (int i = threadIdx.x; i < kN / 8; i += blockDim.x)
+        reinterpret_cast<uint4*>(tile)[i] = reinterpret_cast<const uint4*>(src + t * kN)[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < kN; i += blockDim.x) {
+        // destination index i = ((c/8) 16 + m/8) 64 + (c%8) 8 + m%8
+        const int ms = i & 7, cs = (i >> 3) & 7, mg = (i >> 6) & 15, cg = i >> 10;
+        const int m = mg * 8 + ms, c = cg * 8 + cs;
+        const int from = kCh == 16 ? ((m >> 3) * 2 + (c >> 3)) * 64 + (m & 7) * 8 + (c & 7) : m * 8 + c;
+        dst[t * kN + i] = tile[from];
+    }
+}
+
+__global__ void k_fill_ones(uint16_t* __restrict__ p, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0x3F80u;   // BF16 1.0
+}
+
 int64_t tc_padded(int64_t n) { return (n + kTileM - 1) / kTileM * kTileM; }
 size_t r256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -890,6 +1161,8 @@ t3d_status tc_prepare()
         T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<kTcHead, false>, attr, kColSmemBytes));
         T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<kTcHeadTrain, false>, attr, kColSmemBytes));
         T3D_CUDA_CHECK(cudaFuncSetAttribute(k_conv_col<kTcMask, false>, attr, kColSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_wgrad_tc<8>, attr, kWgSmemBytes));
+        T3D_CUDA_CHECK(cudaFuncSetAttribute(k_wgrad_tc<kC>, attr, kWgSmemBytes));
         configured[dev] = true;
     }
     return T3D_OK;
@@ -978,6 +1251,49 @@ t3d_status tc_backward_data(int L, int64_t n_samples, const __nv_bfloat16* wt, c
     a.w = wt;
     a.mask_act = mask_act;
     return launch_conv_col<kTcMask, false>(a, st);
+}
+
+t3d_status tc_fill_ones(uint8_t* tile, cudaStream_t st)
+{
+    k_fill_ones<<<(2048 + 255) / 256, 256, 0, st>>>(reinterpret_cast<uint16_t*>(tile), 2048);
+    T3D_LAUNCH_CHECK("ones tile");
+    return T3D_OK;
+}
+
+t3d_status tc_weight_grad(int L, int64_t n_samples, int x_ch, int cin_kept, const uint8_t* x, const uint8_t* d,
+                          uint8_t* xt, uint8_t* dt, const uint8_t* ones, float* gw, float* gb, cudaStream_t st)
+{
+    T3D_REQUIRE(x_ch == 8 || x_ch == kC, "weight gradient: %d input channels", x_ch);
+    T3D_TRY(tc_prepare());
+    const int64_t L3 = (int64_t)L * L * L, n_items = tc_padded(n_samples) / kTileM * L3;
+    ProfScope prof(T3D_K_CNN, st);
+    if (x_ch == 8)
+        k_channel_major<8><<<(unsigned)n_items, 256, 0, st>>>(reinterpret_cast<const uint16_t*>(x),
+                                                              reinterpret_cast<uint16_t*>(xt));
+    else
+        k_channel_major<kC><<<(unsigned)n_items, 256, 0, st>>>(reinterpret_cast<const uint16_t*>(x),
+                                                               reinterpret_cast<uint16_t*>(xt));
+    k_channel_major<kC><<<(unsigned)n_items, 256, 0, st>>>(reinterpret_cast<const uint16_t*>(d),
+                                                           reinterpret_cast<uint16_t*>(dt));
+    T3D_LAUNCH_CHECK("channel-major tiles");
+    WgArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.L = L;
+    a.L3 = (int)L3;
+    a.n_items = n_items;
+    a.xt = xt;
+    a.dt = dt;
+    a.ones = ones;
+    a.cin = cin_kept;
+    a.gw = gw;
+    a.gb = gb;
+    const int grid = (int)std::min<int64_t>(n_items, sm_count());
+    if (x_ch == 8)
+        k_wgrad_tc<8><<<grid, kTcThreads, kWgSmemBytes, st>>>(a);
+    else
+        k_wgrad_tc<kC><<<grid, kTcThreads, kWgSmemBytes, st>>>(a);
+    T3D_LAUNCH_CHECK("tensor-core weight gradient");
+    return T3D_OK;
 }
 
 t3d_status tc_set_wait_limit(uint64_t ns)
