@@ -47,8 +47,9 @@ def test_cnn_logits_and_corrections_match_reference(L, S):
     assert np.array_equal(download_bits(s, S), sc ^ oracle.syndrome_batch(L, d))
 
 
-def test_cnn_gradient_matches_reference():
-    L, S = 4, 64
+@pytest.mark.parametrize("L,S", [(4, 64), (5, 200), (3, 300)])
+def test_cnn_gradient_matches_reference(L, S):
+    # 200 and 300 samples: two and three 128-sample tiles, the last one partly padding
     n = 3 * L ** 3
     params = ref.random_params(7)
     sp = inp.random_bits(S, n, 0.15, 1)
