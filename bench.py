@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU baseline sample")
     ap.add_argument("--reference-seconds", type=float, default=60.0,
                     help="--impl reference: oracle time over all steps (default 60 s)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="end-to-end steps (default: as many as --steps, at least 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -500,6 +501,8 @@ def cuda_arm(args):
     # one batch) decoded one after the other on the compute stream, each half with its own
     # copy stream, so one half's copies overlap the other half's decoding.
     e2e = None
+    if not args.e2e_steps:
+        args.e2e_steps = max(3, args.steps)
     if not args.no_e2e:
         S0 = min(S, (S // 2 + 63) // 64 * 64)
         parts = [(0, S0), (S0, S - S0)] if S - S0 > 0 else [(0, S)]

@@ -185,7 +185,9 @@ t3d_status toric3d_bp_step(int L, int64_t n_samples, const uint64_t* s, double p
 /*
  * BP hard decision (Sec. 4.1, after Eq. 4): posterior l_v = l0 + sum of the
  * four incoming messages (msg NULL: l_v = l0); every qubit with l_v < 0 is
- * corrected, e ^= d and s ^= H d.  llr_out (nullable) receives l_v as
+ * corrected, e ^= d and s ^= H d, in samples 0 .. n_samples - 1 only (the
+ * unused tail lanes of the last word get no correction).  llr_out (nullable)
+ * receives l_v as
  * float[3L^3][n_samples].  work: >= toric3d_bp_decide_workspace_bytes(L,
  * n_samples) bytes of 32-byte aligned device scratch for the decision words.
  */

@@ -27,3 +27,18 @@ def bp_messages(args):
     L, s_bits, p, q, m_in = args
     m, _ = oracle.bp_batch(L, s_bits[None, :], p, q, True, 1, m_in=None if m_in is None else m_in[None, :])
     return m[0]
+
+
+def run_sample_if_clear(args):
+    """One sample of a one-cycle BP + p-flip run recomputed by the oracle: (i, e bits, mask),
+    or None when one of the sample's first-cycle BP posteriors lies within 1e-4 of zero (a
+    decision FP32 and FP64 may take differently)."""
+    L, p, q, seed, i, iters, kw = args
+    n = 3 * L ** 3
+    e0 = oracle.noise_batch(L, np.zeros((1, n), np.uint8), p, seed, i, 1)
+    s0 = oracle.measure_batch(L, e0, q, seed, i, 1)
+    _, llr = oracle.bp_batch(L, s0, p, q, True, iters)
+    if not (np.abs(llr) > 1e-4).all():
+        return None
+    mask, e = oracle.run_batch(oracle.make_cfg(L, 1, p, q, seed, **kw), i, 1)
+    return i, e[0], int(mask[0])
