@@ -1266,6 +1266,8 @@ t3d_status tc_weight_grad(int L, int64_t n_samples, int x_ch, int cin_kept, cons
     T3D_REQUIRE(x_ch == 8 || x_ch == kC, "weight gradient: %d input channels", x_ch);
     T3D_TRY(tc_prepare());
     const int64_t L3 = (int64_t)L * L * L, n_items = tc_padded(n_samples) / kTileM * L3;
+    T3D_REQUIRE(n_items <= 0x7fffffffLL, "weight gradient: %lld (sample tile, site) pairs exceed one grid",
+                (long long)n_items);
     ProfScope prof(T3D_K_CNN, st);
     if (x_ch == 8)
         k_channel_major<8><<<(unsigned)n_items, 256, 0, st>>>(reinterpret_cast<const uint16_t*>(x),
