@@ -169,7 +169,8 @@ __device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, 
     if (thr == 0) return 0;
     if (thr >= (1ULL << 32)) return ~0ULL;
     uint64_t lt = 0, eq = ~0ULL;
-#pragma unroll 1
+    // unrolled: each block's two threshold bits sit at compile-time positions
+#pragma unroll
     for (uint32_t blk = 0; blk < 16; ++blk) {
         const Words2 w = stream_words(seed, stream, site, cycle, sweep, group, blk);
 #pragma unroll
