@@ -87,7 +87,7 @@ def _declare(L):
     sig = {
         "t3o_philox4x32": (None, [_P, _P, _P]),
         "t3o_prob_to_threshold": (u64, [dbl]),
-        "t3o_uniform32": (u32, [u64, i32, u64, u64, u64, u64]),
+        "t3o_bernoulli_count": (i64, [dbl, u64, i32, u64, u64, u64, u64, i64]),
         "t3o_bernoulli": (i32, [dbl, u64, i32, u64, u64, u64, u64]),
         "t3o_coin": (i32, [u64, u64, i32, u64, u64, u64]),
         "t3o_face_edges": (None, [i32, i64, _P]),
@@ -158,12 +158,13 @@ def prob_to_threshold(p: float) -> int:
     return int(lib().t3o_prob_to_threshold(float(p)))
 
 
-def uniform32(seed, stream, site, cycle, sweep, sample) -> int:
-    return int(lib().t3o_uniform32(seed, stream, site, cycle, sweep, sample))
-
-
 def bernoulli(p, seed, stream, site, cycle, sweep, sample) -> int:
     return int(lib().t3o_bernoulli(float(p), seed, stream, site, cycle, sweep, sample))
+
+
+def bernoulli_count(p, seed, stream, site, cycle, sweep, sample0, n) -> int:
+    """Events among samples [sample0, sample0 + n) of one stream position."""
+    return int(lib().t3o_bernoulli_count(float(p), seed, stream, site, cycle, sweep, sample0, n))
 
 
 def coin(seed, L, edge, cycle, sweep, sample) -> int:

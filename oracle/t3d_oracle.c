@@ -27,9 +27,14 @@
  * seed >> 32), counter = (group mod 2^32, site, cycle, stream<<30 | sweep<<8
  * | block), where group = sample / 64 (sweep < 2^22).  A block gives two
  * 64-bit words: word i is outputs 2(i%2) (low half) and 2(i%2)+1 (high half)
- * of block i/2.  Bernoulli(p) for a sample with lane = sample % 64: U is the
- * 32-bit integer whose bit (31-j) is bit `lane` of word j (j = 0..31); the
- * event happens iff U < P with P = floor(p * 2^32 + 0.5).  The p-flip coin of
+ * of block i/2.  Bernoulli(p) for a sample with lane = sample % 64, with
+ * P = floor(p * 2^32 + 0.5): the event is U < P for a 32-bit uniform U whose
+ * six high bits (bit 31-j = bit `lane` of word j, j = 0..5, blocks 0..2)
+ * decide it whenever they differ from P's six high bits; the lanes of the
+ * group whose six high bits equal P's take U's low 26 bits from one 32-bit
+ * block output each -- the k-th such lane in lane order (k = 0, 1, ...) the
+ * high 26 bits of output k % 4 of block 3 + k/4 -- and their event is
+ * low26(U) < low26(P).  The p-flip coin of
  * the d-edge at site r is bit `lane` of word d of stream 2 keyed by site r
  * (blocks 0 and 1 serve the three edges of a site).
  *
@@ -102,18 +107,30 @@ uint64_t t3o_prob_to_threshold(double p)
     return (uint64_t)floor(p * 4294967296.0 + 0.5);
 }
 
-/* The 32-bit uniform U of one sample, assembled bit by bit as defined above. */
-uint32_t t3o_uniform32(uint64_t seed, int stream, uint64_t site, uint64_t cycle,
-                       uint64_t sweep, uint64_t sample)
+/* The six high bits of U for every lane of a group: bit 5-j of lane l's value is bit l
+ * of stream word j (j = 0..5). */
+static void high6_of_group(uint64_t seed, int stream, uint64_t site, uint64_t cycle, uint64_t sweep,
+                           uint64_t group, uint32_t high6[64])
 {
-    uint64_t group = sample / 64, lane = sample % 64;
-    uint32_t u = 0;
-    for (int j = 0; j < 32; ++j) {
+    for (int l = 0; l < 64; ++l) high6[l] = 0;
+    for (int j = 0; j < 6; ++j) {
         uint64_t w = stream_word(seed, stream, site, cycle, sweep, group, j);
-        uint32_t bit = (uint32_t)((w >> lane) & 1ULL);
-        u |= bit << (31 - j);
+        for (int l = 0; l < 64; ++l) high6[l] |= (uint32_t)((w >> l) & 1ULL) << (5 - j);
     }
-    return u;
+}
+
+/* The 26-bit value a lane whose six high bits tie P's takes as U's low bits: the lane is the
+ * k-th tied lane of its group (k counts the tied lanes below it), and the value is the high 26
+ * bits of output k % 4 of block 3 + k/4 of the stream position. */
+static uint32_t tail26(uint64_t seed, int stream, uint64_t site, uint64_t cycle, uint64_t sweep,
+                       uint64_t group, int k)
+{
+    uint32_t ctr[4] = { (uint32_t)group, (uint32_t)site, (uint32_t)cycle,
+                        ((uint32_t)stream << 30) | ((uint32_t)sweep << 8) | (uint32_t)(3 + k / 4) };
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t out[4];
+    t3o_philox4x32(ctr, key, out);
+    return out[k % 4] >> 6;
 }
 
 int t3o_bernoulli(double p, uint64_t seed, int stream, uint64_t site, uint64_t cycle,
@@ -121,8 +138,25 @@ int t3o_bernoulli(double p, uint64_t seed, int stream, uint64_t site, uint64_t c
 {
     uint64_t thr = t3o_prob_to_threshold(p);
     if (thr == 0) return 0;
-    uint32_t u = t3o_uniform32(seed, stream, site, cycle, sweep, sample);
-    return (uint64_t)u < thr;
+    if (thr >= (1ULL << 32)) return 1;
+    uint64_t group = sample / 64;
+    int lane = (int)(sample % 64);
+    uint32_t high6[64];
+    high6_of_group(seed, stream, site, cycle, sweep, group, high6);
+    uint32_t p_high = (uint32_t)(thr >> 26), p_low = (uint32_t)(thr & ((1u << 26) - 1));
+    if (high6[lane] != p_high) return high6[lane] < p_high;
+    int k = 0;
+    for (int l = 0; l < lane; ++l) k += high6[l] == p_high;
+    return tail26(seed, stream, site, cycle, sweep, group, k) < p_low;
+}
+
+/* The events of samples [sample0, sample0 + n) of one stream position (statistical tests). */
+int64_t t3o_bernoulli_count(double p, uint64_t seed, int stream, uint64_t site, uint64_t cycle,
+                            uint64_t sweep, uint64_t sample0, int64_t n)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i) c += t3o_bernoulli(p, seed, stream, site, cycle, sweep, sample0 + (uint64_t)i);
+    return c;
 }
 
 int t3o_coin(uint64_t seed, uint64_t site, int dir, uint64_t cycle, uint64_t sweep, uint64_t sample)

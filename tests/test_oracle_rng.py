@@ -102,38 +102,81 @@ def _word(seed, stream, site, cycle, sweep, group, i):
     return int(out[j]) | (int(out[j + 1]) << 32)
 
 
-def test_uniform32_bit_assembly_uses_msb_first_words():
-    # U's bit (31-j) is bit `lane` of word j; word j = outputs 2(j%2), 2(j%2)+1 of block j/2
-    seed, stream, site, cycle, sweep = 9 + (3 << 32), 1, 77, 4, 0
-    for sample in [64 * 3 + 0, 64 * 3 + 17, 64 * 3 + 63]:
-        group, lane = sample // 64, sample % 64
-        u = 0
-        for j in range(32):
-            u |= ((_word(seed, stream, site, cycle, sweep, group, j) >> lane) & 1) << (31 - j)
-        assert oracle.uniform32(seed, stream, site, cycle, sweep, sample) == u
+def _high6(seed, stream, site, cycle, sweep, group):
+    """The six high bits of U for the 64 lanes of a group, from stream words 0..5 (bit 5-j of
+    lane l is bit l of word j)."""
+    words = [_word(seed, stream, site, cycle, sweep, group, j) for j in range(6)]
+    return [sum(((words[j] >> l) & 1) << (5 - j) for j in range(6)) for l in range(64)]
 
 
-@pytest.mark.parametrize("p,expect", [(0.0, 0), (1.0, 1 << 32), (0.5, 1 << 31),
-                                      (0.25, 1 << 30), (2.0 ** -33, 1), (2.0 ** -34, 0)])
-def test_threshold_quantisation(p, expect):
-    assert oracle.prob_to_threshold(p) == expect
+@pytest.mark.parametrize("m", [1, 5, 32, 63])
+def test_bernoulli_is_the_six_bit_comparison_when_p_is_a_multiple_of_one_64th(m):
+    # P = m 2^26 has zero low bits, so U < P iff U's six high bits are below m
+    seed, stream, site, cycle = 7 + (1 << 33), 1, 913, 6
+    for group in (0, 5, 1000):
+        h = _high6(seed, stream, site, cycle, 0, group)
+        got = [oracle.bernoulli(m / 64, seed, stream, site, cycle, 0, 64 * group + l) for l in range(64)]
+        assert got == [int(x < m) for x in h]
 
 
-def test_bernoulli_edges_and_frequency():
+def test_bernoulli_tied_lanes_take_block_outputs_in_lane_order():
+    # groups with at least five lanes whose six high bits tie P's (block 4 serves the fifth);
+    # three thresholds with the same high bits and low parts 1/4, 1/2, 3/4 read three bits of
+    # each tied lane's tail
+    seed, stream, site, cycle, ph = 3, 0, 41, 2, 19
+    ps = [(ph + f) / 64 for f in (0.25, 0.5, 0.75)]
+    found = 0
+    for group in range(40000):
+        h = _high6(seed, stream, site, cycle, 0, group)
+        tied = [l for l in range(64) if h[l] == ph]
+        if len(tied) < 5:
+            continue
+        found += 1
+        for p in ps:
+            P = oracle.prob_to_threshold(p)
+            assert P >> 26 == ph
+            pl = P & ((1 << 26) - 1)
+            for k, lane in enumerate(tied):
+                out = oracle.philox4x32([group, site, cycle, (stream << 30) | (3 + k // 4)], [seed, 0])
+                want = int((int(out[k % 4]) >> 6) < pl)
+                assert oracle.bernoulli(p, seed, stream, site, cycle, 0, 64 * group + lane) == want, (group, k)
+            for lane in set(range(64)) - set(tied):
+                assert oracle.bernoulli(p, seed, stream, site, cycle, 0, 64 * group + lane) == int(h[lane] < ph)
+        if found == 3:
+            break
+    assert found == 3
+
+
+@pytest.mark.parametrize("p", [0.004, 0.04, 0.3, 0.5 + 2.0 ** -30])
+def test_bernoulli_frequency(p):
+    # p = 0.004 < 1/64: every event comes from a tied lane's 26-bit tail
+    n = 64 * 2000
+    hits = sum(oracle.bernoulli_count(p, 11, 0, site, 3, 0, 0, n) for site in range(4))
+    N, q = 4 * n, oracle.prob_to_threshold(p) / 2 ** 32
+    assert abs(hits - N * q) < 5 * (N * q * (1 - q)) ** 0.5
+
+
+def test_bernoulli_lanes_of_a_word_are_independent():
+    # words with two or more events follow Binomial(64, p); tied lanes that shared a tail
+    # value would cluster their events (about 2.5x as many such words at p = 0.004)
+    p, n = 0.004, 20000
+    q = oracle.prob_to_threshold(p) / 2 ** 32
+    multi = sum(oracle.bernoulli_count(p, 5, 1, 77, 9, 0, 64 * g, 64) >= 2 for g in range(n))
+    f = 1 - (1 - q) ** 64 - 64 * q * (1 - q) ** 63
+    assert abs(multi - n * f) < 5 * (n * f * (1 - f)) ** 0.5
+
+
+def test_bernoulli_is_monotone_in_p():
+    # U < P1 implies U < P2 for P1 <= P2, the tied lanes' tails included
+    ps = [0.001, 0.004, 0.0156, 0.0157, 0.04, 0.0401, 0.3, 0.7]
+    for sample in range(0, 64 * 40, 3):
+        ev = [oracle.bernoulli(p, 21, 0, 300, 4, 0, sample) for p in ps]
+        assert ev == sorted(ev), sample
+
+
+def test_bernoulli_edges():
     assert all(oracle.bernoulli(0.0, 1, 0, s, 1, 0, k) == 0 for s in range(5) for k in range(70))
     assert all(oracle.bernoulli(1.0, 1, 0, s, 1, 0, k) == 1 for s in range(5) for k in range(70))
-    n, p = 20000, 0.04
-    hits = sum(oracle.bernoulli(p, 3, 0, i % 997, 1 + i // 997, 0, i) for i in range(n))
-    sd = (n * p * (1 - p)) ** 0.5
-    assert abs(hits - n * p) < 5 * sd
-
-
-def test_bernoulli_is_u_less_than_threshold():
-    seed = 17
-    for sample in range(0, 300, 7):
-        for p in (0.01, 0.04, 0.3):
-            u = oracle.uniform32(seed, 0, 5, 2, 0, sample)
-            assert oracle.bernoulli(p, seed, 0, 5, 2, 0, sample) == int(u < oracle.prob_to_threshold(p))
 
 
 def test_coin_is_bit_of_the_sites_words_and_fair():
@@ -149,7 +192,7 @@ def test_coin_is_bit_of_the_sites_words_and_fair():
 
 
 def test_streams_are_distinct():
-    a = [oracle.uniform32(1, 0, 3, 1, 0, k) for k in range(64)]
-    b = [oracle.uniform32(1, 1, 3, 1, 0, k) for k in range(64)]
-    c = [oracle.uniform32(1, 0, 3, 2, 0, k) for k in range(64)]
+    a = [oracle.bernoulli(0.5, 1, 0, 3, 1, 0, k) for k in range(64)]
+    b = [oracle.bernoulli(0.5, 1, 1, 3, 1, 0, k) for k in range(64)]
+    c = [oracle.bernoulli(0.5, 1, 0, 3, 2, 0, k) for k in range(64)]
     assert a != b and a != c
