@@ -220,4 +220,15 @@ __device__ __forceinline__ uint64_t exactly_two(uint64_t a, uint64_t b, uint64_t
     return (a & b & ~(c | d)) | (c & d & ~(a | b)) | ((a ^ b) & (c ^ d));
 }
 
+// XOR v into a bit-sliced word that only this thread updates during the launch, as a
+// reduction the memory system carries out (the result is not returned): the thread neither
+// loads the word nor waits for it, and a word with no flipped lane (v = 0) is not touched,
+// so after the first applications of a cycle, where few words change, most of the
+// word array is neither read nor written.
+__device__ __forceinline__ void xor_into(uint64_t* w, uint64_t v)
+{
+    static_assert(sizeof(unsigned long long) == sizeof(uint64_t), "64-bit words");
+    if (v) atomicXor(reinterpret_cast<unsigned long long*>(w), (unsigned long long)v);
+}
+
 }  // namespace t3d
