@@ -34,9 +34,12 @@
  * and counter (group mod 2^32, site, cycle, stream<<30 | sweep<<8 | block),
  * group = sample / 64; sweep indices stay below 2^22.  Word i (64 bits) of a
  * stream position is outputs 0 | 1<<32 (i even) or 2 | 3<<32 (i odd) of block
- * i/2.  Bernoulli(p) for a sample in lane j compares the 32-bit U whose bit
- * 31-i is bit j of word i with P = floor(p*2^32 + 1/2): the event happens iff
- * U < P.  Streams: 0 qubit flips (site = edge), 1 measurement flips (site =
+ * i/2.  Bernoulli(p) for a sample in lane j is U < P, P = floor(p*2^32 + 1/2),
+ * for a 32-bit uniform U: its six high bits (bit 31-i = bit j of word i,
+ * i = 0..5) decide the lanes whose six high bits differ from P's; the k-th
+ * lane of the 64 (in lane order) whose six high bits equal P's takes its
+ * low 26 bits from the high 26 bits of output k%4 of block 3 + k/4.
+ * Streams: 0 qubit flips (site = edge), 1 measurement flips (site =
  * face), 2 p-flip coins (site = lattice site r: the coin of r's d-edge is bit
  * j of word d).  `sample0` (a multiple of 64) is the global index of a
  * batch's first sample, so disjoint sample ranges on different GPUs or in

@@ -161,10 +161,14 @@ __device__ __forceinline__ Words2 stream_words(uint64_t seed, uint32_t stream, u
     return r;
 }
 
-// 64 Bernoulli(P / 2^32) bits, one per sample of word `group`: lane j is set
-// iff U_j < P, with U_j the 32-bit integer whose bit 31-i is bit j of stream
-// word i.  Evaluated as a bit-sliced most-significant-first comparison that
-// stops once every lane is decided.
+// 64 Bernoulli(P / 2^32) bits, one per sample of word `group` (P = thr): lane j is set iff
+// U_j < P for a 32-bit uniform U_j.  The six high bits of every lane (bit 31-i of U_j = bit j
+// of stream word i, i = 0..5, blocks 0..2) are compared with P's, most significant first and
+// bit-sliced over the 64 lanes; that decides every lane but the ties (six high bits equal to
+// P's: one lane in 64 on average).  The k-th tied lane in lane order takes U's low 26 bits
+// from the high 26 bits of output k % 4 of block 3 + k/4.  A word costs three blocks plus
+// one per four ties -- about four for a warp of words, where comparing all 32 bits
+// bit-sliced until every lane was decided cost a warp about six (the slowest of its words).
 __device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, uint32_t stream,
                                                    uint64_t site, uint32_t cycle, uint32_t sweep,
                                                    uint64_t group)
@@ -174,7 +178,7 @@ __device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, 
     uint64_t lt = 0, eq = ~0ULL;
     // unrolled: each block's two threshold bits sit at compile-time positions
 #pragma unroll
-    for (uint32_t blk = 0; blk < 16; ++blk) {
+    for (uint32_t blk = 0; blk < 3; ++blk) {
         const Words2 w = stream_words(seed, stream, site, cycle, sweep, group, blk);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
@@ -186,7 +190,17 @@ __device__ __forceinline__ uint64_t bernoulli_word(uint64_t thr, uint64_t seed, 
                 eq &= ~w.w[i];
             }
         }
-        if (eq == 0) break;
+    }
+    const uint32_t low = (uint32_t)thr & ((1u << 26) - 1);
+    for (uint32_t blk = 3; eq != 0; ++blk) {   // at most 16 blocks: four ties each
+        const U32x4 o = philox4x32_10((uint32_t)group, (uint32_t)site, cycle, (stream << 30) | (sweep << 8) | blk,
+                                      (uint32_t)seed, (uint32_t)(seed >> 32));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t b = eq & (0 - eq);   // the lowest tied lane left (0 once none is)
+            if ((o.v[i] >> 6) < low) lt |= b;
+            eq ^= b;
+        }
     }
     return lt;
 }
