@@ -52,18 +52,33 @@ int64_t tile_blocks(int64_t n_sites, int64_t W, int tx)
     return ((n_sites + ty - 1) / ty) * ((W + tx - 1) / tx);
 }
 
+// The same for the kernels that split a block index with 32-bit arithmetic
+// (tile_site_word): T3D_EINVAL if the item needs 2^32 blocks or more (a state
+// array of at least 2^32 x 256 words, far beyond device memory).
+t3d_status tile_blocks_checked(const ItemDesc& d, int64_t n_sites, int64_t W, int tx, int64_t* blocks)
+{
+    *blocks = tile_blocks(n_sites, W, tx);
+    T3D_REQUIRE(n_sites < (1LL << 31) && *blocks < (1LL << 32),
+                "lattice L = %d with %lld words needs too many thread blocks", d.lat.L, (long long)W);
+    return T3D_OK;
+}
+
 // Local block lb of an item -> this thread's (site, word); sites vary fastest
-// across blocks so neighbouring sites run together.
-__device__ __forceinline__ bool tile_site_word(const ItemDesc& d, int64_t lb, int64_t n_sites,
+// across blocks so neighbouring sites run together.  tx and ty = kThreads / tx
+// are powers of two (shifts), and one 32-bit division splits lb: every launcher
+// checks that an item's blocks stay below 2^32 (tile_blocks_checked).  The
+// 64-bit divisions this replaces were a quarter of the noise kernel's
+// instructions.
+__device__ __forceinline__ bool tile_site_word(const ItemDesc& d, int64_t lb, int n_sites,
                                                int& site, int64_t& w)
 {
-    const int tx = d.tx, ty = kThreads / tx;
-    const int64_t site_tiles = (n_sites + ty - 1) / ty;
-    const int64_t word_tile = lb / site_tiles;
-    const int64_t site_tile = lb - word_tile * site_tiles;
+    const int tx = d.tx, lx = __ffs(tx) - 1, ly = __ffs(kThreads) - 1 - lx;
+    const uint32_t site_tiles = ((uint32_t)n_sites + (1u << ly) - 1) >> ly;
+    const uint32_t word_tile = (uint32_t)lb / site_tiles;
+    const uint32_t site_tile = (uint32_t)lb - word_tile * site_tiles;
     const int t = threadIdx.x;
-    w = word_tile * tx + (t & (tx - 1));
-    site = (int)(site_tile * ty + t / tx);
+    w = (int64_t)word_tile * tx + (t & (tx - 1));
+    site = (int)(site_tile << ly) + (t >> lx);
     return w < (d.nw ? d.nw : d.W) && site < n_sites;
 }
 
@@ -75,7 +90,7 @@ k_noise(const __grid_constant__ ItemTable tab, uint64_t thr, uint64_t seed, uint
     for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
         int v;
         int64_t w;
-        if (!tile_site_word(d, lb, 3LL * d.lat.L3, v, w)) return;
+        if (!tile_site_word(d, lb, 3 * d.lat.L3, v, w)) return;
         const uint64_t flips =
             bernoulli_word(thr, seed, kStreamQubit, (uint64_t)v, cycle, 0, d.group0 + w);
         if (flips) d.e[(int64_t)v * d.W + w] ^= flips;
@@ -90,8 +105,8 @@ k_syndrome(const __grid_constant__ ItemTable tab, uint64_t thr, uint64_t seed, u
         const Lattice lat = d.lat;
         int f;
         int64_t w;
-        if (!tile_site_word(d, lb, 3LL * lat.L3, f, w)) return;
-        const int n = f / lat.L3, site = f - n * lat.L3;
+        if (!tile_site_word(d, lb, 3 * lat.L3, f, w)) return;
+        const int n = (f >= lat.L3) + (f >= 2 * lat.L3), site = f - n * lat.L3;
         const FaceEdges fe = face_edges(lat, n, site_coord(lat, site));
         uint64_t acc = 0;
 #pragma unroll
@@ -674,7 +689,7 @@ t3d_status launch_noise(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t cy
         ItemDesc& d = tab.it[i];
         const int64_t nw = d.nw ? d.nw : d.W;
         d.tx = row_words(nw);
-        d.blocks = tile_blocks(3LL * d.lat.L3, nw, d.tx);
+        T3D_TRY(tile_blocks_checked(d, 3LL * d.lat.L3, nw, d.tx, &d.blocks));
     }
     finish_table(tab);
     ProfScope prof(T3D_K_NOISE, st);
@@ -690,7 +705,7 @@ t3d_status launch_syndrome(ItemTable& tab, uint64_t thr, uint64_t seed, uint32_t
         ItemDesc& d = tab.it[i];
         const int64_t nw = d.nw ? d.nw : d.W;
         d.tx = row_words(nw);
-        d.blocks = tile_blocks(3LL * d.lat.L3, nw, d.tx);
+        T3D_TRY(tile_blocks_checked(d, 3LL * d.lat.L3, nw, d.tx, &d.blocks));
     }
     finish_table(tab);
     ProfScope prof(T3D_K_SYNDROME, st);
@@ -708,7 +723,7 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
         ItemDesc& d = tab.it[i];
         const int64_t nw = d.nw ? d.nw : d.W;
         d.tx = row_words(nw);
-        d.blocks = tile_blocks(d.lat.L3, nw, d.tx);
+        T3D_TRY(tile_blocks_checked(d, d.lat.L3, nw, d.tx, &d.blocks));
         d.live_wpu = d.tx;
         d.live_bpu = tile_blocks(d.lat.L3, d.tx, d.tx);   // site tiles of one word row
     }
