@@ -275,10 +275,16 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
         const int zm = z == 0 ? L - 1 : z - 1, zp = z + 1 == L ? 0 : z + 1;
         const int xm = x == 0 ? L - 1 : x - 1, xp = x + 1 == L ? 0 : x + 1;
         const int me = x * Wt + wl;
-        // this thread's word of face n at (x, yy, zz)
-        auto gword = [&](const uint64_t* base, int n, int yy, int zz) {
-            const int yw = (yy + L) % L;
-            return base[(int64_t)n * L3W + ((int64_t)(zz * L + yw) * L + x) * W + w];
+        // element offsets: a y-row of one face-plane is L W words, a z-plane L^2 W; this
+        // thread's column (x, w) of plane zz starts at zz L^2 W + x W + w, and row yy (one
+        // periodic wrap at most: -1 <= yy <= L) adds yy L W
+        const int64_t rowW = (int64_t)L * W, planeW = (int64_t)L * rowW, col = (int64_t)x * W + w;
+        const int64_t cz = (int64_t)z * planeW + col, czp = (int64_t)zp * planeW + col,
+                      czm = (int64_t)zm * planeW + col;
+        auto row = [&](int yy) { return (int64_t)(yy < 0 ? yy + L : (yy >= L ? yy - L : yy)) * rowW; };
+        // this thread's word of face n at (x, yy, zz), given the plane's column offset
+        auto gword = [&](const uint64_t* base, int n, int yy, int64_t cplane) {
+            return base[(int64_t)n * L3W + cplane + row(yy)];
         };
         auto put = [&](int slot, uint64_t v) { sm[slot * kTileWords + me] = v; };
         auto P0 = [&](int yy, int n, int xx) { return sm[(ring3(yy) * 3 + n) * kTileWords + xx * Wt + wl]; };
@@ -291,11 +297,11 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
             if (!act) return;
 #pragma unroll
             for (int n = 0; n < 3; ++n) {
-                nx[n] = gword(d.s, n, yy + 1, z);
-                nx[3 + n] = gword(d.s, n, yy, zp);
+                nx[n] = gword(d.s, n, yy + 1, cz);
+                nx[3 + n] = gword(d.s, n, yy, czp);
             }
-            nx[6] = gword(d.s, 0, yy + 1, zm);
-            nx[7] = gword(d.s, 1, yy + 1, zm);
+            nx[6] = gword(d.s, 0, yy + 1, czm);
+            nx[7] = gword(d.s, 1, yy + 1, czm);
         };
         auto stash = [&](int yy) {
             if (!act) return;
@@ -311,12 +317,12 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
         if (act) {
 #pragma unroll
             for (int n = 0; n < 3; ++n) {
-                put(ring3(-1) * 3 + n, gword(d.s, n, -1, z));
-                put(ring3(0) * 3 + n, gword(d.s, n, 0, z));
-                put(13 + ring2(-1) * 3 + n, gword(d.s, n, -1, zp));
+                put(ring3(-1) * 3 + n, gword(d.s, n, -1, cz));
+                put(ring3(0) * 3 + n, gword(d.s, n, 0, cz));
+                put(13 + ring2(-1) * 3 + n, gword(d.s, n, -1, czp));
             }
-            put(9 + ring2(0) * 2 + 0, gword(d.s, 0, 0, zm));
-            put(9 + ring2(0) * 2 + 1, gword(d.s, 1, 0, zm));
+            put(9 + ring2(0) * 2 + 0, gword(d.s, 0, 0, czm));
+            put(9 + ring2(0) * 2 + 1, gword(d.s, 1, 0, czm));
         }
         fetch(0);
         for (int y = 0; y < L; ++y) {
@@ -325,7 +331,7 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
             if (y + 1 < L) fetch(y + 1);   // in flight while this step computes
             if (act) {
                 const uint64_t s0 = P0(y, 0, x), s1 = P0(y, 1, x), s2 = P0(y, 2, x);
-                const int64_t own = ((int64_t)(z * L + y) * L + x) * W + w;
+                const int64_t own = cz + (int64_t)y * rowW;
                 uint64_t* __restrict__ q0 = d.tmp + own;
                 {
                     const uint64_t q[9][4] = {
