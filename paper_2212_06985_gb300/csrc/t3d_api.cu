@@ -55,11 +55,19 @@ struct GridEntry {
     const void* kernel;
     int threads;
     int device;
+    size_t smem;
     int blocks_per_sm;
+};
+
+struct SmemEntry {
+    const void* kernel;
+    int device;
+    size_t bytes;
 };
 
 std::mutex g_grid_mutex;
 std::vector<GridEntry> g_grids;
+std::vector<SmemEntry> g_smem;
 int g_sms[64] = {0};
 int g_tuned[T3D_K_COUNT] = {0};
 
@@ -77,7 +85,20 @@ void set_tuned_blocks_per_sm(int kind, int blocks_per_sm)
     if (kind >= 0 && kind < T3D_K_COUNT) g_tuned[kind] = blocks_per_sm > 0 ? blocks_per_sm : 0;
 }
 
-unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks, bool device_bound)
+t3d_status allow_dynamic_smem(const void* kernel, size_t bytes)
+{
+    int dev = 0;
+    T3D_CUDA_CHECK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_grid_mutex);
+    for (const auto& e : g_smem)
+        if (e.kernel == kernel && e.device == dev && e.bytes >= bytes) return T3D_OK;
+    T3D_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    g_smem.push_back(SmemEntry{kernel, dev, bytes});
+    return T3D_OK;
+}
+
+unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks, bool device_bound,
+                         size_t dynamic_smem)
 {
     const int64_t max_grid = 0x7fffffffLL;
     if (blocks < 1) return 1;
@@ -97,12 +118,13 @@ unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t bloc
     }
     int per_sm = 0;
     for (const auto& g : g_grids)
-        if (g.kernel == kernel && g.threads == threads && g.device == dev) per_sm = g.blocks_per_sm;
+        if (g.kernel == kernel && g.threads == threads && g.device == dev && g.smem == dynamic_smem)
+            per_sm = g.blocks_per_sm;
     if (per_sm == 0) {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n <= 0)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, dynamic_smem) != cudaSuccess || n <= 0)
             n = 1;
-        g_grids.push_back(GridEntry{kernel, threads, dev, n});
+        g_grids.push_back(GridEntry{kernel, threads, dev, dynamic_smem, n});
         per_sm = n;
     }
     per_sm = std::min(per_sm, cap);

@@ -250,17 +250,29 @@ k_flip(const __grid_constant__ ItemTable tab)
 // flips go to e as XOR reductions, only where an edge flips, so after a cycle's
 // first application nearly all of e is neither read nor written (one
 // application alone 1.14 -> 0.94 ms at L = 32, 10^5 samples, against
-// prefetching e with the face-lines); 64 registers, four blocks per SM.
-constexpr int kTileWords = 256;                 // L x Wt <= 256 words per face-line
+// prefetching e with the face-lines).  A block has L x Wt threads (the launch
+// takes the largest tile of the batch).  When every lattice of the batch has
+// L >= 32 a tile may have up to 1024 threads, so that Wt = 32 at L = 32 and a
+// warp reads one 256-byte run of a row: a copy with this kernel's row pattern
+// moved 2.95 TB/s with 64-byte runs (4 rows per warp, Wt = 8) and 4.97 TB/s
+// with 256-byte runs, and one application at L = 32, 10^5 samples took
+// 0.89 ms (0.91 with Wt = 8; inside the FFPFF cycle 0.71 of the HBM peak
+// against 0.57).  Smaller lattices keep tiles of at most 256 threads (at L = 16
+// and 24 the 512- and 768-thread tiles, fewer blocks per SM, measured 0.121
+// and 0.380 ms against 0.104 and 0.368).  64 registers; the rings are dynamic
+// shared memory, kTileSlots face-lines of blockDim.x words.
+constexpr int kFlipThreads = 1024;              // largest tile: L x Wt threads, all L >= 32
+constexpr int kFlipThreadsSmall = 256;          // largest tile when a lattice has L < 32
 constexpr int kTileSlots = 9 + 4 + 6;           // plane z: 3 lines x 3 faces; z-1: 2 x 2; z+1: 2 x 3
 
 __device__ __forceinline__ int ring3(int y) { return (y + 3) % 3; }
 __device__ __forceinline__ int ring2(int y) { return (y + 2) & 1; }
 
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kFlipThreads, 1)
 k_flip_tiled(const __grid_constant__ ItemTable tab)
 {
-    __shared__ uint64_t sm[kTileSlots * kTileWords];
+    extern __shared__ uint64_t sm[];   // kTileSlots face-lines of tw words
+    const int tw = blockDim.x;
     for_each_item_block(tab, [&](const ItemDesc& d, int64_t lb) {
         if (!stop_run(d, lb)) return;   // the item's syndrome has cleared (uniform over the launch)
         __syncthreads();   // the previous block's last step may still read the rings
@@ -286,10 +298,10 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
         auto gword = [&](const uint64_t* base, int n, int yy, int64_t cplane) {
             return base[(int64_t)n * L3W + cplane + row(yy)];
         };
-        auto put = [&](int slot, uint64_t v) { sm[slot * kTileWords + me] = v; };
-        auto P0 = [&](int yy, int n, int xx) { return sm[(ring3(yy) * 3 + n) * kTileWords + xx * Wt + wl]; };
-        auto Pm = [&](int yy, int n, int xx) { return sm[(9 + ring2(yy) * 2 + n) * kTileWords + xx * Wt + wl]; };
-        auto Pp = [&](int yy, int n, int xx) { return sm[(13 + ring2(yy) * 3 + n) * kTileWords + xx * Wt + wl]; };
+        auto put = [&](int slot, uint64_t v) { sm[slot * tw + me] = v; };
+        auto P0 = [&](int yy, int n, int xx) { return sm[(ring3(yy) * 3 + n) * tw + xx * Wt + wl]; };
+        auto Pm = [&](int yy, int n, int xx) { return sm[(9 + ring2(yy) * 2 + n) * tw + xx * Wt + wl]; };
+        auto Pp = [&](int yy, int n, int xx) { return sm[(13 + ring2(yy) * 3 + n) * tw + xx * Wt + wl]; };
         // the eight face-line words entering at step yy (plane z at yy+1, plane z+1 at yy,
         // plane z-1 at yy+1 faces 0, 1)
         uint64_t nx[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -366,12 +378,12 @@ k_flip_tiled(const __grid_constant__ ItemTable tab)
     });
 }
 
-// Words per tile row of k_flip_tiled: L x Wt <= 256, Wt a power of two <= 32 and
-// no wider than the batch.
-int tiled_words(int L, int64_t nw)
+// Words per tile row of k_flip_tiled: L x Wt <= max_threads, Wt a power of two <= 32
+// and no wider than the batch.
+int tiled_words(int L, int64_t nw, int max_threads)
 {
     int wt = 32;
-    while (wt > 1 && (L * wt > kTileWords || wt / 2 >= nw)) wt /= 2;
+    while (wt > 1 && (L * wt > max_threads || wt / 2 >= nw)) wt /= 2;
     return wt;
 }
 
@@ -735,20 +747,28 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
     }
     finish_table(tab);
     // the shared-memory flip when every face-line of the batch fits a tile row of at
-    // least 8 words (L <= 32); with 4-word rows (L = 40 .. 64) it measured slower than
-    // k_flip (L = 48: 3.18 vs 2.67 ms, L = 64: 3.49 vs 1.57 ms; L = 32: 1.12 vs 1.32 ms)
+    // least 16 words (1024-thread tiles: all L >= 32, so L <= 64) or 8 words (256-thread
+    // tiles: L <= 32); the block takes the batch's largest tile.  Above that k_flip
+    // (L = 48: 1.78 ms tiled against 1.82 untiled, L = 64: 1.05 against 1.08).
+    bool wide = true;
+    for (int i = 0; i < tab.n; ++i) wide = wide && tab.it[i].lat.L >= 32;
+    const int max_threads = wide ? kFlipThreads : kFlipThreadsSmall;
     bool tiled = true;
+    int tile_threads = 32;
     ItemTable tt = tab;
     for (int i = 0; i < tt.n; ++i) {
         ItemDesc& d = tt.it[i];
         const int64_t nw = d.nw ? d.nw : d.W;
-        tiled = tiled && d.lat.L <= kTileWords / 8;
-        d.tx = tiled_words(d.lat.L, nw);
+        tiled = tiled && d.lat.L * (wide ? 16 : 8) <= max_threads;
+        d.tx = tiled_words(d.lat.L, nw, max_threads);
         d.blocks = (int64_t)d.lat.L * ((nw + d.tx - 1) / d.tx);
         d.live_wpu = d.tx;
         d.live_bpu = d.lat.L;   // one z-plane per block, word tiles outermost
+        tile_threads = std::max(tile_threads, (d.lat.L * d.tx + 31) / 32 * 32);
     }
     finish_table(tt);
+    const size_t tile_smem = (size_t)kTileSlots * tile_threads * sizeof(uint64_t);
+    if (tiled) T3D_TRY(allow_dynamic_smem((const void*)k_flip_tiled, tile_smem));
     ItemTable t = tab;  // flip: s and tmp swap roles; p-flip: tmp holds the flip words, s updated in place
     int swaps = 0;
     for (int k = 0; k < n_apply; ++k) {
@@ -765,8 +785,9 @@ t3d_status launch_sweeps(ItemTable& tab, const char* schedule, int slen, int n_a
             T3D_LAUNCH_CHECK("p-flip syndrome update");
         } else {
             if (tiled) {
-                k_flip_tiled<<<persistent_grid((const void*)k_flip_tiled, kThreads, T3D_K_FLIP, tt.prefix[tt.n], has_live(tt)),
-                               kThreads, 0, st>>>(tt);
+                k_flip_tiled<<<persistent_grid((const void*)k_flip_tiled, tile_threads, T3D_K_FLIP, tt.prefix[tt.n],
+                                               has_live(tt), tile_smem),
+                               tile_threads, tile_smem, st>>>(tt);
             } else {
                 k_flip<<<persistent_grid((const void*)k_flip, kThreads, T3D_K_FLIP, t.prefix[t.n], has_live(t)), kThreads, 0,
                          st>>>(t);

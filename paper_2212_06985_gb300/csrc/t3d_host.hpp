@@ -93,7 +93,10 @@ t3d_status check_words(const void* p, const char* name);
 // SMs x min(c, resident blocks) that walks the units.
 // device_bound: the launch's work is bounded by a device-side count (ItemDesc::live); the
 // grid is then at most the resident blocks even when untuned.
-unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks, bool device_bound = false);
+unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks, bool device_bound = false,
+                         size_t dynamic_smem = 0);
+// Raise a kernel's dynamic shared-memory limit on the current device to at least `bytes`.
+t3d_status allow_dynamic_smem(const void* kernel, size_t bytes);
 
 // Launch tuning chosen by the autotuner (0 = use the occupancy limit).
 int tuned_blocks_per_sm(int kind);
