@@ -42,6 +42,12 @@ VALUE_IS = "BP+p-flip; learned_pflip.value = learned+p-flip, learned_pflip.vs_bp
 # proportion to the samples a launch covers, so it scales to full launches).
 # Set to None when the kernel changes until it is captured again.
 BP_STEP_TRAFFIC = {"first_iteration": 15.69, "full_iteration": 31.90}
+# The same for k_flip_tiled inside the FFPFF cycle at p = q = 4% (L = 32, 8192 samples, the
+# four flip applications of one cycle: 322.4 MB of DRAM traffic each on average, per
+# qubit-sample 0.400 B against the dense 0.5 B: e is touched only where a word has a flipped
+# lane, so the figure depends on the noise rates).  None when the kernel changes.
+FLIP_TRAFFIC_P = 0.04
+FLIP_TRAFFIC = 322.4e6 / (98304 * 8192)
 UNIT = "qubit-cycles/s"
 
 
@@ -360,6 +366,8 @@ def sweep_roofline(prof, w, qubits, S, steps, ms, hbm_peak, peak_source, clk):
            "kernels_hbm_frac": {k: SWEEP_BYTES[k] * qubits * S * steps * per_step[k] / (v[0] / 1e3) / 1e9 / hbm_peak
                                 for k, v in kinds.items()},
            "traffic": None, "peak_source": peak_source}
+    if (dom == "flip" and FLIP_TRAFFIC and abs(w.p - FLIP_TRAFFIC_P) < 1e-12 and abs(w.q - FLIP_TRAFFIC_P) < 1e-12):
+        out["traffic"] = FLIP_TRAFFIC * qubits * S          # bytes per launch (one application)
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     units = {"noise": qubits, "syndrome": qubits, "pflip": qubits // 3}   # edges, faces, sites
     issue_peak = 152 * 4 * sm_mhz * 1e6                  # warp instructions per second
