@@ -337,10 +337,10 @@ SWEEP_BYTES = {"noise": 0.25, "syndrome": 0.25, "flip": 0.5, "pflip": 0.875}
 # Warp instructions per 64-sample word of each qubit (noise), check (syndrome)
 # or site (the decision pass of one p-flip application) at p = q = 4%, from one
 # ncu capture of the current kernels (smsp__inst_executed.sum / (units x words),
-# L = 32, 8192 samples: 157.0 M, 199.9 M and 51.8 M instructions).  The Philox
+# L = 32, 8192 samples: 157.0 M, 189.7 M and 51.8 M instructions).  The Philox
 # arithmetic binds these kernels on the instruction issue rate.
 SWEEP_INST_P = 0.04
-SWEEP_INST = {"noise": 157.0e6 / (98304 * 128), "syndrome": 199.9e6 / (98304 * 128), "pflip": 51.8e6 / (32768 * 128)}
+SWEEP_INST = {"noise": 157.0e6 / (98304 * 128), "syndrome": 189.7e6 / (98304 * 128), "pflip": 51.8e6 / (32768 * 128)}
 # The p-flip syndrome pass reads the flip words and updates s in place (0.375 B).
 PFLIP_APPLY_BYTES = 0.375
 

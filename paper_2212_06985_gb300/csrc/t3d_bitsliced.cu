@@ -107,10 +107,18 @@ k_syndrome(const __grid_constant__ ItemTable tab, uint64_t thr, uint64_t seed, u
         int64_t w;
         if (!tile_site_word(d, lb, 3 * lat.L3, f, w)) return;
         const int n = (f >= lat.L3) + (f >= 2 * lat.L3), site = f - n * lat.L3;
-        const FaceEdges fe = face_edges(lat, n, site_coord(lat, site));
-        uint64_t acc = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc ^= d.e[((int64_t)fe.dir[j] * lat.L3 + fe.site[j]) * d.W + w];
+        // face (n, r) spans the axes a < b other than n; its edges are the a-edges at r and
+        // r + e_b and the b-edges at r and r + e_a (periodic site deltas by selects, no
+        // per-thread arrays)
+        const Coord r = site_coord(lat, site);
+        const int L = lat.L;
+        const int dx = r.x[0] + 1 == L ? 1 - L : 1, dy = r.x[1] + 1 == L ? L - lat.L2 : L,
+                  dz = r.x[2] + 1 == L ? lat.L2 - lat.L3 : lat.L2;
+        const int a = n == 0 ? 1 : 0, b = n == 2 ? 1 : 2;
+        const int da = a == 0 ? dx : dy, db = b == 1 ? dy : dz;
+        const uint64_t* __restrict__ pa = d.e + ((int64_t)a * lat.L3 + site) * d.W + w;
+        const uint64_t* __restrict__ pb = d.e + ((int64_t)b * lat.L3 + site) * d.W + w;
+        uint64_t acc = pa[0] ^ pa[(int64_t)db * d.W] ^ pb[0] ^ pb[(int64_t)da * d.W];
         acc ^= bernoulli_word(thr, seed, kStreamMeas, (uint64_t)f, cycle, 0, d.group0 + w);
         d.s[(int64_t)f * d.W + w] = acc;
     });
