@@ -64,6 +64,8 @@ def parse():
                     help="--impl reference: oracle time over all steps (default 60 s)")
     ap.add_argument("--e2e-steps", type=int, default=0,
                     help="end-to-end steps (default: as many as --steps, at least 3)")
+    ap.add_argument("--e2e-parts", type=int, default=2,
+                    help="end-to-end: sample ranges whose copies overlap the others' decoding")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -505,15 +507,15 @@ def cuda_arm(args):
 
     # end-to-end: every step uploads each error state from pinned host memory, decodes one
     # cycle through the C ABI and downloads the state, the masks and the counts.  The batch
-    # runs as two halves (consecutive 64-sample-aligned sample ranges, the same samples as
-    # one batch) decoded one after the other on the compute stream, each half with its own
-    # copy stream, so one half's copies overlap the other half's decoding.
+    # runs as --e2e-parts parts (consecutive 64-sample-aligned sample ranges, the same samples
+    # as one batch) decoded one after the other on the compute stream, each part with its own
+    # copy stream, so a part's copies overlap the other parts' decoding.
     e2e = None
     if not args.e2e_steps:
         args.e2e_steps = max(3, args.steps)
     if not args.no_e2e:
-        S0 = min(S, (S // 2 + 63) // 64 * 64)
-        parts = [(0, S0), (S0, S - S0)] if S - S0 > 0 else [(0, S)]
+        step_s = max(64, (S // max(1, args.e2e_parts) + 63) // 64 * 64)
+        parts = [(off, min(step_s, S - off)) for off in range(0, S, step_s)]
         halves = []
         for off, n in parts:
             hw = inp.words_for(n)
@@ -579,7 +581,7 @@ def cuda_arm(args):
                "steps": args.e2e_steps, "ms_per_step": 1e3 * dt / args.e2e_steps,
                "warmup": 2,
                "note": "error states uploaded from and downloaded to pinned host memory every step, "
-                       "two halves whose copies overlap the other half's decoding"}
+                       f"{len(parts)} parts whose copies overlap the other parts' decoding"}
         del halves
 
     fail_counts = [c.cpu().tolist() for c in counts]
