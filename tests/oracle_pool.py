@@ -42,3 +42,10 @@ def run_sample_if_clear(args):
         return None
     mask, e = oracle.run_batch(oracle.make_cfg(L, 1, p, q, seed, **kw), i, 1)
     return i, e[0], int(mask[0])
+
+
+def run_range(args):
+    """Samples [s0, s0 + n) of a run without BP recomputed by the oracle: (s0, mask, e bits)."""
+    L, T, p, q, seed, kw, s0, n = args
+    mask, e = oracle.run_batch(oracle.make_cfg(L, T, p, q, seed, **kw), s0, n)
+    return s0, mask, e
