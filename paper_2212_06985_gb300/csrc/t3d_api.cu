@@ -1,5 +1,6 @@
 // Library-wide host helpers: the per-thread error message behind
 // toric3d_last_error() and the argument checks every entry point shares.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -48,6 +49,44 @@ t3d_status check_words(const void* p, const char* name)
     return T3D_OK;
 }
 
+// ------------------------------------------------------------ CUDA context ids
+namespace {
+// Driver calls reached through the runtime (the library does not link libcuda).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+std::mutex g_ctx_mutex;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+t3d_status resolve_driver_calls()
+{
+    if (g_ctx_get_current && g_ctx_get_id) return T3D_OK;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    T3D_CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+    T3D_CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+    T3D_REQUIRE(q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2,
+                "the driver lacks cuCtxGetCurrent / cuCtxGetId");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    return T3D_OK;
+}
+}  // namespace
+
+t3d_status current_context_id(unsigned long long* id)
+{
+    *id = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_ctx_mutex);
+        T3D_TRY(resolve_driver_calls());
+    }
+    CUcontext ctx = nullptr;
+    T3D_REQUIRE(g_ctx_get_current(&ctx) == CUDA_SUCCESS, "cuCtxGetCurrent failed");
+    if (ctx) T3D_REQUIRE(g_ctx_get_id(ctx, id) == CUDA_SUCCESS, "cuCtxGetId failed");
+    return T3D_OK;
+}
+
 // ------------------------------------------------------------ persistent grids
 namespace {
 
@@ -61,7 +100,7 @@ struct GridEntry {
 
 struct SmemEntry {
     const void* kernel;
-    int device;
+    unsigned long long ctx;
     size_t bytes;
 };
 
@@ -85,15 +124,17 @@ void set_tuned_blocks_per_sm(int kind, int blocks_per_sm)
     if (kind >= 0 && kind < T3D_K_COUNT) g_tuned[kind] = blocks_per_sm > 0 ? blocks_per_sm : 0;
 }
 
+// The attribute belongs to the current context: the cache is keyed by the context's id, so a
+// new context (after a device reset) sets it again.
 t3d_status allow_dynamic_smem(const void* kernel, size_t bytes)
 {
-    int dev = 0;
-    T3D_CUDA_CHECK(cudaGetDevice(&dev));
+    unsigned long long ctx = 0;
+    T3D_TRY(current_context_id(&ctx));
     std::lock_guard<std::mutex> lock(g_grid_mutex);
     for (const auto& e : g_smem)
-        if (e.kernel == kernel && e.device == dev && e.bytes >= bytes) return T3D_OK;
+        if (e.kernel == kernel && e.ctx == ctx && ctx != 0 && e.bytes >= bytes) return T3D_OK;
     T3D_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    g_smem.push_back(SmemEntry{kernel, dev, bytes});
+    if (ctx != 0) g_smem.push_back(SmemEntry{kernel, ctx, bytes});
     return T3D_OK;
 }
 

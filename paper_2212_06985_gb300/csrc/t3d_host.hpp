@@ -95,8 +95,10 @@ t3d_status check_words(const void* p, const char* name);
 // grid is then at most the resident blocks even when untuned.
 unsigned persistent_grid(const void* kernel, int threads, int kind, int64_t blocks, bool device_bound = false,
                          size_t dynamic_smem = 0);
-// Raise a kernel's dynamic shared-memory limit on the current device to at least `bytes`.
+// Raise a kernel's dynamic shared-memory limit in the current context to at least `bytes`.
 t3d_status allow_dynamic_smem(const void* kernel, size_t bytes);
+// Unique id of the calling thread's current CUDA context, 0 if there is none yet.
+t3d_status current_context_id(unsigned long long* id);
 
 // Launch tuning chosen by the autotuner (0 = use the occupancy limit).
 int tuned_blocks_per_sm(int kind);

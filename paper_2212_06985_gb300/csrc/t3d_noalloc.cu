@@ -51,37 +51,6 @@ struct ScratchAddr {
 };
 ScratchAddr g_scratch_addr[kMaxDevices] = {};
 
-// Driver calls reached through the runtime (the library does not link libcuda).
-using CtxGetCurrentFn = CUresult (*)(CUcontext*);
-using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
-CtxGetCurrentFn g_ctx_get_current = nullptr;
-CtxGetIdFn g_ctx_get_id = nullptr;
-
-t3d_status resolve_driver_calls()
-{
-    if (g_ctx_get_current && g_ctx_get_id) return T3D_OK;
-    void* f1 = nullptr;
-    void* f2 = nullptr;
-    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
-    T3D_CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
-    T3D_CUDA_CHECK(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
-    T3D_REQUIRE(q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess && f1 && f2,
-                "the driver lacks cuCtxGetCurrent / cuCtxGetId");
-    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
-    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
-    return T3D_OK;
-}
-
-// Id of the calling thread's current context, 0 if there is none yet.
-t3d_status current_context_id(unsigned long long* id)
-{
-    CUcontext ctx = nullptr;
-    *id = 0;
-    T3D_REQUIRE(g_ctx_get_current(&ctx) == CUDA_SUCCESS, "cuCtxGetCurrent failed");
-    if (ctx) T3D_REQUIRE(g_ctx_get_id(ctx, id) == CUDA_SUCCESS, "cuCtxGetId failed");
-    return T3D_OK;
-}
-
 // Device address of the scratch array in the current device's current context:
 // looked up on the first call and again whenever that context has changed.
 t3d_status scratch_address(void** out)
@@ -90,7 +59,6 @@ t3d_status scratch_address(void** out)
     T3D_CUDA_CHECK(cudaGetDevice(&dev));
     T3D_REQUIRE(dev >= 0 && dev < kMaxDevices, "device %d outside the %d supported", dev, kMaxDevices);
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    T3D_TRY(resolve_driver_calls());
     unsigned long long id = 0;
     T3D_TRY(current_context_id(&id));
     ScratchAddr& c = g_scratch_addr[dev];
