@@ -1,7 +1,8 @@
 """The benchmark's other configurations at their full sizes, as whole runs through
 the C ABI in the launch configuration the benchmark uses: p-flip at L = 16 with
-10^6 samples, L = 16 and L = 24 mixed in one batch with BP16 + 32 x PFFPFF
-(10^5 samples each), and L = 48 with BP16 + 32 x PFFPFF (10^5 samples, BP in
+10^6 samples, the benchmark's flip / p-flip workload (L = 32, 10^5 samples,
+FFPFF), L = 16 and L = 24 mixed in one batch with BP16 + 32 x PFFPFF (10^5
+samples each), and L = 48 with BP16 + 32 x PFFPFF (10^5 samples, BP in
 chunks).  Whole batches are checked by properties that hold at any size (the
 readout histogram, a batch equal to separate runs); sampled samples are
 recomputed one by one by the oracle."""
@@ -13,7 +14,7 @@ import oracle
 import paper_2212_06985_gb300 as t3d
 import toric3d_inputs as inp
 from gpu_util import dev
-from oracle_pool import run_sample_if_clear, spawn_pool
+from oracle_pool import run_range, run_sample_if_clear, spawn_pool
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +78,38 @@ def test_pflip_L16_million_samples():
         assert np.array_equal(_word_bits(e, wd), ora_e), wd
         assert np.array_equal(m[64 * wd:64 * wd + 64], ora_mask), wd
     del e, work
+    torch.cuda.empty_cache()
+
+
+def test_pflip_L32_full_size_as_the_bench_runs_it():
+    """The flip / p-flip workload (L = 32, 10^5 samples, FFPFF) through toric3d_run_batch one
+    cycle per call, as the benchmark times it (1024-thread flip tiles), three cycles; the first,
+    a middle and the last (half-full) word against the oracle, one sample at a time."""
+    w = inp.WORKLOADS["pflip_L32"]
+    L, S, cycles = w.L, w.n_samples, 3
+    kw = dict(schedule=w.schedule, n_apply=w.n_apply)
+    e, mask, counts = _alloc(L, S)
+    batch = t3d.make_batch([dict(L=L, n_samples=S, e=e, mask=mask, counts8=counts)])
+    cfg = t3d.make_run_cfg(L, 1, w.p, w.q, w.seed, S, **kw)
+    work = torch.empty(t3d.toric3d_run_batch_workspace_bytes(cfg, batch), dtype=torch.uint8, device=dev())
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        for t in range(cycles):
+            cfg.cycle0 = t
+            t3d.toric3d_run_batch(cfg, batch, work, stream=stream)
+    stream.synchronize()
+    del work
+    m = _check_readout(mask, counts, S)
+    W = inp.words_for(S)
+    lanes = sorted(set(range(64)) | set(range(64 * (W // 2), 64 * (W // 2) + 64)) | set(range(64 * (W - 1), S)))
+    with spawn_pool() as pool:
+        got = pool.map(run_range, [(L, cycles, w.p, w.q, w.seed, kw, i, 1) for i in lanes])
+    for i, (s0, ora_mask, ora_e) in zip(lanes, got):
+        assert s0 == i
+        assert np.array_equal(_sample_bits(e, i), ora_e[0]), i
+        assert m[i] == ora_mask[0], i
+    del e
     torch.cuda.empty_cache()
 
 
