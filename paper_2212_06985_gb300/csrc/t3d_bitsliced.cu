@@ -856,11 +856,17 @@ t3d_status launch_logical(ItemTable& tab, cudaStream_t st)
     return T3D_OK;
 }
 
+// The fallback gate splits the faces over Y block rows so that a launch has about four
+// blocks per SM of a GB300 (152 SMs).  The split only shapes the grid and the scratch size
+// (the counts are exact for any Y), and it is computed without a device so that workspace
+// sizes can be asked for on the host alone.
+constexpr int kGateGridSms = 152;
+
 int gate_splits(int L, int64_t W)
 {
     const int64_t faces = 3LL * L * L * L;
     const int64_t tiles = (W + 31) / 32;
-    int64_t y = (4 * 152 + tiles - 1) / tiles;              // about four blocks per SM
+    int64_t y = (4 * kGateGridSms + tiles - 1) / tiles;     // about four blocks per SM
     y = std::min<int64_t>(y, (faces + 8 * 64 - 1) / (8 * 64));  // at least 64 faces per warp
     return (int)std::max<int64_t>(1, std::min<int64_t>(y, 64));
 }
