@@ -51,3 +51,36 @@ def test_sweep_roofline_of_a_pflip_cycle():
     flip = r["kernels_hbm_frac"]["flip"]             # 0.5 B x qubits x S per 1.125 ms application (4 F per cycle)
     assert abs(flip - 0.5 * q * S / 1.125e-3 / 1e9 / 6780.0) < 1e-9
     assert 0 < r["cycle_hbm_frac"] < 1
+
+
+def test_sweep_roofline_cycle_bound_and_flip_traffic():
+    """The cycle's combined bound is the sum over its kernels of the slower of the byte and
+    issue bounds, and the flip's DRAM traffic figure applies at the captured noise rates only."""
+    sys.path.insert(0, ROOT)
+    import dataclasses
+    import bench
+    import toric3d_inputs as inp
+    w = inp.WORKLOADS["pflip_L32"]
+    q, S, steps = inp.n_bits(32), 100_000, 5
+    prof = {k: (0.0, 0) for k in ("noise", "syndrome", "flip", "pflip", "bp_step", "bp_decide", "logical", "layout",
+                                  "cnn")}
+    prof.update(noise=(11.4, 5), syndrome=(13.0, 5), flip=(20.5, 20), pflip=(8.5, 10))
+    ms = 55.3
+    r = bench.sweep_roofline(prof, w, q, S, steps, ms, 6780.0, "test", {"sm_mhz": 2070.0})
+    assert r["kernel"] == "k_flip_tiled"
+    words = (S + 63) // 64
+    hbm, issue = 6780.0e9, 152 * 4 * 2070.0e6
+    b = bench.SWEEP_BYTES
+    i = bench.SWEEP_INST
+    want = (max(b["noise"] * q * S / hbm, i["noise"] * q * words / issue)
+            + max(b["syndrome"] * q * S / hbm, i["syndrome"] * q * words / issue)
+            + 4 * b["flip"] * q * S / hbm
+            + max((b["pflip"] - bench.PFLIP_APPLY_BYTES) * q * S / hbm, i["pflip"] * (q // 3) * words / issue)
+            + bench.PFLIP_APPLY_BYTES * q * S / hbm)
+    assert abs(r["cycle_bound_ms"] - 1e3 * want) < 1e-9
+    assert abs(r["cycle_roofline_frac"] - want / (ms / 1e3 / steps)) < 1e-12
+    assert abs(r["traffic"] - bench.FLIP_TRAFFIC * q * S) < 1.0
+    # another noise rate: no instruction counts and no traffic figure for it
+    w2 = dataclasses.replace(w, p=0.05, q=0.05)
+    r2 = bench.sweep_roofline(prof, w2, q, S, steps, ms, 6780.0, "test", {"sm_mhz": 2070.0})
+    assert r2["traffic"] is None and "cycle_bound_ms" not in r2
